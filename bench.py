@@ -1,0 +1,375 @@
+"""Throughput benchmark of the image-source-method hot path on GB300.
+
+Workload (one "step"): the batched FP32 configuration -- 128 RIRs (4 sources x
+32 receivers) in a 6 x 5 x 3 m room, beta from Sabine for T60 = 0.6 s,
+16 kHz, 0.6 s RIRs (9600 samples), 32-tap windowed sinc, images per axis
+from Tmax ([73, 87, 141] = 895,491 images per RIR).  One step is one
+ism_simulate call: geometry, enumeration, binning, accumulation, finalize.
+
+Prints one JSON line (rank 0).  `value` is RIRs/s of the whole job; the line
+also carries image-contributions/s, the live roofline of the accumulation
+kernel, an end-to-end number through the host-buffer C entry point, the
+oracle timed on the host cores (cpu_baseline) and the SM clocks sampled
+during the timed region.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+--impl reference times the FP64 CPU oracle on a bounded sample of the same
+workload on the host cores (rank 0 only).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_1810_11359_gb300 import workloads  # noqa: E402
+
+METRIC = "RIRs/sec"
+UNIT = "RIR/s"
+FMA_OPS_PER_CONTRIBUTION = 5   # FADD (j - f), 2 FFMA (window), FMUL, FFMA (accumulate)
+L2_BYTES = 129 * 1024 * 1024
+
+
+def _peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(p) as f:
+            d = json.load(f)
+        return d, "measured"
+    except Exception:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+def workload():
+    room = workloads.batched_fp32()
+    return room
+
+
+def contributions(room, beta, N, n_ism):
+    """Image-tap contributions of the step: for every RIR and every image, the
+    samples 0 <= k < n_ism with |k - s| < N_w/2 (FP64, numpy)."""
+    L = np.asarray(room.L, np.float64)
+    fs, c = float(np.float32(room.fs)), float(np.float32(room.c))
+    Nw = round(float(np.float32(room.window())) * fs)
+    half = Nw / 2.0
+    axes = []
+    for a in range(3):
+        lo = -(int(N[a]) // 2)
+        n = np.arange(lo, lo + int(N[a]))
+        axes.append(n)
+    total = 0
+    for ps in room.pos_src.astype(np.float64):
+        for pr in room.pos_rcv.astype(np.float64):
+            sq = []
+            for a in range(3):
+                n = axes[a]
+                m = np.where(n % 2 == 0, n, n + 1).astype(np.float64)
+                off = np.where(n % 2 == 0, ps[a] - pr[a], -ps[a] - pr[a])
+                sq.append(((m * L[a] + off) * fs / c) ** 2)
+            s = np.sqrt(sq[0][:, None, None] + sq[1][None, :, None] + sq[2][None, None, :]).ravel()
+            k_lo = np.maximum(np.floor(s - half) + 1, 0)
+            k_hi = np.minimum(np.ceil(s + half) - 1, n_ism - 1)
+            total += int(np.sum(np.maximum(k_hi - k_lo + 1, 0)))
+    return total
+
+
+class ClockSampler:
+    def __init__(self, index=0):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={q}", "--format=csv,noheader,nounits",
+                                          "-i", str(self.index), "-lms", "200"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, mx, reasons = [], [], set()
+        with open(self.path) as f:
+            for line in f:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) < 9:
+                    continue
+                try:
+                    sm.append(float(parts[1]))
+                    mx.append(float(parts[2]))
+                except ValueError:
+                    continue
+                names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+                for nm, v in zip(names, parts[5:9]):
+                    if v.lower() == "active":
+                        reasons.add(nm)
+        os.unlink(self.path)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def traffic_from_profiles():
+    """DRAM bytes per accumulation launch from the committed ncu summary, or
+    None when the kernel source changed since it was captured."""
+    path = os.path.join(ROOT, "profiles", "accum_batched_128rir.txt")
+    try:
+        from paper_1810_11359_gb300 import build as b
+        import hashlib
+        src = os.path.join(b.CSRC, "ism_accum.cu")
+        dig = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+        vals = {}
+        for line in open(path):
+            if "=" in line and line.strip().startswith("bench_"):
+                k, v = line.strip().split("=", 1)
+                vals[k.strip()] = v.strip()
+        if vals.get("bench_kernel_source_sha256_16") != dig:
+            return None
+        return float(vals["bench_dram_bytes_per_launch"])
+    except Exception:
+        return None
+
+
+def cpu_baseline(room, beta, N, n_ism, budget_s=15.0):
+    """The FP64 oracle, as it stands, on the host cores over a bounded sample
+    of the step's RIRs."""
+    import oracle
+    oracle.build()
+    cores = oracle.max_threads()
+    ps_all = np.repeat(room.pos_src, room.pos_rcv.shape[0], axis=0)
+    pr_all = np.tile(room.pos_rcv, (room.pos_src.shape[0], 1))
+    b32 = np.asarray(beta, np.float32).astype(np.float64)
+    # calibrate on one RIR per core, then size the sample to the budget
+    n = max(1, min(cores, ps_all.shape[0]))
+    t0 = time.perf_counter()
+    oracle.rir_list(room.L, b32, float(np.float32(room.c)), float(np.float32(room.fs)), float(np.float32(room.window())),
+                    ps_all[:n], pr_all[:n], N, n_ism, n_threads=cores)
+    dt = time.perf_counter() - t0
+    total_rirs, total_t = n, dt
+    more = int(max(0, (budget_s - dt) / max(dt / n, 1e-6)))
+    more = min(more, ps_all.shape[0] - n)
+    more = (more // cores) * cores
+    if more > 0:
+        t0 = time.perf_counter()
+        oracle.rir_list(room.L, b32, float(np.float32(room.c)), float(np.float32(room.fs)),
+                        float(np.float32(room.window())), ps_all[n:n + more], pr_all[n:n + more], N, n_ism,
+                        n_threads=cores)
+        total_t += time.perf_counter() - t0
+        total_rirs += more
+    return {"value": total_rirs / total_t, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"{total_rirs} of the step's 128 RIRs (full length, FP64 direct sum), {total_t:.1f} s"}
+
+
+def run_reference(args, rank):
+    if rank != 0:
+        return
+    room = workload()
+    import oracle
+    beta = oracle.beta_sabine(room.L, room.rt60)
+    N = oracle.nb_img_from_t(room.Tmax, room.L, room.c, room.window())
+    n_S = oracle.n_samples(np.float32(room.Tmax), room.fs)
+    oracle.build()
+    cores = oracle.max_threads()
+    sample = max(1, min(128, cores))
+    ps_all = np.repeat(room.pos_src, room.pos_rcv.shape[0], axis=0)[:sample]
+    pr_all = np.tile(room.pos_rcv, (room.pos_src.shape[0], 1))[:sample]
+    b32 = np.asarray(beta, np.float32).astype(np.float64)
+
+    def step():
+        oracle.rir_list(room.L, b32, float(np.float32(room.c)), float(np.float32(room.fs)),
+                        float(np.float32(room.window())), ps_all, pr_all, N, n_S, n_threads=cores)
+
+    for _ in range(args.warmup):
+        step()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        step()
+    dt = (time.perf_counter() - t0) / max(args.steps, 1)
+    value = sample / dt
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": room.name, "rirs_per_step": sample, "of_rirs": 128},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": f"{sample} of the 128 RIRs per step, full length"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+
+    if args.impl == "reference":
+        run_reference(args, rank)
+        return
+
+    import torch
+    import torch.distributed as dist
+
+    import __graft_entry__
+    if rank == 0 or world == 1:
+        __graft_entry__.build()
+    if world > 1:
+        dist.init_process_group("nccl")
+        torch.cuda.set_device(local_rank)
+        dist.barrier()
+        __graft_entry__.build()
+    else:
+        torch.cuda.set_device(0)
+    from paper_1810_11359_gb300 import ism
+
+    room = workload()
+    beta = ism.ism_beta_sabine(room.L, room.rt60)
+    N = ism.ism_nb_img_from_t(room.Tmax, room.L, room.c, room.window())
+    n_S = ism.ism_rir_length(room.Tmax, room.fs)
+    dev = torch.device("cuda", torch.cuda.current_device())
+    ps = torch.from_numpy(room.pos_src).to(dev)
+    pr = torch.from_numpy(room.pos_rcv).to(dev)
+    out = torch.empty((ps.shape[0], pr.shape[0], n_S), dtype=torch.float32, device=dev)
+    ws = ism.Workspace(dev)
+    flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream()
+
+    def step():
+        ism.ism_simulate(room.L, beta, ps, pr, N, room.Tmax, room.fs, Tw=room.window(), c=room.c, out=out,
+                         workspace=ws)
+
+    for _ in range(max(args.warmup, 3)):
+        step()
+    torch.cuda.synchronize()
+
+    clocks = ClockSampler(local_rank)
+    clocks.start()
+    ism.ism_profile_reset()
+    ism.ism_profile_enable(True)
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    for a, b in evs:
+        flush.zero_()                     # evict L2 between timed steps (outside the events)
+        a.record(stream)
+        step()
+        b.record(stream)
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    ism.ism_profile_enable(False)
+    clk = clocks.stop()
+    step_ms = [a.elapsed_time(b) for a, b in evs]
+    ms = sum(step_ms) / len(step_ms)
+    prof = ism.ism_profile_read()
+    if world > 1:
+        t = torch.tensor([ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    rirs = ps.shape[0] * pr.shape[0] * world
+    value = rirs / (ms * 1e-3)
+
+    # end to end through the host-buffer entry point: pinned inputs in, RIRs out
+    h_ps = torch.from_numpy(room.pos_src).pin_memory()
+    h_pr = torch.from_numpy(room.pos_rcv).pin_memory()
+    h_out = torch.empty((ps.shape[0], pr.shape[0], n_S), dtype=torch.float32).pin_memory()
+    ws_h = ism.Workspace(dev)
+
+    def step_host():
+        ism.ism_simulate_host(room.L, beta, h_ps.numpy(), h_pr.numpy(), N, room.Tmax, room.fs, Tw=room.window(),
+                              c=room.c, out=h_out.numpy(), workspace=ws_h)
+
+    for _ in range(2):
+        step_host()
+    torch.cuda.synchronize()
+    e2e_steps = max(3, min(args.steps, 10))
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        step_host()
+    e2e_dt = (time.perf_counter() - t0) / e2e_steps
+    if world > 1:
+        t = torch.tensor([e2e_dt], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_dt = float(t.item())
+
+    if rank != 0:
+        dist.destroy_process_group()
+        return
+
+    n_contrib = contributions(room, beta, N, n_S)
+    acc_ms, acc_launches, acc_calls = prof["accum"]
+    acc_ms_per_launch = acc_ms / max(acc_launches, 1)
+    peaks, peak_kind = _peaks()
+    sm_mhz = float(peaks.get("sm_max_mhz", 2070.0))
+    props = torch.cuda.get_device_properties(dev)
+    n_sm = props.multi_processor_count
+    peak_tops = n_sm * 128 * sm_mhz * 1e6 / 1e12          # FP32 FMA-pipe lane operations / s
+    achieved_tops = FMA_OPS_PER_CONTRIBUTION * n_contrib / (acc_ms_per_launch * 1e-3) / 1e12
+    launches_per_step = sum(v[1] for v in prof.values()) / max(args.steps, 1)
+
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": max(args.warmup, 3), "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic (seeded positions, Sabine beta)",
+        "config": {"workload": room.name, "rirs_per_step": int(ps.shape[0] * pr.shape[0]), "n_samples": n_S,
+                   "images_per_rir": int(np.prod(N)), "nb_img": [int(v) for v in N], "taps": 32,
+                   "l2": "flushed between timed steps (256 MB write)"},
+        "image_contributions_per_sec": n_contrib * world / (ms * 1e-3),
+        "contributions_per_step": n_contrib,
+        "stage_ms_per_step": {k: v[0] / max(args.steps, 1) for k, v in prof.items()},
+        "roofline": {"bound": "alu", "kernel": "accum_kernel<1,false>", "achieved": achieved_tops,
+                     "peak": peak_tops, "unit": "Tops/s (FP32 FMA-pipe lane ops)",
+                     "frac": achieved_tops / peak_tops,
+                     "peak_basis": f"{n_sm} SMs x 128 FP32 lanes x {sm_mhz:.0f} MHz ({peak_kind} max SM clock)",
+                     "ops_per_contribution": FMA_OPS_PER_CONTRIBUTION,
+                     "kernel_ms": acc_ms_per_launch,
+                     "traffic": traffic_from_profiles()},
+        "gpu_launches": int(round(launches_per_step * args.steps)),
+        "e2e": {"value": rirs / e2e_dt, "unit": UNIT,
+                "h2d_bytes_per_step": int(room.pos_src.nbytes + room.pos_rcv.nbytes),
+                "d2h_bytes_per_step": int(h_out.numel() * 4), "ms_per_step": e2e_dt * 1e3,
+                "entry": "ism_simulate_host (pinned host positions in, host RIRs out)"},
+        "clocks": clk,
+    }
+    if not args.no_cpu_baseline and world >= 1:
+        line["cpu_baseline"] = cpu_baseline(room, beta, N, n_S)
+    print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

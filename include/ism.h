@@ -1,0 +1,259 @@
+/*
+ * ism.h -- C ABI of libism, a GB300 (sm_103a) implementation of the
+ * image-source method (ISM) for room impulse responses (RIRs) in shoebox
+ * rooms, after Diaz-Guerra, Miguel and Beltran, "gpuRIR: A Python Library for
+ * Room Impulse Response Simulation with GPU Acceleration".
+ *
+ * What the library computes (paper Section 2):
+ *   For every (source, receiver) pair and every image n of the grid
+ *   ceil(-N/2) <= n < ceil(N/2) per axis (Section 2.1):
+ *     image position       eq. (1)
+ *     distance, delay      eq. (2), eq. (3)   tau_n = d_n / c
+ *     amplitude            eq. (4)            A_n = beta_n / (4 pi d_n)
+ *   and accumulates Peterson's Hann-windowed sinc (eq. (6), cut-off f_s/2)
+ *   of every image into the RIR (eq. (5)).  Beyond Tdiff the RIR is a
+ *   logistic-noise tail with the Sabine power envelope (Section 2.2, eq. (7),
+ *   eq. (8) read as a 60 dB decay over T60).
+ *
+ * Conventions shared by every call:
+ *   - No call allocates device memory on the simulation path: the caller
+ *     passes a device workspace whose size the matching *_workspace_size call
+ *     returns.  Pointers are borrowed for the duration of the work.
+ *   - "device" pointers are CUDA device (or managed) memory of the current
+ *     device; "host" pointers are ordinary host memory.
+ *   - Work is enqueued on `stream` (a cudaStream_t passed as void*; NULL is
+ *     the legacy default stream) and the call returns after the launches:
+ *     results are ready when the stream reaches that point.
+ *   - Every call returns an ism_status.  No C++ exception crosses the ABI.
+ *     On an error the outputs are not written; ism_last_error_message()
+ *     describes the last error of the calling thread.
+ *   - Sample counts: n_S = ceil(Tmax fs (1 - 1e-6)), n_ism = ceil(Tdiff fs (1 - 1e-6))
+ *     (the relative slack absorbs the FP32 rounding of the times).
+ *     Tdiff <= 0 or Tdiff >= Tmax means no diffuse tail (n_ism = n_S).
+ *   - The window length Tw is in seconds (eq. (6)); N_w = Tw fs taps.
+ *     Tw <= 0 selects the paper's typical 4 ms.
+ */
+#ifndef ISM_H
+#define ISM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define ISM_VERSION 100
+
+typedef enum {
+    ISM_OK = 0,
+    ISM_ERR_INVALID_ARG = 1,          /* argument out of its documented range           */
+    ISM_ERR_INFEASIBLE = 2,           /* Sabine: some alpha >= 1, or sum S alpha = 0    */
+    ISM_ERR_WORKSPACE_TOO_SMALL = 3,  /* ws_bytes below the *_workspace_size result     */
+    ISM_ERR_OOM = 4,                  /* allocation failed / HBM budget exceeded        */
+    ISM_ERR_CUDA = 5,                 /* a CUDA runtime call failed                     */
+    ISM_ERR_TIMEOUT = 6,              /* a host-side wait ran out of time               */
+    ISM_ERR_DEVICE_CHECK = 7,         /* the device reported bad input (see status)     */
+    ISM_ERR_UNSUPPORTED = 8,          /* valid but outside this build's limits          */
+    ISM_ERR_CANCELLED = 9             /* a served request was cancelled                 */
+} ism_status;
+
+/* Arithmetic of the windowed-sinc evaluation (Section 3.5 LUT, Section 3.6
+ * mixed precision).  Image enumeration, distances and delays are always
+ * FP32 (with a float-float delay, so fractional delays keep FP32 accuracy);
+ * accumulation is always FP32. */
+typedef enum {
+    ISM_PREC_FP32 = 0,    /* FP32 sin/cos/reciprocal                                  */
+    ISM_PREC_FP16X2 = 1,  /* packed FP16 window and sinc, FP32 accumulation           */
+    ISM_PREC_BF16X2 = 2,  /* packed BF16 window and sinc, FP32 accumulation           */
+    ISM_PREC_LUT = 3      /* 4096-entry FP32 windowed-sinc table (eq. (9)), FP32 lerp */
+} ism_precision;
+
+/* A shoebox room (Section 2.1).  beta is ordered x0, x1, y0, y1, z0, z1:
+ * x0 is the wall x = 0 (closest to the origin), x1 the wall x = L[0].
+ * Negative coefficients are allowed (Section 2.2). */
+typedef struct {
+    double L[3];      /* room size in metres, each > 0                         */
+    float beta[6];    /* reflection coefficients, |beta| <= 1                  */
+    float c;          /* speed of sound in m/s, > 0 (343 if <= 0 is passed)    */
+} ism_room;
+
+/* ------------------------------------------------------------------------- */
+/* Status and errors                                                          */
+/* ------------------------------------------------------------------------- */
+/* Static string naming a status code. */
+const char* ism_status_string(ism_status s);
+/* Message of the last failed call on the calling thread ("" if none).  The
+ * pointer stays valid until the next library call on this thread. */
+const char* ism_last_error_message(void);
+/* ISM_VERSION of the loaded library. */
+int ism_version(void);
+
+/* ------------------------------------------------------------------------- */
+/* Sizing                                                                     */
+/* ------------------------------------------------------------------------- */
+/* n_samples = ceil(T fs (1 - 1e-6)).  T > 0, fs > 0.  Host only. */
+ism_status ism_rir_length(float T, float fs, int* n_samples);
+
+/* Device workspace bytes that ism_simulate needs for these arguments (same
+ * meaning as in ism_simulate).  Host only; no device work. */
+ism_status ism_workspace_size(const ism_room* room, int n_src, int n_rcv, const int nb_img[3],
+                              float Tmax, float fs, float Tdiff, float Tw, ism_precision prec,
+                              size_t* bytes);
+
+/* ------------------------------------------------------------------------- */
+/* Forward simulation (Section 4: "room dimensions, reflection coefficients, */
+/* source and receiver positions, images per dimension, RIR duration, time   */
+/* to switch to the diffuse model, sampling frequency" -> 3-D tensor)        */
+/* ------------------------------------------------------------------------- */
+/* RIRs for all n_src x n_rcv pairs.
+ *   room      host, see ism_room.
+ *   pos_src   device, [n_src][3] FP32 metres; pos_rcv device, [n_rcv][3].
+ *             Positions must lie strictly inside the room.  They live on the
+ *             device, so they are checked there: a pair with a position
+ *             outside the room, or with source == receiver, gets an all-zero
+ *             RIR and raises a flag that ism_workspace_status() returns.
+ *   nb_img    host, images per axis in the paper's units (Section 2.1),
+ *             each in [1, 1023]; ism_nb_img_from_t() picks them from a time.
+ *   Tmax      RIR length in seconds; Tdiff start of the diffuse tail (see
+ *             the conventions above); Tw window length (eq. (6)).
+ *   prec      windowed-sinc arithmetic (ism_precision).
+ *   seed      key of the Philox4x32-10 noise of the diffuse tail; the noise
+ *             of RIR r = i_src * n_rcv + i_rcv, sample k is word k mod 4 of
+ *             Philox4x32-10(counter (k/4, r, 0, 0), key (seed lo, seed hi)).
+ *   out       device, [n_src][n_rcv][n_S] FP32 row-major, written entirely.
+ *   workspace device, >= ism_workspace_size() bytes, 256-byte aligned; its
+ *             contents need no initialisation and are scratch afterwards
+ *             (except the status word read by ism_workspace_status()).
+ * Limits (ISM_ERR_UNSUPPORTED beyond them): N_w = Tw fs <= 256 taps,
+ * n_ism <= 131000 samples, images per axis <= 1023.
+ * The result is bit-identical from run to run for identical arguments
+ * (no floating-point atomics; fixed summation orders). */
+ism_status ism_simulate(const ism_room* room, const float* pos_src, int n_src, const float* pos_rcv,
+                        int n_rcv, const int nb_img[3], float Tmax, float fs, float Tdiff, float Tw,
+                        ism_precision prec, uint64_t seed, float* out, void* workspace,
+                        size_t ws_bytes, void* stream);
+
+/* Same computation from HOST buffers: copies pos_src/pos_rcv to the device,
+ * runs ism_simulate and copies the RIRs back into host `out`
+ * ([n_src][n_rcv][n_S] FP32).  Positions are validated on the host first
+ * (ISM_ERR_INVALID_ARG if one lies outside the room).  Synchronous: returns
+ * when `out` holds the result.  The workspace is device memory as above. */
+ism_status ism_simulate_host(const ism_room* room, const float* pos_src, int n_src,
+                             const float* pos_rcv, int n_rcv, const int nb_img[3], float Tmax,
+                             float fs, float Tdiff, float Tw, ism_precision prec, uint64_t seed,
+                             float* out, void* workspace, size_t ws_bytes, void* stream);
+
+/* Device workspace bytes that ism_simulate_host needs: the ism_simulate
+ * workspace followed by room for the positions and the RIRs. */
+ism_status ism_host_workspace_size(const ism_room* room, int n_src, int n_rcv, const int nb_img[3],
+                                   float Tmax, float fs, float Tdiff, float Tw, ism_precision prec,
+                                   size_t* bytes);
+
+/* Reads the device status word a previous call left in `workspace`
+ * (synchronises `stream`).  *flags = 0 if the inputs were valid, otherwise a
+ * bitwise OR of ISM_DEVICE_FLAG_* values. */
+#define ISM_DEVICE_FLAG_POSITION 1u   /* a source/receiver outside the room or coincident */
+#define ISM_DEVICE_FLAG_BIN 2u        /* an image delay fell outside its bin (internal)    */
+ism_status ism_workspace_status(const void* workspace, void* stream, uint32_t* flags);
+
+/* ------------------------------------------------------------------------- */
+/* Ragged batches: many rooms in one set of launches                         */
+/* ------------------------------------------------------------------------- */
+/* One independent simulation.  Meanings as in ism_simulate; pos_src,
+ * pos_rcv, out and env_amp are device pointers.  env_amp may be NULL; if
+ * not, it receives [n_src * n_rcv] FP32 envelope amplitudes A (eq. (8)) of
+ * the diffuse tail (0 where there is no tail). */
+typedef struct {
+    ism_room room;
+    const float* pos_src;
+    int n_src;
+    const float* pos_rcv;
+    int n_rcv;
+    int nb_img[3];
+    float Tmax, fs, Tdiff, Tw;
+    uint64_t seed;
+    float* out;
+    float* env_amp;
+} ism_job;
+
+/* Workspace bytes for ism_simulate_batch over these jobs. */
+ism_status ism_batch_workspace_size(const ism_job* jobs, int n_jobs, ism_precision prec,
+                                    size_t* bytes);
+
+/* Simulates every job (host array `jobs`, n_jobs >= 1).  Each job's result is
+ * the same as a separate ism_simulate call with the same arguments, bit for
+ * bit: the jobs share launches, not arithmetic. */
+ism_status ism_simulate_batch(const ism_job* jobs, int n_jobs, ism_precision prec, void* workspace,
+                              size_t ws_bytes, void* stream);
+
+/* ------------------------------------------------------------------------- */
+/* Diffuse-tail noise (Section 2.2, Section 3.3)                             */
+/* ------------------------------------------------------------------------- */
+/* Writes the unit-variance logistic noise z of samples k0 .. k0+n-1 of RIR
+ * `rir` into device `z` (FP32): z = (sqrt(3)/pi) ln(u / (1 - u)) with
+ * u = ((x >> 9) + 1/2) 2^-23 and x the Philox4x32-10 word described under
+ * ism_simulate; ln is evaluated by a fixed sequence of correctly rounded
+ * FP32 operations, so z is reproducible bit for bit on any IEEE machine.
+ * The tail of ism_simulate is z times the square root of the envelope. */
+ism_status ism_diffuse_noise(uint64_t seed, uint32_t rir, uint32_t k0, int n, float* z, void* stream);
+
+/* ------------------------------------------------------------------------- */
+/* Helpers of Section 4 (FP64)                                                */
+/* ------------------------------------------------------------------------- */
+/* Eq. (7): T60 = 0.161 V / sum_i S_i (1 - beta_i^2).  Host. */
+ism_status ism_t60_sabine(const double L[3], const double beta[6], double* T60);
+
+/* Inverse of eq. (7): reflection coefficients giving `T60`.  alpha_i =
+ * w_i alpha_0 with abs_weights w (NULL = all ones), beta_i = sqrt(1 - alpha_i),
+ * negated if `negative` (Section 2.2).  ISM_ERR_INFEASIBLE if some alpha_i >= 1.
+ * Host. */
+ism_status ism_beta_sabine(const double L[3], double T60, const double abs_weights[6], int negative,
+                           double beta_out[6]);
+
+/* Batched inverse Sabine on the GPU in FP64: for i < n, L[i][3] and T60[i]
+ * (device) -> beta_out[i][6] (device), status[i] (device int, 0 = ok,
+ * ISM_ERR_INFEASIBLE otherwise; beta_out row then zero).  abs_weights is a
+ * device [6] array or NULL. */
+ism_status ism_beta_sabine_device(const double* L, const double* T60, const double* abs_weights,
+                                  int negative, int n, double* beta_out, int* status, void* stream);
+
+/* Images per axis so that every reflection arriving before T is simulated:
+ * M = ceil(c (T + Tw/2) / L) + 1, N = 2M + 1 (an image of index n is at
+ * least (|n| - 1) L away from any point of the room).  Host. */
+ism_status ism_nb_img_from_t(double T, const double L[3], double c, double Tw, int nb_out[3]);
+
+/* Time at which the Sabine decay reaches att_dB: t = att_dB / 60 * T60.  Host. */
+ism_status ism_att2t_sabine(double att_dB, double T60, double* t);
+
+/* ------------------------------------------------------------------------- */
+/* Per-stage timing (the breakdown of the paper's Table 2)                    */
+/* ------------------------------------------------------------------------- */
+/* Stages of one simulation, in launch order. */
+typedef enum {
+    ISM_STAGE_GEOMETRY = 0,   /* per-RIR axis tables, position checks            */
+    ISM_STAGE_ENUM_COUNT = 1, /* image enumeration, delays, bin counts (a)       */
+    ISM_STAGE_SCAN = 2,       /* prefix sum of the bin counts (b)                */
+    ISM_STAGE_ENUM_SCATTER = 3, /* image enumeration, scatter into bins (a)      */
+    ISM_STAGE_ACCUM = 4,      /* windowed-sinc accumulation, eq. (5)-(6) (c)     */
+    ISM_STAGE_FINALIZE = 5,   /* tile seams and envelope fit                     */
+    ISM_STAGE_TAIL = 6,       /* diffuse tail, eq. (8) (d)                       */
+    ISM_N_STAGES = 7
+} ism_stage;
+
+/* Turns timing on (enable != 0) or off for all later simulation calls of the
+ * process.  While on, each stage is bracketed by CUDA events recorded on the
+ * caller's stream (no synchronisation is added). */
+ism_status ism_profile_enable(int enable);
+/* Zeroes the accumulated timings and counts. */
+ism_status ism_profile_reset(void);
+/* Waits for the recorded events and returns, for `stage`, the summed device
+ * time in milliseconds, the number of kernel launches and the number of
+ * simulation calls that ran it since the last reset. */
+ism_status ism_profile_read(int stage, double* total_ms, long long* launches, long long* calls);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* ISM_H */

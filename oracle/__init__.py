@@ -302,11 +302,11 @@ def rir_grad(L, beta, c, fs, Tw, ps, pr, N, n_ism, g):
 # The library call of Section 4
 # --------------------------------------------------------------------------- #
 def n_samples(T: float, fs: float) -> int:
-    """Samples covering [0, T): ceil(T fs - 1e-3), in FP64 from the FP32 inputs.
+    """Samples covering [0, T): ceil(T fs (1 - 1e-6)), in FP64 from the FP32 inputs.
 
-    The 1e-3 sample slack absorbs the FP32 rounding of T (0.3 s is stored as
-    0.30000001 s, which would otherwise add a sample)."""
-    return int(math.ceil(float(T) * float(fs) - 1e-3))
+    The relative slack absorbs the FP32 rounding of T (1.2 s is stored as
+    1.20000005 s, which would otherwise add a sample at 48 kHz)."""
+    return int(math.ceil(float(T) * float(fs) * (1.0 - 1e-6)))
 
 
 def simulate(L, beta, c, fs, pos_src, pos_rcv, N, Tmax, Tdiff=None, Tw=None, seed: int = 0,

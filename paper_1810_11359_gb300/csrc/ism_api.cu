@@ -1,0 +1,705 @@
+// ism_api.cu -- the C ABI of libism (include/ism.h): argument validation,
+// planning of the launch set and of the workspace, and the launch sequence.
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include <cuda_runtime.h>
+
+#include "ism_internal.h"
+
+namespace {
+
+thread_local std::string g_last_error;
+
+ism_status fail(ism_status s, const char* fmt, ...)
+{
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    g_last_error = buf;
+    return s;
+}
+
+ism_status cuda_fail(int e, const char* where)
+{
+    return fail(ISM_ERR_CUDA, "%s: %s", where, cudaGetErrorString((cudaError_t)e));
+}
+
+size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+// n = ceil(T fs (1 - 1e-6)): the relative slack absorbs the FP32 rounding of T
+// (1.2 s is stored as 1.2000000477 s, which would otherwise add a sample).
+int rir_len(double T, double fs) { return (int)std::ceil(T * fs * (1.0 - 1e-6)); }
+
+bool isfin(double x) { return std::isfinite(x); }
+
+void magic_div(uint32_t d, uint32_t* m, int* l)
+{
+    int ll = 0;
+    while ((1ull << ll) < d) ++ll;
+    unsigned long long mm = ((1ull << 32) * ((1ull << ll) - d)) / d + 1ull;
+    *m = (uint32_t)mm;
+    *l = ll;
+}
+
+double t60_of(const double L[3], const double beta[6])
+{
+    double S[6] = {L[1] * L[2], L[1] * L[2], L[0] * L[2], L[0] * L[2], L[0] * L[1], L[0] * L[1]};
+    double den = 0.0;
+    for (int i = 0; i < 6; ++i) den += S[i] * (1.0 - beta[i] * beta[i]);
+    if (!(den > 0.0)) return INFINITY;
+    return 0.161 * L[0] * L[1] * L[2] / den;
+}
+
+// Window length in taps, snapped to an integer when Tw fs is one up to the
+// FP32 rounding of Tw (32 / 16000 s is not exact in FP32).
+double window_taps(double Tw, double fs)
+{
+    double nw = Tw * fs;
+    double rn = std::nearbyint(nw);
+    if (std::fabs(nw - rn) <= 1e-4 * (rn > 1.0 ? rn : 1.0)) nw = rn;
+    return nw;
+}
+
+struct Validated {
+    ism_job job;
+    double Tw, Nw;
+    int n_S, n_ism, H, slots;
+};
+
+ism_status validate_job(const ism_job& in, Validated& v, bool need_ptrs)
+{
+    v.job = in;
+    ism_job& j = v.job;
+    for (int a = 0; a < 3; ++a)
+        if (!(j.room.L[a] > 0.0) || !isfin(j.room.L[a]))
+            return fail(ISM_ERR_INVALID_ARG, "room size L[%d] = %g must be finite and > 0", a, j.room.L[a]);
+    for (int w = 0; w < 6; ++w)
+        if (!isfin(j.room.beta[w]) || std::fabs(j.room.beta[w]) > 1.0f)
+            return fail(ISM_ERR_INVALID_ARG, "beta[%d] = %g must satisfy |beta| <= 1", w, (double)j.room.beta[w]);
+    if (!(j.room.c > 0.0f)) j.room.c = 343.0f;
+    if (!isfin(j.room.c)) return fail(ISM_ERR_INVALID_ARG, "speed of sound must be finite");
+    if (!(j.fs > 0.0f) || !isfin(j.fs)) return fail(ISM_ERR_INVALID_ARG, "fs = %g must be > 0", (double)j.fs);
+    if (!(j.Tmax > 0.0f) || !isfin(j.Tmax)) return fail(ISM_ERR_INVALID_ARG, "Tmax = %g must be > 0", (double)j.Tmax);
+    if (!isfin(j.Tdiff) || !isfin(j.Tw)) return fail(ISM_ERR_INVALID_ARG, "Tdiff and Tw must be finite");
+    if (j.n_src < 1 || j.n_rcv < 1) return fail(ISM_ERR_INVALID_ARG, "need n_src >= 1 and n_rcv >= 1");
+    if ((long long)j.n_src * j.n_rcv > (1ll << 30)) return fail(ISM_ERR_UNSUPPORTED, "too many RIRs in one job");
+    for (int a = 0; a < 3; ++a) {
+        if (j.nb_img[a] < 1) return fail(ISM_ERR_INVALID_ARG, "nb_img[%d] = %d must be >= 1", a, j.nb_img[a]);
+        if (j.nb_img[a] > ISM_MAX_AXIS)
+            return fail(ISM_ERR_UNSUPPORTED, "nb_img[%d] = %d exceeds %d", a, j.nb_img[a], ISM_MAX_AXIS);
+    }
+    if (need_ptrs && (!j.pos_src || !j.pos_rcv || !j.out))
+        return fail(ISM_ERR_INVALID_ARG, "pos_src, pos_rcv and out must be device pointers, not NULL");
+    v.Tw = (j.Tw > 0.0f) ? (double)j.Tw : 4e-3;
+    v.Nw = window_taps(v.Tw, (double)j.fs);
+    if (!(v.Nw >= 2.0)) return fail(ISM_ERR_INVALID_ARG, "window of %g taps: need Tw * fs >= 2", v.Nw);
+    if (v.Nw > 32.0 * ISM_MAX_SLOTS) return fail(ISM_ERR_UNSUPPORTED, "window of %g taps exceeds 256", v.Nw);
+    v.n_S = rir_len(j.Tmax, j.fs);
+    if (v.n_S < 1) return fail(ISM_ERR_INVALID_ARG, "Tmax * fs < 1 sample");
+    v.n_ism = (j.Tdiff > 0.0f && j.Tdiff < j.Tmax) ? rir_len(j.Tdiff, j.fs) : v.n_S;
+    if (v.n_ism > v.n_S) v.n_ism = v.n_S;
+    if (v.n_ism < 0) v.n_ism = 0;
+    if (v.n_ism > ISM_MAX_NISM)
+        return fail(ISM_ERR_UNSUPPORTED, "%d image-source samples exceed %d", v.n_ism, ISM_MAX_NISM);
+    v.H = (int)std::ceil(0.5 * v.Nw - 1e-9);
+    v.slots = (2 * v.H + 31) / 32;
+    return ISM_OK;
+}
+
+// Builds the device job table and the workspace plan of one launch set.
+ism_status plan(const Validated* vs, int n, JobTable& t, WsPlan& p)
+{
+    std::memset(&t, 0, sizeof t);
+    std::memset(&p, 0, sizeof p);
+    t.n_jobs = n;
+    long long rir = 0, hist = 0, tbl = 0, ecta = 0, acta = 0, tcta = 0, seam = 0, ids = 0;
+    for (int i = 0; i < n; ++i) {
+        const Validated& v = vs[i];
+        const ism_job& in = v.job;
+        JobDev& J = t.j[i];
+        for (int a = 0; a < 3; ++a) {
+            J.L[a] = in.room.L[a];
+            J.N[a] = in.nb_img[a];
+            J.nlo[a] = -(in.nb_img[a] / 2);
+        }
+        for (int w = 0; w < 6; ++w) J.beta[w] = in.room.beta[w];
+        J.c = in.room.c;
+        J.fs = in.fs;
+        J.Nw = (float)v.Nw;
+        double k = (double)in.fs / (double)in.room.c;
+        J.kfs_hi = (float)k;
+        J.kfs_lo = (float)(k - (double)J.kfs_hi);
+        J.amp_scale = (float)(k / (4.0 * M_PI));
+        J.n_src = in.n_src;
+        J.n_rcv = in.n_rcv;
+        J.n_rir = in.n_src * in.n_rcv;
+        J.n_S = v.n_S;
+        J.n_ism = v.n_ism;
+        J.H = v.H;
+        J.slots = v.slots;
+        J.Q = (v.n_ism + v.H) / ISM_SB + 1;
+        J.img_per_rir = (long long)in.nb_img[0] * in.nb_img[1] * in.nb_img[2];
+        int us = 8192;
+        while (us > 256 && (long long)J.n_rir * ((J.img_per_rir + us - 1) / us) < 8192) us >>= 1;
+        J.unit_size = us;
+        J.U = (int)((J.img_per_rir + us - 1) / us);
+        J.n_tiles = (J.Q + ISM_TILE_SB - 1) / ISM_TILE_SB;
+        double s_cut = (double)v.n_ism - 1.0 + (double)v.H + 0.5;
+        J.s_cut2 = (float)(s_cut * s_cut);
+        magic_div((uint32_t)in.nb_img[2], &J.divNz_m, &J.divNz_l);
+        magic_div((uint32_t)in.nb_img[1], &J.divNy_m, &J.divNy_l);
+        J.has_tail = v.n_ism < v.n_S;
+        double beta_d[6];
+        for (int w = 0; w < 6; ++w) beta_d[w] = in.room.beta[w];
+        double T60 = t60_of(in.room.L, beta_d);
+        J.g2 = std::isfinite(T60) ? (float)(6.0 * std::log2(10.0) / ((double)in.fs * T60)) : 0.0f;
+        int W = (int)std::ceil(ISM_FIT_WINDOW_S * (double)in.fs - 1e-9);
+        J.W_env = W < v.n_ism ? W : v.n_ism;
+        J.vec4 = (v.n_S % 4 == 0) && (((uintptr_t)in.out & 15u) == 0);
+        J.seed = in.seed;
+        J.pos_src = in.pos_src;
+        J.pos_rcv = in.pos_rcv;
+        J.out = in.out;
+        J.env_amp = in.env_amp;
+        J.rir_base = rir;
+        J.hist_base = hist;
+        J.tbl_base = tbl;
+        J.enum_cta_base = ecta;
+        J.acc_cta_base = acta;
+        J.tail_cta_base = tcta;
+        J.seam_base = seam;
+        const long long R = J.n_rir;
+        rir += R;
+        hist += R * J.Q * J.U;
+        int axis = in.nb_img[0] + in.nb_img[1] + in.nb_img[2];
+        tbl += R * axis;
+        ecta += R * ((J.U + ISM_ENUM_WARPS - 1) / ISM_ENUM_WARPS);
+        acta += R * J.n_tiles;
+        if (J.has_tail) {
+            int blk0 = v.n_ism >> 2, blk_last = (v.n_S - 1) >> 2;
+            tcta += R * ((blk_last - blk0 + 1 + ISM_TAIL_CHUNK / 4 - 1) / (ISM_TAIL_CHUNK / 4));
+        }
+        seam += R * J.n_tiles * 64LL * J.slots;
+        ids += R * J.img_per_rir;
+        if (J.Q > t.max_Q) t.max_Q = J.Q;
+        if (axis > t.max_axis_sum) t.max_axis_sum = axis;
+    }
+    if (hist > (long long)ISM_SCAN_BLOCK * ISM_SCAN_TOP)
+        return fail(ISM_ERR_UNSUPPORTED, "delay-bin histogram of %lld entries exceeds %lld; split the batch", hist,
+                    (long long)ISM_SCAN_BLOCK * ISM_SCAN_TOP);
+    if (ids >= 0xFFFFFFFFll)
+        return fail(ISM_ERR_UNSUPPORTED, "%lld images in one launch set exceed 2^32; split the batch", ids);
+    if (rir > 0x7FFFFFFFll || ecta > 0x7FFFFFFFll || acta > 0x7FFFFFFFll || tcta > 0x7FFFFFFFll)
+        return fail(ISM_ERR_UNSUPPORTED, "launch set too large; split the batch");
+    p.hist_total = hist;
+    p.ids_total = ids;
+    p.tbl_total = tbl;
+    p.seam_total = seam;
+    p.rir_total = rir;
+    p.n_scan_blocks = (hist + ISM_SCAN_BLOCK - 1) / ISM_SCAN_BLOCK;
+    if (p.n_scan_blocks < 1) p.n_scan_blocks = 1;
+    p.enum_ctas = ecta;
+    p.acc_ctas = acta;
+    p.tail_ctas = tcta;
+    size_t off = 0;
+    p.status_off = off;
+    off = align256(off + 256);
+    p.hist_off = off;
+    off = align256(off + (size_t)(hist + 1) * 4);
+    p.part_off = off;
+    off = align256(off + (size_t)(p.n_scan_blocks + 1) * 4);
+    p.ids_off = off;
+    off = align256(off + (size_t)ids * 4);
+    p.tbl_off = off;
+    off = align256(off + (size_t)tbl * 16);
+    p.seam_off = off;
+    off = align256(off + (size_t)seam * 4);
+    p.amp_off = off;
+    off = align256(off + (size_t)rir * 4);
+    p.total = off;
+    return ISM_OK;
+}
+
+ism_status validate_all(const ism_job* jobs, int n_jobs, std::vector<Validated>& vs, bool need_ptrs)
+{
+    if (!jobs || n_jobs < 1) return fail(ISM_ERR_INVALID_ARG, "need at least one job");
+    vs.resize(n_jobs);
+    for (int i = 0; i < n_jobs; ++i) {
+        ism_status s = validate_job(jobs[i], vs[i], need_ptrs);
+        if (s != ISM_OK) {
+            std::string m = g_last_error;
+            return fail(s, "job %d: %s", i, m.c_str());
+        }
+    }
+    return ISM_OK;
+}
+
+ism_status batch_size(const std::vector<Validated>& vs, size_t* bytes)
+{
+    size_t best = 0;
+    JobTable t;
+    WsPlan p;
+    for (size_t g = 0; g < vs.size(); g += ISM_MAX_JOBS) {
+        int n = (int)std::min<size_t>(ISM_MAX_JOBS, vs.size() - g);
+        ism_status s = plan(vs.data() + g, n, t, p);
+        if (s != ISM_OK) return s;
+        if (p.total > best) best = p.total;
+    }
+    *bytes = best;
+    return ISM_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Per-stage timing: event pairs recorded on the caller's stream, resolved
+// when ism_profile_read() is called.
+// ---------------------------------------------------------------------------
+struct Profiler {
+    std::mutex mu;
+    bool on = false;
+    struct Pending {
+        int stage;
+        cudaEvent_t a, b;
+    };
+    std::vector<Pending> pending;
+    std::vector<cudaEvent_t> pool;
+    double ms[ISM_N_STAGES] = {};
+    long long launches[ISM_N_STAGES] = {};
+    long long calls[ISM_N_STAGES] = {};
+
+    cudaEvent_t get()
+    {
+        if (!pool.empty()) {
+            cudaEvent_t e = pool.back();
+            pool.pop_back();
+            return e;
+        }
+        cudaEvent_t e = nullptr;
+        cudaEventCreate(&e);
+        return e;
+    }
+    void resolve()
+    {
+        for (auto& p : pending) {
+            cudaEventSynchronize(p.b);
+            float t = 0.0f;
+            if (cudaEventElapsedTime(&t, p.a, p.b) == cudaSuccess) ms[p.stage] += t;
+            pool.push_back(p.a);
+            pool.push_back(p.b);
+        }
+        pending.clear();
+    }
+};
+
+Profiler& profiler()
+{
+    static Profiler* p = new Profiler();
+    return *p;
+}
+
+// Brackets one stage; a no-op unless profiling is on.
+struct StageTimer {
+    int stage;
+    cudaStream_t s;
+    bool on;
+    cudaEvent_t a = nullptr;
+    StageTimer(int st, cudaStream_t stream) : stage(st), s(stream)
+    {
+        Profiler& P = profiler();
+        std::lock_guard<std::mutex> g(P.mu);
+        on = P.on;
+        if (on) {
+            a = P.get();
+            cudaEventRecord(a, s);
+        }
+    }
+    void done(int launched)
+    {
+        if (!on) return;
+        Profiler& P = profiler();
+        std::lock_guard<std::mutex> g(P.mu);
+        cudaEvent_t b = P.get();
+        cudaEventRecord(b, s);
+        P.pending.push_back({stage, a, b});
+        P.launches[stage] += launched;
+        P.calls[stage] += 1;
+    }
+};
+
+ism_status run_batch(const std::vector<Validated>& vs, void* workspace, size_t ws_bytes, void* stream)
+{
+    size_t need = 0;
+    ism_status s = batch_size(vs, &need);
+    if (s != ISM_OK) return s;
+    if (!workspace) return fail(ISM_ERR_INVALID_ARG, "workspace is NULL");
+    if (((uintptr_t)workspace & 255u) != 0) return fail(ISM_ERR_INVALID_ARG, "workspace must be 256-byte aligned");
+    if (ws_bytes < need)
+        return fail(ISM_ERR_WORKSPACE_TOO_SMALL, "workspace of %zu bytes, need %zu", ws_bytes, need);
+    char* ws = static_cast<char*>(workspace);
+    cudaStream_t st = (cudaStream_t)stream;
+    int e = (int)cudaMemsetAsync(ws, 0, 256, st);
+    if (e) return cuda_fail(e, "status reset");
+    JobTable t;
+    WsPlan p;
+    for (size_t g = 0; g < vs.size(); g += ISM_MAX_JOBS) {
+        int n = (int)std::min<size_t>(ISM_MAX_JOBS, vs.size() - g);
+        s = plan(vs.data() + g, n, t, p);
+        if (s != ISM_OK) return s;
+        {
+            StageTimer tm(ISM_STAGE_GEOMETRY, st);
+            if ((e = ism_launch_geometry(t, p, ws, stream))) return cuda_fail(e, "geometry kernel");
+            tm.done(p.rir_total > 0);
+        }
+        {
+            StageTimer tm(ISM_STAGE_ENUM_COUNT, st);
+            if ((e = ism_launch_enum(t, p, ws, false, stream))) return cuda_fail(e, "enumeration (count) kernel");
+            tm.done(p.enum_ctas > 0);
+        }
+        {
+            StageTimer tm(ISM_STAGE_SCAN, st);
+            if ((e = ism_launch_scan(p, ws, stream))) return cuda_fail(e, "scan kernels");
+            tm.done(3);
+        }
+        {
+            StageTimer tm(ISM_STAGE_ENUM_SCATTER, st);
+            if ((e = ism_launch_enum(t, p, ws, true, stream))) return cuda_fail(e, "enumeration (scatter) kernel");
+            tm.done(p.enum_ctas > 0);
+        }
+        {
+            StageTimer tm(ISM_STAGE_ACCUM, st);
+            int launched = 0;
+            if ((e = ism_launch_accum(t, p, ws, ISM_PREC_FP32, stream, &launched)))
+                return cuda_fail(e, "accumulation kernel");
+            tm.done(launched);
+        }
+        {
+            StageTimer tm(ISM_STAGE_FINALIZE, st);
+            if ((e = ism_launch_finalize(t, p, ws, stream))) return cuda_fail(e, "finalize kernel");
+            tm.done(p.rir_total > 0);
+        }
+        if (p.tail_ctas > 0) {
+            StageTimer tm(ISM_STAGE_TAIL, st);
+            if ((e = ism_launch_tail(t, p, ws, stream))) return cuda_fail(e, "tail kernel");
+            tm.done(1);
+        }
+    }
+    return ISM_OK;
+}
+
+ism_job make_job(const ism_room* room, const float* pos_src, int n_src, const float* pos_rcv, int n_rcv,
+                 const int nb_img[3], float Tmax, float fs, float Tdiff, float Tw, uint64_t seed, float* out)
+{
+    ism_job j;
+    std::memset(&j, 0, sizeof j);
+    if (room) j.room = *room;
+    j.pos_src = pos_src;
+    j.n_src = n_src;
+    j.pos_rcv = pos_rcv;
+    j.n_rcv = n_rcv;
+    if (nb_img)
+        for (int a = 0; a < 3; ++a) j.nb_img[a] = nb_img[a];
+    j.Tmax = Tmax;
+    j.fs = fs;
+    j.Tdiff = Tdiff;
+    j.Tw = Tw;
+    j.seed = seed;
+    j.out = out;
+    j.env_amp = nullptr;
+    return j;
+}
+
+ism_status check_prec(ism_precision prec)
+{
+    if (prec != ISM_PREC_FP32)
+        return fail(ISM_ERR_UNSUPPORTED, "precision %d is not available in this build", (int)prec);
+    return ISM_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* ism_status_string(ism_status s)
+{
+    switch (s) {
+    case ISM_OK: return "ISM_OK";
+    case ISM_ERR_INVALID_ARG: return "ISM_ERR_INVALID_ARG";
+    case ISM_ERR_INFEASIBLE: return "ISM_ERR_INFEASIBLE";
+    case ISM_ERR_WORKSPACE_TOO_SMALL: return "ISM_ERR_WORKSPACE_TOO_SMALL";
+    case ISM_ERR_OOM: return "ISM_ERR_OOM";
+    case ISM_ERR_CUDA: return "ISM_ERR_CUDA";
+    case ISM_ERR_TIMEOUT: return "ISM_ERR_TIMEOUT";
+    case ISM_ERR_DEVICE_CHECK: return "ISM_ERR_DEVICE_CHECK";
+    case ISM_ERR_UNSUPPORTED: return "ISM_ERR_UNSUPPORTED";
+    case ISM_ERR_CANCELLED: return "ISM_ERR_CANCELLED";
+    }
+    return "ISM_ERR_UNKNOWN";
+}
+
+const char* ism_last_error_message(void) { return g_last_error.c_str(); }
+
+int ism_version(void) { return ISM_VERSION; }
+
+ism_status ism_rir_length(float T, float fs, int* n_samples)
+{
+    if (!n_samples) return fail(ISM_ERR_INVALID_ARG, "n_samples is NULL");
+    if (!(T > 0.0f) || !(fs > 0.0f) || !isfin(T) || !isfin(fs))
+        return fail(ISM_ERR_INVALID_ARG, "T and fs must be finite and > 0");
+    *n_samples = rir_len(T, fs);
+    return ISM_OK;
+}
+
+ism_status ism_workspace_size(const ism_room* room, int n_src, int n_rcv, const int nb_img[3], float Tmax, float fs,
+                              float Tdiff, float Tw, ism_precision prec, size_t* bytes)
+{
+    g_last_error.clear();
+    if (!room || !nb_img || !bytes) return fail(ISM_ERR_INVALID_ARG, "room, nb_img and bytes must not be NULL");
+    ism_status s = check_prec(prec);
+    if (s != ISM_OK) return s;
+    ism_job j = make_job(room, nullptr, n_src, nullptr, n_rcv, nb_img, Tmax, fs, Tdiff, Tw, 0, nullptr);
+    std::vector<Validated> vs;
+    if ((s = validate_all(&j, 1, vs, false)) != ISM_OK) return s;
+    return batch_size(vs, bytes);
+}
+
+ism_status ism_batch_workspace_size(const ism_job* jobs, int n_jobs, ism_precision prec, size_t* bytes)
+{
+    g_last_error.clear();
+    if (!bytes) return fail(ISM_ERR_INVALID_ARG, "bytes is NULL");
+    ism_status s = check_prec(prec);
+    if (s != ISM_OK) return s;
+    std::vector<Validated> vs;
+    if ((s = validate_all(jobs, n_jobs, vs, false)) != ISM_OK) return s;
+    return batch_size(vs, bytes);
+}
+
+ism_status ism_simulate_batch(const ism_job* jobs, int n_jobs, ism_precision prec, void* workspace, size_t ws_bytes,
+                              void* stream)
+{
+    g_last_error.clear();
+    ism_status s = check_prec(prec);
+    if (s != ISM_OK) return s;
+    std::vector<Validated> vs;
+    if ((s = validate_all(jobs, n_jobs, vs, true)) != ISM_OK) return s;
+    return run_batch(vs, workspace, ws_bytes, stream);
+}
+
+ism_status ism_simulate(const ism_room* room, const float* pos_src, int n_src, const float* pos_rcv, int n_rcv,
+                        const int nb_img[3], float Tmax, float fs, float Tdiff, float Tw, ism_precision prec,
+                        uint64_t seed, float* out, void* workspace, size_t ws_bytes, void* stream)
+{
+    g_last_error.clear();
+    if (!room || !nb_img) return fail(ISM_ERR_INVALID_ARG, "room and nb_img must not be NULL");
+    ism_job j = make_job(room, pos_src, n_src, pos_rcv, n_rcv, nb_img, Tmax, fs, Tdiff, Tw, seed, out);
+    return ism_simulate_batch(&j, 1, prec, workspace, ws_bytes, stream);
+}
+
+ism_status ism_simulate_host(const ism_room* room, const float* pos_src, int n_src, const float* pos_rcv, int n_rcv,
+                             const int nb_img[3], float Tmax, float fs, float Tdiff, float Tw, ism_precision prec,
+                             uint64_t seed, float* out, void* workspace, size_t ws_bytes, void* stream)
+{
+    g_last_error.clear();
+    if (!room || !nb_img || !pos_src || !pos_rcv || !out)
+        return fail(ISM_ERR_INVALID_ARG, "room, nb_img, positions and out must not be NULL");
+    ism_status s = check_prec(prec);
+    if (s != ISM_OK) return s;
+    for (int i = 0; i < n_src; ++i)
+        for (int a = 0; a < 3; ++a)
+            if (!(pos_src[3 * i + a] > 0.0f && (double)pos_src[3 * i + a] < room->L[a]))
+                return fail(ISM_ERR_INVALID_ARG, "source %d lies outside the room", i);
+    for (int i = 0; i < n_rcv; ++i)
+        for (int a = 0; a < 3; ++a)
+            if (!(pos_rcv[3 * i + a] > 0.0f && (double)pos_rcv[3 * i + a] < room->L[a]))
+                return fail(ISM_ERR_INVALID_ARG, "receiver %d lies outside the room", i);
+    ism_job j = make_job(room, nullptr, n_src, nullptr, n_rcv, nb_img, Tmax, fs, Tdiff, Tw, seed, nullptr);
+    std::vector<Validated> vs;
+    if ((s = validate_all(&j, 1, vs, false)) != ISM_OK) return s;
+    size_t sim = 0;
+    if ((s = batch_size(vs, &sim)) != ISM_OK) return s;
+    // device layout: [simulation workspace | positions | output]
+    size_t pos_off = align256(sim);
+    size_t out_off = align256(pos_off + (size_t)(n_src + n_rcv) * 3 * sizeof(float));
+    size_t n_out = (size_t)n_src * n_rcv * (size_t)vs[0].n_S;
+    size_t need = align256(out_off + n_out * sizeof(float));
+    if (!workspace) return fail(ISM_ERR_INVALID_ARG, "workspace is NULL");
+    if (ws_bytes < need)
+        return fail(ISM_ERR_WORKSPACE_TOO_SMALL, "workspace of %zu bytes, need %zu (ism_host_workspace_size)",
+                    ws_bytes, need);
+    char* ws = static_cast<char*>(workspace);
+    cudaStream_t st = (cudaStream_t)stream;
+    float* d_pos = reinterpret_cast<float*>(ws + pos_off);
+    float* d_out = reinterpret_cast<float*>(ws + out_off);
+    int e;
+    if ((e = (int)cudaMemcpyAsync(d_pos, pos_src, (size_t)n_src * 3 * sizeof(float), cudaMemcpyHostToDevice, st)))
+        return cuda_fail(e, "copy of source positions");
+    if ((e = (int)cudaMemcpyAsync(d_pos + 3 * n_src, pos_rcv, (size_t)n_rcv * 3 * sizeof(float),
+                                  cudaMemcpyHostToDevice, st)))
+        return cuda_fail(e, "copy of receiver positions");
+    vs[0].job.pos_src = d_pos;
+    vs[0].job.pos_rcv = d_pos + 3 * n_src;
+    vs[0].job.out = d_out;
+    vs[0].job.seed = seed;
+    if ((s = run_batch(vs, workspace, sim, stream)) != ISM_OK) return s;
+    if ((e = (int)cudaMemcpyAsync(out, d_out, n_out * sizeof(float), cudaMemcpyDeviceToHost, st)))
+        return cuda_fail(e, "copy of the RIRs");
+    if ((e = (int)cudaStreamSynchronize(st))) return cuda_fail(e, "stream synchronize");
+    return ISM_OK;
+}
+
+ism_status ism_host_workspace_size(const ism_room* room, int n_src, int n_rcv, const int nb_img[3], float Tmax,
+                                   float fs, float Tdiff, float Tw, ism_precision prec, size_t* bytes)
+{
+    size_t sim = 0;
+    ism_status s = ism_workspace_size(room, n_src, n_rcv, nb_img, Tmax, fs, Tdiff, Tw, prec, &sim);
+    if (s != ISM_OK) return s;
+    int n_S = rir_len(Tmax, fs);
+    size_t pos_off = align256(sim);
+    size_t out_off = align256(pos_off + (size_t)(n_src + n_rcv) * 3 * sizeof(float));
+    *bytes = align256(out_off + (size_t)n_src * n_rcv * (size_t)n_S * sizeof(float));
+    return ISM_OK;
+}
+
+ism_status ism_workspace_status(const void* workspace, void* stream, uint32_t* flags)
+{
+    g_last_error.clear();
+    if (!workspace || !flags) return fail(ISM_ERR_INVALID_ARG, "workspace and flags must not be NULL");
+    uint32_t v = 0;
+    int e;
+    if ((e = (int)cudaMemcpyAsync(&v, workspace, sizeof v, cudaMemcpyDeviceToHost, (cudaStream_t)stream)))
+        return cuda_fail(e, "status read");
+    if ((e = (int)cudaStreamSynchronize((cudaStream_t)stream))) return cuda_fail(e, "stream synchronize");
+    *flags = v;
+    return ISM_OK;
+}
+
+ism_status ism_diffuse_noise(uint64_t seed, uint32_t rir, uint32_t k0, int n, float* z, void* stream)
+{
+    g_last_error.clear();
+    if (n < 0 || (n > 0 && !z)) return fail(ISM_ERR_INVALID_ARG, "need n >= 0 and a device buffer");
+    if ((unsigned long long)k0 + (unsigned long long)n > 0xFFFFFFFFull)
+        return fail(ISM_ERR_INVALID_ARG, "sample range exceeds 2^32");
+    int e = ism_launch_noise(seed, rir, k0, n, z, stream);
+    if (e) return cuda_fail(e, "noise kernel");
+    return ISM_OK;
+}
+
+ism_status ism_t60_sabine(const double L[3], const double beta[6], double* T60)
+{
+    g_last_error.clear();
+    if (!L || !beta || !T60) return fail(ISM_ERR_INVALID_ARG, "NULL argument");
+    for (int a = 0; a < 3; ++a)
+        if (!(L[a] > 0.0)) return fail(ISM_ERR_INVALID_ARG, "room size must be > 0");
+    double t = t60_of(L, beta);
+    if (!std::isfinite(t)) return fail(ISM_ERR_INFEASIBLE, "no absorption: T60 is infinite");
+    *T60 = t;
+    return ISM_OK;
+}
+
+ism_status ism_beta_sabine(const double L[3], double T60, const double abs_weights[6], int negative,
+                           double beta_out[6])
+{
+    g_last_error.clear();
+    if (!L || !beta_out) return fail(ISM_ERR_INVALID_ARG, "NULL argument");
+    for (int a = 0; a < 3; ++a)
+        if (!(L[a] > 0.0) || !isfin(L[a])) return fail(ISM_ERR_INVALID_ARG, "room size must be > 0");
+    if (!(T60 > 0.0) || !isfin(T60)) return fail(ISM_ERR_INVALID_ARG, "T60 must be > 0");
+    double S[6] = {L[1] * L[2], L[1] * L[2], L[0] * L[2], L[0] * L[2], L[0] * L[1], L[0] * L[1]};
+    double w[6], sw = 0.0;
+    for (int i = 0; i < 6; ++i) {
+        w[i] = abs_weights ? abs_weights[i] : 1.0;
+        if (!(w[i] >= 0.0) || !isfin(w[i])) return fail(ISM_ERR_INVALID_ARG, "absorption weights must be >= 0");
+        sw += S[i] * w[i];
+    }
+    if (!(sw > 0.0)) return fail(ISM_ERR_INFEASIBLE, "all absorption weights are zero");
+    double a0 = 0.161 * L[0] * L[1] * L[2] / (T60 * sw);
+    for (int i = 0; i < 6; ++i)
+        if (w[i] * a0 >= 1.0)
+            return fail(ISM_ERR_INFEASIBLE, "T60 = %g s needs absorption %g >= 1 on wall %d", T60, w[i] * a0, i);
+    for (int i = 0; i < 6; ++i) {
+        double b = std::sqrt(1.0 - w[i] * a0);
+        beta_out[i] = negative ? -b : b;
+    }
+    return ISM_OK;
+}
+
+ism_status ism_beta_sabine_device(const double* L, const double* T60, const double* abs_weights, int negative, int n,
+                                  double* beta_out, int* status, void* stream)
+{
+    g_last_error.clear();
+    if (n < 0 || (n > 0 && (!L || !T60 || !beta_out || !status)))
+        return fail(ISM_ERR_INVALID_ARG, "need n >= 0 and device buffers");
+    int e = ism_launch_beta_sabine(L, T60, abs_weights, negative, n, beta_out, status, stream);
+    if (e) return cuda_fail(e, "Sabine kernel");
+    return ISM_OK;
+}
+
+ism_status ism_nb_img_from_t(double T, const double L[3], double c, double Tw, int nb_out[3])
+{
+    g_last_error.clear();
+    if (!L || !nb_out) return fail(ISM_ERR_INVALID_ARG, "NULL argument");
+    if (!(T >= 0.0) || !isfin(T)) return fail(ISM_ERR_INVALID_ARG, "T must be >= 0");
+    if (!(c > 0.0)) c = 343.0;
+    if (!(Tw > 0.0)) Tw = 4e-3;
+    double R = c * (T + 0.5 * Tw);
+    for (int a = 0; a < 3; ++a) {
+        if (!(L[a] > 0.0)) return fail(ISM_ERR_INVALID_ARG, "room size must be > 0");
+        double M = std::ceil(R / L[a]) + 1.0;
+        if (2.0 * M + 1.0 > 1e9) return fail(ISM_ERR_UNSUPPORTED, "image grid too large");
+        nb_out[a] = (int)(2.0 * M + 1.0);
+    }
+    return ISM_OK;
+}
+
+ism_status ism_profile_enable(int enable)
+{
+    g_last_error.clear();
+    Profiler& P = profiler();
+    std::lock_guard<std::mutex> g(P.mu);
+    P.on = enable != 0;
+    return ISM_OK;
+}
+
+ism_status ism_profile_reset(void)
+{
+    g_last_error.clear();
+    Profiler& P = profiler();
+    std::lock_guard<std::mutex> g(P.mu);
+    P.resolve();
+    for (int i = 0; i < ISM_N_STAGES; ++i) {
+        P.ms[i] = 0.0;
+        P.launches[i] = 0;
+        P.calls[i] = 0;
+    }
+    return ISM_OK;
+}
+
+ism_status ism_profile_read(int stage, double* total_ms, long long* launches, long long* calls)
+{
+    g_last_error.clear();
+    if (stage < 0 || stage >= ISM_N_STAGES) return fail(ISM_ERR_INVALID_ARG, "stage %d out of range", stage);
+    Profiler& P = profiler();
+    std::lock_guard<std::mutex> g(P.mu);
+    P.resolve();
+    if (total_ms) *total_ms = P.ms[stage];
+    if (launches) *launches = P.launches[stage];
+    if (calls) *calls = P.calls[stage];
+    return ISM_OK;
+}
+
+ism_status ism_att2t_sabine(double att_dB, double T60, double* t)
+{
+    g_last_error.clear();
+    if (!t) return fail(ISM_ERR_INVALID_ARG, "NULL argument");
+    if (!(T60 > 0.0) || !isfin(att_dB)) return fail(ISM_ERR_INVALID_ARG, "T60 must be > 0");
+    *t = att_dB / 60.0 * T60;
+    return ISM_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,146 @@
+// ism_device.cuh -- device helpers shared by the libism kernels.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "ism_internal.h"
+
+// ---------------------------------------------------------------------------
+// Job lookup: the kernels of a launch set enumerate their CTAs across the
+// jobs of the table; job j owns CTAs [base_j, base_{j+1}).
+// ---------------------------------------------------------------------------
+template <typename F>
+__device__ __forceinline__ int ism_find_job(const JobTable& t, long long cta, F base_of)
+{
+    int j = 0;
+    for (int k = 1; k < t.n_jobs; ++k)
+        if (cta >= base_of(t.j[k])) j = k;
+    return j;
+}
+
+// ---------------------------------------------------------------------------
+// Float-float (unevaluated sum hi + lo) arithmetic on correctly rounded FP32
+// operations (Dekker / Knuth two-sum).  Intrinsics keep the compiler from
+// contracting or reordering the error terms.
+// ---------------------------------------------------------------------------
+struct ff {
+    float hi, lo;
+};
+
+__device__ __forceinline__ ff ff_add(ff a, ff b)
+{
+    float s = __fadd_rn(a.hi, b.hi);
+    float bb = __fsub_rn(s, a.hi);
+    float e = __fadd_rn(__fsub_rn(a.hi, __fsub_rn(s, bb)), __fsub_rn(b.hi, bb));
+    e = __fadd_rn(e, __fadd_rn(a.lo, b.lo));
+    float hi = __fadd_rn(s, e);
+    float lo = __fsub_rn(e, __fsub_rn(hi, s));
+    return {hi, lo};
+}
+
+// sqrt of a positive float-float; the result's lo is the first-order
+// correction (S - r^2) / (2 r) of the correctly rounded FP32 root r.
+__device__ __forceinline__ ff ff_sqrt(ff a)
+{
+    float r = __fsqrt_rn(a.hi);
+    float res = __fadd_rn(__fmaf_rn(-r, r, a.hi), a.lo);
+    float lo = __fmul_rn(res, __fdividef(0.5f, r));
+    return {r, lo};
+}
+
+// ---------------------------------------------------------------------------
+// Division by a run-time constant d >= 1 for 32-bit x (Granlund and
+// Montgomery, "Division by invariant integers using multiplication", 1994):
+// q = (umulhi(x, m) + x) >> l with l = ceil(log2 d), m = 2^32 (2^l - d) / d + 1.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t ism_udiv(uint32_t x, uint32_t m, int l)
+{
+    unsigned long long t = (unsigned long long)__umulhi(x, m) + (unsigned long long)x;
+    return (uint32_t)(t >> l);
+}
+
+// Approximate reciprocal on the special-function unit (max error ~1 ulp).
+__device__ __forceinline__ float ism_rcp(float x)
+{
+    float r;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+
+// ---------------------------------------------------------------------------
+// Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11): ten rounds, each two
+// 32x32 -> 64-bit products of counter words 0 and 2 with M0, M1, mixed with
+// words 1, 3 and the key; the key is bumped by the Weyl constants W0, W1
+// between rounds.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint4 ism_philox(uint4 c, uint32_t k0, uint32_t k1)
+{
+    const uint32_t M0 = 0xD2511F53u, M1 = 0xCD9E8D57u;
+    const uint32_t W0 = 0x9E3779B9u, W1 = 0xBB67AE85u;
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        uint32_t hi0 = __umulhi(M0, c.x), lo0 = M0 * c.x;
+        uint32_t hi1 = __umulhi(M1, c.z), lo1 = M1 * c.z;
+        uint4 n;
+        n.x = hi1 ^ c.y ^ k0;
+        n.y = lo1;
+        n.z = hi0 ^ c.w ^ k1;
+        n.w = lo0;
+        c = n;
+        k0 += W0;
+        k1 += W1;
+    }
+    return c;
+}
+
+// The FP32 noise transform, one correctly rounded operation at a time, in
+// the order of its written specification (uniform, ratio, ln, scale):
+//   u = ((x >> 9) + 1/2) 2^-23                      exact in FP32
+//   r = u / (1 - u)                                 (1 - u exact)
+//   ln r: r = m 2^e, m in (sqrt(1/2), sqrt(2)]; t = (m - 1)/(m + 1);
+//         ln m = 2t + t^3 (2/3 + t^2 (2/5 + t^2 (2/7 + t^2 (2/9 + t^2 2/11))))
+//         ln r = e ln2_hi + (e ln2_lo + ln m)
+//   z = (sqrt(3)/pi) ln r                           unit-variance logistic
+__device__ __forceinline__ float ism_uniform(uint32_t x)
+{
+    float m = __uint2float_rn(x >> 9);
+    return __fmul_rn(__fadd_rn(m, 0.5f), 0x1p-23f);
+}
+
+__device__ __forceinline__ float ism_ln_spec(float x)
+{
+    uint32_t bits = __float_as_uint(x);
+    int e = (int)((bits >> 23) & 0xFFu) - 127;
+    float m = __uint_as_float((bits & 0x007FFFFFu) | 0x3F800000u);
+    if (m > 1.41421353816986083984375f) {
+        m = __fmul_rn(m, 0.5f);
+        e += 1;
+    }
+    float t = __fdiv_rn(__fsub_rn(m, 1.0f), __fadd_rn(m, 1.0f));
+    float t2 = __fmul_rn(t, t);
+    float p = __fmaf_rn(t2, 2.0f / 11.0f, 2.0f / 9.0f);
+    p = __fmaf_rn(t2, p, 2.0f / 7.0f);
+    p = __fmaf_rn(t2, p, 2.0f / 5.0f);
+    p = __fmaf_rn(t2, p, 2.0f / 3.0f);
+    float t3 = __fmul_rn(t, t2);
+    float lnm = __fmaf_rn(t3, p, __fmul_rn(2.0f, t));
+    float ef = __int2float_rn(e);
+    return __fmaf_rn(ef, 0.693145751953125f, __fmaf_rn(ef, 1.428606765330187e-06f, lnm));
+}
+
+__device__ __forceinline__ float ism_logistic(uint32_t x)
+{
+    float u = ism_uniform(x);
+    float r = __fdiv_rn(u, __fsub_rn(1.0f, u));
+    return __fmul_rn(0.5513288974761963f, ism_ln_spec(r));
+}
+
+// Noise of sample k of RIR `rir`: word k mod 4 of Philox(counter (k/4, rir,
+// 0, 0), key (seed lo, seed hi)).  Returns the four logistic values of the
+// counter block k/4.
+__device__ __forceinline__ float4 ism_noise_block(uint64_t seed, uint32_t rir, uint32_t blk)
+{
+    uint4 w = ism_philox(make_uint4(blk, rir, 0u, 0u), (uint32_t)seed, (uint32_t)(seed >> 32));
+    return make_float4(ism_logistic(w.x), ism_logistic(w.y), ism_logistic(w.z), ism_logistic(w.w));
+}

@@ -1,0 +1,239 @@
+// ism_enum.cu -- image enumeration (kernel a) and the counting sort of images
+// into delay bins (kernel b).
+//
+// Kernel (a) walks the whole image grid of every RIR (Section 2.1).  For
+// image (nx, ny, nz) the squared delay in samples is Sx + Sy + Sz (tables of
+// ism_geometry.cu; eq. (2)-(3) with s = d f_s / c); the image is kept when
+// its window (eq. (6), |t - tau| < Tw/2) can reach a sample below n_ism, and
+// its delay bin is q = floor((s + 1/2) / 32).  The delay here is plain FP32:
+// it only chooses the bin.  The accumulation kernel recomputes the delay in
+// float-float and places the image within a window that tolerates the bin
+// being off by the FP32 error (it accepts offsets -1..31 inside a bin).
+//
+// Determinism: each warp owns a fixed slice ("unit") of the grid and walks
+// it in order, 32 images at a time.  Images of one 32-wide step that fall in
+// the same bin are ranked by lane (match.any + popc), so the position of an
+// image inside its bin is a pure function of the inputs:
+//   pass 1 (count):   per-unit per-bin counts -> hist[rir][bin][unit]
+//   scan (b):         exclusive prefix over hist (bin-major, unit-minor)
+//   pass 2 (scatter): same walk, ids[hist[rir][bin][unit] + rank] = image id
+#include "ism_device.cuh"
+
+namespace {
+
+template <bool SCATTER>
+__global__ void __launch_bounds__(ISM_ENUM_WARPS * 32) enum_kernel(const __grid_constant__ JobTable t,
+                                                                    const float4* __restrict__ tbl,
+                                                                    uint32_t* __restrict__ hist,
+                                                                    uint32_t* __restrict__ ids,
+                                                                    uint32_t* __restrict__ status)
+{
+    extern __shared__ __align__(16) unsigned char smem[];
+    const long long g = blockIdx.x;
+    const int jid = ism_find_job(t, g, [](const JobDev& j) { return j.enum_cta_base; });
+    const JobDev& J = t.j[jid];
+    const int ctas_per_rir = (J.U + ISM_ENUM_WARPS - 1) / ISM_ENUM_WARPS;
+    const long long local = g - J.enum_cta_base;
+    const int r = (int)(local / ctas_per_rir);
+    const int c = (int)(local % ctas_per_rir);
+    const int Nx = J.N[0], Ny = J.N[1], Nz = J.N[2];
+    const int n_axis = Nx + Ny + Nz;
+    const int Q = J.Q;
+
+    float* S = reinterpret_cast<float*>(smem);                         // [n_axis] plain FP32 s^2
+    uint32_t* cnt = reinterpret_cast<uint32_t*>(smem) + ((t.max_axis_sum + 3) & ~3);  // [warps][max_Q]
+
+    const float4* T = tbl + J.tbl_base + (long long)r * n_axis;
+    for (int e = threadIdx.x; e < n_axis; e += blockDim.x) {
+        float4 v = T[e];
+        S[e] = v.x;
+    }
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int unit = c * ISM_ENUM_WARPS + warp;
+    const bool active = unit < J.U;
+    uint32_t* my = cnt + warp * t.max_Q;
+    const long long hrow = J.hist_base + (long long)r * Q * J.U;  // + q * U + unit
+    if (active) {
+        for (int q = lane; q < Q; q += 32)
+            my[q] = SCATTER ? hist[hrow + (long long)q * J.U + unit] : 0u;
+    }
+    __syncthreads();
+    if (!active) return;
+
+    const uint32_t n_img = (uint32_t)J.img_per_rir;
+    const uint32_t begin = (uint32_t)unit * (uint32_t)J.unit_size;
+    uint32_t end = begin + (uint32_t)J.unit_size;
+    if (end > n_img) end = n_img;
+    const float* Sy = S + Nx;
+    const float* Sz = S + Nx + Ny;
+    const float s_cut2 = J.s_cut2;
+    uint32_t* out_ids = ids;
+    const unsigned lt_mask = (1u << lane) - 1u;
+
+    for (uint32_t base = begin; base < end; base += 32) {
+        uint32_t id = base + lane;
+        int q = -1;
+        uint32_t packed = 0;
+        if (id < end) {
+            uint32_t t1 = ism_udiv(id, J.divNz_m, J.divNz_l);
+            uint32_t iz = id - t1 * (uint32_t)Nz;
+            uint32_t ix = ism_udiv(t1, J.divNy_m, J.divNy_l);
+            uint32_t iy = t1 - ix * (uint32_t)Ny;
+            float s2 = __fadd_rn(__fadd_rn(S[ix], Sy[iy]), Sz[iz]);
+            if (s2 < s_cut2) {
+                float s = __fsqrt_rn(s2);
+                q = (int)floorf(__fmul_rn(__fadd_rn(s, 0.5f), 1.0f / ISM_SB));
+                if (q >= Q) {  // cannot happen for a consistent s_cut2; keep memory safe
+                    atomicOr(status, (uint32_t)ISM_DEVICE_FLAG_BIN);
+                    q = -1;
+                }
+                packed = ix | (iy << 10) | (iz << 20);
+            }
+        }
+        unsigned peers = __match_any_sync(0xffffffffu, q);
+        uint32_t base_cnt = 0;
+        if (q >= 0) base_cnt = my[q];
+        __syncwarp();
+        if (q >= 0) {
+            int leader = __ffs(peers) - 1;
+            uint32_t rank = (uint32_t)__popc(peers & lt_mask);
+            if (lane == leader) my[q] = base_cnt + (uint32_t)__popc(peers);
+            if (SCATTER) out_ids[base_cnt + rank] = packed;
+        }
+        __syncwarp();
+    }
+    if (!SCATTER) {
+        for (int q = lane; q < Q; q += 32) hist[hrow + (long long)q * J.U + unit] = my[q];
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Exclusive scan of hist[0, n) in place; hist[n] receives the total.
+// Three launches: block totals, scan of the totals (one block), apply.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t warp_incl_scan(uint32_t v, int lane)
+{
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        uint32_t n = __shfl_up_sync(0xffffffffu, v, o);
+        if (lane >= o) v += n;
+    }
+    return v;
+}
+
+// Block-wide exclusive scan of one value per thread (1024 threads); returns
+// the exclusive prefix and writes the block total to *total.
+__device__ __forceinline__ uint32_t block_excl_scan(uint32_t v, uint32_t* sh, uint32_t* total)
+{
+    int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    uint32_t inc = warp_incl_scan(v, lane);
+    if (lane == 31) sh[warp] = inc;
+    __syncthreads();
+    if (warp == 0) {
+        uint32_t w = (lane < (int)(blockDim.x >> 5)) ? sh[lane] : 0u;
+        uint32_t wi = warp_incl_scan(w, lane);
+        sh[lane] = wi - w;
+        if (lane == 31) sh[32] = wi;
+    }
+    __syncthreads();
+    uint32_t r = sh[warp] + inc - v;
+    *total = sh[32];
+    __syncthreads();
+    return r;
+}
+
+__global__ void __launch_bounds__(1024) scan_partials(const uint32_t* __restrict__ a, long long n,
+                                                      uint32_t* __restrict__ part)
+{
+    __shared__ uint32_t sh[33];
+    long long i0 = (long long)blockIdx.x * ISM_SCAN_BLOCK + threadIdx.x * 4;
+    uint32_t v = 0;
+    for (int k = 0; k < 4; ++k)
+        if (i0 + k < n) v += a[i0 + k];
+    uint32_t tot;
+    block_excl_scan(v, sh, &tot);
+    if (threadIdx.x == 0) part[blockIdx.x] = tot;
+}
+
+__global__ void __launch_bounds__(1024) scan_top(uint32_t* __restrict__ part, long long nb,
+                                                 uint32_t* __restrict__ a, long long n)
+{
+    __shared__ uint32_t sh[33];
+    // up to 16 block totals per thread, consecutive
+    uint32_t vals[16];
+    uint32_t s = 0;
+    long long i0 = (long long)threadIdx.x * 16;
+    for (int k = 0; k < 16; ++k) {
+        vals[k] = (i0 + k < nb) ? part[i0 + k] : 0u;
+        s += vals[k];
+    }
+    uint32_t tot;
+    uint32_t ex = block_excl_scan(s, sh, &tot);
+    for (int k = 0; k < 16; ++k) {
+        if (i0 + k < nb) part[i0 + k] = ex;
+        ex += vals[k];
+    }
+    if (threadIdx.x == 0) a[n] = tot;
+}
+
+__global__ void __launch_bounds__(1024) scan_apply(uint32_t* __restrict__ a, long long n,
+                                                   const uint32_t* __restrict__ part)
+{
+    __shared__ uint32_t sh[33];
+    long long i0 = (long long)blockIdx.x * ISM_SCAN_BLOCK + threadIdx.x * 4;
+    uint32_t v[4];
+    uint32_t s = 0;
+    for (int k = 0; k < 4; ++k) {
+        v[k] = (i0 + k < n) ? a[i0 + k] : 0u;
+        s += v[k];
+    }
+    uint32_t tot;
+    uint32_t ex = block_excl_scan(s, sh, &tot) + part[blockIdx.x];
+    for (int k = 0; k < 4; ++k) {
+        if (i0 + k < n) a[i0 + k] = ex;
+        ex += v[k];
+    }
+}
+
+}  // namespace
+
+static size_t enum_smem(const JobTable& t)
+{
+    size_t axis = (size_t)((t.max_axis_sum + 3) & ~3) * 4;
+    return axis + (size_t)ISM_ENUM_WARPS * t.max_Q * 4;
+}
+
+int ism_launch_enum(const JobTable& t, const WsPlan& p, char* ws, bool scatter, void* stream)
+{
+    if (p.enum_ctas <= 0) return 0;
+    size_t sm = enum_smem(t);
+    auto* tbl = reinterpret_cast<const float4*>(ws + p.tbl_off);
+    auto* hist = reinterpret_cast<uint32_t*>(ws + p.hist_off);
+    auto* ids = reinterpret_cast<uint32_t*>(ws + p.ids_off);
+    auto* st = reinterpret_cast<uint32_t*>(ws + p.status_off);
+    cudaError_t e;
+    if (scatter) {
+        e = cudaFuncSetAttribute(enum_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+        if (e != cudaSuccess) return (int)e;
+        enum_kernel<true><<<(unsigned)p.enum_ctas, ISM_ENUM_WARPS * 32, sm, (cudaStream_t)stream>>>(t, tbl, hist,
+                                                                                                      ids, st);
+    } else {
+        e = cudaFuncSetAttribute(enum_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+        if (e != cudaSuccess) return (int)e;
+        enum_kernel<false><<<(unsigned)p.enum_ctas, ISM_ENUM_WARPS * 32, sm, (cudaStream_t)stream>>>(t, tbl, hist,
+                                                                                                       ids, st);
+    }
+    return (int)cudaGetLastError();
+}
+
+int ism_launch_scan(const WsPlan& p, char* ws, void* stream)
+{
+    auto* hist = reinterpret_cast<uint32_t*>(ws + p.hist_off);
+    auto* part = reinterpret_cast<uint32_t*>(ws + p.part_off);
+    long long n = p.hist_total, nb = p.n_scan_blocks;
+    cudaStream_t s = (cudaStream_t)stream;
+    scan_partials<<<(unsigned)nb, 1024, 0, s>>>(hist, n, part);
+    scan_top<<<1, 1024, 0, s>>>(part, nb, hist, n);
+    scan_apply<<<(unsigned)nb, 1024, 0, s>>>(hist, n, part);
+    return (int)cudaGetLastError();
+}

@@ -1,0 +1,125 @@
+// ism_internal.h -- definitions shared by the translation units of libism.
+//
+// The simulation of a batch of jobs (one job = one room with its source and
+// receiver sets) runs as a fixed sequence of launches, all ordered on the
+// caller's stream:
+//
+//   geometry  per RIR and axis: image offsets squared in samples^2 (FP64 ->
+//             float-float) and wall-reflection products (Section 2.1, eq. (1),
+//             eq. (4)); checks the positions.
+//   enum(a)   every image of every RIR: delay in samples (eq. (2)-(3)),
+//             culled when its window misses [0, n_ism); counts the survivors
+//             per (RIR, 32-sample delay bin) for each warp's slice of the grid.
+//   scan(b)   exclusive prefix over the counts -> bin offsets (counting sort).
+//   enum(a')  the same enumeration again, scattering packed image ids into
+//             their bins in a fixed order (stable counting sort).
+//   accum(c)  one CTA per (RIR, tile of 8 delay bins), one warp per bin: the
+//             warp evaluates the windowed sinc (eq. (6)) of every image of its
+//             bin into a register window and the CTA sums the windows of
+//             neighbouring bins in shared memory and stores the tile (eq. (5)).
+//   finalize  per RIR: adds the partial sums at tile seams; fits the envelope
+//             amplitude of the diffuse tail (Section 2.2).
+//   tail(d)   Philox4x32-10 logistic noise times the envelope of eq. (8).
+//
+// No floating-point atomic is used anywhere: every sum has a fixed order, so
+// the output is bit-identical from run to run.
+#pragma once
+
+#include <cstddef>
+#include <cstdint>
+
+#include "../../include/ism.h"
+
+#define ISM_SB 32                 // samples per delay bin (one warp-width)
+#define ISM_TILE_SB 8             // delay bins per accumulation CTA (= its warps)
+#define ISM_ENUM_WARPS 4          // warps per enumeration CTA (one unit each)
+#define ISM_MAX_JOBS 32           // jobs per launch set (kernel-parameter table)
+#define ISM_MAX_AXIS 1023         // images per axis (10-bit packed ids)
+#define ISM_MAX_SLOTS 8           // taps per lane per image: N_w <= 256
+#define ISM_MAX_NISM 131000       // image-source samples per RIR
+#define ISM_SCAN_BLOCK 4096       // elements per scan block
+#define ISM_SCAN_TOP 16384        // max scan blocks (one top-level block)
+#define ISM_FIT_WINDOW_S 0.02     // envelope fit: last 20 ms of the ISM part
+
+// Device-side description of one job.  Everything the kernels need is here
+// so that a whole launch set takes its jobs as one kernel parameter.
+struct JobDev {
+    double L[3];
+    float beta[6];
+    float c, fs, Nw;          // Nw = Tw * fs taps (real)
+    float kfs_hi, kfs_lo;     // fs / c as a float-float pair
+    float amp_scale;          // (fs / c) / (4 pi): A = F / (4 pi d) = F * amp_scale / s
+    float s_cut2;             // cull: keep an image iff s_plain^2 < s_cut2 (samples^2)
+    float g2;                 // log2 of the power decay per sample: 6 log2(10) / (fs T60)
+    int N[3], nlo[3];         // images per axis, lowest index per axis
+    uint32_t divNz_m, divNy_m;  // magic multipliers for id -> (ix, iy, iz)
+    int divNz_l, divNy_l;
+    int n_src, n_rcv, n_rir;
+    int n_S, n_ism;
+    int H;                    // ceil(Nw / 2): taps j in [-H + 1, H]
+    int slots;                // ceil(2H / 32) taps per lane per image
+    int Q;                    // delay bins per RIR
+    int U;                    // enumeration units per RIR
+    int unit_size;            // images per enumeration unit (power of two)
+    int n_tiles;              // accumulation tiles per RIR
+    int has_tail;
+    int W_env;                // samples of the envelope fit window
+    int vec4;                 // out rows 16-byte aligned (float4 stores allowed)
+    uint64_t seed;
+    const float* pos_src;
+    const float* pos_rcv;
+    float* out;
+    float* env_amp;
+    long long img_per_rir;    // N[0] N[1] N[2]
+    long long rir_base;       // global RIR index of the job's first RIR
+    long long hist_base;      // first counter of the job in the histogram
+    long long tbl_base;       // first table entry (float4) of the job
+    long long enum_cta_base;  // first enumeration CTA of the job
+    long long acc_cta_base;   // first accumulation CTA of the job
+    long long tail_cta_base;  // first tail CTA of the job
+    long long seam_base;      // first seam record (tiles) of the job
+};
+
+struct JobTable {
+    int n_jobs;
+    int max_Q;
+    int max_axis_sum;
+    int pad;
+    JobDev j[ISM_MAX_JOBS];
+};
+
+// Workspace carve-up of one launch set (byte offsets into the workspace).
+struct WsPlan {
+    size_t status_off;     // uint32 flags (first 256 bytes)
+    size_t hist_off;       // uint32 [hist_total + 1]
+    size_t part_off;       // uint32 [n_scan_blocks + 1]
+    size_t ids_off;        // uint32 [ids_total]
+    size_t tbl_off;        // float4 [tbl_total]
+    size_t seam_off;       // float  [seam_total]
+    size_t amp_off;        // float  [rir_total]
+    size_t total;
+    long long hist_total;
+    long long ids_total;
+    long long tbl_total;
+    long long seam_total;
+    long long rir_total;
+    long long n_scan_blocks;
+    long long enum_ctas;
+    long long acc_ctas;
+    long long tail_ctas;
+};
+
+#define ISM_TAIL_CHUNK 4096   // tail samples per CTA (256 threads x 16)
+
+// Launch entry points (implemented in the .cu files, called by ism_api.cu).
+// Each returns 0 or a cudaError_t value.
+int ism_launch_geometry(const JobTable& t, const WsPlan& p, char* ws, void* stream);
+int ism_launch_enum(const JobTable& t, const WsPlan& p, char* ws, bool scatter, void* stream);
+int ism_launch_scan(const WsPlan& p, char* ws, void* stream);
+int ism_launch_accum(const JobTable& t, const WsPlan& p, char* ws, ism_precision prec, void* stream,
+                     int* launched);
+int ism_launch_finalize(const JobTable& t, const WsPlan& p, char* ws, void* stream);
+int ism_launch_tail(const JobTable& t, const WsPlan& p, char* ws, void* stream);
+int ism_launch_noise(uint64_t seed, uint32_t rir, uint32_t k0, int n, float* z, void* stream);
+int ism_launch_beta_sabine(const double* L, const double* T60, const double* w, int negative, int n,
+                           double* beta_out, int* status, void* stream);

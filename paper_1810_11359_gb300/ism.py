@@ -1,0 +1,364 @@
+"""Thin Python binding of libism (include/ism.h).
+
+Argument marshalling only: every step of the simulation runs in the CUDA
+kernels of libism.so.  PyTorch provides device memory and the current CUDA
+stream.  The functions carry the names of the C entry points.  There is no
+CPU fallback: if the library has not been built, or no GPU is present, calls
+raise.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+from typing import Optional, Sequence
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libism.so")
+
+ISM_OK = 0
+STATUS_NAMES = {0: "ISM_OK", 1: "ISM_ERR_INVALID_ARG", 2: "ISM_ERR_INFEASIBLE", 3: "ISM_ERR_WORKSPACE_TOO_SMALL",
+                4: "ISM_ERR_OOM", 5: "ISM_ERR_CUDA", 6: "ISM_ERR_TIMEOUT", 7: "ISM_ERR_DEVICE_CHECK",
+                8: "ISM_ERR_UNSUPPORTED", 9: "ISM_ERR_CANCELLED"}
+PRECISIONS = {"fp32": 0, "fp16x2": 1, "bf16x2": 2, "lut": 3}
+DEVICE_FLAG_POSITION = 1
+DEVICE_FLAG_BIN = 2
+
+
+class IsmError(RuntimeError):
+    def __init__(self, status: int, message: str):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {message}")
+        self.status = status
+
+
+class ism_room(ctypes.Structure):
+    _fields_ = [("L", ctypes.c_double * 3), ("beta", ctypes.c_float * 6), ("c", ctypes.c_float)]
+
+
+class ism_job(ctypes.Structure):
+    _fields_ = [("room", ism_room),
+                ("pos_src", ctypes.c_void_p), ("n_src", ctypes.c_int),
+                ("pos_rcv", ctypes.c_void_p), ("n_rcv", ctypes.c_int),
+                ("nb_img", ctypes.c_int * 3),
+                ("Tmax", ctypes.c_float), ("fs", ctypes.c_float), ("Tdiff", ctypes.c_float), ("Tw", ctypes.c_float),
+                ("seed", ctypes.c_uint64),
+                ("out", ctypes.c_void_p), ("env_amp", ctypes.c_void_p)]
+
+
+# Every symbol include/ism.h declares, with its ctypes signature.
+_P = ctypes.POINTER
+_SIGS = {
+    "ism_status_string": (ctypes.c_char_p, [ctypes.c_int]),
+    "ism_last_error_message": (ctypes.c_char_p, []),
+    "ism_version": (ctypes.c_int, []),
+    "ism_rir_length": (ctypes.c_int, [ctypes.c_float, ctypes.c_float, _P(ctypes.c_int)]),
+    "ism_workspace_size": (ctypes.c_int, [_P(ism_room), ctypes.c_int, ctypes.c_int, _P(ctypes.c_int), ctypes.c_float,
+                                          ctypes.c_float, ctypes.c_float, ctypes.c_float, ctypes.c_int,
+                                          _P(ctypes.c_size_t)]),
+    "ism_host_workspace_size": (ctypes.c_int, [_P(ism_room), ctypes.c_int, ctypes.c_int, _P(ctypes.c_int),
+                                               ctypes.c_float, ctypes.c_float, ctypes.c_float, ctypes.c_float,
+                                               ctypes.c_int, _P(ctypes.c_size_t)]),
+    "ism_simulate": (ctypes.c_int, [_P(ism_room), ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_int,
+                                    _P(ctypes.c_int), ctypes.c_float, ctypes.c_float, ctypes.c_float, ctypes.c_float,
+                                    ctypes.c_int, ctypes.c_uint64, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t,
+                                    ctypes.c_void_p]),
+    "ism_simulate_host": (ctypes.c_int, [_P(ism_room), ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_int,
+                                         _P(ctypes.c_int), ctypes.c_float, ctypes.c_float, ctypes.c_float,
+                                         ctypes.c_float, ctypes.c_int, ctypes.c_uint64, ctypes.c_void_p,
+                                         ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p]),
+    "ism_workspace_status": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, _P(ctypes.c_uint32)]),
+    "ism_batch_workspace_size": (ctypes.c_int, [_P(ism_job), ctypes.c_int, ctypes.c_int, _P(ctypes.c_size_t)]),
+    "ism_simulate_batch": (ctypes.c_int, [_P(ism_job), ctypes.c_int, ctypes.c_int, ctypes.c_void_p, ctypes.c_size_t,
+                                          ctypes.c_void_p]),
+    "ism_diffuse_noise": (ctypes.c_int, [ctypes.c_uint64, ctypes.c_uint32, ctypes.c_uint32, ctypes.c_int,
+                                         ctypes.c_void_p, ctypes.c_void_p]),
+    "ism_t60_sabine": (ctypes.c_int, [_P(ctypes.c_double), _P(ctypes.c_double), _P(ctypes.c_double)]),
+    "ism_beta_sabine": (ctypes.c_int, [_P(ctypes.c_double), ctypes.c_double, _P(ctypes.c_double), ctypes.c_int,
+                                       _P(ctypes.c_double)]),
+    "ism_beta_sabine_device": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int,
+                                              ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
+    "ism_nb_img_from_t": (ctypes.c_int, [ctypes.c_double, _P(ctypes.c_double), ctypes.c_double, ctypes.c_double,
+                                         _P(ctypes.c_int)]),
+    "ism_att2t_sabine": (ctypes.c_int, [ctypes.c_double, ctypes.c_double, _P(ctypes.c_double)]),
+    "ism_profile_enable": (ctypes.c_int, [ctypes.c_int]),
+    "ism_profile_reset": (ctypes.c_int, []),
+    "ism_profile_read": (ctypes.c_int, [ctypes.c_int, _P(ctypes.c_double), _P(ctypes.c_longlong),
+                                        _P(ctypes.c_longlong)]),
+}
+
+STAGES = ["geometry", "enum_count", "scan", "enum_scatter", "accum", "finalize", "tail"]
+
+_lock = threading.Lock()
+_lib = None
+
+
+def load(path: Optional[str] = None):
+    """Load libism.so (raises if it has not been built: there is no fallback)."""
+    global _lib
+    with _lock:
+        if _lib is not None and path is None:
+            return _lib
+        p = path or LIB_PATH
+        if not os.path.exists(p):
+            raise RuntimeError(f"libism.so not found at {p}: run __graft_entry__.build() "
+                               "(python -c 'import __graft_entry__ as g; g.build()')")
+        lib = ctypes.CDLL(p)
+        for name, (res, args) in _SIGS.items():
+            fn = getattr(lib, name)
+            fn.restype = res
+            fn.argtypes = args
+        if path is None:
+            _lib = lib
+        return lib
+
+
+def _check(status: int):
+    if status != ISM_OK:
+        msg = load().ism_last_error_message().decode(errors="replace")
+        raise IsmError(status, msg)
+
+
+def _room(L, beta, c):
+    r = ism_room()
+    for a in range(3):
+        r.L[a] = float(L[a])
+    for w in range(6):
+        r.beta[w] = float(beta[w])
+    r.c = float(c)
+    return r
+
+
+def _nb(nb_img):
+    return (ctypes.c_int * 3)(*[int(v) for v in nb_img])
+
+
+def _torch():
+    import torch
+    return torch
+
+
+def _stream_ptr(stream=None):
+    torch = _torch()
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+# --------------------------------------------------------------------------- #
+# Helpers of Section 4 (host FP64)
+# --------------------------------------------------------------------------- #
+def ism_rir_length(T: float, fs: float) -> int:
+    n = ctypes.c_int()
+    _check(load().ism_rir_length(float(T), float(fs), ctypes.byref(n)))
+    return n.value
+
+
+def ism_t60_sabine(L, beta) -> float:
+    Ld = (ctypes.c_double * 3)(*map(float, L))
+    bd = (ctypes.c_double * 6)(*map(float, beta))
+    t = ctypes.c_double()
+    _check(load().ism_t60_sabine(Ld, bd, ctypes.byref(t)))
+    return t.value
+
+
+def ism_beta_sabine(L, T60: float, abs_weights=None, negative: bool = False) -> np.ndarray:
+    Ld = (ctypes.c_double * 3)(*map(float, L))
+    w = None if abs_weights is None else (ctypes.c_double * 6)(*map(float, abs_weights))
+    out = (ctypes.c_double * 6)()
+    _check(load().ism_beta_sabine(Ld, float(T60), w, int(bool(negative)), out))
+    return np.array(list(out))
+
+
+def ism_beta_sabine_device(L, T60, abs_weights=None, negative: bool = False):
+    """Batched inverse Sabine in FP64 on the GPU: L [n,3], T60 [n] (CUDA float64
+    tensors) -> (beta [n,6] float64, status [n] int32)."""
+    torch = _torch()
+    L = L.contiguous()
+    T60 = T60.contiguous()
+    n = T60.shape[0]
+    beta = torch.empty((n, 6), dtype=torch.float64, device=L.device)
+    st = torch.empty((n,), dtype=torch.int32, device=L.device)
+    w = None if abs_weights is None else abs_weights.contiguous()
+    _check(load().ism_beta_sabine_device(ctypes.c_void_p(L.data_ptr()), ctypes.c_void_p(T60.data_ptr()),
+                                         None if w is None else ctypes.c_void_p(w.data_ptr()), int(bool(negative)),
+                                         int(n), ctypes.c_void_p(beta.data_ptr()), ctypes.c_void_p(st.data_ptr()),
+                                         _stream_ptr()))
+    return beta, st
+
+
+def ism_nb_img_from_t(T: float, L, c: float = 343.0, Tw: float = 4e-3) -> np.ndarray:
+    Ld = (ctypes.c_double * 3)(*map(float, L))
+    out = (ctypes.c_int * 3)()
+    _check(load().ism_nb_img_from_t(float(T), Ld, float(c), float(Tw), out))
+    return np.array(list(out), dtype=np.int32)
+
+
+def ism_att2t_sabine(att_dB: float, T60: float) -> float:
+    t = ctypes.c_double()
+    _check(load().ism_att2t_sabine(float(att_dB), float(T60), ctypes.byref(t)))
+    return t.value
+
+
+# --------------------------------------------------------------------------- #
+# Simulation
+# --------------------------------------------------------------------------- #
+def ism_workspace_size(L, beta, n_src, n_rcv, nb_img, Tmax, fs, Tdiff=0.0, Tw=0.0, c=343.0,
+                       prec: str = "fp32") -> int:
+    b = ctypes.c_size_t()
+    r = _room(L, beta, c)
+    _check(load().ism_workspace_size(ctypes.byref(r), int(n_src), int(n_rcv), _nb(nb_img), float(Tmax), float(fs),
+                                     float(Tdiff or 0.0), float(Tw or 0.0), PRECISIONS[prec], ctypes.byref(b)))
+    return b.value
+
+
+def ism_host_workspace_size(L, beta, n_src, n_rcv, nb_img, Tmax, fs, Tdiff=0.0, Tw=0.0, c=343.0,
+                            prec: str = "fp32") -> int:
+    b = ctypes.c_size_t()
+    r = _room(L, beta, c)
+    _check(load().ism_host_workspace_size(ctypes.byref(r), int(n_src), int(n_rcv), _nb(nb_img), float(Tmax),
+                                          float(fs), float(Tdiff or 0.0), float(Tw or 0.0), PRECISIONS[prec],
+                                          ctypes.byref(b)))
+    return b.value
+
+
+class Workspace:
+    """Device scratch memory for the library (a uint8 CUDA tensor), grown on demand."""
+
+    def __init__(self, device=None):
+        self.device = device
+        self.buf = None
+
+    def get(self, nbytes: int):
+        torch = _torch()
+        if self.buf is None or self.buf.numel() < nbytes:
+            dev = self.device if self.device is not None else torch.device("cuda", torch.cuda.current_device())
+            self.buf = torch.empty(max(int(nbytes), 256), dtype=torch.uint8, device=dev)
+        return self.buf
+
+
+_default_ws = {}
+
+
+def _workspace(ws, nbytes):
+    torch = _torch()
+    if ws is None:
+        dev = torch.cuda.current_device()
+        ws = _default_ws.setdefault(dev, Workspace())
+    return ws.get(nbytes)
+
+
+def ism_simulate(L, beta, pos_src, pos_rcv, nb_img, Tmax, fs, Tdiff=0.0, Tw=0.0, c=343.0, prec: str = "fp32",
+                 seed: int = 0, out=None, workspace: Optional[Workspace] = None, stream=None):
+    """RIRs [n_src, n_rcv, n_S] (FP32 CUDA tensor) for all source/receiver pairs.
+
+    pos_src/pos_rcv: [n,3] positions (CUDA FP32 tensors, or anything
+    convertible; copied to the device if needed)."""
+    torch = _torch()
+    dev = torch.device("cuda", torch.cuda.current_device())
+    ps = torch.as_tensor(pos_src, dtype=torch.float32).to(dev).reshape(-1, 3).contiguous()
+    pr = torch.as_tensor(pos_rcv, dtype=torch.float32).to(dev).reshape(-1, 3).contiguous()
+    n_S = ism_rir_length(Tmax, fs)
+    if out is None:
+        out = torch.empty((ps.shape[0], pr.shape[0], n_S), dtype=torch.float32, device=dev)
+    nbytes = ism_workspace_size(L, beta, ps.shape[0], pr.shape[0], nb_img, Tmax, fs, Tdiff, Tw, c, prec)
+    buf = _workspace(workspace, nbytes)
+    r = _room(L, beta, c)
+    _check(load().ism_simulate(ctypes.byref(r), ctypes.c_void_p(ps.data_ptr()), int(ps.shape[0]),
+                               ctypes.c_void_p(pr.data_ptr()), int(pr.shape[0]), _nb(nb_img), float(Tmax), float(fs),
+                               float(Tdiff or 0.0), float(Tw or 0.0), PRECISIONS[prec], int(seed) & (2 ** 64 - 1),
+                               ctypes.c_void_p(out.data_ptr()), ctypes.c_void_p(buf.data_ptr()),
+                               int(buf.numel()), _stream_ptr(stream)))
+    return out
+
+
+def ism_simulate_host(L, beta, pos_src, pos_rcv, nb_img, Tmax, fs, Tdiff=0.0, Tw=0.0, c=343.0, prec: str = "fp32",
+                      seed: int = 0, out: Optional[np.ndarray] = None, workspace: Optional[Workspace] = None,
+                      stream=None) -> np.ndarray:
+    """Same as ism_simulate from host (numpy) positions into a host array;
+    the copies happen inside the library call (synchronous)."""
+    ps = np.ascontiguousarray(np.asarray(pos_src, dtype=np.float32).reshape(-1, 3))
+    pr = np.ascontiguousarray(np.asarray(pos_rcv, dtype=np.float32).reshape(-1, 3))
+    n_S = ism_rir_length(Tmax, fs)
+    if out is None:
+        out = np.empty((ps.shape[0], pr.shape[0], n_S), dtype=np.float32)
+    nbytes = ism_host_workspace_size(L, beta, ps.shape[0], pr.shape[0], nb_img, Tmax, fs, Tdiff, Tw, c, prec)
+    buf = _workspace(workspace, nbytes)
+    r = _room(L, beta, c)
+    _check(load().ism_simulate_host(ctypes.byref(r), ctypes.c_void_p(ps.ctypes.data), int(ps.shape[0]),
+                                    ctypes.c_void_p(pr.ctypes.data), int(pr.shape[0]), _nb(nb_img), float(Tmax),
+                                    float(fs), float(Tdiff or 0.0), float(Tw or 0.0), PRECISIONS[prec],
+                                    int(seed) & (2 ** 64 - 1), ctypes.c_void_p(out.ctypes.data),
+                                    ctypes.c_void_p(buf.data_ptr()), int(buf.numel()), _stream_ptr(stream)))
+    return out
+
+
+def ism_workspace_status(buf, stream=None) -> int:
+    flags = ctypes.c_uint32()
+    _check(load().ism_workspace_status(ctypes.c_void_p(buf.data_ptr()), _stream_ptr(stream), ctypes.byref(flags)))
+    return flags.value
+
+
+def make_job(L, beta, pos_src, pos_rcv, nb_img, Tmax, fs, out, Tdiff=0.0, Tw=0.0, c=343.0, seed=0,
+             env_amp=None) -> ism_job:
+    """An ism_job over CUDA tensors (the tensors must stay alive during the call)."""
+    j = ism_job()
+    j.room = _room(L, beta, c)
+    j.pos_src = pos_src.data_ptr()
+    j.n_src = int(pos_src.shape[0])
+    j.pos_rcv = pos_rcv.data_ptr()
+    j.n_rcv = int(pos_rcv.shape[0])
+    for a in range(3):
+        j.nb_img[a] = int(nb_img[a])
+    j.Tmax, j.fs, j.Tdiff, j.Tw = float(Tmax), float(fs), float(Tdiff or 0.0), float(Tw or 0.0)
+    j.seed = int(seed) & (2 ** 64 - 1)
+    j.out = out.data_ptr()
+    j.env_amp = None if env_amp is None else env_amp.data_ptr()
+    return j
+
+
+def ism_batch_workspace_size(jobs: Sequence[ism_job], prec: str = "fp32") -> int:
+    arr = (ism_job * len(jobs))(*jobs)
+    b = ctypes.c_size_t()
+    _check(load().ism_batch_workspace_size(arr, len(jobs), PRECISIONS[prec], ctypes.byref(b)))
+    return b.value
+
+
+def ism_simulate_batch(jobs: Sequence[ism_job], prec: str = "fp32", workspace: Optional[Workspace] = None,
+                       stream=None):
+    arr = (ism_job * len(jobs))(*jobs)
+    b = ctypes.c_size_t()
+    _check(load().ism_batch_workspace_size(arr, len(jobs), PRECISIONS[prec], ctypes.byref(b)))
+    buf = _workspace(workspace, b.value)
+    _check(load().ism_simulate_batch(arr, len(jobs), PRECISIONS[prec], ctypes.c_void_p(buf.data_ptr()),
+                                     int(buf.numel()), _stream_ptr(stream)))
+    return buf
+
+
+def ism_diffuse_noise(seed: int, rir: int, k0: int, n: int, stream=None):
+    torch = _torch()
+    z = torch.empty(int(n), dtype=torch.float32, device=torch.device("cuda", torch.cuda.current_device()))
+    _check(load().ism_diffuse_noise(int(seed) & (2 ** 64 - 1), int(rir), int(k0), int(n), ctypes.c_void_p(z.data_ptr()),
+                                    _stream_ptr(stream)))
+    return z
+
+
+# --------------------------------------------------------------------------- #
+# Per-stage timing
+# --------------------------------------------------------------------------- #
+def ism_profile_enable(enable: bool = True):
+    _check(load().ism_profile_enable(int(bool(enable))))
+
+
+def ism_profile_reset():
+    _check(load().ism_profile_reset())
+
+
+def ism_profile_read():
+    """{stage: (total_ms, launches, calls)} accumulated since the last reset."""
+    res = {}
+    for i, name in enumerate(STAGES):
+        ms, ln, cl = ctypes.c_double(), ctypes.c_longlong(), ctypes.c_longlong()
+        _check(load().ism_profile_read(i, ctypes.byref(ms), ctypes.byref(ln), ctypes.byref(cl)))
+        res[name] = (ms.value, ln.value, cl.value)
+    return res

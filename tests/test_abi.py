@@ -1,0 +1,116 @@
+"""The C ABI: the library loads on a machine without a GPU, exports every
+symbol include/ism.h declares, and its host-only helpers (sizing, Sabine,
+image counts) agree with the oracle and reject bad arguments.  No device
+work is done here."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_1810_11359_gb300 import build as libbuild
+from paper_1810_11359_gb300 import ism
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    libbuild.build()
+    return ism.load()
+
+
+def _declared():
+    names = set()
+    for h in os.listdir(os.path.join(ROOT, "include")):
+        if h.endswith(".h"):
+            txt = open(os.path.join(ROOT, "include", h)).read()
+            txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+            names |= set(re.findall(r"\b(ism_[a-z0-9_]+)\s*\(", txt))
+    return names
+
+
+def test_every_declared_symbol_is_exported(lib):
+    declared = _declared()
+    assert len(declared) >= 15
+    for name in sorted(declared):
+        assert hasattr(lib, name), name
+        assert name in ism._SIGS, f"binding lacks {name}"
+
+
+def test_status_strings_and_version(lib):
+    assert lib.ism_version() == 100
+    for code, name in ism.STATUS_NAMES.items():
+        assert lib.ism_status_string(code).decode() == name
+
+
+def test_rir_length_rule():
+    assert ism.ism_rir_length(np.float32(0.3), 16000.0) == 4800 == oracle.n_samples(np.float32(0.3), 16000.0)
+    assert ism.ism_rir_length(np.float32(1.2), 48000.0) == 57600
+    assert ism.ism_rir_length(np.float32(0.6), 16000.0) == 9600
+    for T, fs in [(0.123457, 16000.0), (0.77, 44100.0), (1e-3, 8000.0)]:
+        assert ism.ism_rir_length(T, fs) == oracle.n_samples(np.float32(T), np.float32(fs))
+    with pytest.raises(ism.IsmError):
+        ism.ism_rir_length(0.0, 16000.0)
+
+
+def test_sabine_helpers_match_oracle():
+    for L, T in [([6, 5, 3], 0.6), ([10, 8, 3.5], 1.2), ([3, 4, 2.5], 0.7)]:
+        b = ism.ism_beta_sabine(L, T)
+        np.testing.assert_allclose(b, oracle.beta_sabine(L, T), rtol=1e-15)
+        assert ism.ism_t60_sabine(L, b) == pytest.approx(oracle.t60_sabine(L, b), rel=1e-15)
+        np.testing.assert_array_equal(ism.ism_beta_sabine(L, T, negative=True), -b)
+    w = [1, 1, 0.5, 0.5, 2, 2]
+    np.testing.assert_allclose(ism.ism_beta_sabine([6, 5, 3], 0.6, w), oracle.beta_sabine([6, 5, 3], 0.6, w), rtol=1e-15)
+    with pytest.raises(ism.IsmError) as e:
+        ism.ism_beta_sabine([3, 3, 3], 0.01)
+    assert e.value.status == 2
+
+
+def test_nb_img_and_att2t_match_oracle():
+    for T, L, Tw in [(0.6, [6, 5, 3], 32 / 16000), (0.3, [10, 8, 3.5], 32 / 48000), (0.4, [4.5, 7.1, 5.2], 4e-3)]:
+        assert list(ism.ism_nb_img_from_t(T, L, 343.0, Tw)) == list(oracle.nb_img_from_t(T, L, 343.0, Tw))
+    assert ism.ism_att2t_sabine(13.0, 0.6) == pytest.approx(oracle.att2t_sabine(13.0, 0.6))
+
+
+def test_workspace_size_and_validation(lib):
+    L, beta = [6.0, 5.0, 3.0], [0.9] * 6
+    n = ism.ism_workspace_size(L, beta, 4, 32, [73, 87, 141], 0.6, 16000.0, Tw=32 / 16000)
+    # at least the worst-case image-id buffer: 128 RIRs x 895,491 images x 4 B
+    assert n >= 128 * 73 * 87 * 141 * 4
+    assert n % 256 == 0
+    bad = [
+        dict(L=[0, 5, 3]),
+        dict(beta=[1.5] + [0.9] * 5),
+        dict(nb_img=[0, 3, 3]),
+        dict(fs=-1.0),
+        dict(Tmax=0.0),
+        dict(Tw=1.0 / 16000),           # one tap
+    ]
+    base = dict(L=L, beta=beta, n_src=1, n_rcv=1, nb_img=[5, 5, 5], Tmax=0.1, fs=16000.0, Tw=32 / 16000)
+    for b in bad:
+        kw = dict(base, **b)
+        with pytest.raises(ism.IsmError) as e:
+            ism.ism_workspace_size(**kw)
+        assert e.value.status == 1, b
+    with pytest.raises(ism.IsmError) as e:
+        ism.ism_workspace_size(**dict(base, nb_img=[2000, 3, 3]))
+    assert e.value.status == 8
+    with pytest.raises(ism.IsmError) as e:
+        ism.ism_workspace_size(**dict(base, Tw=300 / 16000))
+    assert e.value.status == 8
+    assert lib.ism_last_error_message().decode() != ""
+
+
+def test_host_entry_rejects_outside_positions_without_device_work(lib):
+    r = ism._room([3, 4, 2.5], [0.7] * 6, 343.0)
+    ps = np.array([[1.0, 1.5, 3.0]], np.float32)  # z above the ceiling
+    pr = np.array([[2.0, 2.5, 1.5]], np.float32)
+    out = np.zeros(4800, np.float32)
+    st = lib.ism_simulate_host(ctypes.byref(r), ctypes.c_void_p(ps.ctypes.data), 1, ctypes.c_void_p(pr.ctypes.data), 1,
+                               ism._nb([5, 5, 5]), 0.3, 16000.0, 0.0, 0.0, 0, 0, ctypes.c_void_p(out.ctypes.data),
+                               None, 0, None)
+    assert st == 1
+    assert "outside" in lib.ism_last_error_message().decode()
