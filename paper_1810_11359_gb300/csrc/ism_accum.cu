@@ -99,10 +99,12 @@ __global__ void __launch_bounds__(ISM_TILE_SB * 32) accum_kernel(const __grid_co
                 ff s = ff_sqrt(s2);
                 float b = floorf(s.hi);
                 float f = __fadd_rn(__fsub_rn(s.hi, b), s.lo);
+                // bring f into [0, 1); -tiny + 1 rounds to 1.0, hence two steps
                 if (f < 0.0f) {
                     f = __fadd_rn(f, 1.0f);
                     b -= 1.0f;
-                } else if (f >= 1.0f) {
+                }
+                if (f >= 1.0f) {
                     f = __fsub_rn(f, 1.0f);
                     b += 1.0f;
                 }
