@@ -231,13 +231,13 @@ ism_status ism_att2t_sabine(double att_dB, double T60, double* t);
 /* ------------------------------------------------------------------------- */
 /* Stages of one simulation, in launch order. */
 typedef enum {
-    ISM_STAGE_GEOMETRY = 0,   /* per-RIR axis tables, position checks            */
-    ISM_STAGE_ENUM_COUNT = 1, /* image enumeration, delays, bin counts (a)       */
-    ISM_STAGE_SCAN = 2,       /* prefix sum of the bin counts (b)                */
-    ISM_STAGE_ENUM_SCATTER = 3, /* image enumeration, scatter into bins (a)      */
-    ISM_STAGE_ACCUM = 4,      /* windowed-sinc accumulation, eq. (5)-(6) (c)     */
-    ISM_STAGE_FINALIZE = 5,   /* tile seams and envelope fit                     */
-    ISM_STAGE_TAIL = 6,       /* diffuse tail, eq. (8) (d)                       */
+    ISM_STAGE_GEOMETRY = 0,     /* per-RIR axis tables, position checks          */
+    ISM_STAGE_ENUM_COUNT = 1,   /* image enumeration, delays, bin counts (a)     */
+    ISM_STAGE_SCAN = 2,         /* prefix sum of the bin counts (b)              */
+    ISM_STAGE_ENUM_SCATTER = 3, /* image enumeration, scatter into bins (a, b)   */
+    ISM_STAGE_ACCUM = 4,        /* windowed-sinc accumulation, eq. (5)-(6) (c)   */
+    ISM_STAGE_FINALIZE = 5,     /* tile seams and envelope fit                   */
+    ISM_STAGE_TAIL = 6,         /* diffuse tail, eq. (8) (d)                     */
     ISM_N_STAGES = 7
 } ism_stage;
 

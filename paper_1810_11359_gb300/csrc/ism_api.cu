@@ -40,15 +40,6 @@ int rir_len(double T, double fs) { return (int)std::ceil(T * fs * (1.0 - 1e-6));
 
 bool isfin(double x) { return std::isfinite(x); }
 
-void magic_div(uint32_t d, uint32_t* m, int* l)
-{
-    int ll = 0;
-    while ((1ull << ll) < d) ++ll;
-    unsigned long long mm = ((1ull << 32) * ((1ull << ll) - d)) / d + 1ull;
-    *m = (uint32_t)mm;
-    *l = ll;
-}
-
 double t60_of(const double L[3], const double beta[6])
 {
     double S[6] = {L[1] * L[2], L[1] * L[2], L[0] * L[2], L[0] * L[2], L[0] * L[1], L[0] * L[1]};
@@ -110,6 +101,8 @@ ism_status validate_job(const ism_job& in, Validated& v, bool need_ptrs)
     if (v.n_ism > ISM_MAX_NISM)
         return fail(ISM_ERR_UNSUPPORTED, "%d image-source samples exceed %d", v.n_ism, ISM_MAX_NISM);
     v.H = (int)std::ceil(0.5 * v.Nw - 1e-9);
+    if ((v.n_ism + v.H) / ISM_SB + 1 > ISM_MAX_Q)
+        return fail(ISM_ERR_UNSUPPORTED, "%d image-source samples exceed the bin limit", v.n_ism);
     v.slots = (2 * v.H + 31) / 32;
     return ISM_OK;
 }
@@ -147,15 +140,20 @@ ism_status plan(const Validated* vs, int n, JobTable& t, WsPlan& p)
         J.slots = v.slots;
         J.Q = (v.n_ism + v.H) / ISM_SB + 1;
         J.img_per_rir = (long long)in.nb_img[0] * in.nb_img[1] * in.nb_img[2];
-        int us = 8192;
-        while (us > 256 && (long long)J.n_rir * ((J.img_per_rir + us - 1) / us) < 8192) us >>= 1;
-        J.unit_size = us;
-        J.U = (int)((J.img_per_rir + us - 1) / us);
-        J.n_tiles = (J.Q + ISM_TILE_SB - 1) / ISM_TILE_SB;
+        // enumeration units: contiguous column ranges, about 16k warps over the
+        // job (enough to hide the latency of the walk), at most 512 columns each
+        {
+            const long long cols = (long long)in.nb_img[0] * in.nb_img[1];
+            long long cpu = (cols * J.n_rir + 16383) / 16384;
+            if (cpu < 1) cpu = 1;
+            if (cpu > 512) cpu = 512;
+            J.cols_per_unit = (int)cpu;
+            J.U = (int)((cols + cpu - 1) / cpu);
+        }
+        J.inv_kLz = (float)(1.0 / (k * in.room.L[2]));
+        J.n_tiles = (J.Q + ISM_TILE_BINS - 1) / ISM_TILE_BINS;
         double s_cut = (double)v.n_ism - 1.0 + (double)v.H + 0.5;
         J.s_cut2 = (float)(s_cut * s_cut);
-        magic_div((uint32_t)in.nb_img[2], &J.divNz_m, &J.divNz_l);
-        magic_div((uint32_t)in.nb_img[1], &J.divNy_m, &J.divNy_l);
         J.has_tail = v.n_ism < v.n_S;
         double beta_d[6];
         for (int w = 0; w < 6; ++w) beta_d[w] = in.room.beta[w];
@@ -201,11 +199,11 @@ ism_status plan(const Validated* vs, int n, JobTable& t, WsPlan& p)
         return fail(ISM_ERR_UNSUPPORTED, "launch set too large; split the batch");
     p.hist_total = hist;
     p.ids_total = ids;
+    p.n_scan_blocks = (hist + ISM_SCAN_BLOCK - 1) / ISM_SCAN_BLOCK;
+    if (p.n_scan_blocks < 1) p.n_scan_blocks = 1;
     p.tbl_total = tbl;
     p.seam_total = seam;
     p.rir_total = rir;
-    p.n_scan_blocks = (hist + ISM_SCAN_BLOCK - 1) / ISM_SCAN_BLOCK;
-    if (p.n_scan_blocks < 1) p.n_scan_blocks = 1;
     p.enum_ctas = ecta;
     p.acc_ctas = acta;
     p.tail_ctas = tcta;

@@ -39,33 +39,85 @@ __device__ __forceinline__ ff ff_add(ff a, ff b)
     return {hi, lo};
 }
 
-// sqrt of a positive float-float; the result's lo is the first-order
-// correction (S - r^2) / (2 r) of the correctly rounded FP32 root r.
-__device__ __forceinline__ ff ff_sqrt(ff a)
-{
-    float r = __fsqrt_rn(a.hi);
-    float res = __fadd_rn(__fmaf_rn(-r, r, a.hi), a.lo);
-    float lo = __fmul_rn(res, __fdividef(0.5f, r));
-    return {r, lo};
-}
-
-// ---------------------------------------------------------------------------
-// Division by a run-time constant d >= 1 for 32-bit x (Granlund and
-// Montgomery, "Division by invariant integers using multiplication", 1994):
-// q = (umulhi(x, m) + x) >> l with l = ceil(log2 d), m = 2^32 (2^l - d) / d + 1.
-// ---------------------------------------------------------------------------
-__device__ __forceinline__ uint32_t ism_udiv(uint32_t x, uint32_t m, int l)
-{
-    unsigned long long t = (unsigned long long)__umulhi(x, m) + (unsigned long long)x;
-    return (uint32_t)(t >> l);
-}
-
-// Approximate reciprocal on the special-function unit (max error ~1 ulp).
+// Approximate reciprocal and reciprocal square root on the special-function
+// unit (max error ~1-2 ulp).
 __device__ __forceinline__ float ism_rcp(float x)
 {
     float r;
     asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
     return r;
+}
+
+__device__ __forceinline__ float ism_rsqrt(float x)
+{
+    float r;
+    asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+
+// sqrt of a positive float-float: r = a.hi / sqrt(a.hi) from the approximate
+// reciprocal root, then one Newton correction from the exact residual
+// a - r^2 (FMA) of the full float-float value: lo = (a - r^2) / (2 r).  The
+// pair r + lo is accurate to ~2^-44 relative although r itself is not
+// correctly rounded.
+__device__ __forceinline__ ff ff_sqrt(ff a)
+{
+    float rs = ism_rsqrt(a.hi);
+    float r = __fmul_rn(a.hi, rs);
+    float res = __fadd_rn(__fmaf_rn(-r, r, a.hi), a.lo);
+    float lo = __fmul_rn(__fmul_rn(res, 0.5f), rs);
+    return {r, lo};
+}
+
+// Integer value of a float that holds an integer in [-2^22, 2^22): adding
+// 1.5 * 2^23 moves it to the low mantissa bits (no rounding happens, the
+// value being integral), avoiding a conversion instruction.
+__device__ __forceinline__ int ism_int_of_integral(float b)
+{
+    return __float_as_int(__fadd_rn(b, 12582912.0f)) - 0x4B400000;
+}
+
+// Nearest integer of x for |x| < 2^22 (ties to even), same trick.
+__device__ __forceinline__ int ism_round_int(float x)
+{
+    return __float_as_int(__fadd_rn(x, 12582912.0f)) - 0x4B400000;
+}
+
+// sin(pi f) for f in [0, 1]: g = min(f, 1 - f) in [0, 1/2] (1 - f is exact
+// for f >= 1/2) and the Taylor series of sin(pi g) through (pi g)^11, whose
+// remainder is below (pi/2)^13 / 13! = 5.7e-8 on [0, 1/2].
+__device__ __forceinline__ float ism_sinpi01(float f)
+{
+    const double PI = 3.141592653589793238462643383279502884;
+    const float c1 = (float)PI;
+    const float c3 = (float)(-PI * PI * PI / 6.0);
+    const float c5 = (float)(PI * PI * PI * PI * PI / 120.0);
+    const float c7 = (float)(-PI * PI * PI * PI * PI * PI * PI / 5040.0);
+    const float c9 = (float)(PI * PI * PI * PI * PI * PI * PI * PI * PI / 362880.0);
+    const float c11 = (float)(-PI * PI * PI * PI * PI * PI * PI * PI * PI * PI * PI / 39916800.0);
+    float g = fminf(f, __fsub_rn(1.0f, f));
+    float g2 = g * g;
+    float p = fmaf(g2, c11, c9);
+    p = fmaf(g2, p, c7);
+    p = fmaf(g2, p, c5);
+    p = fmaf(g2, p, c3);
+    p = fmaf(g2, p, c1);
+    return p * g;
+}
+
+// cos(a), sin(a) for |a| <= pi/8 by their Taylor series through a^8 and a^9
+// (remainders below a^10/10! = 2.5e-11 and a^11/11! = 7e-13).
+__device__ __forceinline__ void ism_sincos_small(float a, float* s, float* c)
+{
+    float a2 = a * a;
+    float pc = fmaf(a2, 1.0f / 40320.0f, -1.0f / 720.0f);
+    pc = fmaf(a2, pc, 1.0f / 24.0f);
+    pc = fmaf(a2, pc, -0.5f);
+    *c = fmaf(a2, pc, 1.0f);
+    float ps = fmaf(a2, 1.0f / 362880.0f, -1.0f / 5040.0f);
+    ps = fmaf(a2, ps, 1.0f / 120.0f);
+    ps = fmaf(a2, ps, -1.0f / 6.0f);
+    *s = fmaf(a2 * a, ps, a);
 }
 
 // ---------------------------------------------------------------------------

@@ -1,22 +1,28 @@
-// ism_enum.cu -- image enumeration (kernel a) and the counting sort of images
-// into delay bins (kernel b).
+// ism_enum.cu -- image enumeration (kernel a) and the counting sort of the
+// images into 32-sample delay bins (kernel b).
 //
-// Kernel (a) walks the whole image grid of every RIR (Section 2.1).  For
-// image (nx, ny, nz) the squared delay in samples is Sx + Sy + Sz (tables of
-// ism_geometry.cu; eq. (2)-(3) with s = d f_s / c); the image is kept when
-// its window (eq. (6), |t - tau| < Tw/2) can reach a sample below n_ism, and
-// its delay bin is q = floor((s + 1/2) / 32).  The delay here is plain FP32:
-// it only chooses the bin.  The accumulation kernel recomputes the delay in
-// float-float and places the image within a window that tolerates the bin
-// being off by the FP32 error (it accepts offsets -1..31 inside a bin).
+// Kernel (a) walks the image grid of every RIR (Section 2.1) column by
+// column: one warp owns a contiguous range of columns (ix, iy) and, for each,
+// only the nz range that can hold an image within reach (|n| - 1) L_z <=
+// c (Tmax + Tw/2), the bound that also fixes the grid size.  For image
+// (nx, ny, nz) the squared delay in samples is Sx + Sy + Sz (tables of
+// ism_geometry.cu, eq. (2)-(3) with s = d f_s / c); the image is kept when its
+// window (eq. (6), |t - tau| < Tw/2) can reach a sample below n_ism, and its
+// delay bin is q ~ floor((s + 1/2) / 32).  The delay here is plain FP32: it
+// only chooses the bin.  The accumulation kernel recomputes the delay in
+// float-float and tolerates the bin being off by the FP32 error (it accepts
+// offsets -1..31 inside a bin).
 //
-// Determinism: each warp owns a fixed slice ("unit") of the grid and walks
-// it in order, 32 images at a time.  Images of one 32-wide step that fall in
-// the same bin are ranked by lane (match.any + popc), so the position of an
-// image inside its bin is a pure function of the inputs:
-//   pass 1 (count):   per-unit per-bin counts -> hist[rir][bin][unit]
-//   scan (b):         exclusive prefix over hist (bin-major, unit-minor)
-//   pass 2 (scatter): same walk, ids[hist[rir][bin][unit] + rank] = image id
+// Kernel (b) is a stable counting sort over (RIR, bin) keys:
+//   count:   each warp walks its columns and counts its kept images per bin
+//            (shared-memory integer adds) -> hist[rir][bin][unit]
+//   scan:    exclusive prefix over hist (bin-major, unit-minor)
+//   scatter: the same walk again; each image id goes to hist[rir][bin][unit]
+//            + rank, the rank of images of one 32-wide step sharing a bin
+//            being their lane order (match.any + popc).
+// Every position is a pure function of the inputs, so the order of images
+// inside a bin -- hence the FP32 summation order later -- is the same on
+// every run, and each bin is one contiguous range of ids.
 #include "ism_device.cuh"
 
 namespace {
@@ -40,70 +46,83 @@ __global__ void __launch_bounds__(ISM_ENUM_WARPS * 32) enum_kernel(const __grid_
     const int n_axis = Nx + Ny + Nz;
     const int Q = J.Q;
 
-    float* S = reinterpret_cast<float*>(smem);                         // [n_axis] plain FP32 s^2
-    uint32_t* cnt = reinterpret_cast<uint32_t*>(smem) + ((t.max_axis_sum + 3) & ~3);  // [warps][max_Q]
+    float* S = reinterpret_cast<float*>(smem);  // [n_axis] plain FP32 squared offsets
+    uint32_t* cnt_all = reinterpret_cast<uint32_t*>(smem + (size_t)((t.max_axis_sum + 3) & ~3) * 4);
 
     const float4* T = tbl + J.tbl_base + (long long)r * n_axis;
-    for (int e = threadIdx.x; e < n_axis; e += blockDim.x) {
-        float4 v = T[e];
-        S[e] = v.x;
-    }
+    for (int e = threadIdx.x; e < n_axis; e += blockDim.x) S[e] = T[e].x;
+
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int unit = c * ISM_ENUM_WARPS + warp;
     const bool active = unit < J.U;
-    uint32_t* my = cnt + warp * t.max_Q;
+    uint32_t* cnt = cnt_all + (size_t)warp * t.max_Q;
     const long long hrow = J.hist_base + (long long)r * Q * J.U;  // + q * U + unit
-    if (active) {
-        for (int q = lane; q < Q; q += 32)
-            my[q] = SCATTER ? hist[hrow + (long long)q * J.U + unit] : 0u;
-    }
+    if (active)
+        for (int q = lane; q < Q; q += 32) cnt[q] = SCATTER ? hist[hrow + (long long)q * J.U + unit] : 0u;
     __syncthreads();
     if (!active) return;
 
-    const uint32_t n_img = (uint32_t)J.img_per_rir;
-    const uint32_t begin = (uint32_t)unit * (uint32_t)J.unit_size;
-    uint32_t end = begin + (uint32_t)J.unit_size;
-    if (end > n_img) end = n_img;
+    const float* Sx = S;
     const float* Sy = S + Nx;
     const float* Sz = S + Nx + Ny;
     const float s_cut2 = J.s_cut2;
-    uint32_t* out_ids = ids;
+    const float inv_kLz = J.inv_kLz;       // 1 / (f_s / c * L_z): samples -> z cells
+    const int nlo_z = J.nlo[2];
+    const int col0 = unit * J.cols_per_unit;
+    int col1 = col0 + J.cols_per_unit;
+    if (col1 > Nx * Ny) col1 = Nx * Ny;
     const unsigned lt_mask = (1u << lane) - 1u;
 
-    for (uint32_t base = begin; base < end; base += 32) {
-        uint32_t id = base + lane;
-        int q = -1;
-        uint32_t packed = 0;
-        if (id < end) {
-            uint32_t t1 = ism_udiv(id, J.divNz_m, J.divNz_l);
-            uint32_t iz = id - t1 * (uint32_t)Nz;
-            uint32_t ix = ism_udiv(t1, J.divNy_m, J.divNy_l);
-            uint32_t iy = t1 - ix * (uint32_t)Ny;
-            float s2 = __fadd_rn(__fadd_rn(S[ix], Sy[iy]), Sz[iz]);
-            if (s2 < s_cut2) {
-                float s = __fsqrt_rn(s2);
-                q = (int)floorf(__fmul_rn(__fadd_rn(s, 0.5f), 1.0f / ISM_SB));
-                if (q >= Q) {  // cannot happen for a consistent s_cut2; keep memory safe
-                    atomicOr(status, (uint32_t)ISM_DEVICE_FLAG_BIN);
-                    q = -1;
+    int ix = col0 / Ny, iy = col0 - (col0 / Ny) * Ny;
+    for (int col = col0; col < col1; ++col, ++iy) {
+        if (iy == Ny) {
+            iy = 0;
+            ++ix;
+        }
+        const float sxy = __fadd_rn(Sx[ix], Sy[iy]);
+        const float rem = s_cut2 - sxy;
+        if (!(rem > 0.0f)) continue;
+        // |n| - 1 <= sqrt(rem) / (k L_z) bounds every kept image of the column
+        const int M = (int)(rem * ism_rsqrt(rem) * inv_kLz) + 2;
+        int z0 = -M - nlo_z, z1 = M - nlo_z;
+        if (z0 < 0) z0 = 0;
+        if (z1 > Nz - 1) z1 = Nz - 1;
+        for (int base = z0; base <= z1; base += 32) {
+            const int iz = base + lane;
+            int q = -1;
+            if (iz <= z1) {
+                const float s2 = __fadd_rn(sxy, Sz[iz]);
+                if (s2 < s_cut2) {
+                    const float s = s2 * ism_rsqrt(s2);
+                    // nearest integer of (s + 1/2) / 32 - 1/2, i.e. ~floor((s + 1/2) / 32)
+                    q = ism_round_int(__fmaf_rn(s, 1.0f / ISM_SB, 0.5f / ISM_SB - 0.5f));
+                    if (q >= Q || q < 0) {  // cannot happen for a consistent s_cut2; keep memory safe
+                        atomicOr(status, (uint32_t)ISM_DEVICE_FLAG_BIN);
+                        q = -1;
+                    }
                 }
-                packed = ix | (iy << 10) | (iz << 20);
             }
+            if (!SCATTER) {
+                // counts only: integer adds commute, so the order is immaterial
+                if (q >= 0) atomicAdd(&cnt[q], 1u);
+                continue;
+            }
+            if (!__any_sync(0xffffffffu, q >= 0)) continue;
+            const unsigned peers = __match_any_sync(0xffffffffu, q);
+            uint32_t base_cnt = 0;
+            if (q >= 0) base_cnt = cnt[q];
+            __syncwarp();
+            if (q >= 0) {
+                if (lane == __ffs(peers) - 1) cnt[q] = base_cnt + (uint32_t)__popc(peers);
+                ids[base_cnt + (uint32_t)__popc(peers & lt_mask)] =
+                    (uint32_t)ix | ((uint32_t)iy << 10) | ((uint32_t)iz << 20);
+            }
+            __syncwarp();
         }
-        unsigned peers = __match_any_sync(0xffffffffu, q);
-        uint32_t base_cnt = 0;
-        if (q >= 0) base_cnt = my[q];
-        __syncwarp();
-        if (q >= 0) {
-            int leader = __ffs(peers) - 1;
-            uint32_t rank = (uint32_t)__popc(peers & lt_mask);
-            if (lane == leader) my[q] = base_cnt + (uint32_t)__popc(peers);
-            if (SCATTER) out_ids[base_cnt + rank] = packed;
-        }
-        __syncwarp();
     }
     if (!SCATTER) {
-        for (int q = lane; q < Q; q += 32) hist[hrow + (long long)q * J.U + unit] = my[q];
+        __syncwarp();
+        for (int q = lane; q < Q; q += 32) hist[hrow + (long long)q * J.U + unit] = cnt[q];
     }
 }
 
@@ -159,7 +178,6 @@ __global__ void __launch_bounds__(1024) scan_top(uint32_t* __restrict__ part, lo
                                                  uint32_t* __restrict__ a, long long n)
 {
     __shared__ uint32_t sh[33];
-    // up to 16 block totals per thread, consecutive
     uint32_t vals[16];
     uint32_t s = 0;
     long long i0 = (long long)threadIdx.x * 16;
@@ -197,31 +215,24 @@ __global__ void __launch_bounds__(1024) scan_apply(uint32_t* __restrict__ a, lon
 
 }  // namespace
 
-static size_t enum_smem(const JobTable& t)
-{
-    size_t axis = (size_t)((t.max_axis_sum + 3) & ~3) * 4;
-    return axis + (size_t)ISM_ENUM_WARPS * t.max_Q * 4;
-}
-
 int ism_launch_enum(const JobTable& t, const WsPlan& p, char* ws, bool scatter, void* stream)
 {
     if (p.enum_ctas <= 0) return 0;
-    size_t sm = enum_smem(t);
+    size_t sm = (size_t)((t.max_axis_sum + 3) & ~3) * 4 + (size_t)ISM_ENUM_WARPS * t.max_Q * 4;
     auto* tbl = reinterpret_cast<const float4*>(ws + p.tbl_off);
     auto* hist = reinterpret_cast<uint32_t*>(ws + p.hist_off);
-    auto* ids = reinterpret_cast<uint32_t*>(ws + p.ids_off);
+    auto* idsp = reinterpret_cast<uint32_t*>(ws + p.ids_off);
     auto* st = reinterpret_cast<uint32_t*>(ws + p.status_off);
+    cudaStream_t s = (cudaStream_t)stream;
     cudaError_t e;
     if (scatter) {
         e = cudaFuncSetAttribute(enum_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
         if (e != cudaSuccess) return (int)e;
-        enum_kernel<true><<<(unsigned)p.enum_ctas, ISM_ENUM_WARPS * 32, sm, (cudaStream_t)stream>>>(t, tbl, hist,
-                                                                                                      ids, st);
+        enum_kernel<true><<<(unsigned)p.enum_ctas, ISM_ENUM_WARPS * 32, sm, s>>>(t, tbl, hist, idsp, st);
     } else {
         e = cudaFuncSetAttribute(enum_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
         if (e != cudaSuccess) return (int)e;
-        enum_kernel<false><<<(unsigned)p.enum_ctas, ISM_ENUM_WARPS * 32, sm, (cudaStream_t)stream>>>(t, tbl, hist,
-                                                                                                       ids, st);
+        enum_kernel<false><<<(unsigned)p.enum_ctas, ISM_ENUM_WARPS * 32, sm, s>>>(t, tbl, hist, idsp, st);
     }
     return (int)cudaGetLastError();
 }

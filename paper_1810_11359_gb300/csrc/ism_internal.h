@@ -7,16 +7,16 @@
 //   geometry  per RIR and axis: image offsets squared in samples^2 (FP64 ->
 //             float-float) and wall-reflection products (Section 2.1, eq. (1),
 //             eq. (4)); checks the positions.
-//   enum(a)   every image of every RIR: delay in samples (eq. (2)-(3)),
-//             culled when its window misses [0, n_ism); counts the survivors
-//             per (RIR, 32-sample delay bin) for each warp's slice of the grid.
-//   scan(b)   exclusive prefix over the counts -> bin offsets (counting sort).
-//   enum(a')  the same enumeration again, scattering packed image ids into
-//             their bins in a fixed order (stable counting sort).
+//   enum(a)   per RIR and range of grid columns: delays of the images in
+//             reach (eq. (2)-(3)), culling of those whose window misses
+//             [0, n_ism), counts per 32-sample delay bin.
+//   scan(b)   exclusive prefix over the counts: bin offsets (counting sort).
+//   enum(a')  the same walk, scattering packed image ids into their bins in
+//             a fixed order (stable counting sort).
 //   accum(c)  one CTA per (RIR, tile of 8 delay bins), one warp per bin: the
-//             warp evaluates the windowed sinc (eq. (6)) of every image of its
-//             bin into a register window and the CTA sums the windows of
-//             neighbouring bins in shared memory and stores the tile (eq. (5)).
+//             windowed sinc (eq. (6)) of every image of the bin into a
+//             register window; the CTA sums the windows of neighbouring bins
+//             in shared memory and stores the tile (eq. (5)).
 //   finalize  per RIR: adds the partial sums at tile seams; fits the envelope
 //             amplitude of the diffuse tail (Section 2.2).
 //   tail(d)   Philox4x32-10 logistic noise times the envelope of eq. (8).
@@ -30,13 +30,16 @@
 
 #include "../../include/ism.h"
 
-#define ISM_SB 32                 // samples per delay bin (one warp-width)
-#define ISM_TILE_SB 8             // delay bins per accumulation CTA (= its warps)
+#define ISM_SB 32                 // samples per delay bin
+#define ISM_TILE_SAMPLES 256      // samples per accumulation tile (CTA)
+#define ISM_TILE_BINS (ISM_TILE_SAMPLES / ISM_SB)   // 8 bins per tile
+#define ISM_ACC_WARPS ISM_TILE_BINS                 // one warp per bin
 #define ISM_ENUM_WARPS 4          // warps per enumeration CTA (one unit each)
 #define ISM_MAX_JOBS 32           // jobs per launch set (kernel-parameter table)
 #define ISM_MAX_AXIS 1023         // images per axis (10-bit packed ids)
 #define ISM_MAX_SLOTS 8           // taps per lane per image: N_w <= 256
 #define ISM_MAX_NISM 131000       // image-source samples per RIR
+#define ISM_MAX_Q 4104            // delay bins per RIR ((n_ism + H) / 32 + 1)
 #define ISM_SCAN_BLOCK 4096       // elements per scan block
 #define ISM_SCAN_TOP 16384        // max scan blocks (one top-level block)
 #define ISM_FIT_WINDOW_S 0.02     // envelope fit: last 20 ms of the ISM part
@@ -52,15 +55,14 @@ struct JobDev {
     float s_cut2;             // cull: keep an image iff s_plain^2 < s_cut2 (samples^2)
     float g2;                 // log2 of the power decay per sample: 6 log2(10) / (fs T60)
     int N[3], nlo[3];         // images per axis, lowest index per axis
-    uint32_t divNz_m, divNy_m;  // magic multipliers for id -> (ix, iy, iz)
-    int divNz_l, divNy_l;
     int n_src, n_rcv, n_rir;
     int n_S, n_ism;
     int H;                    // ceil(Nw / 2): taps j in [-H + 1, H]
     int slots;                // ceil(2H / 32) taps per lane per image
     int Q;                    // delay bins per RIR
-    int U;                    // enumeration units per RIR
-    int unit_size;            // images per enumeration unit (power of two)
+    int U;                    // enumeration units (warps) per RIR
+    int cols_per_unit;        // grid columns (ix, iy) per enumeration unit
+    float inv_kLz;            // 1 / ((f_s / c) L_z): samples -> z cells
     int n_tiles;              // accumulation tiles per RIR
     int has_tail;
     int W_env;                // samples of the envelope fit window
@@ -91,7 +93,7 @@ struct JobTable {
 // Workspace carve-up of one launch set (byte offsets into the workspace).
 struct WsPlan {
     size_t status_off;     // uint32 flags (first 256 bytes)
-    size_t hist_off;       // uint32 [hist_total + 1]
+    size_t hist_off;       // uint32 [hist_total + 1]: per (RIR, bin, unit) counts -> offsets
     size_t part_off;       // uint32 [n_scan_blocks + 1]
     size_t ids_off;        // uint32 [ids_total]
     size_t tbl_off;        // float4 [tbl_total]

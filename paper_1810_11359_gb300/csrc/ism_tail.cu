@@ -33,7 +33,7 @@ __global__ void __launch_bounds__(256) finalize_kernel(const __grid_constant__ J
         int tile = e / per_tile;
         int s = (e / 32) % SL;
         int l = e & 31;
-        int k = ISM_SB * (tile * ISM_TILE_SB + s) - J.H + l;
+        int k = ISM_TILE_SAMPLES * tile + 32 * s + l - J.H;
         if (k < 0 || k >= J.n_ism) continue;
         float v = seam[(long long)tile * 64 * SL + s * 32 + l];
         if (tile > 0) v += seam[(long long)(tile - 1) * 64 * SL + (SL + s) * 32 + l];
