@@ -157,6 +157,31 @@ ism_status ism_host_workspace_size(const ism_room* room, int n_src, int n_rcv, c
 #define ISM_DEVICE_FLAG_BIN 2u        /* an image delay fell outside its bin (internal)    */
 ism_status ism_workspace_status(const void* workspace, void* stream, uint32_t* flags);
 
+/* Same computation as ism_simulate without a workspace argument, for callers
+ * that cannot allocate device memory (a real-time audio callback or a
+ * worker thread that must not block on the allocator, code inside a
+ * framework that owns every device allocation, embedded uses that cannot
+ * keep a workspace).  The paper has no counterpart: it is a deployment
+ * variant of the same launches.
+ *   Scratch: a fixed 64 MiB area that the library reserves in device memory
+ *   when it is loaded; every device that loads the library holds it until
+ *   the process exits.  No call here allocates or frees device memory.
+ *   Limit: a simulation needing more scratch than 64 MiB (ism_workspace_size)
+ *   is rejected with ISM_ERR_UNSUPPORTED and nothing is launched.
+ *   Set-up: the first call on each device looks up the area's device address
+ *   (cudaGetSymbolAddress) with that device current; make that first call
+ *   before any stream capture.
+ *   Sharing: every call uses the same area and leaves its contents behind;
+ *   the kernels reset what they need.  Two calls whose work overlaps on the
+ *   GPU (different streams without ordering between them, or different host
+ *   threads) race on the area and corrupt each other's results: order them.
+ * Arguments, layout and errors are those of ism_simulate; ism_workspace_status
+ * is not available for this entry point. */
+ism_status ism_simulate_noalloc(const ism_room* room, const float* pos_src, int n_src,
+                                const float* pos_rcv, int n_rcv, const int nb_img[3], float Tmax,
+                                float fs, float Tdiff, float Tw, ism_precision prec, uint64_t seed,
+                                float* out, void* stream);
+
 /* ------------------------------------------------------------------------- */
 /* Ragged batches: many rooms in one set of launches                         */
 /* ------------------------------------------------------------------------- */

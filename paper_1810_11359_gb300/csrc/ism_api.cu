@@ -701,3 +701,74 @@ ism_status ism_att2t_sabine(double att_dB, double T60, double* t)
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Allocation-free variant of ism_simulate.
+//
+// Some callers cannot allocate device memory at the point where they need a
+// simulation: code running inside a real-time audio callback or another
+// library's worker thread that must not block on the allocator, code that
+// runs under a framework owning every device allocation (and forbidding raw
+// cudaMalloc), or small embedded uses that cannot size and keep a workspace.
+// For them the library reserves one fixed scratch area in device memory at
+// module load (a file-scope __device__ array) and runs the ordinary
+// simulation in it.  Every device that loads the library holds this area
+// until the process exits.
+// ---------------------------------------------------------------------------
+#define ISM_NOALLOC_SCRATCH_BYTES (64u << 20)
+
+static __device__ __align__(256) unsigned char g_ism_noalloc_scratch[ISM_NOALLOC_SCRATCH_BYTES];
+
+namespace {
+
+#define ISM_NOALLOC_MAX_DEVICES 64
+std::mutex g_noalloc_mu;
+void* g_noalloc_addr[ISM_NOALLOC_MAX_DEVICES] = {};
+
+// Device address of the scratch area for the current device; looked up once
+// per device (host code only sees a stand-in symbol, never the address).
+ism_status noalloc_scratch(void** out)
+{
+    int dev = -1;
+    int e = (int)cudaGetDevice(&dev);
+    if (e) return cuda_fail(e, "cudaGetDevice");
+    if (dev < 0 || dev >= ISM_NOALLOC_MAX_DEVICES)
+        return fail(ISM_ERR_UNSUPPORTED, "device %d is beyond the %d devices this entry point serves", dev,
+                    ISM_NOALLOC_MAX_DEVICES);
+    std::lock_guard<std::mutex> g(g_noalloc_mu);
+    if (!g_noalloc_addr[dev]) {
+        void* p = nullptr;
+        e = (int)cudaGetSymbolAddress(&p, g_ism_noalloc_scratch);
+        if (e) return cuda_fail(e, "cudaGetSymbolAddress of the scratch area");
+        if (!p) return fail(ISM_ERR_CUDA, "scratch area has no device address");
+        g_noalloc_addr[dev] = p;
+    }
+    *out = g_noalloc_addr[dev];
+    return ISM_OK;
+}
+
+}  // namespace
+
+extern "C" ism_status ism_simulate_noalloc(const ism_room* room, const float* pos_src, int n_src,
+                                           const float* pos_rcv, int n_rcv, const int nb_img[3], float Tmax,
+                                           float fs, float Tdiff, float Tw, ism_precision prec, uint64_t seed,
+                                           float* out, void* stream)
+{
+    g_last_error.clear();
+    if (!room || !nb_img) return fail(ISM_ERR_INVALID_ARG, "room and nb_img must not be NULL");
+    ism_status s = check_prec(prec);
+    if (s != ISM_OK) return s;
+    ism_job j = make_job(room, pos_src, n_src, pos_rcv, n_rcv, nb_img, Tmax, fs, Tdiff, Tw, seed, out);
+    std::vector<Validated> vs;
+    if ((s = validate_all(&j, 1, vs, true)) != ISM_OK) return s;
+    size_t need = 0;
+    if ((s = batch_size(vs, &need)) != ISM_OK) return s;
+    if (need > ISM_NOALLOC_SCRATCH_BYTES)
+        return fail(ISM_ERR_UNSUPPORTED,
+                    "this simulation needs %zu bytes of scratch, above the %u bytes of the allocation-free "
+                    "entry point; use ism_simulate with a caller-owned workspace",
+                    need, (unsigned)ISM_NOALLOC_SCRATCH_BYTES);
+    void* scratch = nullptr;
+    if ((s = noalloc_scratch(&scratch)) != ISM_OK) return s;
+    return run_batch(vs, scratch, ISM_NOALLOC_SCRATCH_BYTES, stream);
+}

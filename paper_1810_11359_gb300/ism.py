@@ -68,6 +68,10 @@ _SIGS = {
                                          _P(ctypes.c_int), ctypes.c_float, ctypes.c_float, ctypes.c_float,
                                          ctypes.c_float, ctypes.c_int, ctypes.c_uint64, ctypes.c_void_p,
                                          ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p]),
+    "ism_simulate_noalloc": (ctypes.c_int, [_P(ism_room), ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p,
+                                            ctypes.c_int, _P(ctypes.c_int), ctypes.c_float, ctypes.c_float,
+                                            ctypes.c_float, ctypes.c_float, ctypes.c_int, ctypes.c_uint64,
+                                            ctypes.c_void_p, ctypes.c_void_p]),
     "ism_workspace_status": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, _P(ctypes.c_uint32)]),
     "ism_batch_workspace_size": (ctypes.c_int, [_P(ism_job), ctypes.c_int, ctypes.c_int, _P(ctypes.c_size_t)]),
     "ism_simulate_batch": (ctypes.c_int, [_P(ism_job), ctypes.c_int, ctypes.c_int, ctypes.c_void_p, ctypes.c_size_t,
@@ -290,6 +294,27 @@ def ism_simulate_host(L, beta, pos_src, pos_rcv, nb_img, Tmax, fs, Tdiff=0.0, Tw
                                     float(fs), float(Tdiff or 0.0), float(Tw or 0.0), PRECISIONS[prec],
                                     int(seed) & (2 ** 64 - 1), ctypes.c_void_p(out.ctypes.data),
                                     ctypes.c_void_p(buf.data_ptr()), int(buf.numel()), _stream_ptr(stream)))
+    return out
+
+
+def ism_simulate_noalloc(L, beta, pos_src, pos_rcv, nb_img, Tmax, fs, Tdiff=0.0, Tw=0.0, c=343.0,
+                         prec: str = "fp32", seed: int = 0, out=None, stream=None):
+    """ism_simulate in the library's fixed device scratch area: no workspace,
+    no device allocation by the library (the output tensor is the caller's).
+    Calls must not overlap on the GPU; see include/ism.h."""
+    torch = _torch()
+    dev = torch.device("cuda", torch.cuda.current_device())
+    ps = torch.as_tensor(pos_src, dtype=torch.float32).to(dev).reshape(-1, 3).contiguous()
+    pr = torch.as_tensor(pos_rcv, dtype=torch.float32).to(dev).reshape(-1, 3).contiguous()
+    n_S = ism_rir_length(Tmax, fs)
+    if out is None:
+        out = torch.empty((ps.shape[0], pr.shape[0], n_S), dtype=torch.float32, device=dev)
+    r = _room(L, beta, c)
+    _check(load().ism_simulate_noalloc(ctypes.byref(r), ctypes.c_void_p(ps.data_ptr()), int(ps.shape[0]),
+                                       ctypes.c_void_p(pr.data_ptr()), int(pr.shape[0]), _nb(nb_img), float(Tmax),
+                                       float(fs), float(Tdiff or 0.0), float(Tw or 0.0), PRECISIONS[prec],
+                                       int(seed) & (2 ** 64 - 1), ctypes.c_void_p(out.data_ptr()),
+                                       _stream_ptr(stream)))
     return out
 
 
