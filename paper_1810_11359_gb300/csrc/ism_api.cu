@@ -108,12 +108,12 @@ ism_status validate_job(const ism_job& in, Validated& v, bool need_ptrs)
 }
 
 // Builds the device job table and the workspace plan of one launch set.
-ism_status plan(const Validated* vs, int n, JobTable& t, WsPlan& p)
+ism_status plan(const Validated* vs, int n, ism_precision prec, JobTable& t, WsPlan& p)
 {
     std::memset(&t, 0, sizeof t);
     std::memset(&p, 0, sizeof p);
     t.n_jobs = n;
-    long long rir = 0, hist = 0, tbl = 0, ecta = 0, acta = 0, tcta = 0, seam = 0, ids = 0;
+    long long rir = 0, hist = 0, tbl = 0, ecta = 0, acta = 0, tcta = 0, seam = 0, ids = 0, lut = 0;
     for (int i = 0; i < n; ++i) {
         const Validated& v = vs[i];
         const ism_job& in = v.job;
@@ -131,6 +131,14 @@ ism_status plan(const Validated* vs, int n, JobTable& t, WsPlan& p)
         J.kfs_hi = (float)k;
         J.kfs_lo = (float)(k - (double)J.kfs_hi);
         J.amp_scale = (float)(k / (4.0 * M_PI));
+        // FP16X2: |P| <= amp_scale / 2 and |w| <= 2 |P|, so a scale of 2^e with
+        // amp_scale 2^e <= 8192 keeps every packed value below the FP16 maximum
+        J.half_scale = 1.0f;
+        if (prec == ISM_PREC_FP16X2) {
+            int e = (int)std::floor(std::log2(8192.0 / (double)J.amp_scale));
+            e = e < -24 ? -24 : (e > 24 ? 24 : e);
+            J.half_scale = (float)std::ldexp(1.0, e);
+        }
         J.n_src = in.n_src;
         J.n_rcv = in.n_rcv;
         J.n_rir = in.n_src * in.n_rcv;
@@ -174,6 +182,7 @@ ism_status plan(const Validated* vs, int n, JobTable& t, WsPlan& p)
         J.acc_cta_base = acta;
         J.tail_cta_base = tcta;
         J.seam_base = seam;
+        J.lut_base = lut;
         const long long R = J.n_rir;
         rir += R;
         hist += R * J.Q * J.U;
@@ -186,6 +195,7 @@ ism_status plan(const Validated* vs, int n, JobTable& t, WsPlan& p)
             tcta += R * ((blk_last - blk0 + 1 + ISM_TAIL_CHUNK / 4 - 1) / (ISM_TAIL_CHUNK / 4));
         }
         seam += R * J.n_tiles * 64LL * J.slots;
+        if (prec == ISM_PREC_LUT) lut += (long long)(ism_lut_phases(J.slots) + 1) * 32 * J.slots;
         ids += R * J.img_per_rir;
         if (J.Q > t.max_Q) t.max_Q = J.Q;
         if (axis > t.max_axis_sum) t.max_axis_sum = axis;
@@ -204,6 +214,7 @@ ism_status plan(const Validated* vs, int n, JobTable& t, WsPlan& p)
     p.tbl_total = tbl;
     p.seam_total = seam;
     p.rir_total = rir;
+    p.lut_total = lut;
     p.enum_ctas = ecta;
     p.acc_ctas = acta;
     p.tail_ctas = tcta;
@@ -222,6 +233,8 @@ ism_status plan(const Validated* vs, int n, JobTable& t, WsPlan& p)
     off = align256(off + (size_t)seam * 4);
     p.amp_off = off;
     off = align256(off + (size_t)rir * 4);
+    p.lut_off = off;
+    off = align256(off + (size_t)lut * 4);
     p.total = off;
     return ISM_OK;
 }
@@ -240,14 +253,14 @@ ism_status validate_all(const ism_job* jobs, int n_jobs, std::vector<Validated>&
     return ISM_OK;
 }
 
-ism_status batch_size(const std::vector<Validated>& vs, size_t* bytes)
+ism_status batch_size(const std::vector<Validated>& vs, ism_precision prec, size_t* bytes)
 {
     size_t best = 0;
     JobTable t;
     WsPlan p;
     for (size_t g = 0; g < vs.size(); g += ISM_MAX_JOBS) {
         int n = (int)std::min<size_t>(ISM_MAX_JOBS, vs.size() - g);
-        ism_status s = plan(vs.data() + g, n, t, p);
+        ism_status s = plan(vs.data() + g, n, prec, t, p);
         if (s != ISM_OK) return s;
         if (p.total > best) best = p.total;
     }
@@ -331,10 +344,11 @@ struct StageTimer {
     }
 };
 
-ism_status run_batch(const std::vector<Validated>& vs, void* workspace, size_t ws_bytes, void* stream)
+ism_status run_batch(const std::vector<Validated>& vs, ism_precision prec, void* workspace, size_t ws_bytes,
+                     void* stream)
 {
     size_t need = 0;
-    ism_status s = batch_size(vs, &need);
+    ism_status s = batch_size(vs, prec, &need);
     if (s != ISM_OK) return s;
     if (!workspace) return fail(ISM_ERR_INVALID_ARG, "workspace is NULL");
     if (((uintptr_t)workspace & 255u) != 0) return fail(ISM_ERR_INVALID_ARG, "workspace must be 256-byte aligned");
@@ -348,7 +362,7 @@ ism_status run_batch(const std::vector<Validated>& vs, void* workspace, size_t w
     WsPlan p;
     for (size_t g = 0; g < vs.size(); g += ISM_MAX_JOBS) {
         int n = (int)std::min<size_t>(ISM_MAX_JOBS, vs.size() - g);
-        s = plan(vs.data() + g, n, t, p);
+        s = plan(vs.data() + g, n, prec, t, p);
         if (s != ISM_OK) return s;
         {
             StageTimer tm(ISM_STAGE_GEOMETRY, st);
@@ -373,9 +387,14 @@ ism_status run_batch(const std::vector<Validated>& vs, void* workspace, size_t w
         {
             StageTimer tm(ISM_STAGE_ACCUM, st);
             int launched = 0;
-            if ((e = ism_launch_accum(t, p, ws, ISM_PREC_FP32, stream, &launched)))
+            if (p.lut_total > 0) {
+                if ((e = ism_launch_lut_tables(t, p, ws, stream))) return cuda_fail(e, "windowed-sinc table kernel");
+                ++launched;
+            }
+            int acc_launched = 0;
+            if ((e = ism_launch_accum(t, p, ws, prec, stream, &acc_launched)))
                 return cuda_fail(e, "accumulation kernel");
-            tm.done(launched);
+            tm.done(launched + acc_launched);
         }
         {
             StageTimer tm(ISM_STAGE_FINALIZE, st);
@@ -415,8 +434,8 @@ ism_job make_job(const ism_room* room, const float* pos_src, int n_src, const fl
 
 ism_status check_prec(ism_precision prec)
 {
-    if (prec != ISM_PREC_FP32)
-        return fail(ISM_ERR_UNSUPPORTED, "precision %d is not available in this build", (int)prec);
+    if (prec != ISM_PREC_FP32 && prec != ISM_PREC_FP16X2 && prec != ISM_PREC_BF16X2 && prec != ISM_PREC_LUT)
+        return fail(ISM_ERR_INVALID_ARG, "unknown precision %d", (int)prec);
     return ISM_OK;
 }
 
@@ -464,7 +483,7 @@ ism_status ism_workspace_size(const ism_room* room, int n_src, int n_rcv, const 
     ism_job j = make_job(room, nullptr, n_src, nullptr, n_rcv, nb_img, Tmax, fs, Tdiff, Tw, 0, nullptr);
     std::vector<Validated> vs;
     if ((s = validate_all(&j, 1, vs, false)) != ISM_OK) return s;
-    return batch_size(vs, bytes);
+    return batch_size(vs, prec, bytes);
 }
 
 ism_status ism_batch_workspace_size(const ism_job* jobs, int n_jobs, ism_precision prec, size_t* bytes)
@@ -475,7 +494,7 @@ ism_status ism_batch_workspace_size(const ism_job* jobs, int n_jobs, ism_precisi
     if (s != ISM_OK) return s;
     std::vector<Validated> vs;
     if ((s = validate_all(jobs, n_jobs, vs, false)) != ISM_OK) return s;
-    return batch_size(vs, bytes);
+    return batch_size(vs, prec, bytes);
 }
 
 ism_status ism_simulate_batch(const ism_job* jobs, int n_jobs, ism_precision prec, void* workspace, size_t ws_bytes,
@@ -486,7 +505,7 @@ ism_status ism_simulate_batch(const ism_job* jobs, int n_jobs, ism_precision pre
     if (s != ISM_OK) return s;
     std::vector<Validated> vs;
     if ((s = validate_all(jobs, n_jobs, vs, true)) != ISM_OK) return s;
-    return run_batch(vs, workspace, ws_bytes, stream);
+    return run_batch(vs, prec, workspace, ws_bytes, stream);
 }
 
 ism_status ism_simulate(const ism_room* room, const float* pos_src, int n_src, const float* pos_rcv, int n_rcv,
@@ -520,7 +539,7 @@ ism_status ism_simulate_host(const ism_room* room, const float* pos_src, int n_s
     std::vector<Validated> vs;
     if ((s = validate_all(&j, 1, vs, false)) != ISM_OK) return s;
     size_t sim = 0;
-    if ((s = batch_size(vs, &sim)) != ISM_OK) return s;
+    if ((s = batch_size(vs, prec, &sim)) != ISM_OK) return s;
     // device layout: [simulation workspace | positions | output]
     size_t pos_off = align256(sim);
     size_t out_off = align256(pos_off + (size_t)(n_src + n_rcv) * 3 * sizeof(float));
@@ -544,7 +563,7 @@ ism_status ism_simulate_host(const ism_room* room, const float* pos_src, int n_s
     vs[0].job.pos_rcv = d_pos + 3 * n_src;
     vs[0].job.out = d_out;
     vs[0].job.seed = seed;
-    if ((s = run_batch(vs, workspace, sim, stream)) != ISM_OK) return s;
+    if ((s = run_batch(vs, prec, workspace, sim, stream)) != ISM_OK) return s;
     if ((e = (int)cudaMemcpyAsync(out, d_out, n_out * sizeof(float), cudaMemcpyDeviceToHost, st)))
         return cuda_fail(e, "copy of the RIRs");
     if ((e = (int)cudaStreamSynchronize(st))) return cuda_fail(e, "stream synchronize");
@@ -762,7 +781,7 @@ extern "C" ism_status ism_simulate_noalloc(const ism_room* room, const float* po
     std::vector<Validated> vs;
     if ((s = validate_all(&j, 1, vs, true)) != ISM_OK) return s;
     size_t need = 0;
-    if ((s = batch_size(vs, &need)) != ISM_OK) return s;
+    if ((s = batch_size(vs, prec, &need)) != ISM_OK) return s;
     if (need > ISM_NOALLOC_SCRATCH_BYTES)
         return fail(ISM_ERR_UNSUPPORTED,
                     "this simulation needs %zu bytes of scratch, above the %u bytes of the allocation-free "
@@ -770,5 +789,5 @@ extern "C" ism_status ism_simulate_noalloc(const ism_room* room, const float* po
                     need, (unsigned)ISM_NOALLOC_SCRATCH_BYTES);
     void* scratch = nullptr;
     if ((s = noalloc_scratch(&scratch)) != ISM_OK) return s;
-    return run_batch(vs, scratch, ISM_NOALLOC_SCRATCH_BYTES, stream);
+    return run_batch(vs, prec, scratch, ISM_NOALLOC_SCRATCH_BYTES, stream);
 }

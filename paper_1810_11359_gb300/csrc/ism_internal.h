@@ -67,6 +67,7 @@ struct JobDev {
     int has_tail;
     int W_env;                // samples of the envelope fit window
     int vec4;                 // out rows 16-byte aligned (float4 stores allowed)
+    float half_scale;         // FP16X2 records are scaled by this power of two
     uint64_t seed;
     const float* pos_src;
     const float* pos_rcv;
@@ -80,6 +81,7 @@ struct JobDev {
     long long acc_cta_base;   // first accumulation CTA of the job
     long long tail_cta_base;  // first tail CTA of the job
     long long seam_base;      // first seam record (tiles) of the job
+    long long lut_base;       // first entry (float) of the job's windowed-sinc table (LUT form)
 };
 
 struct JobTable {
@@ -99,12 +101,14 @@ struct WsPlan {
     size_t tbl_off;        // float4 [tbl_total]
     size_t seam_off;       // float  [seam_total]
     size_t amp_off;        // float  [rir_total]
+    size_t lut_off;        // float  [lut_total]: polyphase windowed-sinc tables (LUT form)
     size_t total;
     long long hist_total;
     long long ids_total;
     long long tbl_total;
     long long seam_total;
     long long rir_total;
+    long long lut_total;
     long long n_scan_blocks;
     long long enum_ctas;
     long long acc_ctas;
@@ -113,6 +117,15 @@ struct WsPlan {
 
 #define ISM_TAIL_CHUNK 4096   // tail samples per CTA (256 threads x 16)
 
+// Phases per sample of the polyphase windowed-sinc table of the LUT form
+// (eq. (9)): 256 for windows of up to 32 taps, fewer for longer windows so
+// that a table of (Q + 1) x 32 SLOTS FP32 entries stays at ~33 KB of shared
+// memory.
+__host__ __device__ constexpr int ism_lut_phases(int slots)
+{
+    return slots <= 1 ? 256 : slots == 2 ? 128 : slots <= 4 ? 64 : 32;
+}
+
 // Launch entry points (implemented in the .cu files, called by ism_api.cu).
 // Each returns 0 or a cudaError_t value.
 int ism_launch_geometry(const JobTable& t, const WsPlan& p, char* ws, void* stream);
@@ -120,6 +133,10 @@ int ism_launch_enum(const JobTable& t, const WsPlan& p, char* ws, bool scatter, 
 int ism_launch_scan(const WsPlan& p, char* ws, void* stream);
 int ism_launch_accum(const JobTable& t, const WsPlan& p, char* ws, ism_precision prec, void* stream,
                      int* launched);
+int ism_launch_accum_fp16(const JobTable& t, const WsPlan& p, char* ws, void* stream, int* launched);
+int ism_launch_accum_bf16(const JobTable& t, const WsPlan& p, char* ws, void* stream, int* launched);
+int ism_launch_accum_lut(const JobTable& t, const WsPlan& p, char* ws, void* stream, int* launched);
+int ism_launch_lut_tables(const JobTable& t, const WsPlan& p, char* ws, void* stream);
 int ism_launch_finalize(const JobTable& t, const WsPlan& p, char* ws, void* stream);
 int ism_launch_tail(const JobTable& t, const WsPlan& p, char* ws, void* stream);
 int ism_launch_noise(uint64_t seed, uint32_t rir, uint32_t k0, int n, float* z, void* stream);
