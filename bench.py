@@ -1,10 +1,18 @@
 """Throughput benchmark of the image-source-method hot path on GB300.
 
-Workload (one "step"): the batched FP32 configuration -- 128 RIRs (4 sources x
-32 receivers) in a 6 x 5 x 3 m room, beta from Sabine for T60 = 0.6 s,
-16 kHz, 0.6 s RIRs (9600 samples), 32-tap windowed sinc, images per axis
-from Tmax ([73, 87, 141] = 895,491 images per RIR).  One step is one
-ism_simulate call: geometry, enumeration, binning, accumulation, finalize.
+Workload (one "step", default --workload batched): 128 RIRs (4 sources x 32
+receivers) in a 6 x 5 x 3 m room, beta from Sabine for T60 = 0.6 s, 16 kHz,
+0.6 s RIRs (9600 samples), 32-tap windowed sinc, images per axis from Tmax
+([73, 87, 141] = 895,491 images per RIR).  One step is one ism_simulate
+call: geometry, enumeration, binning, accumulation, finalize.
+
+--workload trajectory: 512 RIRs (64-point source trajectory x 8-microphone
+circle) in a 10 x 8 x 3.5 m room, T60 = 1.2 s, 48 kHz, image sources to
+0.3 s and the Philox diffuse tail to 1.2 s (57,600 samples per RIR); the
+line adds the HBM roofline of the tail kernel.
+
+--prec fp32|fp16x2|bf16x2|lut selects the tap arithmetic of the
+accumulation kernel (the image enumeration and delays are FP32 in all).
 
 Prints one JSON line (rank 0).  `value` is RIRs/s of the whole job; the line
 also carries image-contributions/s, the live roofline of the accumulation
@@ -13,6 +21,7 @@ oracle timed on the host cores (cpu_baseline) and the SM clocks sampled
 during the timed region.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                    [--workload batched|trajectory] [--prec fp32|fp16x2|bf16x2|lut]
 
 --impl reference times the FP64 CPU oracle on a bounded sample of the same
 workload on the host cores (rank 0 only).
@@ -40,6 +49,9 @@ METRIC = "RIRs/sec"
 UNIT = "RIR/s"
 FMA_OPS_PER_CONTRIBUTION = 5   # FADD (j - f), 2 FFMA (window), FMUL, FFMA (accumulate)
 L2_BYTES = 129 * 1024 * 1024
+DTYPES = {"fp32": "f32", "fp16x2": "f16x2 taps, f32 accumulation", "bf16x2": "bf16x2 taps, f32 accumulation",
+          "lut": "f32 windowed-sinc table, f32 accumulation"}
+PREC_ID = {"fp32": 0, "fp16x2": 1, "bf16x2": 2, "lut": 3}
 
 
 def _peaks():
@@ -52,9 +64,13 @@ def _peaks():
         return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
 
 
-def workload():
+def workload(name="batched"):
+    """(room, Tdiff, T_img): T_img is the length the images are enumerated for."""
+    if name == "trajectory":
+        room = workloads.trajectory_array()
+        return room, room.Tdiff, room.Tdiff
     room = workloads.batched_fp32()
-    return room
+    return room, 0.0, room.Tmax
 
 
 def contributions(room, beta, N, n_ism):
@@ -142,8 +158,10 @@ def traffic_from_profiles():
     try:
         from paper_1810_11359_gb300 import build as b
         import hashlib
-        src = os.path.join(b.CSRC, "ism_accum.cu")
-        dig = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+        h = hashlib.sha256()
+        for f in ("ism_accum.cuh", "ism_accum.cu"):
+            h.update(open(os.path.join(b.CSRC, f), "rb").read())
+        dig = h.hexdigest()[:16]
         vals = {}
         for line in open(path):
             if "=" in line and line.strip().startswith("bench_"):
@@ -156,54 +174,58 @@ def traffic_from_profiles():
         return None
 
 
-def cpu_baseline(room, beta, N, n_ism, budget_s=15.0):
+def _oracle_pairs(room, beta, N, Tdiff, pairs, cores):
+    """The oracle's RIRs (image sources, then the tail when Tdiff < Tmax) for a
+    list of (source, receiver) pairs."""
+    import oracle
+    b32 = np.asarray(beta, np.float32).astype(np.float64)
+    return oracle.simulate(room.L, b32, float(np.float32(room.c)), float(np.float32(room.fs)), room.pos_src,
+                           room.pos_rcv, N, float(np.float32(room.Tmax)),
+                           Tdiff=float(np.float32(Tdiff)) if Tdiff else None, Tw=float(np.float32(room.window())),
+                           seed=room.seed, pairs=pairs, n_threads=cores)
+
+
+def cpu_baseline(room, beta, N, Tdiff, budget_s=15.0):
     """The FP64 oracle, as it stands, on the host cores over a bounded sample
     of the step's RIRs."""
     import oracle
     oracle.build()
     cores = oracle.max_threads()
-    ps_all = np.repeat(room.pos_src, room.pos_rcv.shape[0], axis=0)
-    pr_all = np.tile(room.pos_rcv, (room.pos_src.shape[0], 1))
-    b32 = np.asarray(beta, np.float32).astype(np.float64)
+    all_pairs = [(i, j) for i in range(room.pos_src.shape[0]) for j in range(room.pos_rcv.shape[0])]
     # calibrate on one RIR per core, then size the sample to the budget
-    n = max(1, min(cores, ps_all.shape[0]))
+    n = max(1, min(cores, len(all_pairs)))
     t0 = time.perf_counter()
-    oracle.rir_list(room.L, b32, float(np.float32(room.c)), float(np.float32(room.fs)), float(np.float32(room.window())),
-                    ps_all[:n], pr_all[:n], N, n_ism, n_threads=cores)
+    _oracle_pairs(room, beta, N, Tdiff, all_pairs[:n], cores)
     dt = time.perf_counter() - t0
     total_rirs, total_t = n, dt
     more = int(max(0, (budget_s - dt) / max(dt / n, 1e-6)))
-    more = min(more, ps_all.shape[0] - n)
+    more = min(more, len(all_pairs) - n)
     more = (more // cores) * cores
     if more > 0:
         t0 = time.perf_counter()
-        oracle.rir_list(room.L, b32, float(np.float32(room.c)), float(np.float32(room.fs)),
-                        float(np.float32(room.window())), ps_all[n:n + more], pr_all[n:n + more], N, n_ism,
-                        n_threads=cores)
+        _oracle_pairs(room, beta, N, Tdiff, all_pairs[n:n + more], cores)
         total_t += time.perf_counter() - t0
         total_rirs += more
     return {"value": total_rirs / total_t, "unit": UNIT, "cores": cores, "kind": "oracle",
-            "sample": f"{total_rirs} of the step's 128 RIRs (full length, FP64 direct sum), {total_t:.1f} s"}
+            "sample": f"{total_rirs} of the step's {len(all_pairs)} RIRs (full length, FP64 direct sum), "
+                      f"{total_t:.1f} s"}
 
 
 def run_reference(args, rank):
     if rank != 0:
         return
-    room = workload()
+    room, Tdiff, T_img = workload(args.workload)
     import oracle
     beta = oracle.beta_sabine(room.L, room.rt60)
-    N = oracle.nb_img_from_t(room.Tmax, room.L, room.c, room.window())
-    n_S = oracle.n_samples(np.float32(room.Tmax), room.fs)
+    N = oracle.nb_img_from_t(T_img, room.L, room.c, room.window())
     oracle.build()
     cores = oracle.max_threads()
-    sample = max(1, min(128, cores))
-    ps_all = np.repeat(room.pos_src, room.pos_rcv.shape[0], axis=0)[:sample]
-    pr_all = np.tile(room.pos_rcv, (room.pos_src.shape[0], 1))[:sample]
-    b32 = np.asarray(beta, np.float32).astype(np.float64)
+    all_pairs = [(i, j) for i in range(room.pos_src.shape[0]) for j in range(room.pos_rcv.shape[0])]
+    sample = max(1, min(len(all_pairs), cores))
+    pairs = all_pairs[:sample]
 
     def step():
-        oracle.rir_list(room.L, b32, float(np.float32(room.c)), float(np.float32(room.fs)),
-                        float(np.float32(room.window())), ps_all, pr_all, N, n_S, n_threads=cores)
+        _oracle_pairs(room, beta, N, Tdiff, pairs, cores)
 
     for _ in range(args.warmup):
         step()
@@ -215,9 +237,9 @@ def run_reference(args, rank):
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1e3, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": room.name, "rirs_per_step": sample, "of_rirs": 128},
+            "config": {"workload": room.name, "rirs_per_step": sample, "of_rirs": len(all_pairs)},
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
-                             "sample": f"{sample} of the 128 RIRs per step, full length"},
+                             "sample": f"{sample} of the {len(all_pairs)} RIRs per step, full length"},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -229,6 +251,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--workload", default="batched", choices=["batched", "trajectory"])
+    ap.add_argument("--prec", default="fp32", choices=list(PREC_ID))
     args = ap.parse_args()
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -254,10 +278,11 @@ def main():
         torch.cuda.set_device(0)
     from paper_1810_11359_gb300 import ism
 
-    room = workload()
+    room, Tdiff, T_img = workload(args.workload)
     beta = ism.ism_beta_sabine(room.L, room.rt60)
-    N = ism.ism_nb_img_from_t(room.Tmax, room.L, room.c, room.window())
+    N = ism.ism_nb_img_from_t(T_img, room.L, room.c, room.window())
     n_S = ism.ism_rir_length(room.Tmax, room.fs)
+    n_ism = ism.ism_rir_length(Tdiff, room.fs) if Tdiff else n_S
     dev = torch.device("cuda", torch.cuda.current_device())
     ps = torch.from_numpy(room.pos_src).to(dev)
     pr = torch.from_numpy(room.pos_rcv).to(dev)
@@ -267,8 +292,8 @@ def main():
     stream = torch.cuda.current_stream()
 
     def step():
-        ism.ism_simulate(room.L, beta, ps, pr, N, room.Tmax, room.fs, Tw=room.window(), c=room.c, out=out,
-                         workspace=ws)
+        ism.ism_simulate(room.L, beta, ps, pr, N, room.Tmax, room.fs, Tdiff=Tdiff, Tw=room.window(), c=room.c,
+                         prec=args.prec, seed=room.seed, out=out, workspace=ws)
 
     for _ in range(max(args.warmup, 3)):
         step()
@@ -309,8 +334,9 @@ def main():
     ws_h = ism.Workspace(dev)
 
     def step_host():
-        ism.ism_simulate_host(room.L, beta, h_ps.numpy(), h_pr.numpy(), N, room.Tmax, room.fs, Tw=room.window(),
-                              c=room.c, out=h_out.numpy(), workspace=ws_h)
+        ism.ism_simulate_host(room.L, beta, h_ps.numpy(), h_pr.numpy(), N, room.Tmax, room.fs, Tdiff=Tdiff,
+                              Tw=room.window(), c=room.c, prec=args.prec, seed=room.seed, out=h_out.numpy(),
+                              workspace=ws_h)
 
     for _ in range(2):
         step_host()
@@ -329,7 +355,7 @@ def main():
         dist.destroy_process_group()
         return
 
-    n_contrib = contributions(room, beta, N, n_S)
+    n_contrib = contributions(room, beta, N, n_ism)
     acc_ms, acc_launches, acc_calls = prof["accum"]
     acc_ms_per_launch = acc_ms / max(acc_launches, 1)
     peaks, peak_kind = _peaks()
@@ -343,20 +369,22 @@ def main():
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": max(args.warmup, 3), "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f32", "data": "synthetic (seeded positions, Sabine beta)",
+        "vs_baseline": None, "dtype": DTYPES[args.prec], "data": "synthetic (seeded positions, Sabine beta)",
         "config": {"workload": room.name, "rirs_per_step": int(ps.shape[0] * pr.shape[0]), "n_samples": n_S,
-                   "images_per_rir": int(np.prod(N)), "nb_img": [int(v) for v in N], "taps": 32,
-                   "l2": "flushed between timed steps (256 MB write)"},
+                   "n_ism_samples": n_ism, "images_per_rir": int(np.prod(N)), "nb_img": [int(v) for v in N],
+                   "taps": 32, "precision": args.prec, "l2": "flushed between timed steps (256 MB write)"},
         "image_contributions_per_sec": n_contrib * world / (ms * 1e-3),
         "contributions_per_step": n_contrib,
         "stage_ms_per_step": {k: v[0] / max(args.steps, 1) for k, v in prof.items()},
-        "roofline": {"bound": "alu", "kernel": "accum_kernel<1,false>", "achieved": achieved_tops,
+        "roofline": {"bound": "alu", "kernel": f"accum_kernel<1,false,{PREC_ID[args.prec]}>",
+                     "achieved": achieved_tops,
                      "peak": peak_tops, "unit": "Tops/s (FP32 FMA-pipe lane ops)",
                      "frac": achieved_tops / peak_tops,
                      "peak_basis": f"{n_sm} SMs x 128 FP32 lanes x {sm_mhz:.0f} MHz ({peak_kind} max SM clock)",
                      "ops_per_contribution": FMA_OPS_PER_CONTRIBUTION,
                      "kernel_ms": acc_ms_per_launch,
-                     "traffic": traffic_from_profiles()},
+                     "traffic": traffic_from_profiles() if (args.prec == "fp32" and args.workload == "batched")
+                     else None},
         "gpu_launches": int(round(launches_per_step * args.steps)),
         "e2e": {"value": rirs / e2e_dt, "unit": UNIT,
                 "h2d_bytes_per_step": int(room.pos_src.nbytes + room.pos_rcv.nbytes),
@@ -364,8 +392,17 @@ def main():
                 "entry": "ism_simulate_host (pinned host positions in, host RIRs out)"},
         "clocks": clk,
     }
+    if n_ism < n_S:
+        tail_ms, tail_launches, _ = prof["tail"]
+        tail_bytes = 4.0 * (n_S - n_ism) * ps.shape[0] * pr.shape[0]   # one FP32 store per tail sample
+        tail_ms_launch = tail_ms / max(tail_launches, 1)
+        hbm = float(peaks.get("hbm_gbs", 6800.0))
+        line["tail_roofline"] = {"bound": "hbm", "kernel": "tail_kernel", "achieved": tail_bytes / tail_ms_launch / 1e6,
+                                 "peak": hbm, "unit": "GB/s", "frac": tail_bytes / tail_ms_launch / 1e6 / hbm,
+                                 "bytes_per_launch": tail_bytes, "kernel_ms": tail_ms_launch,
+                                 "peak_basis": f"{peak_kind} HBM copy bandwidth"}
     if not args.no_cpu_baseline and world >= 1:
-        line["cpu_baseline"] = cpu_baseline(room, beta, N, n_S)
+        line["cpu_baseline"] = cpu_baseline(room, beta, N, Tdiff)
     print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()
