@@ -213,6 +213,56 @@ ism_status ism_simulate_batch(const ism_job* jobs, int n_jobs, ism_precision pre
                               size_t ws_bytes, void* stream);
 
 /* ------------------------------------------------------------------------- */
+/* Gradients (adjoint of eq. (1)-(6))                                        */
+/* ------------------------------------------------------------------------- */
+/* The paper computes RIRs only; the adjoint is the chain rule through its
+ * definitions.  For a loss with dLoss/dh[k] = grad_out[k] over the image-
+ * source samples k < n_ism of every RIR, each image n contributes
+ *   g_A = sum_k grad_out[k] delta'(k - s_n)            (eq. (5), (6))
+ *   g_s = -A_n sum_k grad_out[k] d delta'/dx (k - s_n)
+ * and, with s = f_s d / c (eq. (3)), A = prod beta^e / (4 pi d) (eq. (4)),
+ * d = |p_r - p_n| (eq. (2)), p_n per axis = n L + x_s (n even) or
+ * (n + 1) L - x_s (n odd) (eq. (1)):
+ *   dLoss/d beta_w += g_A e_w beta_w^(e_w - 1) prod_(v != w) beta_v^e_v / (4 pi d)
+ *   g_d = -g_A A / d + g_s f_s / c
+ *   dLoss/d p_r += g_d (p_r - p_n) / d
+ *   dLoss/d x_s += -g_d (x_r - x_n) / d * (+1 if n even else -1), per axis.
+ * The samples of the diffuse tail (k >= n_ism) carry no gradient: the tail
+ * is treated as a constant of the loss.  FP32 tap arithmetic, fixed-order
+ * sums (no atomics): the result is bit-identical from run to run.
+ *
+ * One backward job: the forward job (its `out`, `env_amp` and `seed` are not
+ * used) and device pointers
+ *   grad_out   [n_src][n_rcv][n_S] FP32, dLoss/dh (read)
+ *   grad_beta  [6]  FP32 (written): dLoss/d beta of the room
+ *   grad_src   [n_src][3] FP32 (written)
+ *   grad_rcv   [n_rcv][3] FP32 (written)
+ * Outputs are written, not accumulated; any of the three may be NULL. */
+typedef struct {
+    ism_job job;
+    const float* grad_out;
+    float* grad_beta;
+    float* grad_src;
+    float* grad_rcv;
+} ism_grad_job;
+
+/* Workspace bytes for ism_simulate_backward_batch. */
+ism_status ism_backward_workspace_size(const ism_grad_job* jobs, int n_jobs, size_t* bytes);
+
+/* Gradients of every job (host array `jobs`); ordered on `stream`.  Errors as
+ * for ism_simulate_batch; grad_out must not be NULL. */
+ism_status ism_simulate_backward_batch(const ism_grad_job* jobs, int n_jobs, void* workspace,
+                                       size_t ws_bytes, void* stream);
+
+/* Single-room form: arguments of ism_simulate (FP32 tap arithmetic) plus the
+ * gradient pointers of ism_grad_job. */
+ism_status ism_simulate_backward(const ism_room* room, const float* pos_src, int n_src,
+                                 const float* pos_rcv, int n_rcv, const int nb_img[3], float Tmax,
+                                 float fs, float Tdiff, float Tw, const float* grad_out,
+                                 float* grad_beta, float* grad_src, float* grad_rcv, void* workspace,
+                                 size_t ws_bytes, void* stream);
+
+/* ------------------------------------------------------------------------- */
 /* Diffuse-tail noise (Section 2.2, Section 3.3)                             */
 /* ------------------------------------------------------------------------- */
 /* Writes the unit-variance logistic noise z of samples k0 .. k0+n-1 of RIR
@@ -263,7 +313,8 @@ typedef enum {
     ISM_STAGE_ACCUM = 4,        /* windowed-sinc accumulation, eq. (5)-(6) (c)   */
     ISM_STAGE_FINALIZE = 5,     /* tile seams and envelope fit                   */
     ISM_STAGE_TAIL = 6,         /* diffuse tail, eq. (8) (d)                     */
-    ISM_N_STAGES = 7
+    ISM_STAGE_ADJOINT = 7,      /* backward: per-image gradients and reductions  */
+    ISM_N_STAGES = 8
 } ism_stage;
 
 /* Turns timing on (enable != 0) or off for all later simulation calls of the

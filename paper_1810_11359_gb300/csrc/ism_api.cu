@@ -63,6 +63,11 @@ struct Validated {
     ism_job job;
     double Tw, Nw;
     int n_S, n_ism, H, slots;
+    // backward pass only
+    const float* grad_out = nullptr;
+    float* grad_beta = nullptr;
+    float* grad_src = nullptr;
+    float* grad_rcv = nullptr;
 };
 
 ism_status validate_job(const ism_job& in, Validated& v, bool need_ptrs)
@@ -108,12 +113,12 @@ ism_status validate_job(const ism_job& in, Validated& v, bool need_ptrs)
 }
 
 // Builds the device job table and the workspace plan of one launch set.
-ism_status plan(const Validated* vs, int n, ism_precision prec, JobTable& t, WsPlan& p)
+ism_status plan(const Validated* vs, int n, ism_precision prec, bool backward, JobTable& t, WsPlan& p)
 {
     std::memset(&t, 0, sizeof t);
     std::memset(&p, 0, sizeof p);
     t.n_jobs = n;
-    long long rir = 0, hist = 0, tbl = 0, ecta = 0, acta = 0, tcta = 0, seam = 0, ids = 0, lut = 0;
+    long long rir = 0, hist = 0, tbl = 0, ecta = 0, acta = 0, tcta = 0, seam = 0, ids = 0, lut = 0, gpart = 0;
     for (int i = 0; i < n; ++i) {
         const Validated& v = vs[i];
         const ism_job& in = v.job;
@@ -183,6 +188,12 @@ ism_status plan(const Validated* vs, int n, ism_precision prec, JobTable& t, WsP
         J.tail_cta_base = tcta;
         J.seam_base = seam;
         J.lut_base = lut;
+        J.grad_out = v.grad_out;
+        J.grad_beta = v.grad_beta;
+        J.grad_src = v.grad_src;
+        J.grad_rcv = v.grad_rcv;
+        J.gpart_base = gpart;
+        J.rgrad_base = rir * 12;
         const long long R = J.n_rir;
         rir += R;
         hist += R * J.Q * J.U;
@@ -196,6 +207,7 @@ ism_status plan(const Validated* vs, int n, ism_precision prec, JobTable& t, WsP
         }
         seam += R * J.n_tiles * 64LL * J.slots;
         if (prec == ISM_PREC_LUT) lut += (long long)(ism_lut_phases(J.slots) + 1) * 32 * J.slots;
+        if (backward) gpart += R * J.Q * 12;
         ids += R * J.img_per_rir;
         if (J.Q > t.max_Q) t.max_Q = J.Q;
         if (axis > t.max_axis_sum) t.max_axis_sum = axis;
@@ -215,6 +227,8 @@ ism_status plan(const Validated* vs, int n, ism_precision prec, JobTable& t, WsP
     p.seam_total = seam;
     p.rir_total = rir;
     p.lut_total = lut;
+    p.gpart_total = gpart;
+    p.rgrad_total = backward ? rir * 12 : 0;
     p.enum_ctas = ecta;
     p.acc_ctas = acta;
     p.tail_ctas = tcta;
@@ -235,6 +249,10 @@ ism_status plan(const Validated* vs, int n, ism_precision prec, JobTable& t, WsP
     off = align256(off + (size_t)rir * 4);
     p.lut_off = off;
     off = align256(off + (size_t)lut * 4);
+    p.gpart_off = off;
+    off = align256(off + (size_t)p.gpart_total * 4);
+    p.rgrad_off = off;
+    off = align256(off + (size_t)p.rgrad_total * 4);
     p.total = off;
     return ISM_OK;
 }
@@ -253,14 +271,14 @@ ism_status validate_all(const ism_job* jobs, int n_jobs, std::vector<Validated>&
     return ISM_OK;
 }
 
-ism_status batch_size(const std::vector<Validated>& vs, ism_precision prec, size_t* bytes)
+ism_status batch_size(const std::vector<Validated>& vs, ism_precision prec, size_t* bytes, bool backward = false)
 {
     size_t best = 0;
     JobTable t;
     WsPlan p;
     for (size_t g = 0; g < vs.size(); g += ISM_MAX_JOBS) {
         int n = (int)std::min<size_t>(ISM_MAX_JOBS, vs.size() - g);
-        ism_status s = plan(vs.data() + g, n, prec, t, p);
+        ism_status s = plan(vs.data() + g, n, prec, backward, t, p);
         if (s != ISM_OK) return s;
         if (p.total > best) best = p.total;
     }
@@ -362,7 +380,7 @@ ism_status run_batch(const std::vector<Validated>& vs, ism_precision prec, void*
     WsPlan p;
     for (size_t g = 0; g < vs.size(); g += ISM_MAX_JOBS) {
         int n = (int)std::min<size_t>(ISM_MAX_JOBS, vs.size() - g);
-        s = plan(vs.data() + g, n, prec, t, p);
+        s = plan(vs.data() + g, n, prec, false, t, p);
         if (s != ISM_OK) return s;
         {
             StageTimer tm(ISM_STAGE_GEOMETRY, st);
@@ -406,6 +424,75 @@ ism_status run_batch(const std::vector<Validated>& vs, ism_precision prec, void*
             if ((e = ism_launch_tail(t, p, ws, stream))) return cuda_fail(e, "tail kernel");
             tm.done(1);
         }
+    }
+    return ISM_OK;
+}
+
+// Backward pass: the forward's geometry, enumeration and binning, then the
+// adjoint kernel and its fixed-order reductions.
+ism_status run_backward(const std::vector<Validated>& vs, void* workspace, size_t ws_bytes, void* stream)
+{
+    size_t need = 0;
+    ism_status s = batch_size(vs, ISM_PREC_FP32, &need, true);
+    if (s != ISM_OK) return s;
+    if (!workspace) return fail(ISM_ERR_INVALID_ARG, "workspace is NULL");
+    if (((uintptr_t)workspace & 255u) != 0) return fail(ISM_ERR_INVALID_ARG, "workspace must be 256-byte aligned");
+    if (ws_bytes < need)
+        return fail(ISM_ERR_WORKSPACE_TOO_SMALL, "workspace of %zu bytes, need %zu", ws_bytes, need);
+    char* ws = static_cast<char*>(workspace);
+    cudaStream_t st = (cudaStream_t)stream;
+    int e = (int)cudaMemsetAsync(ws, 0, 256, st);
+    if (e) return cuda_fail(e, "status reset");
+    JobTable t;
+    WsPlan p;
+    for (size_t g = 0; g < vs.size(); g += ISM_MAX_JOBS) {
+        int n = (int)std::min<size_t>(ISM_MAX_JOBS, vs.size() - g);
+        s = plan(vs.data() + g, n, ISM_PREC_FP32, true, t, p);
+        if (s != ISM_OK) return s;
+        {
+            StageTimer tm(ISM_STAGE_GEOMETRY, st);
+            if ((e = ism_launch_geometry(t, p, ws, stream))) return cuda_fail(e, "geometry kernel");
+            tm.done(p.rir_total > 0);
+        }
+        {
+            StageTimer tm(ISM_STAGE_ENUM_COUNT, st);
+            if ((e = ism_launch_enum(t, p, ws, false, stream))) return cuda_fail(e, "enumeration (count) kernel");
+            tm.done(p.enum_ctas > 0);
+        }
+        {
+            StageTimer tm(ISM_STAGE_SCAN, st);
+            if ((e = ism_launch_scan(p, ws, stream))) return cuda_fail(e, "scan kernels");
+            tm.done(3);
+        }
+        {
+            StageTimer tm(ISM_STAGE_ENUM_SCATTER, st);
+            if ((e = ism_launch_enum(t, p, ws, true, stream))) return cuda_fail(e, "enumeration (scatter) kernel");
+            tm.done(p.enum_ctas > 0);
+        }
+        {
+            StageTimer tm(ISM_STAGE_ADJOINT, st);
+            int launched = 0;
+            if ((e = ism_launch_adjoint(t, p, ws, stream, &launched))) return cuda_fail(e, "adjoint kernel");
+            tm.done(launched);
+        }
+    }
+    return ISM_OK;
+}
+
+ism_status validate_grad_jobs(const ism_grad_job* jobs, int n_jobs, std::vector<Validated>& vs)
+{
+    if (!jobs || n_jobs < 1) return fail(ISM_ERR_INVALID_ARG, "need at least one job");
+    std::vector<ism_job> plain(n_jobs);
+    for (int i = 0; i < n_jobs; ++i) plain[i] = jobs[i].job;
+    ism_status s = validate_all(plain.data(), n_jobs, vs, false);
+    if (s != ISM_OK) return s;
+    for (int i = 0; i < n_jobs; ++i) {
+        if (!jobs[i].job.pos_src || !jobs[i].job.pos_rcv || !jobs[i].grad_out)
+            return fail(ISM_ERR_INVALID_ARG, "job %d: pos_src, pos_rcv and grad_out must be device pointers", i);
+        vs[i].grad_out = jobs[i].grad_out;
+        vs[i].grad_beta = jobs[i].grad_beta;
+        vs[i].grad_src = jobs[i].grad_src;
+        vs[i].grad_rcv = jobs[i].grad_rcv;
     }
     return ISM_OK;
 }
@@ -516,6 +603,46 @@ ism_status ism_simulate(const ism_room* room, const float* pos_src, int n_src, c
     if (!room || !nb_img) return fail(ISM_ERR_INVALID_ARG, "room and nb_img must not be NULL");
     ism_job j = make_job(room, pos_src, n_src, pos_rcv, n_rcv, nb_img, Tmax, fs, Tdiff, Tw, seed, out);
     return ism_simulate_batch(&j, 1, prec, workspace, ws_bytes, stream);
+}
+
+ism_status ism_backward_workspace_size(const ism_grad_job* jobs, int n_jobs, size_t* bytes)
+{
+    g_last_error.clear();
+    if (!bytes) return fail(ISM_ERR_INVALID_ARG, "bytes is NULL");
+    if (!jobs || n_jobs < 1) return fail(ISM_ERR_INVALID_ARG, "need at least one job");
+    std::vector<ism_job> plain(n_jobs);
+    for (int i = 0; i < n_jobs; ++i) plain[i] = jobs[i].job;
+    std::vector<Validated> vs;
+    ism_status s = validate_all(plain.data(), n_jobs, vs, false);
+    if (s != ISM_OK) return s;
+    return batch_size(vs, ISM_PREC_FP32, bytes, true);
+}
+
+ism_status ism_simulate_backward_batch(const ism_grad_job* jobs, int n_jobs, void* workspace, size_t ws_bytes,
+                                       void* stream)
+{
+    g_last_error.clear();
+    std::vector<Validated> vs;
+    ism_status s = validate_grad_jobs(jobs, n_jobs, vs);
+    if (s != ISM_OK) return s;
+    return run_backward(vs, workspace, ws_bytes, stream);
+}
+
+ism_status ism_simulate_backward(const ism_room* room, const float* pos_src, int n_src, const float* pos_rcv,
+                                 int n_rcv, const int nb_img[3], float Tmax, float fs, float Tdiff, float Tw,
+                                 const float* grad_out, float* grad_beta, float* grad_src, float* grad_rcv,
+                                 void* workspace, size_t ws_bytes, void* stream)
+{
+    g_last_error.clear();
+    if (!room || !nb_img) return fail(ISM_ERR_INVALID_ARG, "room and nb_img must not be NULL");
+    ism_grad_job gj;
+    std::memset(&gj, 0, sizeof gj);
+    gj.job = make_job(room, pos_src, n_src, pos_rcv, n_rcv, nb_img, Tmax, fs, Tdiff, Tw, 0, nullptr);
+    gj.grad_out = grad_out;
+    gj.grad_beta = grad_beta;
+    gj.grad_src = grad_src;
+    gj.grad_rcv = grad_rcv;
+    return ism_simulate_backward_batch(&gj, 1, workspace, ws_bytes, stream);
 }
 
 ism_status ism_simulate_host(const ism_room* room, const float* pos_src, int n_src, const float* pos_rcv, int n_rcv,

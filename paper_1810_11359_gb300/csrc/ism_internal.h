@@ -82,6 +82,13 @@ struct JobDev {
     long long tail_cta_base;  // first tail CTA of the job
     long long seam_base;      // first seam record (tiles) of the job
     long long lut_base;       // first entry (float) of the job's windowed-sinc table (LUT form)
+    // backward pass only
+    const float* grad_out;    // dLoss/dh [n_rir][n_S]
+    float* grad_beta;         // [6]
+    float* grad_src;          // [n_src][3]
+    float* grad_rcv;          // [n_rcv][3]
+    long long gpart_base;     // first per-(RIR, bin) gradient record (x 12 floats)
+    long long rgrad_base;     // first per-RIR gradient (float; 12 per RIR)
 };
 
 struct JobTable {
@@ -102,6 +109,8 @@ struct WsPlan {
     size_t seam_off;       // float  [seam_total]
     size_t amp_off;        // float  [rir_total]
     size_t lut_off;        // float  [lut_total]: polyphase windowed-sinc tables (LUT form)
+    size_t gpart_off;      // float  [gpart_total]: backward, per-(RIR, bin) gradients
+    size_t rgrad_off;      // float  [rgrad_total]: backward, per-RIR gradients
     size_t total;
     long long hist_total;
     long long ids_total;
@@ -109,6 +118,8 @@ struct WsPlan {
     long long seam_total;
     long long rir_total;
     long long lut_total;
+    long long gpart_total;
+    long long rgrad_total;
     long long n_scan_blocks;
     long long enum_ctas;
     long long acc_ctas;
@@ -137,6 +148,7 @@ int ism_launch_accum_fp16(const JobTable& t, const WsPlan& p, char* ws, void* st
 int ism_launch_accum_bf16(const JobTable& t, const WsPlan& p, char* ws, void* stream, int* launched);
 int ism_launch_accum_lut(const JobTable& t, const WsPlan& p, char* ws, void* stream, int* launched);
 int ism_launch_lut_tables(const JobTable& t, const WsPlan& p, char* ws, void* stream);
+int ism_launch_adjoint(const JobTable& t, const WsPlan& p, char* ws, void* stream, int* launched);
 int ism_launch_finalize(const JobTable& t, const WsPlan& p, char* ws, void* stream);
 int ism_launch_tail(const JobTable& t, const WsPlan& p, char* ws, void* stream);
 int ism_launch_noise(uint64_t seed, uint32_t rir, uint32_t k0, int n, float* z, void* stream);

@@ -47,6 +47,11 @@ class ism_job(ctypes.Structure):
                 ("out", ctypes.c_void_p), ("env_amp", ctypes.c_void_p)]
 
 
+class ism_grad_job(ctypes.Structure):
+    _fields_ = [("job", ism_job), ("grad_out", ctypes.c_void_p), ("grad_beta", ctypes.c_void_p),
+                ("grad_src", ctypes.c_void_p), ("grad_rcv", ctypes.c_void_p)]
+
+
 # Every symbol include/ism.h declares, with its ctypes signature.
 _P = ctypes.POINTER
 _SIGS = {
@@ -76,6 +81,14 @@ _SIGS = {
     "ism_batch_workspace_size": (ctypes.c_int, [_P(ism_job), ctypes.c_int, ctypes.c_int, _P(ctypes.c_size_t)]),
     "ism_simulate_batch": (ctypes.c_int, [_P(ism_job), ctypes.c_int, ctypes.c_int, ctypes.c_void_p, ctypes.c_size_t,
                                           ctypes.c_void_p]),
+    "ism_backward_workspace_size": (ctypes.c_int, [_P(ism_grad_job), ctypes.c_int, _P(ctypes.c_size_t)]),
+    "ism_simulate_backward_batch": (ctypes.c_int, [_P(ism_grad_job), ctypes.c_int, ctypes.c_void_p, ctypes.c_size_t,
+                                                   ctypes.c_void_p]),
+    "ism_simulate_backward": (ctypes.c_int, [_P(ism_room), ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p,
+                                             ctypes.c_int, _P(ctypes.c_int), ctypes.c_float, ctypes.c_float,
+                                             ctypes.c_float, ctypes.c_float, ctypes.c_void_p, ctypes.c_void_p,
+                                             ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t,
+                                             ctypes.c_void_p]),
     "ism_diffuse_noise": (ctypes.c_int, [ctypes.c_uint64, ctypes.c_uint32, ctypes.c_uint32, ctypes.c_int,
                                          ctypes.c_void_p, ctypes.c_void_p]),
     "ism_t60_sabine": (ctypes.c_int, [_P(ctypes.c_double), _P(ctypes.c_double), _P(ctypes.c_double)]),
@@ -92,7 +105,7 @@ _SIGS = {
                                         _P(ctypes.c_longlong)]),
 }
 
-STAGES = ["geometry", "enum_count", "scan", "enum_scatter", "accum", "finalize", "tail"]
+STAGES = ["geometry", "enum_count", "scan", "enum_scatter", "accum", "finalize", "tail", "adjoint"]
 
 _lock = threading.Lock()
 _lib = None
@@ -358,6 +371,54 @@ def ism_simulate_batch(jobs: Sequence[ism_job], prec: str = "fp32", workspace: O
     _check(load().ism_simulate_batch(arr, len(jobs), PRECISIONS[prec], ctypes.c_void_p(buf.data_ptr()),
                                      int(buf.numel()), _stream_ptr(stream)))
     return buf
+
+
+def make_grad_job(job: ism_job, grad_out, grad_beta=None, grad_src=None, grad_rcv=None) -> ism_grad_job:
+    """An ism_grad_job: the forward job plus CUDA tensors for dLoss/dh (read)
+    and the three gradients (written); the tensors must stay alive."""
+    g = ism_grad_job()
+    g.job = job
+    g.grad_out = grad_out.data_ptr()
+    g.grad_beta = None if grad_beta is None else grad_beta.data_ptr()
+    g.grad_src = None if grad_src is None else grad_src.data_ptr()
+    g.grad_rcv = None if grad_rcv is None else grad_rcv.data_ptr()
+    return g
+
+
+def ism_backward_workspace_size(gjobs: Sequence[ism_grad_job]) -> int:
+    arr = (ism_grad_job * len(gjobs))(*gjobs)
+    b = ctypes.c_size_t()
+    _check(load().ism_backward_workspace_size(arr, len(gjobs), ctypes.byref(b)))
+    return b.value
+
+
+def ism_simulate_backward_batch(gjobs: Sequence[ism_grad_job], workspace: Optional[Workspace] = None, stream=None):
+    arr = (ism_grad_job * len(gjobs))(*gjobs)
+    b = ctypes.c_size_t()
+    _check(load().ism_backward_workspace_size(arr, len(gjobs), ctypes.byref(b)))
+    buf = _workspace(workspace, b.value)
+    _check(load().ism_simulate_backward_batch(arr, len(gjobs), ctypes.c_void_p(buf.data_ptr()), int(buf.numel()),
+                                              _stream_ptr(stream)))
+    return buf
+
+
+def ism_simulate_backward(L, beta, pos_src, pos_rcv, nb_img, Tmax, fs, grad_out, Tdiff=0.0, Tw=0.0, c=343.0,
+                          workspace: Optional[Workspace] = None, stream=None):
+    """(grad_beta [6], grad_src [n_src, 3], grad_rcv [n_rcv, 3]) CUDA tensors for
+    dLoss/dh = grad_out [n_src, n_rcv, n_S] through the image-source samples."""
+    torch = _torch()
+    dev = torch.device("cuda", torch.cuda.current_device())
+    ps = torch.as_tensor(pos_src, dtype=torch.float32).to(dev).reshape(-1, 3).contiguous()
+    pr = torch.as_tensor(pos_rcv, dtype=torch.float32).to(dev).reshape(-1, 3).contiguous()
+    go = torch.as_tensor(grad_out, dtype=torch.float32).to(dev).contiguous()
+    gb = torch.empty(6, dtype=torch.float32, device=dev)
+    gs = torch.empty((ps.shape[0], 3), dtype=torch.float32, device=dev)
+    gr = torch.empty((pr.shape[0], 3), dtype=torch.float32, device=dev)
+    job = make_job(L, beta, ps, pr, nb_img, Tmax, fs, go, Tdiff=Tdiff, Tw=Tw, c=c)
+    job.out = None
+    gj = make_grad_job(job, go, gb, gs, gr)
+    ism_simulate_backward_batch([gj], workspace=workspace, stream=stream)
+    return gb, gs, gr
 
 
 def ism_diffuse_noise(seed: int, rir: int, k0: int, n: int, stream=None):
