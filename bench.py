@@ -244,6 +244,177 @@ def run_reference(args, rank):
     print(json.dumps(line), flush=True)
 
 
+def _pct(v, q):
+    return float(np.percentile(np.asarray(v), q)) if len(v) else None
+
+
+def run_serving(args):
+    """The serving stream: rooms with sides U(3, 10) m, T60 U(0.2, 1.0) s, one
+    source and 1-16 receivers, 16 kHz, Tdiff = min(0.25 s, T60), Tmax = T60,
+    through the continuous-batching server.  Three arrival patterns of
+    `--requests` requests each: all at once (saturated), then Poisson at 0.5x
+    and 0.8x the saturated request rate.  Latency = submission to RIRs in the
+    caller's host buffer, measured by the server."""
+    import threading
+    from paper_1810_11359_gb300 import ism
+
+    def feasible(L, rt):
+        try:
+            ism.ism_beta_sabine(L, rt)
+            return True
+        except ism.IsmError:
+            return False
+
+    def prepared(rate):
+        out = []
+        for r in workloads.serving_requests(args.requests, seed=4, rate_hz=rate, feasible=feasible):
+            room = r.room
+            Tdiff = min(0.25, room.rt60)
+            out.append((r.arrival_s, dict(L=room.L, beta=ism.ism_beta_sabine(room.L, room.rt60), pos_src=room.pos_src,
+                                          pos_rcv=room.pos_rcv,
+                                          nb_img=ism.ism_nb_img_from_t(Tdiff, room.L, room.c, room.window()),
+                                          Tmax=room.Tmax, fs=room.fs, Tdiff=Tdiff, Tw=room.window(), seed=i_seed(r))))
+        return out
+
+    def i_seed(r):
+        return int(r.arrival_s * 1e6) & 0xFFFFFFFF
+
+    def run(srv, reqs):
+        n = len(reqs)
+        tickets = [None] * n
+        lat = [0.0] * n
+        ready = threading.Semaphore(0)
+
+        def waiter():
+            for i in range(n):
+                ready.acquire()
+                lat[i] = srv.wait(tickets[i][0])
+
+        th = threading.Thread(target=waiter)
+        th.start()
+        t0 = time.perf_counter()
+        for i, (arr, a) in enumerate(reqs):
+            dt = t0 + arr - time.perf_counter()
+            if dt > 2e-3:
+                time.sleep(dt - 1e-3)
+            while time.perf_counter() < t0 + arr:
+                pass
+            tickets[i] = srv.submit(a["L"], a["beta"], a["pos_src"], a["pos_rcv"], a["nb_img"], a["Tmax"], a["fs"],
+                                    Tdiff=a["Tdiff"], Tw=a["Tw"], seed=a["seed"])
+            ready.release()
+        th.join()
+        dur = time.perf_counter() - t0
+        rirs = sum(a["pos_src"].shape[0] * a["pos_rcv"].shape[0] for _, a in reqs)
+        return {"requests": n, "rirs": rirs, "seconds": dur, "rirs_per_s": rirs / dur, "requests_per_s": n / dur,
+                "p50_ms": _pct(lat, 50) * 1e3, "p99_ms": _pct(lat, 99) * 1e3, "max_ms": max(lat) * 1e3}
+
+    srv = ism.Server(hbm_budget=8 << 30, max_inflight=3, max_batch=32, prec=args.prec)
+    warm = prepared(None)[:300]
+    run(srv, warm)
+    sat_reqs = prepared(None)
+    ism.ism_profile_reset()
+    sat = run(srv, sat_reqs)
+    st_sat = srv.stats()
+    res = {"saturated": sat}
+    for f in (0.5, 0.8):
+        res[f"poisson_{f}x"] = run(srv, prepared(f * sat["requests_per_s"]))
+    st = srv.stats()
+    srv.close()
+    line = {
+        "metric": METRIC, "value": sat["rirs_per_s"], "unit": UNIT, "n_gpus": 1, "steps": 1, "warmup": 1,
+        "ms_per_step": sat["seconds"] * 1e3, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": DTYPES[args.prec], "data": "synthetic (seeded serving stream)",
+        "config": {"workload": "serving_3-10m_rt0.2-1.0_1-16rcv_16k", "requests_per_pattern": args.requests,
+                   "hbm_budget_bytes": 8 << 30, "max_inflight": 3, "max_batch": 32,
+                   "latency": "submission to RIRs in host memory, server clock"},
+        "serving": res,
+        "p50_ms": res["poisson_0.8x"]["p50_ms"], "p99_ms": res["poisson_0.8x"]["p99_ms"],
+        "server_stats": {"batches": st["batches"], "inflight_peak": st["inflight_peak"],
+                         "dev_peak_bytes": st["dev_peak"], "batches_saturated": st_sat["batches"]},
+        "e2e": {"value": sat["rirs_per_s"], "unit": UNIT, "h2d_bytes_per_step": None, "d2h_bytes_per_step": None,
+                "entry": "ism_server_submit / ism_server_wait (host positions in, host RIRs out)"},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def run_differentiation(args, world, rank, dist):
+    """One training step per timed step: 256 rooms (sides U(4, 8) m, T60
+    U(0.3, 0.8) s, 1 source + 1 receiver, 16 kHz, 0.4 s) forward through the
+    autograd front end, L2 loss against fixed targets (the RIRs of the rooms
+    with beta x 0.97 and positions moved by N(0, 5 cm)), backward through the
+    adjoint kernel."""
+    import torch
+    from paper_1810_11359_gb300 import ism, torch_ism
+
+    rooms = workloads.differentiation_rooms()
+    scale, dps, dpr = workloads.differentiation_perturbation()
+    B = len(rooms)
+    L = np.stack([r.L for r in rooms])
+    beta0 = np.stack([ism.ism_beta_sabine(r.L, r.rt60) for r in rooms])
+    ps0 = np.stack([r.pos_src for r in rooms]).astype(np.float32)
+    pr0 = np.stack([r.pos_rcv for r in rooms]).astype(np.float32)
+    Tw = rooms[0].window()
+    nb = np.stack([ism.ism_nb_img_from_t(0.4, r.L, 343.0, Tw) for r in rooms])
+    dev = torch.device("cuda", torch.cuda.current_device())
+    ws_f, ws_b = ism.Workspace(dev), ism.Workspace(dev)
+    with torch.no_grad():
+        target = torch_ism.rir(L, torch.as_tensor(beta0 * scale, dtype=torch.float32),
+                               torch.as_tensor(ps0 + dps[:, None].astype(np.float32)).to(dev),
+                               torch.as_tensor(pr0 + dpr[:, None].astype(np.float32)).to(dev), 0.4, 16000.0, Tw=Tw,
+                               nb_img=nb)
+    beta = torch.tensor(beta0, dtype=torch.float32, requires_grad=True)
+    ps = torch.tensor(ps0, device=dev, requires_grad=True)
+    pr = torch.tensor(pr0, device=dev, requires_grad=True)
+
+    def step():
+        h = torch_ism.rir(L, beta, ps, pr, 0.4, 16000.0, Tw=Tw, nb_img=nb, workspace=ws_f)
+        loss = ((h - target) ** 2).sum()
+        beta.grad = ps.grad = pr.grad = None
+        loss.backward()
+        return loss
+
+    for _ in range(max(args.warmup, 3)):
+        step()
+    torch.cuda.synchronize()
+    ism.ism_profile_reset()
+    ism.ism_profile_enable(True)
+    flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.float32, device=dev)
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    walls = []
+    for a, b in evs:
+        flush.zero_()
+        torch.cuda.synchronize()
+        w0 = time.perf_counter()
+        a.record()
+        loss = step()
+        b.record()
+        torch.cuda.synchronize()
+        walls.append(time.perf_counter() - w0)
+    ism.ism_profile_enable(False)
+    prof = ism.ism_profile_read()
+    ms = sum(a.elapsed_time(b) for a, b in evs) / len(evs)
+    wall = sum(walls) / len(walls)
+    dev_ms = sum(v[0] for v in prof.values()) / args.steps
+    line = {
+        "metric": METRIC, "value": B / (ms * 1e-3), "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": max(args.warmup, 3), "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic (seeded rooms and perturbed targets)",
+        "config": {"workload": "differentiation_256rooms_4-8m_rt0.3-0.8_16k_0.4s", "rooms_per_step": B,
+                   "step": "forward + L2 loss + backward (beta, source, receiver gradients)",
+                   "l2": "flushed between timed steps (256 MB write)"},
+        "training_steps_per_sec": 1e3 / ms,
+        "library_device_ms_per_step": dev_ms,
+        "stage_ms_per_step": {k: v[0] / args.steps for k, v in prof.items()},
+        "gpu_launches": int(sum(v[1] for v in prof.values())),
+        "e2e": {"value": B / wall, "unit": UNIT, "h2d_bytes_per_step": int(beta0.nbytes // 2),
+                "d2h_bytes_per_step": 0, "ms_per_step": wall * 1e3,
+                "entry": "torch_ism.rir + loss.backward() (beta read to the host each step)"},
+        "loss": float(loss.item()),
+    }
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -251,7 +422,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", default="batched", choices=["batched", "trajectory"])
+    ap.add_argument("--workload", default="batched", choices=["batched", "trajectory", "serving", "differentiation"])
+    ap.add_argument("--requests", type=int, default=20000, help="serving: requests per arrival pattern")
     ap.add_argument("--prec", default="fp32", choices=list(PREC_ID))
     args = ap.parse_args()
 
@@ -277,6 +449,19 @@ def main():
     else:
         torch.cuda.set_device(0)
     from paper_1810_11359_gb300 import ism
+
+    if args.workload == "serving":
+        if rank == 0:
+            run_serving(args)
+        if world > 1:
+            dist.barrier()
+            dist.destroy_process_group()
+        return
+    if args.workload == "differentiation":
+        run_differentiation(args, world, rank, dist)
+        if world > 1:
+            dist.destroy_process_group()
+        return
 
     room, Tdiff, T_img = workload(args.workload)
     beta = ism.ism_beta_sabine(room.L, room.rt60)

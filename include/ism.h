@@ -213,6 +213,72 @@ ism_status ism_simulate_batch(const ism_job* jobs, int n_jobs, ism_precision pre
                               size_t ws_bytes, void* stream);
 
 /* ------------------------------------------------------------------------- */
+/* Serving: continuous batching of RIR requests                              */
+/* ------------------------------------------------------------------------- */
+/* A request loop for RIR generation on one GPU (the paper has no serving
+ * layer; each request is one ism_job, computed exactly as ism_simulate would).
+ * The server holds one device allocation of `hbm_budget` bytes and one pinned
+ * host allocation of `host_budget` bytes for its whole life, and carves every
+ * request's positions and RIRs and every batch's workspace out of them.  A
+ * launcher thread takes queued requests in arrival order and admits them into
+ * a batch while memory and a stream are free (up to max_batch requests), then
+ * runs the batch (ism_simulate_batch) on its own stream: up to max_inflight
+ * batches run on the GPU at once, so requests arriving while others are on
+ * the GPU start as soon as memory and a stream free up.  A completer thread
+ * retires finished batches, copies each result to its caller's buffer, frees
+ * the memory and wakes the launcher.  A request is computed with the same
+ * arithmetic whatever batch it lands in: its RIRs are bit-identical alone and
+ * in any mix. */
+typedef struct ism_server ism_server;
+typedef uint64_t ism_ticket;
+
+typedef struct {
+    size_t hbm_budget;    /* device bytes the server allocates at create (>= 16 MiB)   */
+    size_t host_budget;   /* pinned host bytes for staging (0: hbm_budget / 4)        */
+    int max_inflight;     /* batches on the GPU at once, one stream each (0: 3; <= 16) */
+    int max_batch;        /* requests per batch (0: 32; <= 256)                       */
+    int device;           /* CUDA device ordinal                                      */
+    ism_precision prec;   /* tap arithmetic of every request                          */
+} ism_server_config;
+
+typedef struct {
+    long long submitted, completed, failed, batches;
+    size_t dev_in_use, dev_peak, host_in_use;
+    int inflight, queued;
+    int inflight_peak;    /* most batches seen on the GPU at once */
+} ism_server_stats;
+
+/* Creates a server (allocates its two pools, two threads and its streams).
+ * ISM_ERR_OOM if the pools cannot be allocated, ISM_ERR_CUDA without a device. */
+ism_status ism_server_create(const ism_server_config* cfg, ism_server** server);
+
+/* Queues one request.  job->pos_src and job->pos_rcv are HOST pointers, copied
+ * before this returns; job->out is a HOST pointer of n_src * n_rcv * n_S FP32
+ * that the server writes before the request is reported done (it must stay
+ * valid until then); job->env_amp must be NULL.  The job is validated here
+ * (arguments as for ism_simulate, positions strictly inside the room):
+ * errors return at once and no ticket is issued.  A request whose memory can
+ * never fit the budget is rejected with ISM_ERR_OOM. */
+ism_status ism_server_submit(ism_server* server, const ism_job* job, ism_ticket* ticket);
+
+/* *done = 1 if the request has finished (successfully or not), else 0. */
+ism_status ism_server_poll(ism_server* server, ism_ticket ticket, int* done);
+
+/* Waits up to timeout_s seconds (< 0: no limit) for the request.  Returns
+ * ISM_ERR_TIMEOUT if it is still running (the ticket stays valid); otherwise
+ * the request's own status (ISM_OK, or the error that failed it, or
+ * ISM_ERR_CANCELLED) and releases the ticket.  latency_s (may be NULL)
+ * receives the time from submission to the result being in job->out. */
+ism_status ism_server_wait(ism_server* server, ism_ticket ticket, double timeout_s, double* latency_s);
+
+/* Counters and memory use. */
+ism_status ism_server_stats_read(ism_server* server, ism_server_stats* stats);
+
+/* Finishes the batches already on the GPU, cancels the queued requests,
+ * stops the threads and frees everything.  Tickets are invalid afterwards. */
+ism_status ism_server_destroy(ism_server* server);
+
+/* ------------------------------------------------------------------------- */
 /* Gradients (adjoint of eq. (1)-(6))                                        */
 /* ------------------------------------------------------------------------- */
 /* The paper computes RIRs only; the adjoint is the chain rule through its

@@ -528,6 +528,17 @@ ism_status check_prec(ism_precision prec)
 
 }  // namespace
 
+ism_status ism_fail_message(ism_status s, const char* fmt, ...)
+{
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    g_last_error = buf;
+    return s;
+}
+
 extern "C" {
 
 const char* ism_status_string(ism_status s)

@@ -137,6 +137,9 @@ __host__ __device__ constexpr int ism_lut_phases(int slots)
     return slots <= 1 ? 256 : slots == 2 ? 128 : slots <= 4 ? 64 : 32;
 }
 
+// Sets the calling thread's ism_last_error_message() and returns s.
+ism_status ism_fail_message(ism_status s, const char* fmt, ...);
+
 // Launch entry points (implemented in the .cu files, called by ism_api.cu).
 // Each returns 0 or a cudaError_t value.
 int ism_launch_geometry(const JobTable& t, const WsPlan& p, char* ws, void* stream);

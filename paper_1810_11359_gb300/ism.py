@@ -23,6 +23,8 @@ STATUS_NAMES = {0: "ISM_OK", 1: "ISM_ERR_INVALID_ARG", 2: "ISM_ERR_INFEASIBLE", 
                 4: "ISM_ERR_OOM", 5: "ISM_ERR_CUDA", 6: "ISM_ERR_TIMEOUT", 7: "ISM_ERR_DEVICE_CHECK",
                 8: "ISM_ERR_UNSUPPORTED", 9: "ISM_ERR_CANCELLED"}
 PRECISIONS = {"fp32": 0, "fp16x2": 1, "bf16x2": 2, "lut": 3}
+ISM_ERR_TIMEOUT_CODE = 6
+STATUS_CODES = {v: k for k, v in STATUS_NAMES.items()}
 DEVICE_FLAG_POSITION = 1
 DEVICE_FLAG_BIN = 2
 
@@ -50,6 +52,18 @@ class ism_job(ctypes.Structure):
 class ism_grad_job(ctypes.Structure):
     _fields_ = [("job", ism_job), ("grad_out", ctypes.c_void_p), ("grad_beta", ctypes.c_void_p),
                 ("grad_src", ctypes.c_void_p), ("grad_rcv", ctypes.c_void_p)]
+
+
+class ism_server_config(ctypes.Structure):
+    _fields_ = [("hbm_budget", ctypes.c_size_t), ("host_budget", ctypes.c_size_t), ("max_inflight", ctypes.c_int),
+                ("max_batch", ctypes.c_int), ("device", ctypes.c_int), ("prec", ctypes.c_int)]
+
+
+class ism_server_stats(ctypes.Structure):
+    _fields_ = [("submitted", ctypes.c_longlong), ("completed", ctypes.c_longlong), ("failed", ctypes.c_longlong),
+                ("batches", ctypes.c_longlong), ("dev_in_use", ctypes.c_size_t), ("dev_peak", ctypes.c_size_t),
+                ("host_in_use", ctypes.c_size_t), ("inflight", ctypes.c_int), ("queued", ctypes.c_int),
+                ("inflight_peak", ctypes.c_int)]
 
 
 # Every symbol include/ism.h declares, with its ctypes signature.
@@ -81,6 +95,12 @@ _SIGS = {
     "ism_batch_workspace_size": (ctypes.c_int, [_P(ism_job), ctypes.c_int, ctypes.c_int, _P(ctypes.c_size_t)]),
     "ism_simulate_batch": (ctypes.c_int, [_P(ism_job), ctypes.c_int, ctypes.c_int, ctypes.c_void_p, ctypes.c_size_t,
                                           ctypes.c_void_p]),
+    "ism_server_create": (ctypes.c_int, [_P(ism_server_config), _P(ctypes.c_void_p)]),
+    "ism_server_submit": (ctypes.c_int, [ctypes.c_void_p, _P(ism_job), _P(ctypes.c_uint64)]),
+    "ism_server_poll": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_uint64, _P(ctypes.c_int)]),
+    "ism_server_wait": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_uint64, ctypes.c_double, _P(ctypes.c_double)]),
+    "ism_server_stats_read": (ctypes.c_int, [ctypes.c_void_p, _P(ism_server_stats)]),
+    "ism_server_destroy": (ctypes.c_int, [ctypes.c_void_p]),
     "ism_backward_workspace_size": (ctypes.c_int, [_P(ism_grad_job), ctypes.c_int, _P(ctypes.c_size_t)]),
     "ism_simulate_backward_batch": (ctypes.c_int, [_P(ism_grad_job), ctypes.c_int, ctypes.c_void_p, ctypes.c_size_t,
                                                    ctypes.c_void_p]),
@@ -448,3 +468,90 @@ def ism_profile_read():
         _check(load().ism_profile_read(i, ctypes.byref(ms), ctypes.byref(ln), ctypes.byref(cl)))
         res[name] = (ms.value, ln.value, cl.value)
     return res
+
+
+# --------------------------------------------------------------------------- #
+# Serving
+# --------------------------------------------------------------------------- #
+class Server:
+    """Continuous-batching RIR server (ism_server_*): submit host-side requests,
+    wait for their RIRs.  The ctypes calls release the GIL, so submissions and
+    waits from several Python threads run concurrently."""
+
+    def __init__(self, hbm_budget: int = 4 << 30, host_budget: int = 0, max_inflight: int = 3, max_batch: int = 32,
+                 device: int = 0, prec: str = "fp32"):
+        cfg = ism_server_config(int(hbm_budget), int(host_budget), int(max_inflight), int(max_batch), int(device),
+                                PRECISIONS[prec])
+        h = ctypes.c_void_p()
+        _check(load().ism_server_create(ctypes.byref(cfg), ctypes.byref(h)))
+        self._h = h
+        self._outs = {}
+        self._lock = threading.Lock()
+
+    def submit(self, L, beta, pos_src, pos_rcv, nb_img, Tmax, fs, Tdiff=0.0, Tw=0.0, c=343.0, seed=0,
+               out: Optional[np.ndarray] = None):
+        """Queues one room; returns (ticket, out) where `out` [n_src, n_rcv, n_S]
+        FP32 receives the RIRs once the ticket is done."""
+        ps = np.ascontiguousarray(np.asarray(pos_src, dtype=np.float32).reshape(-1, 3))
+        pr = np.ascontiguousarray(np.asarray(pos_rcv, dtype=np.float32).reshape(-1, 3))
+        n_S = ism_rir_length(Tmax, fs)
+        if out is None:
+            out = np.empty((ps.shape[0], pr.shape[0], n_S), dtype=np.float32)
+        assert out.dtype == np.float32 and out.flags["C_CONTIGUOUS"] and out.size == ps.shape[0] * pr.shape[0] * n_S
+        j = ism_job()
+        j.room = _room(L, beta, c)
+        j.pos_src = ps.ctypes.data
+        j.n_src = ps.shape[0]
+        j.pos_rcv = pr.ctypes.data
+        j.n_rcv = pr.shape[0]
+        for a in range(3):
+            j.nb_img[a] = int(nb_img[a])
+        j.Tmax, j.fs, j.Tdiff, j.Tw = float(Tmax), float(fs), float(Tdiff or 0.0), float(Tw or 0.0)
+        j.seed = int(seed) & (2 ** 64 - 1)
+        j.out = out.ctypes.data
+        j.env_amp = None
+        t = ctypes.c_uint64()
+        _check(load().ism_server_submit(self._h, ctypes.byref(j), ctypes.byref(t)))
+        with self._lock:
+            self._outs[t.value] = out
+        return t.value, out
+
+    def poll(self, ticket: int) -> bool:
+        d = ctypes.c_int()
+        _check(load().ism_server_poll(self._h, ctypes.c_uint64(ticket), ctypes.byref(d)))
+        return bool(d.value)
+
+    def wait(self, ticket: int, timeout_s: float = -1.0) -> float:
+        """Blocks until the request is done; returns its submit-to-ready latency
+        in seconds.  Raises IsmError with the request's status if it failed
+        (ISM_ERR_TIMEOUT leaves the ticket valid)."""
+        lat = ctypes.c_double()
+        st = load().ism_server_wait(self._h, ctypes.c_uint64(ticket), float(timeout_s), ctypes.byref(lat))
+        if st != ISM_ERR_TIMEOUT_CODE:
+            with self._lock:
+                self._outs.pop(ticket, None)
+        _check(st)
+        return lat.value
+
+    def stats(self) -> dict:
+        s = ism_server_stats()
+        _check(load().ism_server_stats_read(self._h, ctypes.byref(s)))
+        return {k: getattr(s, k) for k, _ in ism_server_stats._fields_}
+
+    def close(self):
+        if self._h:
+            _check(load().ism_server_destroy(self._h))
+            self._h = None
+            self._outs.clear()
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

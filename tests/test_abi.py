@@ -114,3 +114,30 @@ def test_host_entry_rejects_outside_positions_without_device_work(lib):
                                None, 0, None)
     assert st == 1
     assert "outside" in lib.ism_last_error_message().decode()
+
+
+def test_server_config_is_checked_before_any_device_work(lib):
+    cfg = ism.ism_server_config(64 << 20, 0, 99, 32, 0, 0)        # max_inflight out of range
+    h = ctypes.c_void_p()
+    assert lib.ism_server_create(ctypes.byref(cfg), ctypes.byref(h)) == 1
+    cfg = ism.ism_server_config(1 << 20, 0, 2, 32, 0, 0)          # budget below 16 MiB
+    assert lib.ism_server_create(ctypes.byref(cfg), ctypes.byref(h)) == 1
+    assert h.value is None
+    assert lib.ism_server_submit(None, None, None) == 1
+    assert lib.ism_server_destroy(None) == 1
+
+
+def test_backward_validates_like_the_forward(lib):
+    gj = ism.ism_grad_job()
+    gj.job.room = ism._room([3, 4, 2.5], [0.7] * 6, 343.0)
+    gj.job.n_src = gj.job.n_rcv = 1
+    for a in range(3):
+        gj.job.nb_img[a] = 5
+    gj.job.Tmax, gj.job.fs, gj.job.Tw = 0.1, 16000.0, 32 / 16000
+    b = ctypes.c_size_t()
+    assert lib.ism_backward_workspace_size(ctypes.byref(gj), 1, ctypes.byref(b)) == 0
+    assert b.value > 0
+    # missing grad_out / positions: rejected before any launch
+    assert lib.ism_simulate_backward_batch(ctypes.byref(gj), 1, None, 0, None) == 1
+    gj.job.fs = -1.0
+    assert lib.ism_backward_workspace_size(ctypes.byref(gj), 1, ctypes.byref(b)) == 1
