@@ -118,6 +118,9 @@ ism_status plan(const Validated* vs, int n, ism_precision prec, bool backward, J
     std::memset(&t, 0, sizeof t);
     std::memset(&p, 0, sizeof p);
     t.n_jobs = n;
+    long long set_cols = 0;   // grid columns x RIRs over the launch set
+    for (int i = 0; i < n; ++i)
+        set_cols += (long long)vs[i].job.nb_img[0] * vs[i].job.nb_img[1] * vs[i].job.n_src * vs[i].job.n_rcv;
     long long rir = 0, hist = 0, tbl = 0, ecta = 0, acta = 0, tcta = 0, seam = 0, ids = 0, lut = 0, gpart = 0;
     for (int i = 0; i < n; ++i) {
         const Validated& v = vs[i];
@@ -154,12 +157,14 @@ ism_status plan(const Validated* vs, int n, ism_precision prec, bool backward, J
         J.Q = (v.n_ism + v.H) / ISM_SB + 1;
         J.img_per_rir = (long long)in.nb_img[0] * in.nb_img[1] * in.nb_img[2];
         // enumeration units: contiguous column ranges, about 16k warps over the
-        // job (enough to hide the latency of the walk), at most 512 columns each
+        // launch set (enough to hide the latency of the walk while keeping the
+        // per-unit histogram small), at most 512 columns each
         {
             const long long cols = (long long)in.nb_img[0] * in.nb_img[1];
-            long long cpu = (cols * J.n_rir + 16383) / 16384;
+            long long cpu = (set_cols + 16383) / 16384;
             if (cpu < 1) cpu = 1;
             if (cpu > 512) cpu = 512;
+            if (cpu > cols) cpu = cols;
             J.cols_per_unit = (int)cpu;
             J.U = (int)((cols + cpu - 1) / cpu);
         }

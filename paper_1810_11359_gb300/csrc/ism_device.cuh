@@ -8,15 +8,20 @@
 
 // ---------------------------------------------------------------------------
 // Job lookup: the kernels of a launch set enumerate their CTAs across the
-// jobs of the table; job j owns CTAs [base_j, base_{j+1}).
+// jobs of the table; job j owns CTAs [base_j, base_{j+1}).  Bases never
+// decrease; a job without CTAs of a kind shares its base with the next one,
+// so the owner is the last job whose base is <= cta (binary search).
 // ---------------------------------------------------------------------------
 template <typename F>
 __device__ __forceinline__ int ism_find_job(const JobTable& t, long long cta, F base_of)
 {
-    int j = 0;
-    for (int k = 1; k < t.n_jobs; ++k)
-        if (cta >= base_of(t.j[k])) j = k;
-    return j;
+    int lo = 0, hi = t.n_jobs - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (base_of(t.j[mid]) <= cta) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
 }
 
 // ---------------------------------------------------------------------------

@@ -35,7 +35,7 @@
 #define ISM_TILE_BINS (ISM_TILE_SAMPLES / ISM_SB)   // 8 bins per tile
 #define ISM_ACC_WARPS ISM_TILE_BINS                 // one warp per bin
 #define ISM_ENUM_WARPS 4          // warps per enumeration CTA (one unit each)
-#define ISM_MAX_JOBS 32           // jobs per launch set (kernel-parameter table)
+#define ISM_MAX_JOBS 64           // jobs per launch set (kernel-parameter table, < 32 KB)
 #define ISM_MAX_AXIS 1023         // images per axis (10-bit packed ids)
 #define ISM_MAX_SLOTS 8           // taps per lane per image: N_w <= 256
 #define ISM_MAX_NISM 131000       // image-source samples per RIR
@@ -98,6 +98,8 @@ struct JobTable {
     int pad;
     JobDev j[ISM_MAX_JOBS];
 };
+
+static_assert(sizeof(JobTable) <= 32000, "the job table is passed as one kernel parameter");
 
 // Workspace carve-up of one launch set (byte offsets into the workspace).
 struct WsPlan {
