@@ -50,8 +50,8 @@ UNIT = "RIR/s"
 FMA_OPS_PER_CONTRIBUTION = 5   # FADD (j - f), 2 FFMA (window), FMUL, FFMA (accumulate)
 L2_BYTES = 129 * 1024 * 1024
 DTYPES = {"fp32": "f32", "fp16x2": "f16x2 taps, f32 accumulation", "bf16x2": "bf16x2 taps, f32 accumulation",
-          "lut": "f32 windowed-sinc table, f32 accumulation"}
-PREC_ID = {"fp32": 0, "fp16x2": 1, "bf16x2": 2, "lut": 3}
+          "lut": "f32 windowed-sinc table, f32 accumulation", "fp32_direct": "f32 (every tap evaluated)"}
+PREC_ID = {"fp32": 0, "fp16x2": 1, "bf16x2": 2, "lut": 3, "fp32_direct": 4}
 
 
 def _peaks():

@@ -61,12 +61,20 @@ typedef enum {
 /* Arithmetic of the windowed-sinc evaluation (Section 3.5 LUT, Section 3.6
  * mixed precision).  Image enumeration, distances and delays are always
  * FP32 (with a float-float delay, so fractional delays keep FP32 accuracy);
- * accumulation is always FP32. */
+ * accumulation is always FP32.
+ *   ISM_PREC_FP32: for a window of exactly 32 taps, the windowed sinc of tap
+ *   j as a function of the fractional delay f, delta'(j - f), is expanded in
+ *   Chebyshev polynomials of 2f - 1 (degree 9, error < 3e-9 of the image's
+ *   amplitude, below FP32 rounding); the images of a delay bin that share
+ *   their integer offset are summed as 10 moments sum A T_i(2f - 1), and
+ *   each offset's moments are expanded once into the 32 taps.  Other
+ *   windows use the direct evaluation of ISM_PREC_FP32_DIRECT. */
 typedef enum {
-    ISM_PREC_FP32 = 0,    /* FP32 sin/cos/reciprocal                                  */
-    ISM_PREC_FP16X2 = 1,  /* packed FP16 window and sinc, FP32 accumulation           */
-    ISM_PREC_BF16X2 = 2,  /* packed BF16 window and sinc, FP32 accumulation           */
-    ISM_PREC_LUT = 3      /* 4096-entry FP32 windowed-sinc table (eq. (9)), FP32 lerp */
+    ISM_PREC_FP32 = 0,        /* FP32, Chebyshev moments (32-tap windows), else direct */
+    ISM_PREC_FP16X2 = 1,      /* packed FP16 window and sinc, FP32 accumulation        */
+    ISM_PREC_BF16X2 = 2,      /* packed BF16 window and sinc, FP32 accumulation        */
+    ISM_PREC_LUT = 3,         /* FP32 windowed-sinc table (eq. (9)), FP32 lerp         */
+    ISM_PREC_FP32_DIRECT = 4  /* FP32 sin/cos/reciprocal for every image tap (eq. (6)) */
 } ism_precision;
 
 /* A shoebox room (Section 2.1).  beta is ordered x0, x1, y0, y1, z0, z1:

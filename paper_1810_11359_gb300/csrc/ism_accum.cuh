@@ -5,8 +5,11 @@
 // translation unit of its own (ism_accum.cu, ism_accum_fp16.cu,
 // ism_accum_bf16.cu, ism_accum_lut.cu).
 //
-// One CTA owns a tile of 256 output samples of one RIR, i.e. 8 delay bins of
-// 32 samples, one per warp.  An image of bin q has delay s = b + f (b integer,
+// One CTA owns ism_acc_bins(PREC) delay bins of 32 samples of one RIR, one
+// warp per bin; warps share nothing but the per-axis tables, so a CTA holds few
+// resources and finishes as soon as its bins do (no end-of-tile barrier: the
+// schedule balances itself across many small CTAs).  An image of bin q has
+// delay s = b + f (b integer,
 // f in [0, 1)) with b = 32 q + rr, rr in [-1, 31] (the enumeration binned it
 // by its plain-FP32 delay).  Its taps are the samples k with |k - s| < N_w/2:
 // j = k - b in [-H + 1, H], H = N_w / 2.
@@ -59,11 +62,9 @@
 // offsets (Section 2.1 factorisation), so f keeps FP32 resolution even for
 // delays of tens of thousands of samples.
 //
-// After its bins the CTA sums, for each sample, the window rows of the bins
-// overlapping it in ascending bin order and stores it once.  The first and
-// the last 32 SLOTS samples of the tile region also receive contributions
-// from the neighbouring tiles; they go to a seam buffer that the finalize
-// kernel combines, again in a fixed order.
+// Each warp stores its bin's window row (32 (SLOTS + 1) samples, coalesced)
+// once; the finalize kernel adds, for every sample, the rows of the SLOTS + 1
+// bins covering it in ascending bin order.  Every sum has a fixed order.
 #pragma once
 
 #include <cuda_bf16.h>
@@ -73,7 +74,7 @@
 
 namespace {
 
-#define ISM_PIECE 1024
+#define ISM_PIECE 512              // ids sorted per step (shared memory per warp ~5 KB)
 #define ISM_NB 33                  // delay offsets rr = -1 .. 31 inside a bin
 #define ISM_CHUNK 64               // records computed per step (two per lane)
 #define ISM_PAD (ISM_PIECE + 4 * ISM_NB)
@@ -270,7 +271,7 @@ __device__ __forceinline__ void taps_pair(const uint4 pr, uint32_t ps2, const fl
 }
 
 // Taps of one LUT record {A (1 - phi), A phi, row offset (int bits)}: two
-// rows of the polyphase table, column = tap.
+// rows of the polyphase table in shared memory, column = tap.
 template <int SLOTS, int ROW>
 __device__ __forceinline__ void taps_lut(const float4 rc, const float* __restrict__ lut_lane, float (&D)[SLOTS])
 {
@@ -283,13 +284,13 @@ __device__ __forceinline__ void taps_lut(const float4 rc, const float* __restric
 }
 
 template <int SLOTS, bool MASK, int PREC>
-__global__ void __launch_bounds__(ISM_ACC_WARPS * 32) accum_kernel(const __grid_constant__ JobTable t,
-                                                                    const float4* __restrict__ tbl,
-                                                                    const uint32_t* __restrict__ hist,
-                                                                    const uint32_t* __restrict__ ids,
-                                                                    const float* __restrict__ lut_g,
-                                                                    float* __restrict__ seams,
-                                                                    uint32_t* __restrict__ status)
+__global__ void __launch_bounds__(ism_acc_bins(PREC) * 32) accum_kernel(const __grid_constant__ JobTable t,
+                                                                  const float4* __restrict__ tbl,
+                                                                  const uint32_t* __restrict__ hist,
+                                                                  const uint32_t* __restrict__ ids,
+                                                                  const float* __restrict__ lut_g,
+                                                                  float* __restrict__ rows,
+                                                                  uint32_t* __restrict__ status)
 {
     constexpr bool HALF = PREC == PREC_FP16 || PREC == PREC_BF16;
     constexpr int LQ = ism_lut_phases(SLOTS);   // LUT phases per sample
@@ -299,23 +300,23 @@ __global__ void __launch_bounds__(ISM_ACC_WARPS * 32) accum_kernel(const __grid_
     const int jid = ism_find_job(t, g, [](const JobDev& j) { return j.acc_cta_base; });
     const JobDev& J = t.j[jid];
     const bool exact = (J.Nw == (float)(2 * J.H)) && (2 * J.H == 32 * J.slots);
-    if (J.slots != SLOTS) return;                              // another instantiation handles this job
+    if (J.slots != SLOTS || J.use_cheb) return;                // another kernel handles this job
     if (PREC != PREC_LUT && exact == MASK) return;             // (the LUT carries its own mask)
 
     const long long local = g - J.acc_cta_base;
-    const int r = (int)(local / J.n_tiles);
-    const int tile = J.n_tiles - 1 - (int)(local % J.n_tiles);  // densest (latest) tiles first
+    const int r = (int)(local / J.acc_groups);
+    const int grp = J.acc_groups - 1 - (int)(local % J.acc_groups);  // densest (latest) bins first
     const int Nx = J.N[0], Ny = J.N[1], Nz = J.N[2];
     const int n_axis = Nx + Ny + Nz;
     const int H = J.H;
     constexpr int WIN = 32 * (SLOTS + 1);  // window registers x 32 lanes
 
+    constexpr int BPC = ism_acc_bins(PREC);
     float4* T = reinterpret_cast<float4*>(smem);
     unsigned char* after_T = smem + (size_t)((t.max_axis_sum + 1) & ~1) * sizeof(float4);
     float* lut = reinterpret_cast<float*>(after_T);
     constexpr size_t LUT_BYTES = PREC == PREC_LUT ? (size_t)(LQ + 1) * ROW * sizeof(float) : 0;
     WarpSmem* Wall = reinterpret_cast<WarpSmem*>(after_T + LUT_BYTES);
-    float* rows = reinterpret_cast<float*>(Wall + ISM_ACC_WARPS);  // [bin][WIN]
 
     const float4* Tg = tbl + J.tbl_base + (long long)r * n_axis;
     for (int e = threadIdx.x; e < n_axis; e += blockDim.x) T[e] = Tg[e];
@@ -363,8 +364,7 @@ __global__ void __launch_bounds__(ISM_ACC_WARPS * 32) accum_kernel(const __grid_
     (void)rscale;
 
     {
-        const int b_in_tile = warp;
-        const int q = tile * ISM_TILE_BINS + b_in_tile;
+        const int q = grp * BPC + warp;
 #pragma unroll
         for (int s = 0; s < SLOTS; ++s) {
             D[s] = 0.0f;
@@ -589,30 +589,10 @@ __global__ void __launch_bounds__(ISM_ACC_WARPS * 32) accum_kernel(const __grid_
                 flush_run<SLOTS, PREC == PREC_FP16>(D, acc, cur_rr, lane, dscale);
             }
         }
+        if (q < J.Q) {
+            float* row = rows + J.rows_base + ((long long)r * J.Q + q) * WIN;
 #pragma unroll
-        for (int m = 0; m <= SLOTS; ++m) rows[b_in_tile * WIN + 32 * m + lane] = acc[m];
-    }
-    __syncthreads();
-
-    // sample d of the tile region [256 tile - H, 256 tile - H + 256 + 32 SLOTS):
-    // sum of the bins whose window covers it, in ascending bin order
-    float* out = J.out + (long long)r * J.n_S;
-    float* seam = seams + J.seam_base + ((long long)r * J.n_tiles + tile) * (64LL * SLOTS);
-    const int base0 = ISM_TILE_SAMPLES * tile - H;
-    for (int d = threadIdx.x; d < ISM_TILE_SAMPLES + 32 * SLOTS; d += blockDim.x) {
-        // bins b with 0 <= d - 32 b < WIN
-        const int b_lo = d >= WIN ? (d - WIN) / ISM_SB + 1 : 0;
-        int b_hi = d / ISM_SB;
-        if (b_hi > ISM_TILE_BINS - 1) b_hi = ISM_TILE_BINS - 1;
-        float v = 0.0f;
-        for (int b = b_lo; b <= b_hi; ++b) v += rows[b * WIN + (d - ISM_SB * b)];
-        if (d < 32 * SLOTS) {
-            seam[d] = v;
-        } else if (d >= ISM_TILE_SAMPLES) {
-            seam[32 * SLOTS + (d - ISM_TILE_SAMPLES)] = v;
-        } else {
-            const int k = base0 + d;
-            if (k >= 0 && k < J.n_ism) out[k] = v;
+            for (int m = 0; m <= SLOTS; ++m) row[32 * m + lane] = acc[m];
         }
     }
 }
@@ -620,17 +600,17 @@ __global__ void __launch_bounds__(ISM_ACC_WARPS * 32) accum_kernel(const __grid_
 template <int SLOTS, bool MASK, int PREC>
 int launch_one(const JobTable& t, const WsPlan& p, char* ws, cudaStream_t s)
 {
+    constexpr int BPC = ism_acc_bins(PREC);
     const size_t lut_bytes =
         PREC == PREC_LUT ? (size_t)(ism_lut_phases(SLOTS) + 1) * 32 * SLOTS * sizeof(float) : 0;
-    size_t sm = (size_t)((t.max_axis_sum + 1) & ~1) * sizeof(float4) + lut_bytes +
-                ISM_ACC_WARPS * sizeof(WarpSmem) + (size_t)ISM_TILE_BINS * 32 * (SLOTS + 1) * sizeof(float);
+    size_t sm = (size_t)((t.max_axis_sum + 1) & ~1) * sizeof(float4) + lut_bytes + BPC * sizeof(WarpSmem);
     cudaError_t e = cudaFuncSetAttribute(accum_kernel<SLOTS, MASK, PREC>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (e != cudaSuccess) return (int)e;
-    accum_kernel<SLOTS, MASK, PREC><<<(unsigned)p.acc_ctas, ISM_ACC_WARPS * 32, sm, s>>>(
+    accum_kernel<SLOTS, MASK, PREC><<<(unsigned)p.acc_ctas, BPC * 32, sm, s>>>(
         t, reinterpret_cast<const float4*>(ws + p.tbl_off), reinterpret_cast<const uint32_t*>(ws + p.hist_off),
         reinterpret_cast<const uint32_t*>(ws + p.ids_off), reinterpret_cast<const float*>(ws + p.lut_off),
-        reinterpret_cast<float*>(ws + p.seam_off), reinterpret_cast<uint32_t*>(ws + p.status_off));
+        reinterpret_cast<float*>(ws + p.rows_off), reinterpret_cast<uint32_t*>(ws + p.status_off));
     return (int)cudaGetLastError();
 }
 
@@ -645,6 +625,7 @@ int launch_accum_prec(const JobTable& t, const WsPlan& p, char* ws, void* stream
     bool need[2][ISM_MAX_SLOTS + 1] = {};
     for (int i = 0; i < t.n_jobs; ++i) {
         const JobDev& J = t.j[i];
+        if (J.use_cheb) continue;
         bool exact = (J.Nw == (float)(2 * J.H)) && (2 * J.H == 32 * J.slots);
         need[(exact || PREC == PREC_LUT) ? 0 : 1][J.slots] = true;
     }

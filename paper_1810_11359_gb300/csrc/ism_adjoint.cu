@@ -60,12 +60,12 @@ __global__ void __launch_bounds__(ISM_ACC_WARPS * 32) adjoint_kernel(const __gri
     constexpr int WIN = 32 * (SLOTS + 1);
     extern __shared__ __align__(16) unsigned char smem[];
     const long long g = blockIdx.x;
-    const int jid = ism_find_job(t, g, [](const JobDev& j) { return j.acc_cta_base; });
+    const int jid = ism_find_job(t, g, [](const JobDev& j) { return j.adj_cta_base; });
     const JobDev& J = t.j[jid];
     const bool exact = (J.Nw == (float)(2 * J.H)) && (2 * J.H == 32 * J.slots);
     if (J.slots != SLOTS || exact == MASK) return;  // another instantiation handles this job
 
-    const long long local = g - J.acc_cta_base;
+    const long long local = g - J.adj_cta_base;
     const int r = (int)(local / J.n_tiles);
     const int tile = J.n_tiles - 1 - (int)(local % J.n_tiles);
     const int Nx = J.N[0], Ny = J.N[1], Nz = J.N[2];
@@ -292,7 +292,7 @@ int launch_adj(const JobTable& t, const WsPlan& p, char* ws, cudaStream_t s)
     cudaError_t e = cudaFuncSetAttribute(adjoint_kernel<SLOTS, MASK>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)sm);
     if (e != cudaSuccess) return (int)e;
-    adjoint_kernel<SLOTS, MASK><<<(unsigned)p.acc_ctas, ISM_ACC_WARPS * 32, sm, s>>>(
+    adjoint_kernel<SLOTS, MASK><<<(unsigned)p.adj_ctas, ISM_ACC_WARPS * 32, sm, s>>>(
         t, reinterpret_cast<const float4*>(ws + p.tbl_off), reinterpret_cast<const uint32_t*>(ws + p.hist_off),
         reinterpret_cast<const uint32_t*>(ws + p.ids_off), reinterpret_cast<float*>(ws + p.gpart_off),
         reinterpret_cast<uint32_t*>(ws + p.status_off));
@@ -304,7 +304,7 @@ int launch_adj(const JobTable& t, const WsPlan& p, char* ws, cudaStream_t s)
 int ism_launch_adjoint(const JobTable& t, const WsPlan& p, char* ws, void* stream, int* launched)
 {
     *launched = 0;
-    if (p.acc_ctas <= 0) return 0;
+    if (p.adj_ctas <= 0) return 0;
     cudaStream_t s = (cudaStream_t)stream;
     bool need[2][ISM_MAX_SLOTS + 1] = {};
     for (int i = 0; i < t.n_jobs; ++i) {

@@ -121,7 +121,8 @@ ism_status plan(const Validated* vs, int n, ism_precision prec, bool backward, J
     long long set_cols = 0;   // grid columns x RIRs over the launch set
     for (int i = 0; i < n; ++i)
         set_cols += (long long)vs[i].job.nb_img[0] * vs[i].job.nb_img[1] * vs[i].job.n_src * vs[i].job.n_rcv;
-    long long rir = 0, hist = 0, tbl = 0, ecta = 0, acta = 0, tcta = 0, seam = 0, ids = 0, lut = 0, gpart = 0;
+    long long rir = 0, hist = 0, tbl = 0, ecta = 0, acta = 0, adta = 0, tcta = 0, rows = 0, ids = 0, lut = 0, gpart = 0,
+              cheb = 0;
     for (int i = 0; i < n; ++i) {
         const Validated& v = vs[i];
         const ism_job& in = v.job;
@@ -169,6 +170,7 @@ ism_status plan(const Validated* vs, int n, ism_precision prec, bool backward, J
             J.U = (int)((cols + cpu - 1) / cpu);
         }
         J.inv_kLz = (float)(1.0 / (k * in.room.L[2]));
+        J.acc_groups = (J.Q + ism_acc_bins((int)prec) - 1) / ism_acc_bins((int)prec);
         J.n_tiles = (J.Q + ISM_TILE_BINS - 1) / ISM_TILE_BINS;
         double s_cut = (double)v.n_ism - 1.0 + (double)v.H + 0.5;
         J.s_cut2 = (float)(s_cut * s_cut);
@@ -190,9 +192,23 @@ ism_status plan(const Validated* vs, int n, ism_precision prec, bool backward, J
         J.tbl_base = tbl;
         J.enum_cta_base = ecta;
         J.acc_cta_base = acta;
+        J.adj_cta_base = adta;
         J.tail_cta_base = tcta;
-        J.seam_base = seam;
+        J.rows_base = rows;
         J.lut_base = lut;
+        J.cheb_base = cheb;
+        // Chebyshev moments pay off when a delay bin holds enough images to
+        // amortise the expansion of its 33 offsets: estimate the images in
+        // reach per bin from the sphere of radius n_ism + H samples
+        {
+            const double reach = ((double)v.n_ism + v.H) / k;                     // metres
+            const double vol = in.room.L[0] * in.room.L[1] * in.room.L[2];
+            const double in_reach = std::min((double)in.nb_img[0] * in.nb_img[1] * in.nb_img[2],
+                                             4.18879020478639 * reach * reach * reach / vol);
+            const double per_bin = in_reach / (double)((v.n_ism + v.H) / ISM_SB + 1);
+            J.use_cheb = (prec == ISM_PREC_FP32 && !backward && v.Nw == 32.0 && v.H == 16 && v.slots == 1 &&
+                          per_bin >= 256.0) ? 1 : 0;
+        }
         J.grad_out = v.grad_out;
         J.grad_beta = v.grad_beta;
         J.grad_src = v.grad_src;
@@ -205,13 +221,15 @@ ism_status plan(const Validated* vs, int n, ism_precision prec, bool backward, J
         int axis = in.nb_img[0] + in.nb_img[1] + in.nb_img[2];
         tbl += R * axis;
         ecta += R * ((J.U + ISM_ENUM_WARPS - 1) / ISM_ENUM_WARPS);
-        acta += R * J.n_tiles;
+        acta += R * J.acc_groups;
+        adta += R * J.n_tiles;
         if (J.has_tail) {
             int blk0 = v.n_ism >> 2, blk_last = (v.n_S - 1) >> 2;
             tcta += R * ((blk_last - blk0 + 1 + ISM_TAIL_CHUNK / 4 - 1) / (ISM_TAIL_CHUNK / 4));
         }
-        seam += R * J.n_tiles * 64LL * J.slots;
+        rows += R * J.Q * 32LL * (J.slots + 1);
         if (prec == ISM_PREC_LUT) lut += (long long)(ism_lut_phases(J.slots) + 1) * 32 * J.slots;
+        if (J.use_cheb) cheb += 32LL * ISM_CHEB_N;
         if (backward) gpart += R * J.Q * 12;
         ids += R * J.img_per_rir;
         if (J.Q > t.max_Q) t.max_Q = J.Q;
@@ -222,20 +240,23 @@ ism_status plan(const Validated* vs, int n, ism_precision prec, bool backward, J
                     (long long)ISM_SCAN_BLOCK * ISM_SCAN_TOP);
     if (ids >= 0xFFFFFFFFll)
         return fail(ISM_ERR_UNSUPPORTED, "%lld images in one launch set exceed 2^32; split the batch", ids);
-    if (rir > 0x7FFFFFFFll || ecta > 0x7FFFFFFFll || acta > 0x7FFFFFFFll || tcta > 0x7FFFFFFFll)
+    if (rir > 0x7FFFFFFFll || ecta > 0x7FFFFFFFll || acta > 0x7FFFFFFFll || adta > 0x7FFFFFFFll ||
+        tcta > 0x7FFFFFFFll)
         return fail(ISM_ERR_UNSUPPORTED, "launch set too large; split the batch");
     p.hist_total = hist;
     p.ids_total = ids;
     p.n_scan_blocks = (hist + ISM_SCAN_BLOCK - 1) / ISM_SCAN_BLOCK;
     if (p.n_scan_blocks < 1) p.n_scan_blocks = 1;
     p.tbl_total = tbl;
-    p.seam_total = seam;
+    p.rows_total = rows;
     p.rir_total = rir;
     p.lut_total = lut;
+    p.cheb_total = cheb;
     p.gpart_total = gpart;
     p.rgrad_total = backward ? rir * 12 : 0;
     p.enum_ctas = ecta;
     p.acc_ctas = acta;
+    p.adj_ctas = adta;
     p.tail_ctas = tcta;
     size_t off = 0;
     p.status_off = off;
@@ -248,12 +269,14 @@ ism_status plan(const Validated* vs, int n, ism_precision prec, bool backward, J
     off = align256(off + (size_t)ids * 4);
     p.tbl_off = off;
     off = align256(off + (size_t)tbl * 16);
-    p.seam_off = off;
-    off = align256(off + (size_t)seam * 4);
+    p.rows_off = off;
+    off = align256(off + (size_t)rows * 4);
     p.amp_off = off;
     off = align256(off + (size_t)rir * 4);
     p.lut_off = off;
     off = align256(off + (size_t)lut * 4);
+    p.cheb_off = off;
+    off = align256(off + (size_t)cheb * 4);
     p.gpart_off = off;
     off = align256(off + (size_t)p.gpart_total * 4);
     p.rgrad_off = off;
@@ -414,6 +437,10 @@ ism_status run_batch(const std::vector<Validated>& vs, ism_precision prec, void*
                 if ((e = ism_launch_lut_tables(t, p, ws, stream))) return cuda_fail(e, "windowed-sinc table kernel");
                 ++launched;
             }
+            if (p.cheb_total > 0) {
+                if ((e = ism_launch_cheb_tables(t, p, ws, stream))) return cuda_fail(e, "Chebyshev table kernel");
+                ++launched;
+            }
             int acc_launched = 0;
             if ((e = ism_launch_accum(t, p, ws, prec, stream, &acc_launched)))
                 return cuda_fail(e, "accumulation kernel");
@@ -526,7 +553,8 @@ ism_job make_job(const ism_room* room, const float* pos_src, int n_src, const fl
 
 ism_status check_prec(ism_precision prec)
 {
-    if (prec != ISM_PREC_FP32 && prec != ISM_PREC_FP16X2 && prec != ISM_PREC_BF16X2 && prec != ISM_PREC_LUT)
+    if (prec != ISM_PREC_FP32 && prec != ISM_PREC_FP16X2 && prec != ISM_PREC_BF16X2 && prec != ISM_PREC_LUT &&
+        prec != ISM_PREC_FP32_DIRECT)
         return fail(ISM_ERR_INVALID_ARG, "unknown precision %d", (int)prec);
     return ISM_OK;
 }

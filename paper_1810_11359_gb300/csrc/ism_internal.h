@@ -13,12 +13,12 @@
 //   scan(b)   exclusive prefix over the counts: bin offsets (counting sort).
 //   enum(a')  the same walk, scattering packed image ids into their bins in
 //             a fixed order (stable counting sort).
-//   accum(c)  one CTA per (RIR, tile of 8 delay bins), one warp per bin: the
-//             windowed sinc (eq. (6)) of every image of the bin into a
-//             register window; the CTA sums the windows of neighbouring bins
-//             in shared memory and stores the tile (eq. (5)).
-//   finalize  per RIR: adds the partial sums at tile seams; fits the envelope
-//             amplitude of the diffuse tail (Section 2.2).
+//   accum(c)  one CTA per (RIR, ISM_ACC_BPC delay bins), one warp per bin:
+//             the windowed sinc (eq. (6)) of every image of the bin into a
+//             register window, stored as the bin's window row.
+//   finalize  per RIR: each sample is the sum of the rows of the bins that
+//             cover it, in bin order (eq. (5)); fits the envelope amplitude
+//             of the diffuse tail (Section 2.2).
 //   tail(d)   Philox4x32-10 logistic noise times the envelope of eq. (8).
 //
 // No floating-point atomic is used anywhere: every sum has a fixed order, so
@@ -31,9 +31,10 @@
 #include "../../include/ism.h"
 
 #define ISM_SB 32                 // samples per delay bin
-#define ISM_TILE_SAMPLES 256      // samples per accumulation tile (CTA)
-#define ISM_TILE_BINS (ISM_TILE_SAMPLES / ISM_SB)   // 8 bins per tile
-#define ISM_ACC_WARPS ISM_TILE_BINS                 // one warp per bin
+#define ISM_ACC_BPC 2             // delay bins per accumulation CTA (one warp each)
+#define ISM_TILE_SAMPLES 256      // samples per adjoint tile (CTA)
+#define ISM_TILE_BINS (ISM_TILE_SAMPLES / ISM_SB)   // 8 bins per adjoint tile
+#define ISM_ACC_WARPS ISM_TILE_BINS                 // adjoint: one warp per bin
 #define ISM_ENUM_WARPS 4          // warps per enumeration CTA (one unit each)
 #define ISM_MAX_JOBS 64           // jobs per launch set (kernel-parameter table, < 32 KB)
 #define ISM_MAX_AXIS 1023         // images per axis (10-bit packed ids)
@@ -43,6 +44,7 @@
 #define ISM_SCAN_BLOCK 4096       // elements per scan block
 #define ISM_SCAN_TOP 16384        // max scan blocks (one top-level block)
 #define ISM_FIT_WINDOW_S 0.02     // envelope fit: last 20 ms of the ISM part
+#define ISM_CHEB_N 10             // Chebyshev terms of a tap function (degree 9)
 
 // Device-side description of one job.  Everything the kernels need is here
 // so that a whole launch set takes its jobs as one kernel parameter.
@@ -63,11 +65,13 @@ struct JobDev {
     int U;                    // enumeration units (warps) per RIR
     int cols_per_unit;        // grid columns (ix, iy) per enumeration unit
     float inv_kLz;            // 1 / ((f_s / c) L_z): samples -> z cells
-    int n_tiles;              // accumulation tiles per RIR
+    int acc_groups;           // accumulation CTAs per RIR (groups of ISM_ACC_BPC bins)
+    int n_tiles;              // adjoint tiles (8 bins) per RIR
     int has_tail;
     int W_env;                // samples of the envelope fit window
     int vec4;                 // out rows 16-byte aligned (float4 stores allowed)
     float half_scale;         // FP16X2 records are scaled by this power of two
+    int use_cheb;             // FP32 accumulation through Chebyshev moments (32-tap window)
     uint64_t seed;
     const float* pos_src;
     const float* pos_rcv;
@@ -79,9 +83,11 @@ struct JobDev {
     long long tbl_base;       // first table entry (float4) of the job
     long long enum_cta_base;  // first enumeration CTA of the job
     long long acc_cta_base;   // first accumulation CTA of the job
+    long long adj_cta_base;   // first adjoint CTA of the job
     long long tail_cta_base;  // first tail CTA of the job
-    long long seam_base;      // first seam record (tiles) of the job
+    long long rows_base;      // first window row (float) of the job: [n_rir][Q][32 (slots + 1)]
     long long lut_base;       // first entry (float) of the job's windowed-sinc table (LUT form)
+    long long cheb_base;      // first Chebyshev coefficient (float) of the job: [32 taps][ISM_CHEB_N]
     // backward pass only
     const float* grad_out;    // dLoss/dh [n_rir][n_S]
     float* grad_beta;         // [6]
@@ -108,27 +114,34 @@ struct WsPlan {
     size_t part_off;       // uint32 [n_scan_blocks + 1]
     size_t ids_off;        // uint32 [ids_total]
     size_t tbl_off;        // float4 [tbl_total]
-    size_t seam_off;       // float  [seam_total]
+    size_t rows_off;       // float  [rows_total]: per-bin window rows of the accumulation
     size_t amp_off;        // float  [rir_total]
     size_t lut_off;        // float  [lut_total]: polyphase windowed-sinc tables (LUT form)
+    size_t cheb_off;       // float  [cheb_total]: Chebyshev coefficients of the 32 tap functions
     size_t gpart_off;      // float  [gpart_total]: backward, per-(RIR, bin) gradients
     size_t rgrad_off;      // float  [rgrad_total]: backward, per-RIR gradients
     size_t total;
     long long hist_total;
     long long ids_total;
     long long tbl_total;
-    long long seam_total;
+    long long rows_total;
     long long rir_total;
     long long lut_total;
+    long long cheb_total;
     long long gpart_total;
     long long rgrad_total;
     long long n_scan_blocks;
     long long enum_ctas;
     long long acc_ctas;
+    long long adj_ctas;
     long long tail_ctas;
 };
 
 #define ISM_TAIL_CHUNK 4096   // tail samples per CTA (256 threads x 16)
+
+// Delay bins (warps) per accumulation CTA: the LUT form copies its ~33 KB
+// table into shared memory once per CTA, so it takes 8 bins per CTA.
+__host__ __device__ constexpr int ism_acc_bins(int prec) { return prec == 3 ? 8 : ISM_ACC_BPC; }
 
 // Phases per sample of the polyphase windowed-sinc table of the LUT form
 // (eq. (9)): 256 for windows of up to 32 taps, fewer for longer windows so
@@ -153,6 +166,8 @@ int ism_launch_accum_fp16(const JobTable& t, const WsPlan& p, char* ws, void* st
 int ism_launch_accum_bf16(const JobTable& t, const WsPlan& p, char* ws, void* stream, int* launched);
 int ism_launch_accum_lut(const JobTable& t, const WsPlan& p, char* ws, void* stream, int* launched);
 int ism_launch_lut_tables(const JobTable& t, const WsPlan& p, char* ws, void* stream);
+int ism_launch_cheb_tables(const JobTable& t, const WsPlan& p, char* ws, void* stream);
+int ism_launch_accum_cheb(const JobTable& t, const WsPlan& p, char* ws, void* stream, int* launched);
 int ism_launch_adjoint(const JobTable& t, const WsPlan& p, char* ws, void* stream, int* launched);
 int ism_launch_finalize(const JobTable& t, const WsPlan& p, char* ws, void* stream);
 int ism_launch_tail(const JobTable& t, const WsPlan& p, char* ws, void* stream);

@@ -1,4 +1,4 @@
-// ism_tail.cu -- tile seams, envelope fit and the diffuse tail (kernel d).
+// ism_tail.cu -- window-row sums, envelope fit and the diffuse tail (kernel d).
 //
 // Section 2.2 ("Diffuse reverberation") models the late RIR as logistic
 // noise whose power follows the Sabine decay: 60 dB in T60 (eq. (7)) from
@@ -17,26 +17,25 @@
 namespace {
 
 __global__ void __launch_bounds__(256) finalize_kernel(const __grid_constant__ JobTable t,
-                                                       const float* __restrict__ seams, float* __restrict__ amp)
+                                                       const float* __restrict__ rows, float* __restrict__ amp)
 {
     const long long g = blockIdx.x;
     const int jid = ism_find_job(t, g, [](const JobDev& j) { return j.rir_base; });
     const JobDev& J = t.j[jid];
     const int r = (int)(g - J.rir_base);
-    const int SL = J.slots;
+    const int WIN = 32 * (J.slots + 1);
     float* out = J.out + (long long)r * J.n_S;
-    const float* seam = seams + J.seam_base + (long long)r * J.n_tiles * (64LL * SL);
+    const float* R = rows + J.rows_base + (long long)r * J.Q * WIN;
 
-    // segments s < SL of every tile: own partial (lo) + spill of the previous tile (hi)
-    const int per_tile = SL * 32;
-    for (int e = threadIdx.x; e < J.n_tiles * per_tile; e += blockDim.x) {
-        int tile = e / per_tile;
-        int s = (e / 32) % SL;
-        int l = e & 31;
-        int k = ISM_TILE_SAMPLES * tile + 32 * s + l - J.H;
-        if (k < 0 || k >= J.n_ism) continue;
-        float v = seam[(long long)tile * 64 * SL + s * 32 + l];
-        if (tile > 0) v += seam[(long long)(tile - 1) * 64 * SL + (SL + s) * 32 + l];
+    // eq. (5): sample k is the sum of the window rows of the bins q with
+    // 0 <= k - (32 q - H) < WIN, added in ascending q
+    for (int k = threadIdx.x; k < J.n_ism; k += blockDim.x) {
+        const int top = k + J.H;                      // k - (32 q - H) = top - 32 q
+        int q_hi = top / ISM_SB;
+        if (q_hi > J.Q - 1) q_hi = J.Q - 1;
+        int q_lo = top - WIN + 1 <= 0 ? 0 : (top - WIN + 1 + ISM_SB - 1) / ISM_SB;
+        float v = 0.0f;
+        for (int q = q_lo; q <= q_hi; ++q) v += R[(long long)q * WIN + (top - ISM_SB * q)];
         out[k] = v;
     }
     __syncthreads();
@@ -115,7 +114,7 @@ int ism_launch_finalize(const JobTable& t, const WsPlan& p, char* ws, void* stre
 {
     if (p.rir_total <= 0) return 0;
     finalize_kernel<<<(unsigned)p.rir_total, 256, 0, (cudaStream_t)stream>>>(
-        t, reinterpret_cast<const float*>(ws + p.seam_off), reinterpret_cast<float*>(ws + p.amp_off));
+        t, reinterpret_cast<const float*>(ws + p.rows_off), reinterpret_cast<float*>(ws + p.amp_off));
     return (int)cudaGetLastError();
 }
 
