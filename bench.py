@@ -505,6 +505,23 @@ def main():
     step_ms = [a.elapsed_time(b) for a, b in evs]
     ms = sum(step_ms) / len(step_ms)
     prof = ism.ism_profile_read()
+
+    # the kernel roofline: the same steps with every launch on one stream, so
+    # that the accumulation kernel's events bracket it alone
+    ism.ism_set_lanes(1)
+    for _ in range(2):
+        step()
+    torch.cuda.synchronize()
+    k_roof = max(5, min(args.steps, 20))
+    ism.ism_profile_reset()
+    ism.ism_profile_enable(True)
+    for _ in range(k_roof):
+        flush.zero_()
+        step()
+    torch.cuda.synchronize()
+    ism.ism_profile_enable(False)
+    prof_roof = ism.ism_profile_read()
+    ism.ism_set_lanes(2)
     if world > 1:
         t = torch.tensor([ms], device=dev)
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
@@ -541,14 +558,16 @@ def main():
         return
 
     n_contrib = contributions(room, beta, N, n_ism)
-    acc_ms, acc_launches, acc_calls = prof["accum"]
-    acc_ms_per_launch = acc_ms / max(acc_launches, 1)
+    acc_ms, acc_launches, acc_calls = prof_roof["accum"]
+    # the accumulation stage of one step, timed with every launch on one
+    # stream (the coefficient table and the accumulation kernel)
+    acc_ms_per_step = acc_ms / k_roof
     peaks, peak_kind = _peaks()
     sm_mhz = float(peaks.get("sm_max_mhz", 2070.0))
     props = torch.cuda.get_device_properties(dev)
     n_sm = props.multi_processor_count
     peak_tops = n_sm * 128 * sm_mhz * 1e6 / 1e12          # FP32 FMA-pipe lane operations / s
-    achieved_tops = FMA_OPS_PER_CONTRIBUTION * n_contrib / (acc_ms_per_launch * 1e-3) / 1e12
+    achieved_tops = FMA_OPS_PER_CONTRIBUTION * n_contrib / (acc_ms_per_step * 1e-3) / 1e12
     launches_per_step = sum(v[1] for v in prof.values()) / max(args.steps, 1)
 
     line = {
@@ -561,13 +580,17 @@ def main():
         "image_contributions_per_sec": n_contrib * world / (ms * 1e-3),
         "contributions_per_step": n_contrib,
         "stage_ms_per_step": {k: v[0] / max(args.steps, 1) for k, v in prof.items()},
-        "roofline": {"bound": "alu", "kernel": f"accum_kernel<1,false,{PREC_ID[args.prec]}>",
+        "roofline": {"bound": "alu",
+                     "kernel": ("cheb_kernel (Chebyshev moments)" if args.prec == "fp32" and args.workload == "batched"
+                                else f"accum_kernel<1,false,{PREC_ID[args.prec]}>"),
                      "achieved": achieved_tops,
                      "peak": peak_tops, "unit": "Tops/s (FP32 FMA-pipe lane ops)",
                      "frac": achieved_tops / peak_tops,
                      "peak_basis": f"{n_sm} SMs x 128 FP32 lanes x {sm_mhz:.0f} MHz ({peak_kind} max SM clock)",
                      "ops_per_contribution": FMA_OPS_PER_CONTRIBUTION,
-                     "kernel_ms": acc_ms_per_launch,
+                     "kernel_ms": acc_ms_per_step,
+                     "kernel_launches_per_step": acc_launches / k_roof,
+                     "timing": "CUDA events around the accumulation stage, launches on one stream, L2 flushed",
                      "traffic": traffic_from_profiles() if (args.prec == "fp32" and args.workload == "batched")
                      else None},
         "gpu_launches": int(round(launches_per_step * args.steps)),
@@ -578,13 +601,13 @@ def main():
         "clocks": clk,
     }
     if n_ism < n_S:
-        tail_ms, tail_launches, _ = prof["tail"]
+        tail_ms, tail_launches, _ = prof_roof["tail"]
         tail_bytes = 4.0 * (n_S - n_ism) * ps.shape[0] * pr.shape[0]   # one FP32 store per tail sample
-        tail_ms_launch = tail_ms / max(tail_launches, 1)
+        tail_ms_launch = tail_ms / k_roof                              # one stream, summed over the step's launches
         hbm = float(peaks.get("hbm_gbs", 6800.0))
         line["tail_roofline"] = {"bound": "hbm", "kernel": "tail_kernel", "achieved": tail_bytes / tail_ms_launch / 1e6,
                                  "peak": hbm, "unit": "GB/s", "frac": tail_bytes / tail_ms_launch / 1e6 / hbm,
-                                 "bytes_per_launch": tail_bytes, "kernel_ms": tail_ms_launch,
+                                 "bytes_per_step": tail_bytes, "kernel_ms_per_step": tail_ms_launch,
                                  "peak_basis": f"{peak_kind} HBM copy bandwidth"}
     if not args.no_cpu_baseline and world >= 1:
         line["cpu_baseline"] = cpu_baseline(room, beta, N, Tdiff)

@@ -391,6 +391,15 @@ typedef enum {
     ISM_N_STAGES = 8
 } ism_stage;
 
+/* Internal concurrency (no counterpart in the paper; a deployment setting):
+ * a forward call with enough work (about 2e7 image sources in reach) runs
+ * as two halves, split by source, on two internal streams forked from and
+ * joined back into the caller's stream, so that one half's enumeration
+ * overlaps the other's accumulation.  n_lanes = 1 keeps every launch on the
+ * caller's stream (each kernel then runs alone, e.g. for timing it); 2 is
+ * the default.  The results are bit-identical either way.  Process-wide. */
+ism_status ism_set_lanes(int n_lanes);
+
 /* Turns timing on (enable != 0) or off for all later simulation calls of the
  * process.  While on, each stage is bracketed by CUDA events recorded on the
  * caller's stream (no synchronisation is added). */

@@ -317,9 +317,14 @@ __global__ void __launch_bounds__(ism_acc_bins(PREC) * 32) accum_kernel(const __
     float* lut = reinterpret_cast<float*>(after_T);
     constexpr size_t LUT_BYTES = PREC == PREC_LUT ? (size_t)(LQ + 1) * ROW * sizeof(float) : 0;
     WarpSmem* Wall = reinterpret_cast<WarpSmem*>(after_T + LUT_BYTES);
+    float* Sh = reinterpret_cast<float*>(Wall + BPC);   // plain S_hi per axis index (conflict-light keys)
 
     const float4* Tg = tbl + J.tbl_base + (long long)r * n_axis;
-    for (int e = threadIdx.x; e < n_axis; e += blockDim.x) T[e] = Tg[e];
+    for (int e = threadIdx.x; e < n_axis; e += blockDim.x) {
+        const float4 v = Tg[e];
+        T[e] = v;
+        Sh[e] = v.x;
+    }
     if constexpr (PREC == PREC_LUT) {
         const float4* Lg = reinterpret_cast<const float4*>(lut_g + J.lut_base);
         for (int e = threadIdx.x; e < (LQ + 1) * ROW / 4; e += blockDim.x) reinterpret_cast<float4*>(lut)[e] = Lg[e];
@@ -351,7 +356,6 @@ __global__ void __launch_bounds__(ism_acc_bins(PREC) * 32) accum_kernel(const __
     }
     const float halfNw = 0.5f * J.Nw;
     const unsigned lt_mask = (1u << lane) - 1u;
-    const float* Sh = reinterpret_cast<const float*>(T);  // .x of the float4 entries: stride 4
     // FP16 records are scaled by 2^e; f is kept away from 0 and 1 in both
     // packed forms so that the packed reciprocal stays finite
     const float rscale = (PREC == PREC_FP16) ? J.half_scale : 1.0f;
@@ -399,8 +403,7 @@ __global__ void __launch_bounds__(ism_acc_bins(PREC) * 32) accum_kernel(const __
                         int bucket = -1;
                         if (i < n) {
                             const int ix = pid[u] & 1023, iy = (pid[u] >> 10) & 1023, iz = pid[u] >> 20;
-                            const float s2 =
-                                __fadd_rn(__fadd_rn(Sh[4 * ix], Sh[4 * (Nx + iy)]), Sh[4 * (Nx + Ny + iz)]);
+                            const float s2 = __fadd_rn(__fadd_rn(Sh[ix], Sh[Nx + iy]), Sh[Nx + Ny + iz]);
                             const float sp = s2 * ism_rsqrt(s2);
                             const int key = ism_round_int(sp - 0.5f) - ISM_SB * q + 1;  // ~floor(s) - 32q + 1
                             bucket = key < 0 ? 0 : (key > ISM_SB ? ISM_SB : key);
@@ -603,7 +606,8 @@ int launch_one(const JobTable& t, const WsPlan& p, char* ws, cudaStream_t s)
     constexpr int BPC = ism_acc_bins(PREC);
     const size_t lut_bytes =
         PREC == PREC_LUT ? (size_t)(ism_lut_phases(SLOTS) + 1) * 32 * SLOTS * sizeof(float) : 0;
-    size_t sm = (size_t)((t.max_axis_sum + 1) & ~1) * sizeof(float4) + lut_bytes + BPC * sizeof(WarpSmem);
+    size_t sm = (size_t)((t.max_axis_sum + 1) & ~1) * sizeof(float4) + lut_bytes + BPC * sizeof(WarpSmem) +
+                (size_t)t.max_axis_sum * sizeof(float);
     cudaError_t e = cudaFuncSetAttribute(accum_kernel<SLOTS, MASK, PREC>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (e != cudaSuccess) return (int)e;

@@ -113,8 +113,13 @@ __global__ void __launch_bounds__(ISM_ACC_BPC * 32) cheb_kernel(const __grid_con
 
     float4* T = reinterpret_cast<float4*>(smem);
     ChebWarp* Wall = reinterpret_cast<ChebWarp*>(smem + (size_t)((t.max_axis_sum + 1) & ~1) * sizeof(float4));
+    float* Sh = reinterpret_cast<float*>(Wall + ISM_ACC_BPC);   // plain S_hi per axis index (conflict-light keys)
     const float4* Tg = tbl + J.tbl_base + (long long)r * n_axis;
-    for (int e = threadIdx.x; e < n_axis; e += blockDim.x) T[e] = Tg[e];
+    for (int e = threadIdx.x; e < n_axis; e += blockDim.x) {
+        const float4 v = Tg[e];
+        T[e] = v;
+        Sh[e] = v.x;
+    }
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     ChebWarp& W = Wall[warp];
@@ -136,7 +141,6 @@ __global__ void __launch_bounds__(ISM_ACC_BPC * 32) cheb_kernel(const __grid_con
     }
     const float twopi_Nw = 6.283185307179586f / 32.0f;
     const unsigned lt_mask = (1u << lane) - 1u;
-    const float* Sh = reinterpret_cast<const float*>(T);
     float* U = reinterpret_cast<float*>(W.sorted);
     __syncthreads();
     if (q >= J.Q) return;
@@ -173,7 +177,7 @@ __global__ void __launch_bounds__(ISM_ACC_BPC * 32) cheb_kernel(const __grid_con
                 int bucket = -1;
                 if (i < n) {
                     const int ix = pid[u] & 1023, iy = (pid[u] >> 10) & 1023, iz = pid[u] >> 20;
-                    const float s2 = __fadd_rn(__fadd_rn(Sh[4 * ix], Sh[4 * (Nx + iy)]), Sh[4 * (Nx + Ny + iz)]);
+                    const float s2 = __fadd_rn(__fadd_rn(Sh[ix], Sh[Nx + iy]), Sh[Nx + Ny + iz]);
                     const float sp = s2 * ism_rsqrt(s2);
                     const int key = ism_round_int(sp - 0.5f) - ISM_SB * q + 1;  // ~floor(s) - 32q + 1
                     bucket = key < 0 ? 0 : (key > ISM_SB ? ISM_SB : key);
@@ -339,7 +343,8 @@ int ism_launch_accum_cheb(const JobTable& t, const WsPlan& p, char* ws, void* st
 {
     *launched = 0;
     if (p.acc_ctas <= 0 || p.cheb_total <= 0) return 0;
-    const size_t sm = (size_t)((t.max_axis_sum + 1) & ~1) * sizeof(float4) + ISM_ACC_BPC * sizeof(ChebWarp);
+    const size_t sm = (size_t)((t.max_axis_sum + 1) & ~1) * sizeof(float4) + ISM_ACC_BPC * sizeof(ChebWarp) +
+                      (size_t)t.max_axis_sum * sizeof(float);
     cudaError_t e = cudaFuncSetAttribute(cheb_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (e != cudaSuccess) return (int)e;
     cheb_kernel<<<(unsigned)p.acc_ctas, ISM_ACC_BPC * 32, sm, (cudaStream_t)stream>>>(

@@ -4,6 +4,7 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <atomic>
 #include <mutex>
 #include <string>
 #include <vector>
@@ -63,6 +64,7 @@ struct Validated {
     ism_job job;
     double Tw, Nw;
     int n_S, n_ism, H, slots;
+    int rir_index0 = 0;   // index of the first RIR in the caller's job (a sub-job of a split job)
     // backward pass only
     const float* grad_out = nullptr;
     float* grad_beta = nullptr;
@@ -113,7 +115,10 @@ ism_status validate_job(const ism_job& in, Validated& v, bool need_ptrs)
 }
 
 // Builds the device job table and the workspace plan of one launch set.
-ism_status plan(const Validated* vs, int n, ism_precision prec, bool backward, JobTable& t, WsPlan& p)
+// Lays the launch set out in the workspace from byte offset `base` on (the
+// status word is always at offset 0, shared by every launch set of a call).
+ism_status plan(const Validated* vs, int n, ism_precision prec, bool backward, JobTable& t, WsPlan& p,
+                size_t base = 0)
 {
     std::memset(&t, 0, sizeof t);
     std::memset(&p, 0, sizeof p);
@@ -183,6 +188,7 @@ ism_status plan(const Validated* vs, int n, ism_precision prec, bool backward, J
         J.W_env = W < v.n_ism ? W : v.n_ism;
         J.vec4 = (v.n_S % 4 == 0) && (((uintptr_t)in.out & 15u) == 0);
         J.seed = in.seed;
+        J.rir_index0 = v.rir_index0;
         J.pos_src = in.pos_src;
         J.pos_rcv = in.pos_rcv;
         J.out = in.out;
@@ -258,9 +264,9 @@ ism_status plan(const Validated* vs, int n, ism_precision prec, bool backward, J
     p.acc_ctas = acta;
     p.adj_ctas = adta;
     p.tail_ctas = tcta;
-    size_t off = 0;
-    p.status_off = off;
-    off = align256(off + 256);
+    size_t off = base;
+    p.status_off = 0;
+    if (base == 0) off = 256;
     p.hist_off = off;
     off = align256(off + (size_t)(hist + 1) * 4);
     p.part_off = off;
@@ -299,8 +305,102 @@ ism_status validate_all(const ism_job* jobs, int n_jobs, std::vector<Validated>&
     return ISM_OK;
 }
 
+// Image sources in reach of one RIR of a job: the grid, or the sphere of
+// radius n_ism + H samples (its volume over the room's), whichever is smaller.
+double images_in_reach(const Validated& v)
+{
+    const ism_job& in = v.job;
+    const double k = (double)in.fs / (double)in.room.c;
+    const double reach = ((double)v.n_ism + v.H) / k;
+    const double vol = in.room.L[0] * in.room.L[1] * in.room.L[2];
+    return std::min((double)in.nb_img[0] * in.nb_img[1] * in.nb_img[2], 4.18879020478639 * reach * reach * reach / vol);
+}
+
+// Execution schedule of a forward call: launch sets (<= ISM_MAX_JOBS jobs
+// each) and the lane (internal stream) of each.  A call with enough work is
+// cut into two halves by source (or by receiver for one source) that run on
+// two lanes, so that one half's enumeration overlaps the other half's
+// accumulation; sets alternate between the lanes.  A sub-job keeps the
+// RIR index of its first RIR (the noise counter), so every RIR is computed
+// exactly as in the unsplit job.
+struct Schedule {
+    std::vector<std::vector<Validated>> sets;
+    int lanes = 1;
+};
+
+std::atomic<int> g_lanes{2};
+
+Schedule schedule(const std::vector<Validated>& vs)
+{
+    Schedule sc;
+    double work = 0.0;
+    for (const Validated& v : vs) work += images_in_reach(v) * (double)v.job.n_src * v.job.n_rcv;
+    const bool split = work >= 2.0e7 && g_lanes.load() >= 2;
+    std::vector<Validated> halves[2];
+    for (const Validated& v : vs) {
+        const ism_job& j = v.job;
+        const bool by_src = j.n_src >= 2, by_rcv = j.n_src == 1 && j.n_rcv >= 2;
+        if (!split || !(by_src || by_rcv)) {
+            halves[0].push_back(v);
+            continue;
+        }
+        const int n = by_src ? j.n_src : j.n_rcv;
+        const int h = n / 2;
+        for (int part = 0; part < 2; ++part) {
+            Validated w = v;
+            const int i0 = part == 0 ? 0 : h, cnt = part == 0 ? h : n - h;
+            const long long stride = by_src ? (long long)j.n_rcv * v.n_S : (long long)v.n_S;   // out elements
+            if (by_src) {
+                w.job.pos_src = j.pos_src ? j.pos_src + 3 * i0 : nullptr;
+                w.job.n_src = cnt;
+                w.rir_index0 = v.rir_index0 + i0 * j.n_rcv;
+                if (j.env_amp) w.job.env_amp = j.env_amp + (long long)i0 * j.n_rcv;
+            } else {
+                w.job.pos_rcv = j.pos_rcv ? j.pos_rcv + 3 * i0 : nullptr;
+                w.job.n_rcv = cnt;
+                w.rir_index0 = v.rir_index0 + i0;
+                if (j.env_amp) w.job.env_amp = j.env_amp + i0;
+            }
+            if (j.out) w.job.out = j.out + (long long)i0 * stride;
+            halves[part].push_back(w);
+        }
+    }
+    for (int part = 0; part < 2; ++part)
+        for (size_t g = 0; g < halves[part].size(); g += ISM_MAX_JOBS) {
+            const size_t e = std::min(halves[part].size(), g + ISM_MAX_JOBS);
+            sc.sets.emplace_back(halves[part].begin() + g, halves[part].begin() + e);
+        }
+    sc.lanes = (sc.sets.size() >= 2 && g_lanes.load() >= 2) ? 2 : 1;
+    return sc;
+}
+
+// Workspace of a schedule: lane 0's sets reuse [0, base1), lane 1's sets
+// [base1, need); *base1_out receives base1.
+ism_status schedule_size(const Schedule& sc, ism_precision prec, size_t* bytes, size_t* base1_out)
+{
+    JobTable t;
+    WsPlan p;
+    size_t size0 = 256, size1 = 0;
+    for (size_t k = 0; k < sc.sets.size(); k += sc.lanes) {
+        ism_status s = plan(sc.sets[k].data(), (int)sc.sets[k].size(), prec, false, t, p, 0);
+        if (s != ISM_OK) return s;
+        size0 = std::max(size0, p.total);
+    }
+    const size_t base1 = align256(size0);
+    if (sc.lanes == 2)
+        for (size_t k = 1; k < sc.sets.size(); k += 2) {
+            ism_status s = plan(sc.sets[k].data(), (int)sc.sets[k].size(), prec, false, t, p, base1);
+            if (s != ISM_OK) return s;
+            size1 = std::max(size1, p.total - base1);
+        }
+    *bytes = base1 + size1;
+    if (base1_out) *base1_out = base1;
+    return ISM_OK;
+}
+
 ism_status batch_size(const std::vector<Validated>& vs, ism_precision prec, size_t* bytes, bool backward = false)
 {
+    if (!backward) return schedule_size(schedule(vs), prec, bytes, nullptr);
     size_t best = 0;
     JobTable t;
     WsPlan p;
@@ -312,6 +412,42 @@ ism_status batch_size(const std::vector<Validated>& vs, ism_precision prec, size
     }
     *bytes = best;
     return ISM_OK;
+}
+
+// The two internal streams (lanes) of the calling thread on the current
+// device, with the events of the fork and the join; created on first use.
+struct Lanes {
+    int dev = -1;
+    cudaStream_t s[2] = {nullptr, nullptr};
+    cudaEvent_t fork = nullptr, join[2] = {nullptr, nullptr};
+    ~Lanes()
+    {
+        for (int i = 0; i < 2; ++i) {
+            if (s[i]) cudaStreamDestroy(s[i]);
+            if (join[i]) cudaEventDestroy(join[i]);
+        }
+        if (fork) cudaEventDestroy(fork);
+    }
+};
+
+int lanes_of_device(Lanes** out)
+{
+    thread_local std::vector<Lanes> all(64);
+    int d = 0;
+    int e = (int)cudaGetDevice(&d);
+    if (e) return e;
+    if (d < 0 || d >= 64) return (int)cudaErrorInvalidDevice;
+    Lanes& L = all[d];
+    if (L.dev != d) {
+        for (int i = 0; i < 2; ++i) {
+            if ((e = (int)cudaStreamCreateWithFlags(&L.s[i], cudaStreamNonBlocking))) return e;
+            if ((e = (int)cudaEventCreateWithFlags(&L.join[i], cudaEventDisableTiming))) return e;
+        }
+        if ((e = (int)cudaEventCreateWithFlags(&L.fork, cudaEventDisableTiming))) return e;
+        L.dev = d;
+    }
+    *out = &L;
+    return 0;
 }
 
 // ---------------------------------------------------------------------------
@@ -390,11 +526,69 @@ struct StageTimer {
     }
 };
 
+// The launches of one launch set, in order, on `st`.
+ism_status run_set(const std::vector<Validated>& set, ism_precision prec, size_t base, char* ws, cudaStream_t st)
+{
+    JobTable t;
+    WsPlan p;
+    ism_status s = plan(set.data(), (int)set.size(), prec, false, t, p, base);
+    if (s != ISM_OK) return s;
+    void* stream = (void*)st;
+    int e;
+    {
+        StageTimer tm(ISM_STAGE_GEOMETRY, st);
+        if ((e = ism_launch_geometry(t, p, ws, stream))) return cuda_fail(e, "geometry kernel");
+        tm.done(p.rir_total > 0);
+    }
+    {
+        StageTimer tm(ISM_STAGE_ENUM_COUNT, st);
+        if ((e = ism_launch_enum(t, p, ws, false, stream))) return cuda_fail(e, "enumeration (count) kernel");
+        tm.done(p.enum_ctas > 0);
+    }
+    {
+        StageTimer tm(ISM_STAGE_SCAN, st);
+        if ((e = ism_launch_scan(p, ws, stream))) return cuda_fail(e, "scan kernels");
+        tm.done(3);
+    }
+    {
+        StageTimer tm(ISM_STAGE_ENUM_SCATTER, st);
+        if ((e = ism_launch_enum(t, p, ws, true, stream))) return cuda_fail(e, "enumeration (scatter) kernel");
+        tm.done(p.enum_ctas > 0);
+    }
+    {
+        StageTimer tm(ISM_STAGE_ACCUM, st);
+        int launched = 0;
+        if (p.lut_total > 0) {
+            if ((e = ism_launch_lut_tables(t, p, ws, stream))) return cuda_fail(e, "windowed-sinc table kernel");
+            ++launched;
+        }
+        if (p.cheb_total > 0) {
+            if ((e = ism_launch_cheb_tables(t, p, ws, stream))) return cuda_fail(e, "Chebyshev table kernel");
+            ++launched;
+        }
+        int acc_launched = 0;
+        if ((e = ism_launch_accum(t, p, ws, prec, stream, &acc_launched))) return cuda_fail(e, "accumulation kernel");
+        tm.done(launched + acc_launched);
+    }
+    {
+        StageTimer tm(ISM_STAGE_FINALIZE, st);
+        if ((e = ism_launch_finalize(t, p, ws, stream))) return cuda_fail(e, "finalize kernel");
+        tm.done(p.rir_total > 0);
+    }
+    if (p.tail_ctas > 0) {
+        StageTimer tm(ISM_STAGE_TAIL, st);
+        if ((e = ism_launch_tail(t, p, ws, stream))) return cuda_fail(e, "tail kernel");
+        tm.done(1);
+    }
+    return ISM_OK;
+}
+
 ism_status run_batch(const std::vector<Validated>& vs, ism_precision prec, void* workspace, size_t ws_bytes,
                      void* stream)
 {
-    size_t need = 0;
-    ism_status s = batch_size(vs, prec, &need);
+    const Schedule sc = schedule(vs);
+    size_t need = 0, base1 = 0;
+    ism_status s = schedule_size(sc, prec, &need, &base1);
     if (s != ISM_OK) return s;
     if (!workspace) return fail(ISM_ERR_INVALID_ARG, "workspace is NULL");
     if (((uintptr_t)workspace & 255u) != 0) return fail(ISM_ERR_INVALID_ARG, "workspace must be 256-byte aligned");
@@ -404,60 +598,30 @@ ism_status run_batch(const std::vector<Validated>& vs, ism_precision prec, void*
     cudaStream_t st = (cudaStream_t)stream;
     int e = (int)cudaMemsetAsync(ws, 0, 256, st);
     if (e) return cuda_fail(e, "status reset");
-    JobTable t;
-    WsPlan p;
-    for (size_t g = 0; g < vs.size(); g += ISM_MAX_JOBS) {
-        int n = (int)std::min<size_t>(ISM_MAX_JOBS, vs.size() - g);
-        s = plan(vs.data() + g, n, prec, false, t, p);
-        if (s != ISM_OK) return s;
-        {
-            StageTimer tm(ISM_STAGE_GEOMETRY, st);
-            if ((e = ism_launch_geometry(t, p, ws, stream))) return cuda_fail(e, "geometry kernel");
-            tm.done(p.rir_total > 0);
-        }
-        {
-            StageTimer tm(ISM_STAGE_ENUM_COUNT, st);
-            if ((e = ism_launch_enum(t, p, ws, false, stream))) return cuda_fail(e, "enumeration (count) kernel");
-            tm.done(p.enum_ctas > 0);
-        }
-        {
-            StageTimer tm(ISM_STAGE_SCAN, st);
-            if ((e = ism_launch_scan(p, ws, stream))) return cuda_fail(e, "scan kernels");
-            tm.done(3);
-        }
-        {
-            StageTimer tm(ISM_STAGE_ENUM_SCATTER, st);
-            if ((e = ism_launch_enum(t, p, ws, true, stream))) return cuda_fail(e, "enumeration (scatter) kernel");
-            tm.done(p.enum_ctas > 0);
-        }
-        {
-            StageTimer tm(ISM_STAGE_ACCUM, st);
-            int launched = 0;
-            if (p.lut_total > 0) {
-                if ((e = ism_launch_lut_tables(t, p, ws, stream))) return cuda_fail(e, "windowed-sinc table kernel");
-                ++launched;
-            }
-            if (p.cheb_total > 0) {
-                if ((e = ism_launch_cheb_tables(t, p, ws, stream))) return cuda_fail(e, "Chebyshev table kernel");
-                ++launched;
-            }
-            int acc_launched = 0;
-            if ((e = ism_launch_accum(t, p, ws, prec, stream, &acc_launched)))
-                return cuda_fail(e, "accumulation kernel");
-            tm.done(launched + acc_launched);
-        }
-        {
-            StageTimer tm(ISM_STAGE_FINALIZE, st);
-            if ((e = ism_launch_finalize(t, p, ws, stream))) return cuda_fail(e, "finalize kernel");
-            tm.done(p.rir_total > 0);
-        }
-        if (p.tail_ctas > 0) {
-            StageTimer tm(ISM_STAGE_TAIL, st);
-            if ((e = ism_launch_tail(t, p, ws, stream))) return cuda_fail(e, "tail kernel");
-            tm.done(1);
-        }
+    if (sc.lanes == 1) {
+        for (const auto& set : sc.sets)
+            if ((s = run_set(set, prec, 0, ws, st)) != ISM_OK) return s;
+        return ISM_OK;
     }
-    return ISM_OK;
+    // two lanes forked from and joined back into the caller's stream; their
+    // launches interleave on the GPU (the enumeration of one half, bound by
+    // scattered stores, overlaps the arithmetic of the other)
+    Lanes* L = nullptr;
+    if ((e = lanes_of_device(&L))) return cuda_fail(e, "internal streams");
+    if ((e = (int)cudaEventRecord(L->fork, st))) return cuda_fail(e, "event record");
+    for (int i = 0; i < 2; ++i)
+        if ((e = (int)cudaStreamWaitEvent(L->s[i], L->fork, 0))) return cuda_fail(e, "stream wait");
+    ism_status first_err = ISM_OK;
+    for (size_t k = 0; k < sc.sets.size() && first_err == ISM_OK; ++k) {
+        const int lane = (int)(k % 2);
+        first_err = run_set(sc.sets[k], prec, lane == 0 ? 0 : base1, ws, L->s[lane]);
+    }
+    // join even after an error, so that the caller's stream orders after all work enqueued
+    for (int i = 0; i < 2; ++i) {
+        if ((e = (int)cudaEventRecord(L->join[i], L->s[i])) && first_err == ISM_OK) first_err = cuda_fail(e, "event");
+        if ((e = (int)cudaStreamWaitEvent(st, L->join[i], 0)) && first_err == ISM_OK) first_err = cuda_fail(e, "wait");
+    }
+    return first_err;
 }
 
 // Backward pass: the forward's geometry, enumeration and binning, then the
@@ -842,6 +1006,14 @@ ism_status ism_nb_img_from_t(double T, const double L[3], double c, double Tw, i
         if (2.0 * M + 1.0 > 1e9) return fail(ISM_ERR_UNSUPPORTED, "image grid too large");
         nb_out[a] = (int)(2.0 * M + 1.0);
     }
+    return ISM_OK;
+}
+
+ism_status ism_set_lanes(int n_lanes)
+{
+    g_last_error.clear();
+    if (n_lanes != 1 && n_lanes != 2) return fail(ISM_ERR_INVALID_ARG, "n_lanes must be 1 or 2");
+    g_lanes.store(n_lanes);
     return ISM_OK;
 }
 

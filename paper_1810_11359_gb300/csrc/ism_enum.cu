@@ -27,6 +27,21 @@
 
 namespace {
 
+// Delay bin of an image from its plain-FP32 squared delay s2 (samples^2), or
+// -1 when its window cannot reach a sample below n_ism.
+__device__ __forceinline__ int bin_of(float s2, float s_cut2, int Q, uint32_t* status)
+{
+    if (!(s2 < s_cut2)) return -1;
+    const float s = s2 * ism_rsqrt(s2);
+    // nearest integer of (s + 1/2) / 32 - 1/2, i.e. ~floor((s + 1/2) / 32)
+    int q = ism_round_int(__fmaf_rn(s, 1.0f / ISM_SB, 0.5f / ISM_SB - 0.5f));
+    if (q >= Q || q < 0) {  // cannot happen for a consistent s_cut2; keep memory safe
+        atomicOr(status, (uint32_t)ISM_DEVICE_FLAG_BIN);
+        q = -1;
+    }
+    return q;
+}
+
 template <bool SCATTER>
 __global__ void __launch_bounds__(ISM_ENUM_WARPS * 32) enum_kernel(const __grid_constant__ JobTable t,
                                                                     const float4* __restrict__ tbl,
@@ -59,8 +74,33 @@ __global__ void __launch_bounds__(ISM_ENUM_WARPS * 32) enum_kernel(const __grid_
     const long long hrow = J.hist_base + (long long)r * Q * J.U;  // + q * U + unit
     if (active)
         for (int q = lane; q < Q; q += 32) cnt[q] = SCATTER ? hist[hrow + (long long)q * J.U + unit] : 0u;
+    __shared__ int iz_min_s;
+    __syncthreads();
+    if (SCATTER && warp == 0) {
+        // the z index of the image plane nearest the receiver: Sz falls
+        // towards it and rises beyond it (image coordinates increase with n)
+        const float* Szs = S + Nx + Ny;
+        float best = __int_as_float(0x7f800000);
+        int bi = 0;
+        for (int iz = lane; iz < Nz; iz += 32)
+            if (Szs[iz] < best) {
+                best = Szs[iz];
+                bi = iz;
+            }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            const float ob = __shfl_xor_sync(0xffffffffu, best, o);
+            const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+            if (ob < best || (ob == best && oi < bi)) {
+                best = ob;
+                bi = oi;
+            }
+        }
+        if (lane == 0) iz_min_s = bi;
+    }
     __syncthreads();
     if (!active) return;
+    const int iz_min = SCATTER ? iz_min_s : 0;
 
     const float* Sx = S;
     const float* Sy = S + Nx;
@@ -87,37 +127,60 @@ __global__ void __launch_bounds__(ISM_ENUM_WARPS * 32) enum_kernel(const __grid_
         int z0 = -M - nlo_z, z1 = M - nlo_z;
         if (z0 < 0) z0 = 0;
         if (z1 > Nz - 1) z1 = Nz - 1;
-        for (int base = z0; base <= z1; base += 32) {
-            const int iz = base + lane;
-            int q = -1;
-            if (iz <= z1) {
-                const float s2 = __fadd_rn(sxy, Sz[iz]);
-                if (s2 < s_cut2) {
-                    const float s = s2 * ism_rsqrt(s2);
-                    // nearest integer of (s + 1/2) / 32 - 1/2, i.e. ~floor((s + 1/2) / 32)
-                    q = ism_round_int(__fmaf_rn(s, 1.0f / ISM_SB, 0.5f / ISM_SB - 0.5f));
-                    if (q >= Q || q < 0) {  // cannot happen for a consistent s_cut2; keep memory safe
-                        atomicOr(status, (uint32_t)ISM_DEVICE_FLAG_BIN);
-                        q = -1;
-                    }
-                }
-            }
-            if (!SCATTER) {
+        if (!SCATTER) {
+            for (int base = z0; base <= z1; base += 32) {
+                const int iz = base + lane;
+                if (iz > z1) continue;
+                const int q = bin_of(__fadd_rn(sxy, Sz[iz]), s_cut2, Q, status);
                 // counts only: integer adds commute, so the order is immaterial
                 if (q >= 0) atomicAdd(&cnt[q], 1u);
-                continue;
             }
-            if (!__any_sync(0xffffffffu, q >= 0)) continue;
-            const unsigned peers = __match_any_sync(0xffffffffu, q);
-            uint32_t base_cnt = 0;
-            if (q >= 0) base_cnt = cnt[q];
-            __syncwarp();
-            if (q >= 0) {
-                if (lane == __ffs(peers) - 1) cnt[q] = base_cnt + (uint32_t)__popc(peers);
-                ids[base_cnt + (uint32_t)__popc(peers & lt_mask)] =
-                    (uint32_t)ix | ((uint32_t)iy << 10) | ((uint32_t)iz << 20);
+            continue;
+        }
+        // scatter: the column's z range as two arms walked away from the
+        // receiver's plane, along which the delay never decreases, so equal
+        // bins are contiguous lanes and a lane's rank among its bin's images
+        // is its distance to the first lane of its run (match.any only when
+        // FP32 rounding breaks the order)
+        for (int arm = 0; arm < 2; ++arm) {
+            const int first = arm == 0 ? max(z0, iz_min) : min(z1, iz_min - 1);
+            const int len = arm == 0 ? z1 - first + 1 : first - z0 + 1;
+            for (int k0 = 0; k0 < len; k0 += 32) {
+                const int k = k0 + lane;
+                const int iz = arm == 0 ? first + k : first - k;
+                const int q = k < len ? bin_of(__fadd_rn(sxy, Sz[iz]), s_cut2, Q, status) : -1;
+                const bool valid = q >= 0;
+                const unsigned vmask = __ballot_sync(0xffffffffu, valid);
+                if (!vmask) break;   // the rest of the arm lies beyond the cut as well
+                const int qp = __shfl_up_sync(0xffffffffu, q, 1);
+                const unsigned down = __ballot_sync(0xffffffffu, valid && lane > 0 && q < qp);
+                const uint32_t id = (uint32_t)ix | ((uint32_t)iy << 10) | ((uint32_t)iz << 20);
+                if (down == 0u && (vmask & (vmask + 1u)) == 0u) {
+                    // valid lanes are a prefix with non-decreasing bins
+                    const unsigned starts = __ballot_sync(0xffffffffu, valid && (lane == 0 || q != qp));
+                    const int run0 = 31 - __clz(starts & (0xffffffffu >> (31 - lane)));
+                    const unsigned after = starts & ~((2u << lane) - 1u);
+                    const int run1 = after ? __ffs(after) - 1 : __popc(vmask);
+                    uint32_t base_cnt = 0;
+                    if (valid) base_cnt = cnt[q];
+                    __syncwarp();
+                    if (valid) {
+                        ids[base_cnt + (uint32_t)(lane - run0)] = id;
+                        if (lane == run1 - 1) cnt[q] = base_cnt + (uint32_t)(run1 - run0);
+                    }
+                    __syncwarp();
+                } else {
+                    const unsigned peers = __match_any_sync(0xffffffffu, q);
+                    uint32_t base_cnt = 0;
+                    if (valid) base_cnt = cnt[q];
+                    __syncwarp();
+                    if (valid) {
+                        if (lane == __ffs(peers) - 1) cnt[q] = base_cnt + (uint32_t)__popc(peers);
+                        ids[base_cnt + (uint32_t)__popc(peers & lt_mask)] = id;
+                    }
+                    __syncwarp();
+                }
             }
-            __syncwarp();
         }
     }
     if (!SCATTER) {

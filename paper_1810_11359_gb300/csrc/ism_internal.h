@@ -31,7 +31,7 @@
 #include "../../include/ism.h"
 
 #define ISM_SB 32                 // samples per delay bin
-#define ISM_ACC_BPC 2             // delay bins per accumulation CTA (one warp each)
+#define ISM_ACC_BPC 4             // delay bins per accumulation CTA (one warp each)
 #define ISM_TILE_SAMPLES 256      // samples per adjoint tile (CTA)
 #define ISM_TILE_BINS (ISM_TILE_SAMPLES / ISM_SB)   // 8 bins per adjoint tile
 #define ISM_ACC_WARPS ISM_TILE_BINS                 // adjoint: one warp per bin
@@ -72,6 +72,7 @@ struct JobDev {
     int vec4;                 // out rows 16-byte aligned (float4 stores allowed)
     float half_scale;         // FP16X2 records are scaled by this power of two
     int use_cheb;             // FP32 accumulation through Chebyshev moments (32-tap window)
+    int rir_index0;           // RIR index of the job's first RIR in its caller's job (noise counter)
     uint64_t seed;
     const float* pos_src;
     const float* pos_rcv;

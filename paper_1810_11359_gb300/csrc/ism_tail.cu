@@ -80,7 +80,7 @@ __global__ void __launch_bounds__(256) tail_kernel(const __grid_constant__ JobTa
     for (int i = 0; i < ISM_TAIL_CHUNK / 4 / 256; ++i) {
         int blk = blk0 + c * (ISM_TAIL_CHUNK / 4) + i * 256 + (int)threadIdx.x;
         if (blk > blk_last) break;
-        float4 z = ism_noise_block(J.seed, (uint32_t)r, (uint32_t)blk);
+        float4 z = ism_noise_block(J.seed, (uint32_t)(r + J.rir_index0), (uint32_t)blk);
         int k = 4 * blk;
         float e0 = sqA * exp2f(-hg * (float)(k - J.n_ism));
         float e1 = sqA * exp2f(-hg * (float)(k + 1 - J.n_ism));

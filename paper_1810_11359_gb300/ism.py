@@ -119,6 +119,7 @@ _SIGS = {
     "ism_nb_img_from_t": (ctypes.c_int, [ctypes.c_double, _P(ctypes.c_double), ctypes.c_double, ctypes.c_double,
                                          _P(ctypes.c_int)]),
     "ism_att2t_sabine": (ctypes.c_int, [ctypes.c_double, ctypes.c_double, _P(ctypes.c_double)]),
+    "ism_set_lanes": (ctypes.c_int, [ctypes.c_int]),
     "ism_profile_enable": (ctypes.c_int, [ctypes.c_int]),
     "ism_profile_reset": (ctypes.c_int, []),
     "ism_profile_read": (ctypes.c_int, [ctypes.c_int, _P(ctypes.c_double), _P(ctypes.c_longlong),
@@ -452,6 +453,12 @@ def ism_diffuse_noise(seed: int, rir: int, k0: int, n: int, stream=None):
 # --------------------------------------------------------------------------- #
 # Per-stage timing
 # --------------------------------------------------------------------------- #
+def ism_set_lanes(n_lanes: int):
+    """1: every launch on the caller's stream; 2 (default): large calls run
+    as two halves on two internal streams."""
+    _check(load().ism_set_lanes(int(n_lanes)))
+
+
 def ism_profile_enable(enable: bool = True):
     _check(load().ism_profile_enable(int(bool(enable))))
 

@@ -269,3 +269,43 @@ def test_sabine_on_device_fp64():
         else:
             assert st[i] == 0
             np.testing.assert_allclose(beta[i], ref, rtol=1e-14)
+
+
+def test_large_call_on_two_lanes_equals_per_source_calls_bitwise():
+    """A call with enough work runs as two halves (split by source) on two
+    internal streams; every RIR must equal, bit for bit, the same RIR from a
+    call on one source alone (too small to be split)."""
+    room = workloads.batched_fp32()
+    beta = oracle.beta_sabine(room.L, room.rt60)
+    N = oracle.nb_img_from_t(room.Tmax, room.L, room.c, room.window())
+    full = lib_run(room.L, beta, room.pos_src, room.pos_rcv, N, room.Tmax, room.fs, Tw=room.window())
+    for i in range(4):
+        one = lib_run(room.L, beta, room.pos_src[i:i + 1], room.pos_rcv, N, room.Tmax, room.fs, Tw=room.window())
+        assert np.array_equal(full[i].view(np.uint32), one[0].view(np.uint32)), i
+
+
+def test_split_call_keeps_the_noise_index_of_every_rir():
+    """A call with a diffuse tail large enough to be split: the tail of RIRs
+    of the second half still uses their index in the whole call (Philox
+    counter), checked against the oracle's tail for the same amplitude."""
+    room = workloads.trajectory_array()
+    beta = oracle.beta_sabine(room.L, room.rt60)
+    Tdiff, Tmax = 0.6, 0.9
+    N = oracle.nb_img_from_t(Tdiff, room.L, room.c, room.window())
+    n_S = oracle.n_samples(f32(Tmax), room.fs)
+    n_ism = oracle.n_samples(f32(Tdiff), room.fs)
+    ps = torch.as_tensor(room.pos_src).cuda()
+    pr = torch.as_tensor(room.pos_rcv).cuda()
+    out = torch.empty((64, 8, n_S), device="cuda")
+    amp = torch.empty(512, device="cuda")
+    job = ism.make_job(room.L, beta, ps, pr, N, Tmax, room.fs, out, Tdiff=Tdiff, Tw=room.window(), seed=11,
+                       env_amp=amp)
+    ism.ism_simulate_batch([job])
+    torch.cuda.synchronize()
+    got = out.cpu().numpy().reshape(512, n_S)
+    A = amp.cpu().numpy()
+    T60 = oracle.t60_sabine(room.L, np.asarray(beta, np.float32).astype(np.float64))
+    for r in [3, 255, 256, 300, 511]:
+        tail_ref = oracle.tail(11, r, float(A[r]), n_ism, n_S, float(f32(room.fs)), T60)[n_ism:]
+        np.testing.assert_allclose(got[r, n_ism:].astype(np.float64), tail_ref, rtol=2e-6,
+                                   atol=1e-12 * np.sqrt(A[r]))
