@@ -7,8 +7,8 @@
 // an entire function of f on [0, 1] (the window's zeros fall at the ends of
 // the interval, so no mask cuts it), and its Chebyshev series in u = 2f - 1
 // converges fast: degree 9 reproduces each g_j to 2e-9 (the coefficients
-// c_{j,i} are computed once per job in FP64 by interpolation at the 10
-// Chebyshev-Gauss nodes).  Hence for the images of one delay bin that share
+// c_{j,i}, interpolated at the 10 Chebyshev-Gauss nodes in FP64 on the host,
+// travel in the kernel's parameter table).  Hence for the images of one delay bin that share
 // the integer offset rr = b - 32 q,
 //   sum_n A_n g_j(f_n) = sum_i c_{j,i} M_i,   M_i = sum_n A_n T_i(2 f_n - 1),
 // so each image costs 10 moment updates on one lane instead of 32 tap
@@ -94,7 +94,6 @@ __global__ void __launch_bounds__(ISM_ACC_BPC * 32) cheb_kernel(const __grid_con
                                                                  const float4* __restrict__ tbl,
                                                                  const uint32_t* __restrict__ hist,
                                                                  const uint32_t* __restrict__ ids,
-                                                                 const float* __restrict__ cheb,
                                                                  float* __restrict__ rows,
                                                                  uint32_t* __restrict__ status)
 {
@@ -129,7 +128,7 @@ __global__ void __launch_bounds__(ISM_ACC_BPC * 32) cheb_kernel(const __grid_con
     // the direct evaluation used for flagged images
     float c[ISM_CHEB_N];
 #pragma unroll
-    for (int i = 0; i < ISM_CHEB_N; ++i) c[i] = cheb[J.cheb_base + lane * ISM_CHEB_N + i];
+    for (int i = 0; i < ISM_CHEB_N; ++i) c[i] = t.cheb[lane * ISM_CHEB_N + i];
     float xj[1], nsg[1], Cj[1], Sj[1];
     bool tap_ok[1] = {true};
     {
@@ -300,57 +299,20 @@ __global__ void __launch_bounds__(ISM_ACC_BPC * 32) cheb_kernel(const __grid_con
     row[32 + lane] = acc[1];
 }
 
-// c_{t,i} of the 32 tap functions g_t(f) = delta'(t - 15 - f), f = (u + 1) / 2,
-// by interpolation at the Chebyshev-Gauss nodes u_k = cos(pi (k + 1/2) / N):
-// c_i = (2 / N) sum_k g(u_k) T_i(u_k), c_0 halved.  FP64.
-__global__ void cheb_table_kernel(const __grid_constant__ JobTable t, float* __restrict__ out)
-{
-    const int jid = blockIdx.x;
-    const JobDev& J = t.j[jid];
-    if (!J.use_cheb) return;
-    const double PI = 3.141592653589793238462643383279502884;
-    for (int e = threadIdx.x; e < 32 * ISM_CHEB_N; e += blockDim.x) {
-        const int tap = e / ISM_CHEB_N, i = e % ISM_CHEB_N;
-        const int j = tap - 15;
-        double s = 0.0;
-        for (int k = 0; k < ISM_CHEB_N; ++k) {
-            const double th = PI * (k + 0.5) / ISM_CHEB_N;
-            const double f = 0.5 * (cos(th) + 1.0);
-            const double x = (double)j - f;
-            double g = 0.0;
-            if (fabs(x) < 16.0) {
-                const double w = 0.5 * (1.0 + cospi(x / 16.0));
-                g = w * (x == 0.0 ? 1.0 : sinpi(x) / (PI * x));
-            }
-            s += g * cos(i * th);
-        }
-        s *= 2.0 / ISM_CHEB_N;
-        if (i == 0) s *= 0.5;
-        out[J.cheb_base + e] = (float)s;
-    }
-}
-
 }  // namespace
-
-int ism_launch_cheb_tables(const JobTable& t, const WsPlan& p, char* ws, void* stream)
-{
-    if (p.cheb_total <= 0) return 0;
-    cheb_table_kernel<<<(unsigned)t.n_jobs, 128, 0, (cudaStream_t)stream>>>(t, reinterpret_cast<float*>(ws + p.cheb_off));
-    return (int)cudaGetLastError();
-}
 
 int ism_launch_accum_cheb(const JobTable& t, const WsPlan& p, char* ws, void* stream, int* launched)
 {
     *launched = 0;
-    if (p.acc_ctas <= 0 || p.cheb_total <= 0) return 0;
+    if (p.acc_ctas <= 0 || !t.any_cheb) return 0;
     const size_t sm = (size_t)((t.max_axis_sum + 1) & ~1) * sizeof(float4) + ISM_ACC_BPC * sizeof(ChebWarp) +
                       (size_t)t.max_axis_sum * sizeof(float);
     cudaError_t e = cudaFuncSetAttribute(cheb_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (e != cudaSuccess) return (int)e;
     cheb_kernel<<<(unsigned)p.acc_ctas, ISM_ACC_BPC * 32, sm, (cudaStream_t)stream>>>(
         t, reinterpret_cast<const float4*>(ws + p.tbl_off), reinterpret_cast<const uint32_t*>(ws + p.hist_off),
-        reinterpret_cast<const uint32_t*>(ws + p.ids_off), reinterpret_cast<const float*>(ws + p.cheb_off),
-        reinterpret_cast<float*>(ws + p.rows_off), reinterpret_cast<uint32_t*>(ws + p.status_off));
+        reinterpret_cast<const uint32_t*>(ws + p.ids_off), reinterpret_cast<float*>(ws + p.rows_off),
+        reinterpret_cast<uint32_t*>(ws + p.status_off));
     *launched = 1;
     return (int)cudaGetLastError();
 }

@@ -115,6 +115,39 @@ ism_status validate_job(const ism_job& in, Validated& v, bool need_ptrs)
 }
 
 // Builds the device job table and the workspace plan of one launch set.
+// Chebyshev coefficients of the 32 tap functions of a 32-tap window:
+// g_t(f) = delta'(t - 15 - f) (eq. (6)), f = (u + 1) / 2, interpolated at the
+// Chebyshev-Gauss nodes u_k = cos(pi (k + 1/2) / N): c_i = (2 / N) sum_k
+// g_t(u_k) T_i(u_k), c_0 halved.  FP64 on the host, once per process.
+const float* cheb_coefficients()
+{
+    static float c[32 * ISM_CHEB_N];
+    static std::once_flag once;
+    std::call_once(once, [] {
+        const int N = ISM_CHEB_N;
+        for (int tap = 0; tap < 32; ++tap) {
+            const int j = tap - 15;
+            for (int i = 0; i < N; ++i) {
+                double s = 0.0;
+                for (int k = 0; k < N; ++k) {
+                    const double th = M_PI * (k + 0.5) / N;
+                    const double x = (double)j - 0.5 * (std::cos(th) + 1.0);
+                    double g = 0.0;
+                    if (std::fabs(x) < 16.0) {
+                        const double w = 0.5 * (1.0 + std::cos(M_PI * x / 16.0));
+                        g = w * (x == 0.0 ? 1.0 : std::sin(M_PI * x) / (M_PI * x));
+                    }
+                    s += g * std::cos(i * th);
+                }
+                s *= 2.0 / N;
+                if (i == 0) s *= 0.5;
+                c[tap * N + i] = (float)s;
+            }
+        }
+    });
+    return c;
+}
+
 // Lays the launch set out in the workspace from byte offset `base` on (the
 // status word is always at offset 0, shared by every launch set of a call).
 ism_status plan(const Validated* vs, int n, ism_precision prec, bool backward, JobTable& t, WsPlan& p,
@@ -126,8 +159,8 @@ ism_status plan(const Validated* vs, int n, ism_precision prec, bool backward, J
     long long set_cols = 0;   // grid columns x RIRs over the launch set
     for (int i = 0; i < n; ++i)
         set_cols += (long long)vs[i].job.nb_img[0] * vs[i].job.nb_img[1] * vs[i].job.n_src * vs[i].job.n_rcv;
-    long long rir = 0, hist = 0, tbl = 0, ecta = 0, acta = 0, adta = 0, tcta = 0, rows = 0, ids = 0, lut = 0, gpart = 0,
-              cheb = 0;
+    long long rir = 0, hist = 0, tbl = 0, ecta = 0, acta = 0, adta = 0, tcta = 0, fcta = 0, rows = 0, ids = 0, lut = 0,
+              gpart = 0;
     for (int i = 0; i < n; ++i) {
         const Validated& v = vs[i];
         const ism_job& in = v.job;
@@ -200,9 +233,11 @@ ism_status plan(const Validated* vs, int n, ism_precision prec, bool backward, J
         J.acc_cta_base = acta;
         J.adj_cta_base = adta;
         J.tail_cta_base = tcta;
+        J.fin_cta_base = fcta;
+        J.fin_chunk = std::max(2048, (J.W_env + 255) / 256 * 256);
+        J.fin_chunks = std::max(1, (v.n_ism + J.fin_chunk - 1) / J.fin_chunk);
         J.rows_base = rows;
         J.lut_base = lut;
-        J.cheb_base = cheb;
         // Chebyshev moments pay off when a delay bin holds enough images to
         // amortise the expansion of its 33 offsets: estimate the images in
         // reach per bin from the sphere of radius n_ism + H samples
@@ -228,6 +263,7 @@ ism_status plan(const Validated* vs, int n, ism_precision prec, bool backward, J
         tbl += R * axis;
         ecta += R * ((J.U + ISM_ENUM_WARPS - 1) / ISM_ENUM_WARPS);
         acta += R * J.acc_groups;
+        fcta += R * J.fin_chunks;
         adta += R * J.n_tiles;
         if (J.has_tail) {
             int blk0 = v.n_ism >> 2, blk_last = (v.n_S - 1) >> 2;
@@ -235,7 +271,7 @@ ism_status plan(const Validated* vs, int n, ism_precision prec, bool backward, J
         }
         rows += R * J.Q * 32LL * (J.slots + 1);
         if (prec == ISM_PREC_LUT) lut += (long long)(ism_lut_phases(J.slots) + 1) * 32 * J.slots;
-        if (J.use_cheb) cheb += 32LL * ISM_CHEB_N;
+        if (J.use_cheb) t.any_cheb = 1;
         if (backward) gpart += R * J.Q * 12;
         ids += R * J.img_per_rir;
         if (J.Q > t.max_Q) t.max_Q = J.Q;
@@ -247,7 +283,7 @@ ism_status plan(const Validated* vs, int n, ism_precision prec, bool backward, J
     if (ids >= 0xFFFFFFFFll)
         return fail(ISM_ERR_UNSUPPORTED, "%lld images in one launch set exceed 2^32; split the batch", ids);
     if (rir > 0x7FFFFFFFll || ecta > 0x7FFFFFFFll || acta > 0x7FFFFFFFll || adta > 0x7FFFFFFFll ||
-        tcta > 0x7FFFFFFFll)
+        tcta > 0x7FFFFFFFll || fcta > 0x7FFFFFFFll)
         return fail(ISM_ERR_UNSUPPORTED, "launch set too large; split the batch");
     p.hist_total = hist;
     p.ids_total = ids;
@@ -255,15 +291,16 @@ ism_status plan(const Validated* vs, int n, ism_precision prec, bool backward, J
     if (p.n_scan_blocks < 1) p.n_scan_blocks = 1;
     p.tbl_total = tbl;
     p.rows_total = rows;
+    if (t.any_cheb) std::memcpy(t.cheb, cheb_coefficients(), sizeof t.cheb);
     p.rir_total = rir;
     p.lut_total = lut;
-    p.cheb_total = cheb;
     p.gpart_total = gpart;
     p.rgrad_total = backward ? rir * 12 : 0;
     p.enum_ctas = ecta;
     p.acc_ctas = acta;
     p.adj_ctas = adta;
     p.tail_ctas = tcta;
+    p.fin_ctas = fcta;
     size_t off = base;
     p.status_off = 0;
     if (base == 0) off = 256;
@@ -281,8 +318,6 @@ ism_status plan(const Validated* vs, int n, ism_precision prec, bool backward, J
     off = align256(off + (size_t)rir * 4);
     p.lut_off = off;
     off = align256(off + (size_t)lut * 4);
-    p.cheb_off = off;
-    off = align256(off + (size_t)cheb * 4);
     p.gpart_off = off;
     off = align256(off + (size_t)p.gpart_total * 4);
     p.rgrad_off = off;
@@ -560,10 +595,6 @@ ism_status run_set(const std::vector<Validated>& set, ism_precision prec, size_t
         int launched = 0;
         if (p.lut_total > 0) {
             if ((e = ism_launch_lut_tables(t, p, ws, stream))) return cuda_fail(e, "windowed-sinc table kernel");
-            ++launched;
-        }
-        if (p.cheb_total > 0) {
-            if ((e = ism_launch_cheb_tables(t, p, ws, stream))) return cuda_fail(e, "Chebyshev table kernel");
             ++launched;
         }
         int acc_launched = 0;

@@ -66,6 +66,8 @@ struct JobDev {
     int cols_per_unit;        // grid columns (ix, iy) per enumeration unit
     float inv_kLz;            // 1 / ((f_s / c) L_z): samples -> z cells
     int acc_groups;           // accumulation CTAs per RIR (groups of ISM_ACC_BPC bins)
+    int fin_chunk;            // samples per finalize CTA (>= the envelope-fit window)
+    int fin_chunks;           // finalize CTAs per RIR (chunk 0 holds the last samples)
     int n_tiles;              // adjoint tiles (8 bins) per RIR
     int has_tail;
     int W_env;                // samples of the envelope fit window
@@ -86,9 +88,9 @@ struct JobDev {
     long long acc_cta_base;   // first accumulation CTA of the job
     long long adj_cta_base;   // first adjoint CTA of the job
     long long tail_cta_base;  // first tail CTA of the job
+    long long fin_cta_base;   // first finalize CTA of the job
     long long rows_base;      // first window row (float) of the job: [n_rir][Q][32 (slots + 1)]
     long long lut_base;       // first entry (float) of the job's windowed-sinc table (LUT form)
-    long long cheb_base;      // first Chebyshev coefficient (float) of the job: [32 taps][ISM_CHEB_N]
     // backward pass only
     const float* grad_out;    // dLoss/dh [n_rir][n_S]
     float* grad_beta;         // [6]
@@ -102,7 +104,8 @@ struct JobTable {
     int n_jobs;
     int max_Q;
     int max_axis_sum;
-    int pad;
+    int any_cheb;                      // some job accumulates through Chebyshev moments
+    float cheb[32 * ISM_CHEB_N];       // Chebyshev coefficients of the 32 tap functions (32-tap window)
     JobDev j[ISM_MAX_JOBS];
 };
 
@@ -118,7 +121,6 @@ struct WsPlan {
     size_t rows_off;       // float  [rows_total]: per-bin window rows of the accumulation
     size_t amp_off;        // float  [rir_total]
     size_t lut_off;        // float  [lut_total]: polyphase windowed-sinc tables (LUT form)
-    size_t cheb_off;       // float  [cheb_total]: Chebyshev coefficients of the 32 tap functions
     size_t gpart_off;      // float  [gpart_total]: backward, per-(RIR, bin) gradients
     size_t rgrad_off;      // float  [rgrad_total]: backward, per-RIR gradients
     size_t total;
@@ -128,7 +130,6 @@ struct WsPlan {
     long long rows_total;
     long long rir_total;
     long long lut_total;
-    long long cheb_total;
     long long gpart_total;
     long long rgrad_total;
     long long n_scan_blocks;
@@ -136,6 +137,7 @@ struct WsPlan {
     long long acc_ctas;
     long long adj_ctas;
     long long tail_ctas;
+    long long fin_ctas;
 };
 
 #define ISM_TAIL_CHUNK 4096   // tail samples per CTA (256 threads x 16)
@@ -167,7 +169,6 @@ int ism_launch_accum_fp16(const JobTable& t, const WsPlan& p, char* ws, void* st
 int ism_launch_accum_bf16(const JobTable& t, const WsPlan& p, char* ws, void* stream, int* launched);
 int ism_launch_accum_lut(const JobTable& t, const WsPlan& p, char* ws, void* stream, int* launched);
 int ism_launch_lut_tables(const JobTable& t, const WsPlan& p, char* ws, void* stream);
-int ism_launch_cheb_tables(const JobTable& t, const WsPlan& p, char* ws, void* stream);
 int ism_launch_accum_cheb(const JobTable& t, const WsPlan& p, char* ws, void* stream, int* launched);
 int ism_launch_adjoint(const JobTable& t, const WsPlan& p, char* ws, void* stream, int* launched);
 int ism_launch_finalize(const JobTable& t, const WsPlan& p, char* ws, void* stream);

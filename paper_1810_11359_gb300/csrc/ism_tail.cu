@@ -16,20 +16,27 @@
 
 namespace {
 
+// One CTA per (RIR, chunk of fin_chunk image-source samples); chunk c holds
+// samples [n_ism - (c + 1) fin_chunk, n_ism - c fin_chunk), so chunk 0 holds
+// the envelope-fit window and also fits the amplitude.
 __global__ void __launch_bounds__(256) finalize_kernel(const __grid_constant__ JobTable t,
                                                        const float* __restrict__ rows, float* __restrict__ amp)
 {
     const long long g = blockIdx.x;
-    const int jid = ism_find_job(t, g, [](const JobDev& j) { return j.rir_base; });
+    const int jid = ism_find_job(t, g, [](const JobDev& j) { return j.fin_cta_base; });
     const JobDev& J = t.j[jid];
-    const int r = (int)(g - J.rir_base);
+    const long long local = g - J.fin_cta_base;
+    const int r = (int)(local / J.fin_chunks);
+    const int c = (int)(local % J.fin_chunks);
     const int WIN = 32 * (J.slots + 1);
     float* out = J.out + (long long)r * J.n_S;
     const float* R = rows + J.rows_base + (long long)r * J.Q * WIN;
+    const int k_end = J.n_ism - c * J.fin_chunk;
+    const int k_beg = max(0, k_end - J.fin_chunk);
 
     // eq. (5): sample k is the sum of the window rows of the bins q with
     // 0 <= k - (32 q - H) < WIN, added in ascending q
-    for (int k = threadIdx.x; k < J.n_ism; k += blockDim.x) {
+    for (int k = k_beg + (int)threadIdx.x; k < k_end; k += blockDim.x) {
         const int top = k + J.H;                      // k - (32 q - H) = top - 32 q
         int q_hi = top / ISM_SB;
         if (q_hi > J.Q - 1) q_hi = J.Q - 1;
@@ -38,8 +45,8 @@ __global__ void __launch_bounds__(256) finalize_kernel(const __grid_constant__ J
         for (int q = q_lo; q <= q_hi; ++q) v += R[(long long)q * WIN + (top - ISM_SB * q)];
         out[k] = v;
     }
+    if (c != 0) return;
     __syncthreads();
-
     __shared__ float red[256];
     float A = 0.0f;
     if (J.has_tail && J.W_env > 0) {
@@ -112,8 +119,8 @@ __global__ void noise_kernel(uint64_t seed, uint32_t rir, uint32_t k0, int n, fl
 
 int ism_launch_finalize(const JobTable& t, const WsPlan& p, char* ws, void* stream)
 {
-    if (p.rir_total <= 0) return 0;
-    finalize_kernel<<<(unsigned)p.rir_total, 256, 0, (cudaStream_t)stream>>>(
+    if (p.fin_ctas <= 0) return 0;
+    finalize_kernel<<<(unsigned)p.fin_ctas, 256, 0, (cudaStream_t)stream>>>(
         t, reinterpret_cast<const float*>(ws + p.rows_off), reinterpret_cast<float*>(ws + p.amp_off));
     return (int)cudaGetLastError();
 }
