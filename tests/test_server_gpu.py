@@ -119,12 +119,13 @@ def test_admission_under_a_small_budget():
 
 
 def test_request_larger_than_the_budget_is_rejected_at_submit():
-    room = workloads.batched_fp32()
+    room = workloads.trajectory_array()      # 512 RIRs x 57,600 samples: 118 MB of output alone
     beta = ism.ism_beta_sabine(room.L, room.rt60)
-    N = ism.ism_nb_img_from_t(room.Tmax, room.L, room.c, room.window())
+    N = ism.ism_nb_img_from_t(room.Tdiff, room.L, room.c, room.window())
     with ism.Server(hbm_budget=32 << 20) as srv:
         with pytest.raises(ism.IsmError) as ei:
-            srv.submit(room.L, beta, room.pos_src, room.pos_rcv, N, room.Tmax, room.fs, Tw=room.window())
+            srv.submit(room.L, beta, room.pos_src, room.pos_rcv, N, room.Tmax, room.fs, Tdiff=room.Tdiff,
+                       Tw=room.window())
         assert ei.value.status == ism.STATUS_CODES["ISM_ERR_OOM"]
         assert srv.stats()["submitted"] == 0
 
