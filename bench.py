@@ -154,12 +154,12 @@ class ClockSampler:
 def traffic_from_profiles():
     """DRAM bytes per accumulation launch from the committed ncu summary, or
     None when the kernel source changed since it was captured."""
-    path = os.path.join(ROOT, "profiles", "accum_batched_128rir.txt")
+    path = os.path.join(ROOT, "profiles", "cheb_batched_128rir.txt")
     try:
         from paper_1810_11359_gb300 import build as b
         import hashlib
         h = hashlib.sha256()
-        for f in ("ism_accum.cuh", "ism_accum.cu"):
+        for f in ("ism_accum_cheb.cu", "ism_accum.cuh", "ism_device.cuh", "ism_internal.h"):
             h.update(open(os.path.join(b.CSRC, f), "rb").read())
         dig = h.hexdigest()[:16]
         vals = {}
@@ -605,10 +605,18 @@ def main():
         tail_bytes = 4.0 * (n_S - n_ism) * ps.shape[0] * pr.shape[0]   # one FP32 store per tail sample
         tail_ms_launch = tail_ms / k_roof                              # one stream, summed over the step's launches
         hbm = float(peaks.get("hbm_gbs", 6800.0))
-        line["tail_roofline"] = {"bound": "hbm", "kernel": "tail_kernel", "achieved": tail_bytes / tail_ms_launch / 1e6,
-                                 "peak": hbm, "unit": "GB/s", "frac": tail_bytes / tail_ms_launch / 1e6 / hbm,
-                                 "bytes_per_step": tail_bytes, "kernel_ms_per_step": tail_ms_launch,
-                                 "peak_basis": f"{peak_kind} HBM copy bandwidth"}
+        # the tail kernel is issue-bound (ncu: 81 % issue, 21 % of the copy bandwidth): count
+        # the operations of its specification per sample -- Philox4x32-10 (100 integer ops per
+        # 4 samples), the uniform (4), the ratio u / (1 - u) (2), the FP32 ln (22), the
+        # logistic scale (1), the envelope (4) and the product (1)
+        tail_ops = 59.0 * (n_S - n_ism) * ps.shape[0] * pr.shape[0]
+        tail_tops = tail_ops / (tail_ms_launch * 1e-3) / 1e12
+        line["tail_roofline"] = {"bound": "alu", "kernel": "tail_kernel", "achieved": tail_tops, "peak": peak_tops,
+                                 "unit": "Tops/s (lane ops)", "frac": tail_tops / peak_tops, "ops_per_sample": 59,
+                                 "kernel_ms_per_step": tail_ms_launch,
+                                 "hbm_gbs": tail_bytes / tail_ms_launch / 1e6, "hbm_frac": tail_bytes / tail_ms_launch / 1e6 / hbm,
+                                 "bytes_per_step": tail_bytes,
+                                 "peak_basis": f"{n_sm} SMs x 128 lanes x {sm_mhz:.0f} MHz; HBM {peak_kind} copy bandwidth"}
     if not args.no_cpu_baseline and world >= 1:
         line["cpu_baseline"] = cpu_baseline(room, beta, N, Tdiff)
     print(json.dumps(line), flush=True)
