@@ -522,12 +522,10 @@ def main():
     ism.ism_profile_enable(False)
     prof_roof = ism.ism_profile_read()
     ism.ism_set_lanes(2)
-    if world > 1:
-        t = torch.tensor([ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    from paper_1810_11359_gb300 import replicas
+    ms = replicas.max_over_ranks(ms, device=dev)           # the slowest rank's step
     rirs = ps.shape[0] * pr.shape[0] * world
-    value = rirs / (ms * 1e-3)
+    value = replicas.whole_job_rate(ps.shape[0] * pr.shape[0], world, ms * 1e-3)
 
     # end to end through the host-buffer entry point: pinned inputs in, RIRs out
     h_ps = torch.from_numpy(room.pos_src).pin_memory()
@@ -548,10 +546,7 @@ def main():
     for _ in range(e2e_steps):
         step_host()
     e2e_dt = (time.perf_counter() - t0) / e2e_steps
-    if world > 1:
-        t = torch.tensor([e2e_dt], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_dt = float(t.item())
+    e2e_dt = replicas.max_over_ranks(e2e_dt, device=dev)
 
     if rank != 0:
         dist.destroy_process_group()
