@@ -64,11 +64,14 @@ typedef enum {
  * accumulation is always FP32.
  *   ISM_PREC_FP32: for a window of exactly 32 taps, the windowed sinc of tap
  *   j as a function of the fractional delay f, delta'(j - f), is expanded in
- *   Chebyshev polynomials of 2f - 1 (degree 9, error < 3e-9 of the image's
- *   amplitude, below FP32 rounding); the images of a delay bin that share
- *   their integer offset are summed as 10 moments sum A T_i(2f - 1), and
- *   each offset's moments are expanded once into the 32 taps.  Other
- *   windows use the direct evaluation of ISM_PREC_FP32_DIRECT. */
+ *   Chebyshev polynomials of 2f - 1 (degree 8, error < 6.5e-8 of the image's
+ *   amplitude); the images of a delay bin that share their integer offset
+ *   are summed as 9 moments sum A T_i(2f - 1), each term rounded to a
+ *   fixed-point integer with a step of 2^-23 of the bin's largest possible
+ *   amplitude and summed exactly (so the result does not depend on the
+ *   order of the images), and each offset's moments are expanded once into
+ *   the 32 taps.  Other windows use the direct evaluation of
+ *   ISM_PREC_FP32_DIRECT. */
 typedef enum {
     ISM_PREC_FP32 = 0,        /* FP32, Chebyshev moments (32-tap windows), else direct */
     ISM_PREC_FP16X2 = 1,      /* packed FP16 window and sinc, FP32 accumulation        */

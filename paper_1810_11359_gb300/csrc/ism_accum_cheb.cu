@@ -6,18 +6,20 @@
 // N_w = 32 taps every tap function g_j(f) = delta'(j - f), j = -15 .. 16, is
 // an entire function of f on [0, 1] (the window's zeros fall at the ends of
 // the interval, so no mask cuts it), and its Chebyshev series in u = 2f - 1
-// converges fast: degree 9 reproduces each g_j to 2e-9 (the coefficients
-// c_{j,i}, interpolated at the 10 Chebyshev-Gauss nodes in FP64 on the host,
-// travel in the kernel's parameter table).  Hence for the images of one delay
-// bin that share the integer offset rr = b - 32 q,
+// converges fast: degree 8 reproduces each g_j to 6.4e-8 of the image's
+// amplitude (degree 9: 2.1e-9; degree 7: 4.2e-7), below the fixed-point step
+// of the moment terms (2^-23 of the bin's largest amplitude, see below).  The
+// coefficients c_{j,i}, interpolated at the 9 Chebyshev-Gauss nodes in FP64
+// on the host, travel in the kernel's parameter table.  Hence for the images
+// of one delay bin that share the integer offset rr = b - 32 q,
 //   sum_n A_n g_j(f_n) = sum_i c_{j,i} M_i,   M_i = sum_n A_n T_i(2 f_n - 1),
-// so each image costs 10 moment terms instead of 32 tap evaluations, and each
-// offset costs 10 FMAs per tap once per bin.
+// so each image costs 9 moment terms instead of 32 tap evaluations, and each
+// offset costs 9 FMAs per tap once per bin.
 //
 // One warp per bin.  Each lane takes every 32nd id of the bin, computes the
 // image's exact float-float delay and amplitude (eq. (2)-(4)) -- so its offset
 // rr in [-1, 31] is exact and no image needs special handling -- and adds its
-// 10 moment terms, as integers, into the bin's moment table in shared memory
+// 9 moment terms, as integers, into the bin's moment table in shared memory
 // with integer atomics.  Integer addition is associative, so the sums, and
 // everything computed from them, are the same in every run whatever the order
 // in which lanes and warps reach the table; no sort of the images by offset is
@@ -206,7 +208,6 @@ __global__ void __launch_bounds__(ISM_ACC_BPC * 32, 10) cheb_kernel(const __grid
         D[0] = __fmaf_rn(c[6], m1.z, D[0]);
         D[0] = __fmaf_rn(c[7], m1.w, D[0]);
         D[0] = __fmaf_rn(c[8], m2.x, D[0]);
-        D[0] = __fmaf_rn(c[9], m2.y, D[0]);
         flush_run<1, false>(D, acc, o - 1, lane, 1.0f);
     }
     float* row = rows + J.rows_base + ((long long)r * J.Q + q) * WIN;

@@ -44,7 +44,7 @@
 #define ISM_SCAN_BLOCK 4096       // elements per scan block
 #define ISM_SCAN_TOP 16384        // max scan blocks (one top-level block)
 #define ISM_FIT_WINDOW_S 0.02     // envelope fit: last 20 ms of the ISM part
-#define ISM_CHEB_N 10             // Chebyshev terms of a tap function (degree 9)
+#define ISM_CHEB_N 9              // Chebyshev terms of a tap function (degree 8)
 
 // Device-side description of one job.  Everything the kernels need is here
 // so that a whole launch set takes its jobs as one kernel parameter.
