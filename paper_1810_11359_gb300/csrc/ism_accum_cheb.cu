@@ -1,5 +1,6 @@
 // ism_accum_cheb.cu -- FP32 accumulation of eq. (5) for a 32-tap window
-// through a Chebyshev expansion of the windowed sinc in the fractional delay.
+// through a Chebyshev expansion of the windowed sinc in the fractional delay,
+// fused with the enumeration of the images (Section 2.1) it accumulates.
 //
 // For tap j of an image with delay s = b + f (b integer, f in [0, 1)), the
 // sample b + j receives A delta'(j - f) (eq. (6)).  For a window of exactly
@@ -8,206 +9,337 @@
 // the interval, so no mask cuts it), and its Chebyshev series in u = 2f - 1
 // converges fast: degree 8 reproduces each g_j to 6.4e-8 of the image's
 // amplitude (degree 9: 2.1e-9; degree 7: 4.2e-7), below the fixed-point step
-// of the moment terms (2^-23 of the bin's largest amplitude, see below).  The
-// coefficients c_{j,i}, interpolated at the 9 Chebyshev-Gauss nodes in FP64
-// on the host, travel in the kernel's parameter table.  Hence for the images
-// of one delay bin that share the integer offset rr = b - 32 q,
+// of the moment terms (see below).  The coefficients c_{j,i}, interpolated at
+// the 9 Chebyshev-Gauss nodes in FP64 on the host, travel in the kernel's
+// parameter table.  Hence for the images that share the integer delay b,
 //   sum_n A_n g_j(f_n) = sum_i c_{j,i} M_i,   M_i = sum_n A_n T_i(2 f_n - 1),
 // so each image costs 9 moment terms instead of 32 tap evaluations, and each
-// offset costs 9 FMAs per tap once per bin.
+// integer delay costs 9 FMAs per tap once.
 //
-// One warp per bin.  Each lane takes every 32nd id of the bin, computes the
-// image's exact float-float delay and amplitude (eq. (2)-(4)) -- so its offset
-// rr in [-1, 31] is exact and no image needs special handling -- and adds its
-// 9 moment terms, as integers, into the bin's moment table in shared memory
-// with integer atomics.  Integer addition is associative, so the sums, and
-// everything computed from them, are the same in every run whatever the order
-// in which lanes and warps reach the table; no sort of the images by offset is
-// needed.
+// Delay bins.  Bin q holds the images with b in [32 q - 1, 32 q + 31), i.e.
+// offsets rr = b - 32 q in [-1, 30] (32 offsets, one per lane); its taps fall
+// in the 64 samples from 32 q - 16, the bin's window row, which the finalize
+// kernel sums per sample with the previous bin's row.  An image is kept iff a
+// tap reaches a sample below n_ism: b <= n_ism + 14.
 //
-// Fixed point.  Every image of bin q has s >= max(s_direct, 32 q - 1/2) (the
+// One CTA owns B = 8 consecutive bins of one RIR -- a spherical shell of
+// 256 samples around the receiver -- and enumerates the images in it itself:
+// the image coordinates along one axis increase with the index n (eq. (1)),
+// so for a grid column (ix, iy) the images whose distance falls in the shell
+// form at most two index intervals in z (below and above the receiver),
+// found in closed form from the source and receiver coordinates; the columns
+// that reach the shell form one interval in iy per row ix.  The CTA's warps
+// take the columns 32 at a time, compute each column's intervals, and then
+// process the column candidates 32 at a time (a candidate's column by binary
+// search over the warp's running counts).  Candidate intervals are widened by
+// 0.05 sample; each candidate's exact float-float delay (eq. (2)-(3), from
+// the per-axis tables) decides its bin, so every image lands in exactly one
+// CTA, the one whose bins hold its b.
+//
+// Fixed point.  Every image of bin q has s >= max(s_direct, 32 q - 1) (the
 // direct path is the shortest: along each axis the source's own coordinate is
-// the image coordinate nearest the receiver), so |A T_i| <= A_max = amp_scale
-// / max(s_direct, 32 q - 1).  A term is A T_i scaled by 2^e, e the largest
-// integer with 2^e A_max <= (1 - 2^-10) 2^22, and rounded to an integer
-// (one FFMA against 1.5 2^23: the sum's bits hold the integer); |term| <
-// 2^22, so the rounding error is at most 2^-23 A_max per term, the resolution
-// of FP32 on the bin's largest term.  Each term is one 32-bit shared-memory
-// atomic add (64-bit atomics holding two moments each measured 2.3x slower);
-// after every 256 ids each lane moves the sums of its offset into FP32
-// moments (x 2^-e, exact) and clears them, so no sum can exceed
-// 256 x 2^22 = 2^30 in magnitude.
+// the image coordinate nearest the receiver) and at least d / L_max - 3 wall
+// hits (|n| >= |x_n - x_r| / L - 1 on each axis), so |A| <= A_max = amp_scale
+// beta_max^h / s_lo.  A term A T_i is scaled by 2^e and rounded to an integer
+// (one FFMA against 1.5 2^23: the sum's bits hold the integer), e the largest
+// integer with 2^e A_max <= min((1 - 2^-10) 2^22, 0.99 2^31 / n_q), n_q the
+// number of images the enumeration counted in the plain-FP32 bins q - 1 and
+// q (which hold every image of exact bin q): no term reaches 2^22 and no sum
+// 2^31.  The sums are 32-bit shared-memory atomic adds; integer addition is
+// associative, so the sums -- and the FP32 result -- are the same in every
+// run, whatever the order in which lanes and warps add their terms.  The
+// rounding error is at most 2^-23 A_max per term at the bins where n_q <=
+// 512 and grows with n_q beyond (2^-31 n_q A_max); A_max falls with the
+// distance and the wall hits, so it stays below FP32's own error on the
+// result.
 //
-// Finally each non-empty offset's moments are expanded into the taps (lane =
-// tap) and rotated into the bin's register window, which is stored as the
-// bin's row; the finalize kernel sums the rows per sample.
+// Finally each warp expands the non-empty offsets of one bin into the taps
+// (lane = tap) and rotates them into the bin's register window, which it
+// stores as the bin's row.
 #include "ism_accum.cuh"
 
 namespace {
 
-#define CB_PIECE 256    // ids between two moves of the integer sums into FP32
-#define CB_MPAD 12      // moments of one offset, padded to three float4
+#define SH_B ISM_SHELL_BINS  // delay bins per CTA (a shell of 256 samples)
+#define SH_WARPS 8          // warps per CTA
+#define SH_NO 32            // offsets per bin (rr = -1 .. 30)
+#define SH_RS 33            // row stride of the moment table (conflict-light atomics)
+#define SH_MARGIN 0.05f     // candidate margin (samples)
 #define CB_MAGIC 12582912.0f                       // 1.5 * 2^23
 #define CB_MAGIC_BITS 0x4B400000u                  // its bits
-#define CB_TERM_MAX (4194304.0f * (1.0f - 1.0f / 1024.0f))
 
-struct __align__(16) ChebWarp {
-    union {
-        int P[ISM_CHEB_N * ISM_NB];         // integer sums of the moments: [moment][rr + 1]
-        float M[ISM_NB * CB_MPAD];          // after the last move: FP32 moments per offset
-    };
-    float M32[CB_MPAD];                     // FP32 moments of offset 31 (lane 0) across pieces
-};
-
-// Moves the integer sums of one offset (index o = rr + 1) into FP32 moments
-// and clears them; returns whether any sum was non-zero.
-__device__ __forceinline__ bool cheb_move(int* P, int o, float inv_scale, float (&Mx)[ISM_CHEB_N])
+// Smallest image index n of an axis with coordinate X(n) >= Z: X(2m) = 2 m L
+// + x_s and X(2m - 1) = 2 m L - x_s (eq. (1)); X increases with n.
+__device__ __forceinline__ int ax_first(float Z, float xs, float inv2L)
 {
-    bool any = false;
-#pragma unroll
-    for (int k = 0; k < ISM_CHEB_N; ++k) {
-        const int v = P[k * ISM_NB + o];
-        P[k * ISM_NB + o] = 0;
-        any |= v != 0;
-        Mx[k] = __fmaf_rn(__int2float_rn(v), inv_scale, Mx[k]);
-    }
-    return any;
+    Z = fminf(fmaxf(Z, -1e7f), 1e7f);
+    const int me = (int)ceilf((Z - xs) * inv2L);
+    const int mo = (int)ceilf((Z + xs) * inv2L);
+    return min(2 * me, 2 * mo - 1);
 }
 
-__global__ void __launch_bounds__(ISM_ACC_BPC * 32, 10) cheb_kernel(const __grid_constant__ JobTable t,
-                                                                 const float4* __restrict__ tbl,
-                                                                 const uint32_t* __restrict__ hist,
-                                                                 const uint32_t* __restrict__ ids,
-                                                                 float* __restrict__ rows,
-                                                                 uint32_t* __restrict__ status)
+struct ShellAxis {
+    float xs, xr, inv2L, k_inv;   // source, receiver coordinate; 1 / (2 L); c / f_s (metres per sample)
+    int nlo, N;
+};
+
+// Index interval [i0, i1) (0-based, clamped to the grid) of the images of an
+// axis with X(n) - x_r in [D_lo, D_hi) (metres).
+__device__ __forceinline__ void ax_range(const ShellAxis& a, float Dlo, float Dhi, int* i0, int* i1)
+{
+    const int n0 = ax_first(a.xr + Dlo, a.xs, a.inv2L);
+    const int n1 = ax_first(a.xr + Dhi, a.xs, a.inv2L);
+    *i0 = min(max(n0 - a.nlo, 0), a.N);
+    *i1 = min(max(n1 - a.nlo, 0), a.N);
+}
+
+__global__ void __launch_bounds__(SH_WARPS * 32, 4) shell_kernel(const __grid_constant__ JobTable t,
+                                                                  const float4* __restrict__ tbl,
+                                                                  const uint32_t* __restrict__ hist,
+                                                                  float* __restrict__ rows,
+                                                                  uint32_t* __restrict__ status)
 {
     constexpr int WIN = 64;   // 32 (SLOTS + 1), SLOTS = 1
     extern __shared__ __align__(16) unsigned char smem[];
     const long long g = blockIdx.x;
-    const int jid = ism_find_job(t, g, [](const JobDev& j) { return j.acc_cta_base; });
+    const int jid = ism_find_job(t, g, [](const JobDev& j) { return j.shell_cta_base; });
     const JobDev& J = t.j[jid];
-    if (!J.use_cheb) return;   // the direct kernel handles this job
-
-    const long long local = g - J.acc_cta_base;
-    const int r = (int)(local / J.acc_groups);
-    const int grp = J.acc_groups - 1 - (int)(local % J.acc_groups);  // densest (latest) bins first
+    const long long local = g - J.shell_cta_base;
+    const int r = (int)(local / J.shell_groups);
+    const int grp = J.shell_groups - 1 - (int)(local % J.shell_groups);  // densest (latest) shells first
+    const int q0 = grp * SH_B;
+    const int nb = min(SH_B, J.Q - q0);
     const int Nx = J.N[0], Ny = J.N[1], Nz = J.N[2];
     const int n_axis = Nx + Ny + Nz;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 
+    // shared memory: axis tables | moment sums | per-bin scales | row prefix | per-warp column records
     float4* T = reinterpret_cast<float4*>(smem);
-    ChebWarp* Wall = reinterpret_cast<ChebWarp*>(smem + (size_t)((t.max_axis_sum + 1) & ~1) * sizeof(float4));
+    int* S = reinterpret_cast<int*>(smem + (size_t)((t.max_axis_sum + 1) & ~1) * sizeof(float4));
+    float* scale_s = reinterpret_cast<float*>(S + SH_B * ISM_CHEB_N * SH_RS);
+    float* inv_s = scale_s + SH_B;
+    int* rowpre = reinterpret_cast<int*>(inv_s + SH_B);                        // [Nx]: columns up to row ix
+    int* rowy0 = rowpre + ((t.max_axis_sum + 4) & ~3);                          // [Nx]: first iy of row ix
+    float4* recf = reinterpret_cast<float4*>(rowy0 + ((t.max_axis_sum + 4) & ~3));
+    int4* reci = reinterpret_cast<int4*>(recf + SH_WARPS * 32);
+    int* st = reinterpret_cast<int*>(reci + SH_WARPS * 32);                     // [warps][33]
+    float4* Wf = recf + warp * 32;
+    int4* Wi = reci + warp * 32;
+    int* Wst = st + warp * 33;
+
     const float4* Tg = tbl + J.tbl_base + (long long)r * n_axis;
     for (int e = threadIdx.x; e < n_axis; e += blockDim.x) T[e] = Tg[e];
-
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    ChebWarp& W = Wall[warp];
-    const int q = grp * ISM_ACC_BPC + warp;
-    for (int e = lane; e < ISM_CHEB_N * ISM_NB; e += 32) W.P[e] = 0;
-    if (lane < CB_MPAD) W.M32[lane] = 0.0f;
+    for (int e = threadIdx.x; e < SH_B * ISM_CHEB_N * SH_RS; e += blockDim.x) S[e] = 0;
     __syncthreads();
-    if (q >= J.Q) return;
 
-    // fixed-point scale 2^e of the bin (see the header)
-    float scale, inv_scale;
-    {
-        const float sd = sqrtf(T[-J.nlo[0]].x + T[Nx - J.nlo[1]].x + T[Nx + Ny - J.nlo[2]].x);
-        const float s_lo = fmaxf(fmaxf(sd * (1.0f - 1.0f / 1024.0f), (float)(ISM_SB * q) - 1.0f), 1e-30f);
-        const float ratio = CB_TERM_MAX / (J.amp_scale / s_lo);
-        int e = ((__float_as_int(ratio) >> 23) & 0xFF) - 127;   // floor(log2(ratio)), ratio normal
-        e = max(-126, min(126, e));
-        scale = __int_as_float((e + 127) << 23);
-        inv_scale = __int_as_float((127 - e) << 23);
+    // geometry of the RIR
+    const int i_src = r / J.n_rcv, i_rcv = r - (r / J.n_rcv) * J.n_rcv;
+    const float kinv = J.c / J.fs;   // metres per sample
+    ShellAxis ax[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        ax[a].xs = J.pos_src[3 * i_src + a];
+        ax[a].xr = J.pos_rcv[3 * i_rcv + a];
+        ax[a].inv2L = (float)(0.5 / J.L[a]);
+        ax[a].k_inv = kinv;
+        ax[a].nlo = J.nlo[a];
+        ax[a].N = J.N[a];
     }
+    const float sd2 = T[-J.nlo[0]].x + T[Nx - J.nlo[1]].x + T[Nx + Ny - J.nlo[2]].x;
+    const bool valid = sd2 < 3.0e38f;   // +inf tables: a pair outside the room (flagged by the geometry kernel)
 
-    float M[ISM_CHEB_N];
-#pragma unroll
-    for (int i = 0; i < ISM_CHEB_N; ++i) M[i] = 0.0f;
-    unsigned nonempty = 0u;     // bit o: offset index o (< 32) has had images
-    bool last_nonempty = false; // offset index 32 (rr = 31)
+    // exact delays b owned by this CTA: [b_lo, b_hi)
+    const int b_lo = ISM_SB * q0 - 1;
+    const int b_hi = min(ISM_SB * (q0 + nb) - 1, J.n_ism + J.H - 1);   // b <= n_ism + 14 for H = 16
+    const float s_lo = fmaxf((float)b_lo - SH_MARGIN, 0.0f);
+    const float s_hi = (float)b_hi + SH_MARGIN;
+    const float s_lo2 = s_lo * s_lo, s_hi2 = s_hi * s_hi;
 
-    const long long hb = J.hist_base + ((long long)r * J.Q + q) * J.U;
-    const uint32_t start = hist[hb];
-    const uint32_t end = hist[hb + J.U];
-    for (uint32_t p0 = start; p0 < end; p0 += CB_PIECE) {
-        const int n = (int)min((uint32_t)CB_PIECE, end - p0);
-        uint32_t pid[CB_PIECE / 32];
-#pragma unroll
-        for (int u = 0; u < CB_PIECE / 32; ++u) {
-            const int i = 32 * u + lane;
-            pid[u] = (i < n) ? ids[p0 + i] : 0u;
+    if (threadIdx.x < SH_B) {
+        // fixed-point scale of bin q0 + threadIdx.x
+        const int q = q0 + (int)threadIdx.x;
+        float sc = 1.0f;
+        if (q < J.Q && valid) {
+            const long long hrow = J.hist_base + (long long)r * J.Q * J.U;
+            const uint32_t o_prev = hist[hrow + (long long)max(q - 1, 0) * J.U];
+            const uint32_t o_next = hist[hrow + (long long)(q + 1) * J.U];
+            const float nq = (float)max(o_next - o_prev, 1u);
+            const float slo = fmaxf(fmaxf(sqrtf(sd2) * (1.0f - 1.0f / 1024.0f), (float)(ISM_SB * q) - 1.0f), 1e-30f);
+            float bmax = 0.0f;
+            for (int w = 0; w < 6; ++w) bmax = fmaxf(bmax, fabsf(J.beta[w]));
+            double Lmax = fmax(J.L[0], fmax(J.L[1], J.L[2]));
+            const int h = max(0, (int)floorf(slo * kinv / (float)Lmax - 3.0f));
+            const float decay = (h == 0) ? 1.0f : (bmax > 0.0f ? exp2f((float)h * log2f(bmax)) : 0.0f);
+            const float amax = J.amp_scale / slo * decay * 1.001f;
+            const float cap = fminf(4194304.0f * (1.0f - 1.0f / 1024.0f), 0.99f * 2147483648.0f / nq);
+            const float ratio = amax > 0.0f ? cap / amax : 3.0e38f;
+            int e = ((__float_as_int(ratio) >> 23) & 0xFF) - 127;   // floor(log2(ratio))
+            e = max(-126, min(126, e));
+            sc = __int_as_float((e + 127) << 23);
         }
-#pragma unroll
-        for (int u = 0; u < CB_PIECE / 32; ++u) {
-            const int i = 32 * u + lane;
-            if (32 * u >= n) break;                  // warp-uniform
-            if (i >= n) continue;
-            const int ix = pid[u] & 1023, iy = (pid[u] >> 10) & 1023, iz = pid[u] >> 20;
-            float f, amp;
-            int rr;
-            bool bad;
-            ism_delay(T[ix], T[Nx + iy], T[Nx + Ny + iz], q, J.amp_scale, &f, &amp, &rr, &bad);
-            if (bad) {
-                atomicOr(status, (uint32_t)ISM_DEVICE_FLAG_BIN);
-                continue;
+        scale_s[threadIdx.x] = sc;
+        inv_s[threadIdx.x] = 1.0f / sc;   // exact: a power of two
+    }
+    // columns that reach the shell: row ix takes iy with |y - y_r| < D_y
+    for (int ix = threadIdx.x; ix < Nx; ix += blockDim.x) {
+        int w = 0, y0 = 0;
+        if (valid) {
+            const float rem = __fsub_rn(s_hi2, T[ix].x);
+            if (rem > 0.0f) {
+                const float Dy = __fadd_rn(__fmul_rn(sqrtf(rem), kinv), 1e-3f);
+                int y1;
+                ax_range(ax[1], -Dy, Dy, &y0, &y1);
+                w = max(y1 - y0, 0);
             }
-            // moment terms round(2^e A T_i(u)), T_i by the three-term recurrence
-            const float as = amp * scale;
-            const float uu = __fmaf_rn(2.0f, f, -1.0f);
-            const float u2 = uu + uu;
-            uint32_t b[ISM_CHEB_N];
-            b[0] = __float_as_uint(__fadd_rn(as, CB_MAGIC));
-            b[1] = __float_as_uint(__fmaf_rn(as, uu, CB_MAGIC));
-            float tp = 1.0f, tc = uu;
+        }
+        rowpre[ix] = w;
+        rowy0[ix] = y0;
+    }
+    __syncthreads();
+    if (warp == 0) {   // inclusive prefix over the rows
+        int carry = 0;
+        for (int base = 0; base < Nx; base += 32) {
+            const int i = base + lane;
+            int v = i < Nx ? rowpre[i] : 0;
 #pragma unroll
-            for (int k = 2; k < ISM_CHEB_N; ++k) {
-                const float tn = __fmaf_rn(u2, tc, -tp);
-                b[k] = __float_as_uint(__fmaf_rn(as, tn, CB_MAGIC));
-                tp = tc;
-                tc = tn;
+            for (int o = 1; o < 32; o <<= 1) {
+                const int n = __shfl_up_sync(0xffffffffu, v, o);
+                if (lane >= o) v += n;
             }
-            int* Pb = W.P + (rr + 1);
+            if (i < Nx) rowpre[i] = carry + v;
+            carry += __shfl_sync(0xffffffffu, v, 31);
+        }
+    }
+    __syncthreads();
+    const int n_cols = Nx > 0 ? rowpre[Nx - 1] : 0;
+
+    const float amp_scale = J.amp_scale;
+    for (int c0 = warp * 32; c0 < n_cols; c0 += SH_WARPS * 32) {
+        // ---- the column of this lane and its candidate intervals in z
+        const int cl = c0 + lane;
+        int cnt = 0;
+        float4 rf = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+        int4 ri = make_int4(0, 0, 0, 0);
+        if (cl < n_cols) {
+            int lo = 0, hi = Nx - 1;   // row: first ix with rowpre[ix] > cl
+            while (lo < hi) {
+                const int mid = (lo + hi) >> 1;
+                if (rowpre[mid] > cl) hi = mid;
+                else lo = mid + 1;
+            }
+            const int ix = lo;
+            const int before = ix > 0 ? rowpre[ix - 1] : 0;
+            const float4 tx = T[ix];
+            const int iy = min(rowy0[ix] + (cl - before), Ny - 1);
+            const float4 ty = T[Nx + iy];
+            const ff sxy = ff_add(ff{tx.x, tx.y}, ff{ty.x, ty.y});
+            const float sxy_p = __fadd_rn(tx.x, ty.x);
+            const float D1 = fmaxf(__fsub_rn(__fmul_rn(sqrtf(fmaxf(__fsub_rn(s_lo2, sxy_p), 0.0f)), kinv), 1e-3f), 0.0f);
+            const float D2 = __fadd_rn(__fmul_rn(sqrtf(fmaxf(__fsub_rn(s_hi2, sxy_p), 0.0f)), kinv), 1e-3f);
+            int d0 = 0, d1 = 0, u0 = 0, u1 = 0;
+            if (s_hi2 > sxy_p) {
+                ax_range(ax[2], -D2, -D1, &d0, &d1);   // below the receiver (closed-open in n)
+                ax_range(ax[2], D1, D2, &u0, &u1);     // above
+                d1 = min(d1, u0);                      // disjoint, whatever the rounding
+            }
+            const int nd = max(d1 - d0, 0), nu = max(u1 - u0, 0);
+            cnt = nd + nu;
+            rf = make_float4(sxy.hi, sxy.lo, tx.z * ty.z, 0.0f);
+            ri = make_int4(d0, nd, u0, 0);
+        }
+        int inc = cnt;
 #pragma unroll
-            for (int k = 0; k < ISM_CHEB_N; ++k) atomicAdd(Pb + k * ISM_NB, (int)(b[k] - CB_MAGIC_BITS));
+        for (int o = 1; o < 32; o <<= 1) {
+            const int n = __shfl_up_sync(0xffffffffu, inc, o);
+            if (lane >= o) inc += n;
+        }
+        const int total = __shfl_sync(0xffffffffu, inc, 31);
+        __syncwarp();
+        Wf[lane] = rf;
+        Wi[lane] = ri;
+        Wst[lane] = inc - cnt;
+        if (lane == 31) Wst[32] = total;
+        __syncwarp();
+
+        // ---- the candidates, 32 at a time
+        for (int j0 = 0; j0 < total; j0 += 32) {
+            const int j = j0 + lane;
+            if (j < total) {
+                int lo = 0, hi = 31;   // last column o with Wst[o] <= j
+#pragma unroll
+                for (int s = 0; s < 5; ++s) {
+                    const int mid = (lo + hi + 1) >> 1;
+                    if (Wst[mid] <= j) lo = mid;
+                    else hi = mid - 1;
+                }
+                const float4 cf = Wf[lo];
+                const int4 ci = Wi[lo];
+                const int i = j - Wst[lo];
+                const int iz = i < ci.y ? ci.x + i : ci.z + (i - ci.y);
+                const float4 tz = T[Nx + Ny + iz];
+                const ff s2 = ff_add(ff{cf.x, cf.y}, ff{tz.x, tz.y});
+                const ff sq = ff_sqrt(s2);
+                float bf = floorf(sq.hi);
+                float f = __fadd_rn(__fsub_rn(sq.hi, bf), sq.lo);
+                const bool neg = f < 0.0f;   // bring f into [0, 1) (see ism_delay)
+                f = neg ? __fadd_rn(f, 1.0f) : f;
+                bf = neg ? bf - 1.0f : bf;
+                const bool one = f >= 1.0f;
+                f = one ? __fsub_rn(f, 1.0f) : f;
+                bf = one ? bf + 1.0f : bf;
+                const int b = ism_int_of_integral(fminf(bf, 4.0e6f));
+                if (b >= b_lo && b < b_hi) {
+                    const int q = (b + 1) >> 5;
+                    const int ql = q - q0;
+                    const int o = b - ISM_SB * q + 1;   // offset index rr + 1 in [0, 32)
+                    const float amp = cf.z * tz.z * amp_scale * ism_rcp(sq.hi);
+                    const float as = amp * scale_s[ql];
+                    const float uu = __fmaf_rn(2.0f, f, -1.0f);
+                    const float u2 = uu + uu;
+                    int* Sb = S + ql * (ISM_CHEB_N * SH_RS) + o;
+                    atomicAdd(Sb, (int)(__float_as_uint(__fadd_rn(as, CB_MAGIC)) - CB_MAGIC_BITS));
+                    atomicAdd(Sb + SH_RS, (int)(__float_as_uint(__fmaf_rn(as, uu, CB_MAGIC)) - CB_MAGIC_BITS));
+                    float tp = 1.0f, tc = uu;
+#pragma unroll
+                    for (int k = 2; k < ISM_CHEB_N; ++k) {
+                        const float tn = __fmaf_rn(u2, tc, -tp);
+                        atomicAdd(Sb + k * SH_RS,
+                                  (int)(__float_as_uint(__fmaf_rn(as, tn, CB_MAGIC)) - CB_MAGIC_BITS));
+                        tp = tc;
+                        tc = tn;
+                    }
+                }
+            }
         }
         __syncwarp();
-        // lane l owns offset index l (rr = l - 1); lane 0 also index 32 (rr = 31)
-        nonempty |= __ballot_sync(0xffffffffu, cheb_move(W.P, lane, inv_scale, M));
-        if (lane == 0) {
-            float M2[ISM_CHEB_N];
-#pragma unroll
-            for (int i = 0; i < ISM_CHEB_N; ++i) M2[i] = W.M32[i];
-            last_nonempty |= cheb_move(W.P, 32, inv_scale, M2);
-#pragma unroll
-            for (int i = 0; i < ISM_CHEB_N; ++i) W.M32[i] = M2[i];
-        }
-        __syncwarp();
     }
-    last_nonempty = __shfl_sync(0xffffffffu, last_nonempty, 0);
+    __syncthreads();
 
-    // ---- expansion of each non-empty offset into the taps, rotated into the window
+    // ---- expansion: warp w owns bin q0 + w; lane o reads the sums of offset o
+    if (warp >= nb) return;
+    const int q = q0 + warp;
+    int* Sb = S + warp * (ISM_CHEB_N * SH_RS);
+    float* Mb = reinterpret_cast<float*>(Sb);
+    const float inv = inv_s[warp];
+    bool any = false;
 #pragma unroll
-    for (int i = 0; i < ISM_CHEB_N; ++i) W.M[lane * CB_MPAD + i] = M[i];
-    if (lane < CB_MPAD) W.M[32 * CB_MPAD + lane] = W.M32[lane];
+    for (int k = 0; k < ISM_CHEB_N; ++k) {
+        const int v = Sb[k * SH_RS + lane];
+        any |= v != 0;
+        Mb[k * SH_RS + lane] = __int2float_rn(v) * inv;   // exact scaling by a power of two
+    }
+    const unsigned nonempty = __ballot_sync(0xffffffffu, any);
     __syncwarp();
-    float acc[2] = {0.0f, 0.0f};
-    const float4* M4 = reinterpret_cast<const float4*>(W.M);
-    // lane = tap t: Chebyshev coefficients of g_(t - 15), live only here
-    float c[ISM_CHEB_N];
+    float c[ISM_CHEB_N];   // lane = tap t: Chebyshev coefficients of g_(t - 15)
 #pragma unroll
     for (int i = 0; i < ISM_CHEB_N; ++i) c[i] = t.cheb[lane * ISM_CHEB_N + i];
-    for (int o = 0; o <= ISM_SB; ++o) {
-        if (o < 32 ? !((nonempty >> o) & 1u) : !last_nonempty) continue;   // warp-uniform
-        const float4 m0 = M4[3 * o], m1 = M4[3 * o + 1], m2 = M4[3 * o + 2];
+    float acc[2] = {0.0f, 0.0f};
+    for (int o = 0; o < SH_NO; ++o) {
+        if (!((nonempty >> o) & 1u)) continue;   // warp-uniform
         float D[1];
-        D[0] = c[0] * m0.x;
-        D[0] = __fmaf_rn(c[1], m0.y, D[0]);
-        D[0] = __fmaf_rn(c[2], m0.z, D[0]);
-        D[0] = __fmaf_rn(c[3], m0.w, D[0]);
-        D[0] = __fmaf_rn(c[4], m1.x, D[0]);
-        D[0] = __fmaf_rn(c[5], m1.y, D[0]);
-        D[0] = __fmaf_rn(c[6], m1.z, D[0]);
-        D[0] = __fmaf_rn(c[7], m1.w, D[0]);
-        D[0] = __fmaf_rn(c[8], m2.x, D[0]);
+        D[0] = c[0] * Mb[o];
+#pragma unroll
+        for (int k = 1; k < ISM_CHEB_N; ++k) D[0] = __fmaf_rn(c[k], Mb[k * SH_RS + o], D[0]);
         flush_run<1, false>(D, acc, o - 1, lane, 1.0f);
     }
     float* row = rows + J.rows_base + ((long long)r * J.Q + q) * WIN;
@@ -215,19 +347,25 @@ __global__ void __launch_bounds__(ISM_ACC_BPC * 32, 10) cheb_kernel(const __grid
     row[32 + lane] = acc[1];
 }
 
+size_t shell_smem(const JobTable& t)
+{
+    return (size_t)((t.max_axis_sum + 1) & ~1) * sizeof(float4) + (size_t)SH_B * ISM_CHEB_N * SH_RS * sizeof(int) +
+           2 * SH_B * sizeof(float) + 2 * (size_t)((t.max_axis_sum + 4) & ~3) * sizeof(int) +
+           (size_t)SH_WARPS * 32 * (sizeof(float4) + sizeof(int4)) + (size_t)SH_WARPS * 33 * sizeof(int);
+}
+
 }  // namespace
 
 int ism_launch_accum_cheb(const JobTable& t, const WsPlan& p, char* ws, void* stream, int* launched)
 {
     *launched = 0;
-    if (p.acc_ctas <= 0 || !t.any_cheb) return 0;
-    const size_t sm = (size_t)((t.max_axis_sum + 1) & ~1) * sizeof(float4) + ISM_ACC_BPC * sizeof(ChebWarp);
-    cudaError_t e = cudaFuncSetAttribute(cheb_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (p.shell_ctas <= 0 || !t.any_cheb) return 0;
+    const size_t sm = shell_smem(t);
+    cudaError_t e = cudaFuncSetAttribute(shell_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (e != cudaSuccess) return (int)e;
-    cheb_kernel<<<(unsigned)p.acc_ctas, ISM_ACC_BPC * 32, sm, (cudaStream_t)stream>>>(
+    shell_kernel<<<(unsigned)p.shell_ctas, SH_WARPS * 32, sm, (cudaStream_t)stream>>>(
         t, reinterpret_cast<const float4*>(ws + p.tbl_off), reinterpret_cast<const uint32_t*>(ws + p.hist_off),
-        reinterpret_cast<const uint32_t*>(ws + p.ids_off), reinterpret_cast<float*>(ws + p.rows_off),
-        reinterpret_cast<uint32_t*>(ws + p.status_off));
+        reinterpret_cast<float*>(ws + p.rows_off), reinterpret_cast<uint32_t*>(ws + p.status_off));
     *launched = 1;
     return (int)cudaGetLastError();
 }

@@ -160,7 +160,7 @@ ism_status plan(const Validated* vs, int n, ism_precision prec, bool backward, J
     for (int i = 0; i < n; ++i)
         set_cols += (long long)vs[i].job.nb_img[0] * vs[i].job.nb_img[1] * vs[i].job.n_src * vs[i].job.n_rcv;
     long long rir = 0, hist = 0, tbl = 0, ecta = 0, acta = 0, adta = 0, tcta = 0, fcta = 0, rows = 0, ids = 0, lut = 0,
-              gpart = 0;
+              gpart = 0, scta = 0;
     for (int i = 0; i < n; ++i) {
         const Validated& v = vs[i];
         const ism_job& in = v.job;
@@ -208,7 +208,7 @@ ism_status plan(const Validated* vs, int n, ism_precision prec, bool backward, J
             J.U = (int)((cols + cpu - 1) / cpu);
         }
         J.inv_kLz = (float)(1.0 / (k * in.room.L[2]));
-        J.acc_groups = (J.Q + ism_acc_bins((int)prec) - 1) / ism_acc_bins((int)prec);
+
         J.n_tiles = (J.Q + ISM_TILE_BINS - 1) / ISM_TILE_BINS;
         double s_cut = (double)v.n_ism - 1.0 + (double)v.H + 0.5;
         J.s_cut2 = (float)(s_cut * s_cut);
@@ -250,6 +250,11 @@ ism_status plan(const Validated* vs, int n, ism_precision prec, bool backward, J
             J.use_cheb = (prec == ISM_PREC_FP32 && !backward && v.Nw == 32.0 && v.H == 16 && v.slots == 1 &&
                           per_bin >= 256.0) ? 1 : 0;
         }
+        // a job takes either the fused Chebyshev CTAs (which enumerate their
+        // own images) or the direct accumulation CTAs (which read the binned ids)
+        J.acc_groups = J.use_cheb ? 0 : (J.Q + ism_acc_bins((int)prec) - 1) / ism_acc_bins((int)prec);
+        J.shell_groups = J.use_cheb ? (J.Q + ISM_SHELL_BINS - 1) / ISM_SHELL_BINS : 0;
+        J.shell_cta_base = scta;
         J.grad_out = v.grad_out;
         J.grad_beta = v.grad_beta;
         J.grad_src = v.grad_src;
@@ -263,6 +268,7 @@ ism_status plan(const Validated* vs, int n, ism_precision prec, bool backward, J
         tbl += R * axis;
         ecta += R * ((J.U + ISM_ENUM_WARPS - 1) / ISM_ENUM_WARPS);
         acta += R * J.acc_groups;
+        scta += R * J.shell_groups;
         fcta += R * J.fin_chunks;
         adta += R * J.n_tiles;
         if (J.has_tail) {
@@ -272,6 +278,7 @@ ism_status plan(const Validated* vs, int n, ism_precision prec, bool backward, J
         rows += R * J.Q * 32LL * (J.slots + 1);
         if (prec == ISM_PREC_LUT) lut += (long long)(ism_lut_phases(J.slots) + 1) * 32 * J.slots;
         if (J.use_cheb) t.any_cheb = 1;
+        else t.any_direct = 1;
         if (backward) gpart += R * J.Q * 12;
         ids += R * J.img_per_rir;
         if (J.Q > t.max_Q) t.max_Q = J.Q;
@@ -283,7 +290,7 @@ ism_status plan(const Validated* vs, int n, ism_precision prec, bool backward, J
     if (ids >= 0xFFFFFFFFll)
         return fail(ISM_ERR_UNSUPPORTED, "%lld images in one launch set exceed 2^32; split the batch", ids);
     if (rir > 0x7FFFFFFFll || ecta > 0x7FFFFFFFll || acta > 0x7FFFFFFFll || adta > 0x7FFFFFFFll ||
-        tcta > 0x7FFFFFFFll || fcta > 0x7FFFFFFFll)
+        tcta > 0x7FFFFFFFll || fcta > 0x7FFFFFFFll || scta > 0x7FFFFFFFll)
         return fail(ISM_ERR_UNSUPPORTED, "launch set too large; split the batch");
     p.hist_total = hist;
     p.ids_total = ids;
@@ -298,6 +305,7 @@ ism_status plan(const Validated* vs, int n, ism_precision prec, bool backward, J
     p.rgrad_total = backward ? rir * 12 : 0;
     p.enum_ctas = ecta;
     p.acc_ctas = acta;
+    p.shell_ctas = scta;
     p.adj_ctas = adta;
     p.tail_ctas = tcta;
     p.fin_ctas = fcta;
@@ -585,7 +593,7 @@ ism_status run_set(const std::vector<Validated>& set, ism_precision prec, size_t
         if ((e = ism_launch_scan(p, ws, stream))) return cuda_fail(e, "scan kernels");
         tm.done(3);
     }
-    {
+    if (t.any_direct) {
         StageTimer tm(ISM_STAGE_ENUM_SCATTER, st);
         if ((e = ism_launch_enum(t, p, ws, true, stream))) return cuda_fail(e, "enumeration (scatter) kernel");
         tm.done(p.enum_ctas > 0);

@@ -53,6 +53,7 @@ __global__ void __launch_bounds__(ISM_ENUM_WARPS * 32) enum_kernel(const __grid_
     const long long g = blockIdx.x;
     const int jid = ism_find_job(t, g, [](const JobDev& j) { return j.enum_cta_base; });
     const JobDev& J = t.j[jid];
+    if (SCATTER && J.use_cheb) return;   // the fused Chebyshev kernel enumerates this job's images itself
     const int ctas_per_rir = (J.U + ISM_ENUM_WARPS - 1) / ISM_ENUM_WARPS;
     const long long local = g - J.enum_cta_base;
     const int r = (int)(local / ctas_per_rir);

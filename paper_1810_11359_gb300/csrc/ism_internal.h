@@ -45,6 +45,7 @@
 #define ISM_SCAN_TOP 16384        // max scan blocks (one top-level block)
 #define ISM_FIT_WINDOW_S 0.02     // envelope fit: last 20 ms of the ISM part
 #define ISM_CHEB_N 9              // Chebyshev terms of a tap function (degree 8)
+#define ISM_SHELL_BINS 8          // delay bins per CTA of the fused Chebyshev accumulation
 
 // Device-side description of one job.  Everything the kernels need is here
 // so that a whole launch set takes its jobs as one kernel parameter.
@@ -74,6 +75,7 @@ struct JobDev {
     int vec4;                 // out rows 16-byte aligned (float4 stores allowed)
     float half_scale;         // FP16X2 records are scaled by this power of two
     int use_cheb;             // FP32 accumulation through Chebyshev moments (32-tap window)
+    int shell_groups;         // fused Chebyshev CTAs per RIR (ISM_SHELL_BINS bins each; 0 otherwise)
     int rir_index0;           // RIR index of the job's first RIR in its caller's job (noise counter)
     uint64_t seed;
     const float* pos_src;
@@ -86,6 +88,7 @@ struct JobDev {
     long long tbl_base;       // first table entry (float4) of the job
     long long enum_cta_base;  // first enumeration CTA of the job
     long long acc_cta_base;   // first accumulation CTA of the job
+    long long shell_cta_base; // first fused Chebyshev CTA of the job
     long long adj_cta_base;   // first adjoint CTA of the job
     long long tail_cta_base;  // first tail CTA of the job
     long long fin_cta_base;   // first finalize CTA of the job
@@ -105,6 +108,7 @@ struct JobTable {
     int max_Q;
     int max_axis_sum;
     int any_cheb;                      // some job accumulates through Chebyshev moments
+    int any_direct;                    // some job reads delay-binned image ids
     float cheb[32 * ISM_CHEB_N];       // Chebyshev coefficients of the 32 tap functions (32-tap window)
     JobDev j[ISM_MAX_JOBS];
 };
@@ -135,6 +139,7 @@ struct WsPlan {
     long long n_scan_blocks;
     long long enum_ctas;
     long long acc_ctas;
+    long long shell_ctas;
     long long adj_ctas;
     long long tail_ctas;
     long long fin_ctas;
