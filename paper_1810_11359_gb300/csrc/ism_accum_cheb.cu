@@ -43,8 +43,8 @@
 // beta_max^h / s_lo.  A term A T_i is scaled by 2^e and rounded to an integer
 // (one FFMA against 1.5 2^23: the sum's bits hold the integer), e the largest
 // integer with 2^e A_max <= min((1 - 2^-10) 2^22, 0.99 2^31 / n_q), n_q the
-// number of images the enumeration counted in the plain-FP32 bins q - 1 and
-// q (which hold every image of exact bin q): no term reaches 2^22 and no sum
+// number of images the count pass found in the plain-FP32 bins q - 1 and q
+// (which hold every image of exact bin q): no term reaches 2^22 and no sum
 // 2^31.  The sums are 32-bit shared-memory atomic adds; integer addition is
 // associative, so the sums -- and the FP32 result -- are the same in every
 // run, whatever the order in which lanes and warps add their terms.  The
@@ -95,7 +95,7 @@ __device__ __forceinline__ void ax_range(const ShellAxis& a, float Dlo, float Dh
 
 __global__ void __launch_bounds__(SH_WARPS * 32, 4) shell_kernel(const __grid_constant__ JobTable t,
                                                                   const float4* __restrict__ tbl,
-                                                                  const uint32_t* __restrict__ hist,
+                                                                  const uint32_t* __restrict__ chist,
                                                                   float* __restrict__ rows,
                                                                   uint32_t* __restrict__ status)
 {
@@ -160,10 +160,8 @@ __global__ void __launch_bounds__(SH_WARPS * 32, 4) shell_kernel(const __grid_co
         const int q = q0 + (int)threadIdx.x;
         float sc = 1.0f;
         if (q < J.Q && valid) {
-            const long long hrow = J.hist_base + (long long)r * J.Q * J.U;
-            const uint32_t o_prev = hist[hrow + (long long)max(q - 1, 0) * J.U];
-            const uint32_t o_next = hist[hrow + (long long)(q + 1) * J.U];
-            const float nq = (float)max(o_next - o_prev, 1u);
+            const uint32_t* ch = chist + J.chist_base + (long long)r * J.Q;
+            const float nq = (float)max(ch[q] + (q > 0 ? ch[q - 1] : 0u), 1u);
             const float slo = fmaxf(fmaxf(sqrtf(sd2) * (1.0f - 1.0f / 1024.0f), (float)(ISM_SB * q) - 1.0f), 1e-30f);
             float bmax = 0.0f;
             for (int w = 0; w < 6; ++w) bmax = fmaxf(bmax, fabsf(J.beta[w]));
@@ -364,7 +362,7 @@ int ism_launch_accum_cheb(const JobTable& t, const WsPlan& p, char* ws, void* st
     cudaError_t e = cudaFuncSetAttribute(shell_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (e != cudaSuccess) return (int)e;
     shell_kernel<<<(unsigned)p.shell_ctas, SH_WARPS * 32, sm, (cudaStream_t)stream>>>(
-        t, reinterpret_cast<const float4*>(ws + p.tbl_off), reinterpret_cast<const uint32_t*>(ws + p.hist_off),
+        t, reinterpret_cast<const float4*>(ws + p.tbl_off), reinterpret_cast<const uint32_t*>(ws + p.chist_off),
         reinterpret_cast<float*>(ws + p.rows_off), reinterpret_cast<uint32_t*>(ws + p.status_off));
     *launched = 1;
     return (int)cudaGetLastError();

@@ -46,6 +46,7 @@ template <bool SCATTER>
 __global__ void __launch_bounds__(ISM_ENUM_WARPS * 32) enum_kernel(const __grid_constant__ JobTable t,
                                                                     const float4* __restrict__ tbl,
                                                                     uint32_t* __restrict__ hist,
+                                                                    uint32_t* __restrict__ chist,
                                                                     uint32_t* __restrict__ ids,
                                                                     uint32_t* __restrict__ status)
 {
@@ -73,8 +74,8 @@ __global__ void __launch_bounds__(ISM_ENUM_WARPS * 32) enum_kernel(const __grid_
     const bool active = unit < J.U;
     uint32_t* cnt = cnt_all + (size_t)warp * t.max_Q;
     const long long hrow = J.hist_base + (long long)r * Q * J.U;  // + q * U + unit
-    if (active)
-        for (int q = lane; q < Q; q += 32) cnt[q] = SCATTER ? hist[hrow + (long long)q * J.U + unit] : 0u;
+    if (active || !SCATTER)
+        for (int q = lane; q < Q; q += 32) cnt[q] = (SCATTER && active) ? hist[hrow + (long long)q * J.U + unit] : 0u;
     __shared__ int iz_min_s;
     __syncthreads();
     if (SCATTER && warp == 0) {
@@ -100,7 +101,8 @@ __global__ void __launch_bounds__(ISM_ENUM_WARPS * 32) enum_kernel(const __grid_
         if (lane == 0) iz_min_s = bi;
     }
     __syncthreads();
-    if (!active) return;
+    // inactive warps of a fused-Chebyshev count stay for the CTA-wide sum (their column range is empty)
+    if (!active && (SCATTER || !J.use_cheb)) return;
     const int iz_min = SCATTER ? iz_min_s : 0;
 
     const float* Sx = S;
@@ -185,8 +187,19 @@ __global__ void __launch_bounds__(ISM_ENUM_WARPS * 32) enum_kernel(const __grid_
         }
     }
     if (!SCATTER) {
-        __syncwarp();
-        for (int q = lane; q < Q; q += 32) hist[hrow + (long long)q * J.U + unit] = cnt[q];
+        if (J.use_cheb) {
+            // per-bin counts of the RIR: the CTA's warps summed, one integer atomic per bin
+            __syncthreads();
+            uint32_t* ch = chist + J.chist_base + (long long)r * Q;
+            for (int q = threadIdx.x; q < Q; q += blockDim.x) {
+                uint32_t s = 0;
+                for (int w = 0; w < ISM_ENUM_WARPS; ++w) s += cnt_all[(size_t)w * t.max_Q + q];
+                if (s) atomicAdd(ch + q, s);
+            }
+        } else {
+            __syncwarp();
+            for (int q = lane; q < Q; q += 32) hist[hrow + (long long)q * J.U + unit] = cnt[q];
+        }
     }
 }
 
@@ -285,6 +298,7 @@ int ism_launch_enum(const JobTable& t, const WsPlan& p, char* ws, bool scatter, 
     size_t sm = (size_t)((t.max_axis_sum + 3) & ~3) * 4 + (size_t)ISM_ENUM_WARPS * t.max_Q * 4;
     auto* tbl = reinterpret_cast<const float4*>(ws + p.tbl_off);
     auto* hist = reinterpret_cast<uint32_t*>(ws + p.hist_off);
+    auto* chist = reinterpret_cast<uint32_t*>(ws + p.chist_off);
     auto* idsp = reinterpret_cast<uint32_t*>(ws + p.ids_off);
     auto* st = reinterpret_cast<uint32_t*>(ws + p.status_off);
     cudaStream_t s = (cudaStream_t)stream;
@@ -292,11 +306,11 @@ int ism_launch_enum(const JobTable& t, const WsPlan& p, char* ws, bool scatter, 
     if (scatter) {
         e = cudaFuncSetAttribute(enum_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
         if (e != cudaSuccess) return (int)e;
-        enum_kernel<true><<<(unsigned)p.enum_ctas, ISM_ENUM_WARPS * 32, sm, s>>>(t, tbl, hist, idsp, st);
+        enum_kernel<true><<<(unsigned)p.enum_ctas, ISM_ENUM_WARPS * 32, sm, s>>>(t, tbl, hist, chist, idsp, st);
     } else {
         e = cudaFuncSetAttribute(enum_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
         if (e != cudaSuccess) return (int)e;
-        enum_kernel<false><<<(unsigned)p.enum_ctas, ISM_ENUM_WARPS * 32, sm, s>>>(t, tbl, hist, idsp, st);
+        enum_kernel<false><<<(unsigned)p.enum_ctas, ISM_ENUM_WARPS * 32, sm, s>>>(t, tbl, hist, chist, idsp, st);
     }
     return (int)cudaGetLastError();
 }

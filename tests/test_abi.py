@@ -77,10 +77,16 @@ def test_nb_img_and_att2t_match_oracle():
 
 def test_workspace_size_and_validation(lib):
     L, beta = [6.0, 5.0, 3.0], [0.9] * 6
-    n = ism.ism_workspace_size(L, beta, 4, 32, [73, 87, 141], 0.6, 16000.0, Tw=32 / 16000)
-    # at least the worst-case image-id buffer: 128 RIRs x 895,491 images x 4 B
+    # the direct evaluation bins image ids: at least the worst-case id buffer,
+    # 128 RIRs x 895,491 images x 4 B
+    n = ism.ism_workspace_size(L, beta, 4, 32, [73, 87, 141], 0.6, 16000.0, Tw=32 / 16000, prec="fp32_direct")
     assert n >= 128 * 73 * 87 * 141 * 4
     assert n % 256 == 0
+    # the fused Chebyshev form enumerates its images itself: per-bin counts,
+    # tables and window rows only (128 x 301 bins x 64 FP32 rows = 9.9 MB)
+    n32 = ism.ism_workspace_size(L, beta, 4, 32, [73, 87, 141], 0.6, 16000.0, Tw=32 / 16000)
+    assert 128 * 301 * 64 * 4 <= n32 < 32 << 20
+    assert n32 % 256 == 0
     bad = [
         dict(L=[0, 5, 3]),
         dict(beta=[1.5] + [0.9] * 5),

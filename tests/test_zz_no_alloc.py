@@ -81,6 +81,8 @@ def test_noalloc_matches_workspace_entry_two_calls_in_a_row():
 
 
 def test_noalloc_rejects_simulations_above_its_scratch():
+    # the direct evaluation of the 128-RIR workload bins 0.4 GB of image ids:
+    # more than the 64 MiB scratch
     room = workloads.batched_fp32()
     beta = ism.ism_beta_sabine(room.L, room.rt60)
     N = ism.ism_nb_img_from_t(room.Tmax, room.L, room.c, room.window())
@@ -90,9 +92,18 @@ def test_noalloc_rejects_simulations_above_its_scratch():
     r = ism._room(room.L, beta, 343.0)
     lib = ism.load()
     st = lib.ism_simulate_noalloc(ctypes.byref(r), ctypes.c_void_p(ps.data_ptr()), 4, ctypes.c_void_p(pr.data_ptr()),
-                                  32, ism._nb(N), 0.6, 16000.0, 0.0, 32 / 16000, 0, 0,
+                                  32, ism._nb(N), 0.6, 16000.0, 0.0, 32 / 16000, ism.PRECISIONS["fp32_direct"], 0,
                                   ctypes.c_void_p(out.data_ptr()), None)
     assert st == 8
     assert "scratch" in lib.ism_last_error_message().decode()
     torch.cuda.synchronize()
     assert torch.all(out == 7.0)
+
+
+def test_noalloc_runs_the_fused_fp32_form_of_the_128_rir_workload():
+    # the fused Chebyshev form keeps no image ids: the same workload fits the scratch
+    room = workloads.batched_fp32()
+    beta = ism.ism_beta_sabine(room.L, room.rt60)
+    N = ism.ism_nb_img_from_t(room.Tmax, room.L, room.c, room.window())
+    args = (room.L, beta, room.pos_src, room.pos_rcv, N, room.Tmax, room.fs, 0.0, room.window(), 0)
+    _close(_noalloc_c_abi(*args), _with_workspace(*args))
