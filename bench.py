@@ -48,6 +48,7 @@ from paper_1810_11359_gb300 import workloads  # noqa: E402
 METRIC = "RIRs/sec"
 UNIT = "RIR/s"
 FMA_OPS_PER_CONTRIBUTION = 5   # FADD (j - f), 2 FFMA (window), FMUL, FFMA (accumulate)
+OPS_PER_IMAGE = 42             # per image: the geometry of its delay and amplitude (~40), sin(pi f), the window phase
 L2_BYTES = 129 * 1024 * 1024
 DTYPES = {"fp32": "f32", "fp16x2": "f16x2 taps, f32 accumulation", "bf16x2": "bf16x2 taps, f32 accumulation",
           "lut": "f32 windowed-sinc table, f32 accumulation", "fp32_direct": "f32 (every tap evaluated)"}
@@ -74,8 +75,9 @@ def workload(name="batched"):
 
 
 def contributions(room, beta, N, n_ism):
-    """Image-tap contributions of the step: for every RIR and every image, the
-    samples 0 <= k < n_ism with |k - s| < N_w/2 (FP64, numpy)."""
+    """(image-tap contributions, contributing images) of the step: for every
+    RIR and every image, the samples 0 <= k < n_ism with |k - s| < N_w/2, and
+    the images with at least one such sample (FP64, numpy)."""
     L = np.asarray(room.L, np.float64)
     fs, c = float(np.float32(room.fs)), float(np.float32(room.c))
     Nw = round(float(np.float32(room.window())) * fs)
@@ -86,6 +88,7 @@ def contributions(room, beta, N, n_ism):
         n = np.arange(lo, lo + int(N[a]))
         axes.append(n)
     total = 0
+    images = 0
     for ps in room.pos_src.astype(np.float64):
         for pr in room.pos_rcv.astype(np.float64):
             sq = []
@@ -97,8 +100,10 @@ def contributions(room, beta, N, n_ism):
             s = np.sqrt(sq[0][:, None, None] + sq[1][None, :, None] + sq[2][None, None, :]).ravel()
             k_lo = np.maximum(np.floor(s - half) + 1, 0)
             k_hi = np.minimum(np.ceil(s + half) - 1, n_ism - 1)
-            total += int(np.sum(np.maximum(k_hi - k_lo + 1, 0)))
-    return total
+            taps = np.maximum(k_hi - k_lo + 1, 0)
+            total += int(np.sum(taps))
+            images += int(np.count_nonzero(taps))
+    return total, images
 
 
 class ClockSampler:
@@ -154,7 +159,7 @@ class ClockSampler:
 def traffic_from_profiles():
     """DRAM bytes per accumulation launch from the committed ncu summary, or
     None when the kernel source changed since it was captured."""
-    path = os.path.join(ROOT, "profiles", "cheb_batched_128rir.txt")
+    path = os.path.join(ROOT, "profiles", "shell_batched_128rir.txt")
     try:
         from paper_1810_11359_gb300 import build as b
         import hashlib
@@ -552,7 +557,7 @@ def main():
         dist.destroy_process_group()
         return
 
-    n_contrib = contributions(room, beta, N, n_ism)
+    n_contrib, n_images = contributions(room, beta, N, n_ism)
     acc_ms, acc_launches, acc_calls = prof_roof["accum"]
     # the accumulation stage of one step, timed with every launch on one
     # stream (the coefficient table and the accumulation kernel)
@@ -562,7 +567,10 @@ def main():
     props = torch.cuda.get_device_properties(dev)
     n_sm = props.multi_processor_count
     peak_tops = n_sm * 128 * sm_mhz * 1e6 / 1e12          # FP32 FMA-pipe lane operations / s
-    achieved_tops = FMA_OPS_PER_CONTRIBUTION * n_contrib / (acc_ms_per_step * 1e-3) / 1e12
+    # the accumulation kernels compute each image's delay and amplitude (eq. (1)-(4))
+    # and its taps (eq. (5)-(6)); the fused FP32 kernel also enumerates the images
+    alg_ops = FMA_OPS_PER_CONTRIBUTION * n_contrib + OPS_PER_IMAGE * n_images
+    achieved_tops = alg_ops / (acc_ms_per_step * 1e-3) / 1e12
     launches_per_step = sum(v[1] for v in prof.values()) / max(args.steps, 1)
 
     line = {
@@ -574,15 +582,18 @@ def main():
                    "taps": 32, "precision": args.prec, "l2": "flushed between timed steps (256 MB write)"},
         "image_contributions_per_sec": n_contrib * world / (ms * 1e-3),
         "contributions_per_step": n_contrib,
+        "images_in_reach_per_step": n_images,
         "stage_ms_per_step": {k: v[0] / max(args.steps, 1) for k, v in prof.items()},
         "roofline": {"bound": "alu",
-                     "kernel": ("cheb_kernel (Chebyshev moments)" if args.prec == "fp32" and args.workload == "batched"
+                     "kernel": ("shell_kernel (fused enumeration, exact delays, Chebyshev moments)"
+                                if args.prec == "fp32" and args.workload == "batched"
                                 else f"accum_kernel<1,false,{PREC_ID[args.prec]}>"),
                      "achieved": achieved_tops,
                      "peak": peak_tops, "unit": "Tops/s (FP32 FMA-pipe lane ops)",
                      "frac": achieved_tops / peak_tops,
                      "peak_basis": f"{n_sm} SMs x 128 FP32 lanes x {sm_mhz:.0f} MHz ({peak_kind} max SM clock)",
-                     "ops_per_contribution": FMA_OPS_PER_CONTRIBUTION,
+                     "ops_per_contribution": FMA_OPS_PER_CONTRIBUTION, "ops_per_image": OPS_PER_IMAGE,
+                     "ops_per_step": alg_ops,
                      "kernel_ms": acc_ms_per_step,
                      "kernel_launches_per_step": acc_launches / k_roof,
                      "timing": "CUDA events around the accumulation stage, launches on one stream, L2 flushed",
