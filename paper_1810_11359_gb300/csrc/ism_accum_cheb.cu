@@ -42,16 +42,17 @@
 // hits (|n| >= |x_n - x_r| / L - 1 on each axis), so |A| <= A_max = amp_scale
 // beta_max^h / s_lo.  A term A T_i is scaled by 2^e and rounded to an integer
 // (one FFMA against 1.5 2^23: the sum's bits hold the integer), e the largest
-// integer with 2^e A_max <= min((1 - 2^-10) 2^22, 0.99 2^31 / n_q), n_q the
-// number of images the count pass found in the plain-FP32 bins q - 1 and q
-// (which hold every image of exact bin q): no term reaches 2^22 and no sum
-// 2^31.  The sums are 32-bit shared-memory atomic adds; integer addition is
-// associative, so the sums -- and the FP32 result -- are the same in every
-// run, whatever the order in which lanes and warps add their terms.  The
-// rounding error is at most 2^-23 A_max per term at the bins where n_q <=
-// 512 and grows with n_q beyond (2^-31 n_q A_max); A_max falls with the
-// distance and the wall hits, so it stays below FP32's own error on the
-// result.
+// integer with 2^e A_max <= min((1 - 2^-10) 2^22, 0.98 2^31 / n - 1), n first
+// four times the expected number of images per integer delay, 4 pi s^2 /
+// (k^3 V) (one image per room volume V), plus 64.  The sums are 32-bit
+// shared-memory atomic adds; integer addition is associative, so the sums --
+// and the FP32 result -- are the same in every run, whatever the order in which
+// lanes and warps add their terms.  The CTA also counts its images per (bin,
+// integer delay); if some count times the largest term could reach 2^31 a sum
+// may have wrapped, and the CTA redoes its shell with scales set from the exact
+// counts (which do not depend on the scales), so the second pass is safe.  The
+// rounding error is at most 2^-22 A_max per term wherever the counts stay below
+// ~500 per integer delay; A_max falls with the distance and the wall hits.
 //
 // Finally each warp expands the non-empty offsets of one bin into the taps
 // (lane = tap) and rotates them into the bin's register window, which it
@@ -78,6 +79,17 @@ __device__ __forceinline__ int ax_first(float Z, float xs, float inv2L)
     return min(2 * me, 2 * mo - 1);
 }
 
+// Largest power of two 2^e with 2^e a_max <= min((1 - 2^-10) 2^22, 0.98 2^31 / n - 1):
+// no term reaches 2^22 (the FFMA rounding trick) and n terms cannot sum to 2^31.
+__device__ __forceinline__ float shell_scale(float a_max, float n)
+{
+    const float cap = fminf(4194304.0f * (1.0f - 1.0f / 1024.0f), 0.98f * 2147483648.0f / fmaxf(n, 1.0f) - 1.0f);
+    const float ratio = a_max > 0.0f ? cap / a_max : 3.0e38f;
+    int e = ((__float_as_int(ratio) >> 23) & 0xFF) - 127;   // floor(log2(ratio)), ratio normal
+    e = max(-126, min(126, e));
+    return __int_as_float((e + 127) << 23);
+}
+
 struct ShellAxis {
     float xs, xr, inv2L, k_inv;   // source, receiver coordinate; 1 / (2 L); c / f_s (metres per sample)
     int nlo, N;
@@ -95,7 +107,6 @@ __device__ __forceinline__ void ax_range(const ShellAxis& a, float Dlo, float Dh
 
 __global__ void __launch_bounds__(SH_WARPS * 32, 4) shell_kernel(const __grid_constant__ JobTable t,
                                                                   const float4* __restrict__ tbl,
-                                                                  const uint32_t* __restrict__ chist,
                                                                   float* __restrict__ rows,
                                                                   uint32_t* __restrict__ status)
 {
@@ -113,12 +124,16 @@ __global__ void __launch_bounds__(SH_WARPS * 32, 4) shell_kernel(const __grid_co
     const int n_axis = Nx + Ny + Nz;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 
-    // shared memory: axis tables | moment sums | per-bin scales | row prefix | per-warp column records
+    // shared memory: axis tables | moment sums | image counts | per-bin scales | row prefix |
+    // per-warp column records
     float4* T = reinterpret_cast<float4*>(smem);
     int* S = reinterpret_cast<int*>(smem + (size_t)((t.max_axis_sum + 1) & ~1) * sizeof(float4));
-    float* scale_s = reinterpret_cast<float*>(S + SH_B * ISM_CHEB_N * SH_RS);
+    int* Cn = S + SH_B * ISM_CHEB_N * SH_RS;                                      // [bin][offset] images
+    float* scale_s = reinterpret_cast<float*>(Cn + SH_B * SH_RS);
     float* inv_s = scale_s + SH_B;
-    int* rowpre = reinterpret_cast<int*>(inv_s + SH_B);                        // [Nx]: columns up to row ix
+    float* amax_s = inv_s + SH_B;                                                 // per-bin amplitude bound
+    int* redo = reinterpret_cast<int*>(amax_s + SH_B);                            // [4]: retry flag
+    int* rowpre = reinterpret_cast<int*>(redo + 4);                             // [Nx]: columns up to row ix
     int* rowy0 = rowpre + ((t.max_axis_sum + 4) & ~3);                          // [Nx]: first iy of row ix
     float4* recf = reinterpret_cast<float4*>(rowy0 + ((t.max_axis_sum + 4) & ~3));
     int4* reci = reinterpret_cast<int4*>(recf + SH_WARPS * 32);
@@ -129,7 +144,7 @@ __global__ void __launch_bounds__(SH_WARPS * 32, 4) shell_kernel(const __grid_co
 
     const float4* Tg = tbl + J.tbl_base + (long long)r * n_axis;
     for (int e = threadIdx.x; e < n_axis; e += blockDim.x) T[e] = Tg[e];
-    for (int e = threadIdx.x; e < SH_B * ISM_CHEB_N * SH_RS; e += blockDim.x) S[e] = 0;
+    if (threadIdx.x == 0) *redo = 0;
     __syncthreads();
 
     // geometry of the RIR
@@ -156,27 +171,28 @@ __global__ void __launch_bounds__(SH_WARPS * 32, 4) shell_kernel(const __grid_co
     const float s_lo2 = s_lo * s_lo, s_hi2 = s_hi * s_hi;
 
     if (threadIdx.x < SH_B) {
-        // fixed-point scale of bin q0 + threadIdx.x
+        // fixed-point scale of bin q0 + threadIdx.x, first from the expected number of images
+        // per integer delay (verified, and redone from the exact counts if it was too small)
         const int q = q0 + (int)threadIdx.x;
-        float sc = 1.0f;
+        float sc = 1.0f, amax = 0.0f;
         if (q < J.Q && valid) {
-            const uint32_t* ch = chist + J.chist_base + (long long)r * J.Q;
-            const float nq = (float)max(ch[q] + (q > 0 ? ch[q - 1] : 0u), 1u);
             const float slo = fmaxf(fmaxf(sqrtf(sd2) * (1.0f - 1.0f / 1024.0f), (float)(ISM_SB * q) - 1.0f), 1e-30f);
             float bmax = 0.0f;
             for (int w = 0; w < 6; ++w) bmax = fmaxf(bmax, fabsf(J.beta[w]));
-            double Lmax = fmax(J.L[0], fmax(J.L[1], J.L[2]));
+            const double Lmax = fmax(J.L[0], fmax(J.L[1], J.L[2]));
             const int h = max(0, (int)floorf(slo * kinv / (float)Lmax - 3.0f));
             const float decay = (h == 0) ? 1.0f : (bmax > 0.0f ? exp2f((float)h * log2f(bmax)) : 0.0f);
-            const float amax = J.amp_scale / slo * decay * 1.001f;
-            const float cap = fminf(4194304.0f * (1.0f - 1.0f / 1024.0f), 0.99f * 2147483648.0f / nq);
-            const float ratio = amax > 0.0f ? cap / amax : 3.0e38f;
-            int e = ((__float_as_int(ratio) >> 23) & 0xFF) - 127;   // floor(log2(ratio))
-            e = max(-126, min(126, e));
-            sc = __int_as_float((e + 127) << 23);
+            amax = J.amp_scale / slo * decay * 1.001f;
+            // images per integer delay at s: 4 pi s^2 / (k^3 V) (one image per volume V)
+            const float shi = (float)(ISM_SB * q + ISM_SB);
+            const float k = 1.0f / kinv;
+            const float vol = (float)(J.L[0] * J.L[1] * J.L[2]);
+            const float n_est = 4.0f * (12.566371f * shi * shi / (k * k * k * vol)) + 64.0f;
+            sc = shell_scale(amax, n_est);
         }
         scale_s[threadIdx.x] = sc;
         inv_s[threadIdx.x] = 1.0f / sc;   // exact: a power of two
+        amax_s[threadIdx.x] = amax;
     }
     // columns that reach the shell: row ix takes iy with |y - y_r| < D_y
     for (int ix = threadIdx.x; ix < Nx; ix += blockDim.x) {
@@ -212,6 +228,10 @@ __global__ void __launch_bounds__(SH_WARPS * 32, 4) shell_kernel(const __grid_co
     const int n_cols = Nx > 0 ? rowpre[Nx - 1] : 0;
 
     const float amp_scale = J.amp_scale;
+    for (int pass = 0; pass < 2; ++pass) {
+    for (int e = threadIdx.x; e < SH_B * ISM_CHEB_N * SH_RS; e += blockDim.x) S[e] = 0;
+    for (int e = threadIdx.x; e < SH_B * SH_RS; e += blockDim.x) Cn[e] = 0;
+    __syncthreads();
     for (int c0 = warp * 32; c0 < n_cols; c0 += SH_WARPS * 32) {
         // ---- the column of this lane and its candidate intervals in z
         const int cl = c0 + lane;
@@ -295,6 +315,7 @@ __global__ void __launch_bounds__(SH_WARPS * 32, 4) shell_kernel(const __grid_co
                     const float uu = __fmaf_rn(2.0f, f, -1.0f);
                     const float u2 = uu + uu;
                     int* Sb = S + ql * (ISM_CHEB_N * SH_RS) + o;
+                    atomicAdd(Cn + ql * SH_RS + o, 1);
                     atomicAdd(Sb, (int)(__float_as_uint(__fadd_rn(as, CB_MAGIC)) - CB_MAGIC_BITS));
                     atomicAdd(Sb + SH_RS, (int)(__float_as_uint(__fmaf_rn(as, uu, CB_MAGIC)) - CB_MAGIC_BITS));
                     float tp = 1.0f, tc = uu;
@@ -312,6 +333,23 @@ __global__ void __launch_bounds__(SH_WARPS * 32, 4) shell_kernel(const __grid_co
         __syncwarp();
     }
     __syncthreads();
+    // every sum of bin q holds at most Cn[q][o] terms of magnitude <= scale * A_max + 1/2:
+    // below 2^31 means no sum can have wrapped; otherwise redo the shell with scales from
+    // the exact counts (the counts do not depend on the scales, so the second pass is safe)
+    if (pass == 0 && threadIdx.x < SH_B) {
+        int mx = 0;
+        for (int o = 0; o < SH_NO; ++o) mx = max(mx, Cn[threadIdx.x * SH_RS + o]);
+        const float bound = (float)mx * (scale_s[threadIdx.x] * amax_s[threadIdx.x] + 0.5f);
+        if (!(bound < 0.99f * 2147483648.0f)) {
+            const float sc = shell_scale(amax_s[threadIdx.x], (float)mx);
+            scale_s[threadIdx.x] = sc;
+            inv_s[threadIdx.x] = 1.0f / sc;
+            atomicOr(redo, 1);
+        }
+    }
+    __syncthreads();
+    if (!*redo || pass == 1) break;   // CTA-uniform
+    }
 
     // ---- expansion: warp w owns bin q0 + w; lane o reads the sums of offset o
     if (warp >= nb) return;
@@ -348,7 +386,8 @@ __global__ void __launch_bounds__(SH_WARPS * 32, 4) shell_kernel(const __grid_co
 size_t shell_smem(const JobTable& t)
 {
     return (size_t)((t.max_axis_sum + 1) & ~1) * sizeof(float4) + (size_t)SH_B * ISM_CHEB_N * SH_RS * sizeof(int) +
-           2 * SH_B * sizeof(float) + 2 * (size_t)((t.max_axis_sum + 4) & ~3) * sizeof(int) +
+           (size_t)SH_B * SH_RS * sizeof(int) + 3 * SH_B * sizeof(float) + 4 * sizeof(int) +
+           2 * (size_t)((t.max_axis_sum + 4) & ~3) * sizeof(int) +
            (size_t)SH_WARPS * 32 * (sizeof(float4) + sizeof(int4)) + (size_t)SH_WARPS * 33 * sizeof(int);
 }
 
@@ -362,8 +401,8 @@ int ism_launch_accum_cheb(const JobTable& t, const WsPlan& p, char* ws, void* st
     cudaError_t e = cudaFuncSetAttribute(shell_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (e != cudaSuccess) return (int)e;
     shell_kernel<<<(unsigned)p.shell_ctas, SH_WARPS * 32, sm, (cudaStream_t)stream>>>(
-        t, reinterpret_cast<const float4*>(ws + p.tbl_off), reinterpret_cast<const uint32_t*>(ws + p.chist_off),
-        reinterpret_cast<float*>(ws + p.rows_off), reinterpret_cast<uint32_t*>(ws + p.status_off));
+        t, reinterpret_cast<const float4*>(ws + p.tbl_off), reinterpret_cast<float*>(ws + p.rows_off),
+        reinterpret_cast<uint32_t*>(ws + p.status_off));
     *launched = 1;
     return (int)cudaGetLastError();
 }

@@ -160,7 +160,7 @@ ism_status plan(const Validated* vs, int n, ism_precision prec, bool backward, J
     for (int i = 0; i < n; ++i)
         set_cols += (long long)vs[i].job.nb_img[0] * vs[i].job.nb_img[1] * vs[i].job.n_src * vs[i].job.n_rcv;
     long long rir = 0, hist = 0, tbl = 0, ecta = 0, acta = 0, adta = 0, tcta = 0, fcta = 0, rows = 0, ids = 0, lut = 0,
-              gpart = 0, scta = 0, chist = 0;
+              gpart = 0, scta = 0;
     for (int i = 0; i < n; ++i) {
         const Validated& v = vs[i];
         const ism_job& in = v.job;
@@ -228,7 +228,6 @@ ism_status plan(const Validated* vs, int n, ism_precision prec, bool backward, J
         J.env_amp = in.env_amp;
         J.rir_base = rir;
         J.hist_base = hist;
-        J.chist_base = chist;
         J.tbl_base = tbl;
         J.enum_cta_base = ecta;
         J.acc_cta_base = acta;
@@ -264,13 +263,11 @@ ism_status plan(const Validated* vs, int n, ism_precision prec, bool backward, J
         J.rgrad_base = rir * 12;
         const long long R = J.n_rir;
         rir += R;
-        // a fused Chebyshev job needs only per-bin counts (for its fixed-point
-        // scales) and no binned ids; a direct job needs both
-        if (J.use_cheb) chist += R * J.Q;
-        else hist += R * J.Q * J.U;
+        // a fused Chebyshev job enumerates its images itself: no counts, no binned ids
+        if (!J.use_cheb) hist += R * J.Q * J.U;
         int axis = in.nb_img[0] + in.nb_img[1] + in.nb_img[2];
         tbl += R * axis;
-        ecta += R * ((J.U + ISM_ENUM_WARPS - 1) / ISM_ENUM_WARPS);
+        if (!J.use_cheb) ecta += R * ((J.U + ISM_ENUM_WARPS - 1) / ISM_ENUM_WARPS);
         acta += R * J.acc_groups;
         scta += R * J.shell_groups;
         fcta += R * J.fin_chunks;
@@ -297,7 +294,6 @@ ism_status plan(const Validated* vs, int n, ism_precision prec, bool backward, J
         tcta > 0x7FFFFFFFll || fcta > 0x7FFFFFFFll || scta > 0x7FFFFFFFll)
         return fail(ISM_ERR_UNSUPPORTED, "launch set too large; split the batch");
     p.hist_total = hist;
-    p.chist_total = chist;
     p.ids_total = ids;
     p.n_scan_blocks = (hist + ISM_SCAN_BLOCK - 1) / ISM_SCAN_BLOCK;
     if (p.n_scan_blocks < 1) p.n_scan_blocks = 1;
@@ -321,8 +317,6 @@ ism_status plan(const Validated* vs, int n, ism_precision prec, bool backward, J
     off = align256(off + (size_t)(hist + 1) * 4);
     p.part_off = off;
     off = align256(off + (size_t)(p.n_scan_blocks + 1) * 4);
-    p.chist_off = off;
-    off = align256(off + (size_t)chist * 4);
     p.ids_off = off;
     off = align256(off + (size_t)ids * 4);
     p.tbl_off = off;

@@ -46,7 +46,6 @@ template <bool SCATTER>
 __global__ void __launch_bounds__(ISM_ENUM_WARPS * 32) enum_kernel(const __grid_constant__ JobTable t,
                                                                     const float4* __restrict__ tbl,
                                                                     uint32_t* __restrict__ hist,
-                                                                    uint32_t* __restrict__ chist,
                                                                     uint32_t* __restrict__ ids,
                                                                     uint32_t* __restrict__ status)
 {
@@ -54,7 +53,6 @@ __global__ void __launch_bounds__(ISM_ENUM_WARPS * 32) enum_kernel(const __grid_
     const long long g = blockIdx.x;
     const int jid = ism_find_job(t, g, [](const JobDev& j) { return j.enum_cta_base; });
     const JobDev& J = t.j[jid];
-    if (SCATTER && J.use_cheb) return;   // the fused Chebyshev kernel enumerates this job's images itself
     const int ctas_per_rir = (J.U + ISM_ENUM_WARPS - 1) / ISM_ENUM_WARPS;
     const long long local = g - J.enum_cta_base;
     const int r = (int)(local / ctas_per_rir);
@@ -74,8 +72,8 @@ __global__ void __launch_bounds__(ISM_ENUM_WARPS * 32) enum_kernel(const __grid_
     const bool active = unit < J.U;
     uint32_t* cnt = cnt_all + (size_t)warp * t.max_Q;
     const long long hrow = J.hist_base + (long long)r * Q * J.U;  // + q * U + unit
-    if (active || !SCATTER)
-        for (int q = lane; q < Q; q += 32) cnt[q] = (SCATTER && active) ? hist[hrow + (long long)q * J.U + unit] : 0u;
+    if (active)
+        for (int q = lane; q < Q; q += 32) cnt[q] = SCATTER ? hist[hrow + (long long)q * J.U + unit] : 0u;
     __shared__ int iz_min_s;
     __syncthreads();
     if (SCATTER && warp == 0) {
@@ -101,8 +99,7 @@ __global__ void __launch_bounds__(ISM_ENUM_WARPS * 32) enum_kernel(const __grid_
         if (lane == 0) iz_min_s = bi;
     }
     __syncthreads();
-    // inactive warps of a fused-Chebyshev count stay for the CTA-wide sum (their column range is empty)
-    if (!active && (SCATTER || !J.use_cheb)) return;
+    if (!active) return;
     const int iz_min = SCATTER ? iz_min_s : 0;
 
     const float* Sx = S;
@@ -187,19 +184,8 @@ __global__ void __launch_bounds__(ISM_ENUM_WARPS * 32) enum_kernel(const __grid_
         }
     }
     if (!SCATTER) {
-        if (J.use_cheb) {
-            // per-bin counts of the RIR: the CTA's warps summed, one integer atomic per bin
-            __syncthreads();
-            uint32_t* ch = chist + J.chist_base + (long long)r * Q;
-            for (int q = threadIdx.x; q < Q; q += blockDim.x) {
-                uint32_t s = 0;
-                for (int w = 0; w < ISM_ENUM_WARPS; ++w) s += cnt_all[(size_t)w * t.max_Q + q];
-                if (s) atomicAdd(ch + q, s);
-            }
-        } else {
-            __syncwarp();
-            for (int q = lane; q < Q; q += 32) hist[hrow + (long long)q * J.U + unit] = cnt[q];
-        }
+        __syncwarp();
+        for (int q = lane; q < Q; q += 32) hist[hrow + (long long)q * J.U + unit] = cnt[q];
     }
 }
 
@@ -298,7 +284,6 @@ int ism_launch_enum(const JobTable& t, const WsPlan& p, char* ws, bool scatter, 
     size_t sm = (size_t)((t.max_axis_sum + 3) & ~3) * 4 + (size_t)ISM_ENUM_WARPS * t.max_Q * 4;
     auto* tbl = reinterpret_cast<const float4*>(ws + p.tbl_off);
     auto* hist = reinterpret_cast<uint32_t*>(ws + p.hist_off);
-    auto* chist = reinterpret_cast<uint32_t*>(ws + p.chist_off);
     auto* idsp = reinterpret_cast<uint32_t*>(ws + p.ids_off);
     auto* st = reinterpret_cast<uint32_t*>(ws + p.status_off);
     cudaStream_t s = (cudaStream_t)stream;
@@ -306,11 +291,11 @@ int ism_launch_enum(const JobTable& t, const WsPlan& p, char* ws, bool scatter, 
     if (scatter) {
         e = cudaFuncSetAttribute(enum_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
         if (e != cudaSuccess) return (int)e;
-        enum_kernel<true><<<(unsigned)p.enum_ctas, ISM_ENUM_WARPS * 32, sm, s>>>(t, tbl, hist, chist, idsp, st);
+        enum_kernel<true><<<(unsigned)p.enum_ctas, ISM_ENUM_WARPS * 32, sm, s>>>(t, tbl, hist, idsp, st);
     } else {
         e = cudaFuncSetAttribute(enum_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
         if (e != cudaSuccess) return (int)e;
-        enum_kernel<false><<<(unsigned)p.enum_ctas, ISM_ENUM_WARPS * 32, sm, s>>>(t, tbl, hist, chist, idsp, st);
+        enum_kernel<false><<<(unsigned)p.enum_ctas, ISM_ENUM_WARPS * 32, sm, s>>>(t, tbl, hist, idsp, st);
     }
     return (int)cudaGetLastError();
 }

@@ -29,7 +29,7 @@ __device__ double dpow_int(double b, int e)
 }
 
 __global__ void __launch_bounds__(128) geometry_kernel(const __grid_constant__ JobTable t, float4* tbl,
-                                                       uint32_t* chist, uint32_t* status)
+                                                       uint32_t* status)
 {
     const long long g = blockIdx.x;  // one CTA per RIR of the launch set
     const int jid = ism_find_job(t, g, [](const JobDev& j) { return j.rir_base; });
@@ -38,8 +38,6 @@ __global__ void __launch_bounds__(128) geometry_kernel(const __grid_constant__ J
     const int i_src = r / J.n_rcv, i_rcv = r % J.n_rcv;
     const float* ps = J.pos_src + 3 * i_src;
     const float* pr = J.pos_rcv + 3 * i_rcv;
-    if (J.use_cheb)   // per-bin image counts of the RIR, summed by the count pass
-        for (int q = threadIdx.x; q < J.Q; q += blockDim.x) chist[J.chist_base + (long long)r * J.Q + q] = 0u;
 
     __shared__ int ok_s;
     __shared__ double ps_s[3], pr_s[3];
@@ -125,8 +123,7 @@ int ism_launch_geometry(const JobTable& t, const WsPlan& p, char* ws, void* stre
     long long n_rir = p.rir_total;
     if (n_rir <= 0) return 0;
     geometry_kernel<<<(unsigned)n_rir, 128, 0, (cudaStream_t)stream>>>(
-        t, reinterpret_cast<float4*>(ws + p.tbl_off), reinterpret_cast<uint32_t*>(ws + p.chist_off),
-        reinterpret_cast<uint32_t*>(ws + p.status_off));
+        t, reinterpret_cast<float4*>(ws + p.tbl_off), reinterpret_cast<uint32_t*>(ws + p.status_off));
     return (int)cudaGetLastError();
 }
 

@@ -85,7 +85,6 @@ struct JobDev {
     long long img_per_rir;    // N[0] N[1] N[2]
     long long rir_base;       // global RIR index of the job's first RIR
     long long hist_base;      // first counter of the job in the histogram (direct jobs)
-    long long chist_base;     // first per-bin image count of the job (fused Chebyshev jobs)
     long long tbl_base;       // first table entry (float4) of the job
     long long enum_cta_base;  // first enumeration CTA of the job
     long long acc_cta_base;   // first accumulation CTA of the job
@@ -121,7 +120,6 @@ struct WsPlan {
     size_t status_off;     // uint32 flags (first 256 bytes)
     size_t hist_off;       // uint32 [hist_total + 1]: per (RIR, bin, unit) counts -> offsets
     size_t part_off;       // uint32 [n_scan_blocks + 1]
-    size_t chist_off;      // uint32 [chist_total]: per (RIR, bin) image counts of the fused Chebyshev jobs
     size_t ids_off;        // uint32 [ids_total]
     size_t tbl_off;        // float4 [tbl_total]
     size_t rows_off;       // float  [rows_total]: per-bin window rows of the accumulation
@@ -131,7 +129,6 @@ struct WsPlan {
     size_t rgrad_off;      // float  [rgrad_total]: backward, per-RIR gradients
     size_t total;
     long long hist_total;
-    long long chist_total;
     long long ids_total;
     long long tbl_total;
     long long rows_total;

@@ -309,3 +309,39 @@ def test_split_call_keeps_the_noise_index_of_every_rir():
         tail_ref = oracle.tail(11, r, float(A[r]), n_ism, n_S, float(f32(room.fs)), T60)[n_ism:]
         np.testing.assert_allclose(got[r, n_ism:].astype(np.float64), tail_ref, rtol=2e-6,
                                    atol=1e-12 * np.sqrt(A[r]))
+
+
+def test_degenerate_distances_exceed_the_density_estimate():
+    """A cube room with the receiver at its centre and the source next to it puts
+    the images on a near-cubic lattice around the receiver: many share one
+    integer delay, far more than the smooth density estimate (4 pi s^2 / (k^3
+    V)) that sets the first fixed-point scales of the fused FP32 form.  The
+    exact counts per integer delay are computed here: above 1016 images on one
+    integer delay, no first scale (terms of at least 2^21 for a term cap of
+    2^22) can pass the kernel's overflow check, so the kernel must redo that
+    shell with scales from its exact counts.  The result must match the oracle
+    at the FP32 tolerance."""
+    L = np.array([4.0, 4.0, 4.0])
+    beta = np.full(6, 0.95, np.float32)
+    ps = np.array([[2.0, 2.0, 2.0009765625]], np.float32)   # 2 + 2^-10 m: exactly representable
+    pr = np.array([[2.0, 2.0, 2.0]], np.float32)
+    fs, Tmax, Tw = 16000.0, 0.7, 32 / 16000
+    N = oracle.nb_img_from_t(Tmax, L, 343.0, Tw)
+    n = oracle.n_samples(f32(Tmax), fs)
+    # exact delays (FP64) of every image and the largest count per integer delay
+    k = float(f32(fs)) / float(f32(343.0))
+    coords = []
+    for a in range(3):
+        nn = np.arange(-(N[a] // 2), -(N[a] // 2) + N[a])
+        even = nn % 2 == 0
+        x = np.where(even, nn * L[a] + float(ps[0, a]), (nn + 1) * L[a] - float(ps[0, a]))
+        coords.append(((x - float(pr[0, a])) * k) ** 2)
+    s = np.sqrt(coords[0][:, None, None] + coords[1][None, :, None] + coords[2][None, None, :]).ravel()
+    b = np.floor(s).astype(np.int64)
+    counts = np.bincount(b[b <= n + 14])
+    assert counts.max() > 1016, counts.max()
+    got = lib_run(L, beta, ps, pr, N, Tmax, fs, Tw=Tw).reshape(1, -1)
+    ref = oracle_ism(L, beta, ps, pr, N, n, fs, Tw)
+    assert np.all(np.isfinite(got))
+    err = np.max(np.abs(got.astype(np.float64) - ref)) / np.max(np.abs(ref))
+    assert err <= TOL_FP32, err
