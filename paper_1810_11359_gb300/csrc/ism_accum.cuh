@@ -382,7 +382,33 @@ __global__ void __launch_bounds__(ism_acc_bins(PREC) * 32) accum_kernel(const __
             const uint32_t start = hist[hb];
             const uint32_t end = hist[hb + J.U];
             int cur_rr = -1000;
-            for (uint32_t p0 = start; p0 < end; p0 += ISM_PIECE) {
+            // sparse bins (FP32): 32 images at a time in list order, no sort; each image's
+            // record is computed by its lane and its taps are rotated into the window at once
+            const bool sparse = PREC == PREC_FP32 && J.sparse;
+            if (sparse) {
+                for (uint32_t p0 = start; p0 < end; p0 += 32) {
+                    const int n = (int)min(32u, end - p0);
+                    float4 rc = make_float4(0.5f, 0.0f, 0.0f, 0.0f);
+                    int rr = 0;
+                    if (lane < n) {
+                        const uint32_t pid = ids[p0 + lane];
+                        const int ix = pid & 1023, iy = (pid >> 10) & 1023, iz = pid >> 20;
+                        bool bad;
+                        float f, amp;
+                        ism_delay(T[ix], T[Nx + iy], T[Nx + Ny + iz], q, J.amp_scale, &f, &amp, &rr, &bad);
+                        if (bad) atomicOr(status, (uint32_t)ISM_DEVICE_FLAG_BIN);
+                        f = fminf(fmaxf(f, f_lo), f_hi);
+                        rc = ism_sinc_record(f, amp, small_phase, twopi_Nw, inv2Nw);   // amp = 0 if bad
+                    }
+                    __syncwarp();
+                    W.rec[lane] = rc;
+                    __syncwarp();
+                    for (int l = 0; l < n; ++l)
+                        add_single<SLOTS, MASK>(W.rec[l], __shfl_sync(0xffffffffu, rr, l), xj, nsg, Cj, Sj, tap_ok,
+                                                halfNw, acc, lane);
+                }
+            }
+            for (uint32_t p0 = start; !sparse && p0 < end; p0 += ISM_PIECE) {
                 const int n = (int)min((uint32_t)ISM_PIECE, end - p0);
                 const uint32_t* src = ids + p0;
 

@@ -249,6 +249,10 @@ ism_status plan(const Validated* vs, int n, ism_precision prec, bool backward, J
             const double per_bin = in_reach / (double)((v.n_ism + v.H) / ISM_SB + 1);
             J.use_cheb = (prec == ISM_PREC_FP32 && !backward && v.Nw == 32.0 && v.H == 16 && v.slots == 1 &&
                           per_bin >= 256.0) ? 1 : 0;
+            // sparse bins: sorting by offset and padding each offset to a group of 4
+            // images costs more than adding every image's taps on its own
+            J.sparse = ((prec == ISM_PREC_FP32 || prec == ISM_PREC_FP32_DIRECT) && !backward && !J.use_cheb &&
+                        per_bin < 128.0) ? 1 : 0;
         }
         // a job takes either the fused Chebyshev CTAs (which enumerate their
         // own images) or the direct accumulation CTAs (which read the binned ids)

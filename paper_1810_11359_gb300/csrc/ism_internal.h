@@ -76,6 +76,7 @@ struct JobDev {
     float half_scale;         // FP16X2 records are scaled by this power of two
     int use_cheb;             // FP32 accumulation through Chebyshev moments (32-tap window)
     int shell_groups;         // fused Chebyshev CTAs per RIR (ISM_SHELL_BINS bins each; 0 otherwise)
+    int sparse;               // direct FP32 form, few images per bin: no sort, each image's taps added at once
     int rir_index0;           // RIR index of the job's first RIR in its caller's job (noise counter)
     uint64_t seed;
     const float* pos_src;
