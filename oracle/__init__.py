@@ -68,6 +68,11 @@ def _load():
         lib.oracle_rir_list.restype = None
         lib.oracle_rir_list.argtypes = [Dp, Dp, D, D, D, Dp, Dp, ctypes.c_int, Ip, ctypes.c_int,
                                         Dp, ctypes.c_int]
+        lib.oracle_rir_list_pattern.restype = None
+        lib.oracle_rir_list_pattern.argtypes = [Dp, Dp, D, D, D, Dp, Dp, Dp, D, ctypes.c_int, Ip, ctypes.c_int,
+                                                Dp, ctypes.c_int]
+        lib.oracle_pattern_gain.restype = D
+        lib.oracle_pattern_gain.argtypes = [D, Dp, Dp, Dp]
         lib.oracle_delta_prime.restype = D
         lib.oracle_delta_prime.argtypes = [D, D, D]
         lib.oracle_image_coord.restype = D
@@ -189,6 +194,33 @@ def rir_list(L, beta, c, fs, Tw, ps_list, pr_list, N, n_ism, n_threads: int = 0)
     if ps.shape[0] and n_ism > 0:
         _load().oracle_rir_list(_dp(L), _dp(beta), float(c), float(fs), float(Tw), _dp(ps), _dp(pr),
                                 int(ps.shape[0]), _ip(Nn), int(n_ism), _dp(out), int(n_threads))
+    return out
+
+
+# Receiver polar patterns (Section 4; the formula is a reading, see
+# oracle_pattern_gain): alpha of g(theta) = alpha + (1 - alpha) cos(theta).
+PATTERN_ALPHA = {"omni": 1.0, "subcardioid": 0.75, "cardioid": 0.5, "hypercardioid": 0.25, "bidirectional": 0.0}
+
+
+def pattern_gain(pattern, orient, pr, p_img) -> float:
+    """Gain of one image for a receiver at pr oriented along orient."""
+    return _load().oracle_pattern_gain(float(PATTERN_ALPHA[pattern]), _dp(_d(orient, 3)), _dp(_d(pr, 3)),
+                                       _dp(_d(p_img, 3)))
+
+
+def rir_list_pattern(L, beta, c, fs, Tw, ps_list, pr_list, orient_list, pattern, N, n_ism, n_threads: int = 0):
+    """As rir_list, each image's amplitude scaled by the receiver's polar pattern."""
+    L, beta = _d(L, 3), _d(beta, 6)
+    ps = np.ascontiguousarray(np.asarray(ps_list, dtype=np.float64).reshape(-1, 3))
+    pr = np.ascontiguousarray(np.asarray(pr_list, dtype=np.float64).reshape(-1, 3))
+    orient = np.ascontiguousarray(np.asarray(orient_list, dtype=np.float64).reshape(-1, 3))
+    assert ps.shape == pr.shape == orient.shape
+    Nn = np.ascontiguousarray(np.asarray(N, dtype=np.int32).reshape(3))
+    out = np.zeros((ps.shape[0], int(n_ism)), np.float64)
+    if ps.shape[0] and n_ism > 0:
+        _load().oracle_rir_list_pattern(_dp(L), _dp(beta), float(c), float(fs), float(Tw), _dp(ps), _dp(pr),
+                                        _dp(orient), float(PATTERN_ALPHA[pattern]), int(ps.shape[0]), _ip(Nn),
+                                        int(n_ism), _dp(out), int(n_threads))
     return out
 
 

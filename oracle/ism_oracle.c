@@ -144,11 +144,32 @@ long oracle_enumerate_images(const double L[3], const double beta[6], double c,
     return idx;
 }
 
-/* Eq. (5) with eq. (6): h[k] = sum_n A_n delta'(k/f_s - tau_n) for the samples
- * 0 <= k < n_ism of one pair.  Image-major, every image of the grid, every
- * sample inside its window; no binning, no tiling. */
+/* Receiver polar pattern (Section 4 names polar patterns and orientation of
+ * the receivers without a formula).  Reading: the first-order family
+ * g(theta) = alpha + (1 - alpha) cos(theta), theta the angle between the
+ * receiver's orientation o and the direction from the receiver to the image
+ * source; alpha = 1 omnidirectional, 3/4 subcardioid, 1/2 cardioid, 1/4
+ * hypercardioid, 0 bidirectional.  The gain multiplies the image's amplitude
+ * A of eq. (4).  o need not be of unit length. */
+double oracle_pattern_gain(double alpha, const double o[3], const double pr[3], const double p_img[3])
+{
+    double dot = 0.0, oo = 0.0, dd = 0.0;
+    for (int a = 0; a < 3; ++a) {
+        double v = p_img[a] - pr[a];
+        dot += o[a] * v;
+        oo += o[a] * o[a];
+        dd += v * v;
+    }
+    return alpha + (1.0 - alpha) * dot / (sqrt(oo) * sqrt(dd));
+}
+
+/* Eq. (5) with eq. (6): h[k] = sum_n g_n A_n delta'(k/f_s - tau_n) for the
+ * samples 0 <= k < n_ism of one pair (g_n = 1 without a polar pattern, i.e.
+ * orient == NULL).  Image-major, every image of the grid, every sample inside
+ * its window; no binning, no tiling. */
 static void rir_one(const double L[3], const double beta[6], double c, double fs, double Tw,
-                    const double ps[3], const double pr[3], const int N[3], int n_ism, double* h)
+                    const double ps[3], const double pr[3], const int N[3], int n_ism, double* h,
+                    const double* orient, double alpha)
 {
     int lo[3], hi[3];
     for (int a = 0; a < 3; ++a) oracle_grid_bounds(N[a], &lo[a], &hi[a]);
@@ -157,18 +178,19 @@ static void rir_one(const double L[3], const double beta[6], double c, double fs
         for (int ny = lo[1]; ny < hi[1]; ++ny)
             for (int nz = lo[2]; nz < hi[2]; ++nz) {
                 int n[3] = {nx, ny, nz};
-                double bn = 1.0, d2 = 0.0;
+                double bn = 1.0, d2 = 0.0, p[3];
                 for (int a = 0; a < 3; ++a) {
-                    double p = oracle_image_coord(n[a], L[a], ps[a]);
+                    p[a] = oracle_image_coord(n[a], L[a], ps[a]);
                     int e0, e1;
                     oracle_image_exponents(n[a], &e0, &e1);
                     bn *= ipow(beta[2 * a], e0) * ipow(beta[2 * a + 1], e1);
-                    double dd = pr[a] - p;
+                    double dd = pr[a] - p[a];
                     d2 += dd * dd;
                 }
                 double d = sqrt(d2);
                 double tau = d / c;
                 double A = bn / (4.0 * ORACLE_PI * d);
+                if (orient) A *= oracle_pattern_gain(alpha, orient, pr, p);
                 double s = fs * d / c;                       /* tau in samples */
                 /* samples with |k/f_s - tau| < Tw/2 */
                 double half = 0.5 * Tw * fs;
@@ -195,7 +217,22 @@ void oracle_rir_list(const double L[3], const double beta[6], double c, double f
 #pragma omp parallel for schedule(dynamic, 1)
 #endif
     for (int i = 0; i < n_pairs; ++i)
-        rir_one(L, beta, c, fs, Tw, ps + 3 * i, pr + 3 * i, N, n_ism, out + (long)i * n_ism);
+        rir_one(L, beta, c, fs, Tw, ps + 3 * i, pr + 3 * i, N, n_ism, out + (long)i * n_ism, NULL, 1.0);
+    (void)n_threads;
+}
+
+/* As oracle_rir_list, with a receiver polar pattern: orient is [n_pairs][3],
+ * the orientation of each pair's receiver. */
+void oracle_rir_list_pattern(const double L[3], const double beta[6], double c, double fs, double Tw,
+                             const double* ps, const double* pr, const double* orient, double alpha,
+                             int n_pairs, const int N[3], int n_ism, double* out, int n_threads)
+{
+#ifdef _OPENMP
+    if (n_threads > 0) omp_set_num_threads(n_threads);
+#pragma omp parallel for schedule(dynamic, 1)
+#endif
+    for (int i = 0; i < n_pairs; ++i)
+        rir_one(L, beta, c, fs, Tw, ps + 3 * i, pr + 3 * i, N, n_ism, out + (long)i * n_ism, orient + 3 * i, alpha);
     (void)n_threads;
 }
 

@@ -376,3 +376,68 @@ def test_gradient_at_beta_zero_product_rule():
         b[w] = eps
         fd = (oracle.rir(L, b, c, fs, Tw, ps, pr, N, n).sum() - oracle.rir(L, np.zeros(6), c, fs, Tw, ps, pr, N, n).sum()) / eps
         assert db[w] == pytest.approx(fd, rel=1e-5)
+
+
+# --------------------------------------------------------------------------- #
+# Receiver polar patterns (Section 4 names them; the first-order formula
+# g = alpha + (1 - alpha) cos(theta) is the reading taken)
+# --------------------------------------------------------------------------- #
+@pytest.mark.parametrize("pattern,front,side,back", [
+    ("omni", 1.0, 1.0, 1.0),
+    ("subcardioid", 1.0, 0.75, 0.5),
+    ("cardioid", 1.0, 0.5, 0.0),
+    ("hypercardioid", 1.0, 0.25, -0.5),
+    ("bidirectional", 1.0, 0.0, -1.0),
+])
+def test_pattern_gain_textbook_values(pattern, front, side, back):
+    """A receiver at pr looking along +x: an image straight ahead, at 90 degrees
+    and straight behind gives the textbook gains of each first-order pattern
+    (cardioid null behind, figure-eight nulls at the sides and inverted rear
+    lobe, hypercardioid rear lobe -1/2); the length of the orientation vector
+    does not matter."""
+    pr = np.array([1.0, 2.0, 1.5])
+    for o in ([1.0, 0.0, 0.0], [3.5, 0.0, 0.0]):
+        assert oracle.pattern_gain(pattern, o, pr, pr + [4.0, 0, 0]) == pytest.approx(front, abs=1e-15)
+        assert oracle.pattern_gain(pattern, o, pr, pr + [0, -2.5, 0]) == pytest.approx(side, abs=1e-15)
+        assert oracle.pattern_gain(pattern, o, pr, pr + [0, 0, 7.0]) == pytest.approx(side, abs=1e-15)
+        assert oracle.pattern_gain(pattern, o, pr, pr + [-0.3, 0, 0]) == pytest.approx(back, abs=1e-15)
+    # 60 degrees off axis: cos = 1/2
+    a = {"omni": 1.0, "subcardioid": 0.75, "cardioid": 0.5, "hypercardioid": 0.25, "bidirectional": 0.0}[pattern]
+    img = pr + [1.0, math.sqrt(3.0), 0.0]
+    assert oracle.pattern_gain(pattern, [1, 0, 0], pr, img) == pytest.approx(a + (1 - a) * 0.5, abs=1e-15)
+
+
+def test_pattern_direct_path_only_scales_by_the_gain():
+    """With beta = 0 only the direct path remains, so every sample of a patterned
+    RIR is the omnidirectional one times the gain toward the source, computed
+    here from the positions alone."""
+    L = [4.0, 3.5, 2.7]
+    ps, pr = np.array([1.2, 0.8, 1.9]), np.array([3.1, 2.6, 0.7])
+    c, fs, Tw, N, n = 343.0, 8000.0, 32 / 8000.0, [5, 5, 5], 200
+    h0 = oracle.rir(L, [0.0] * 6, c, fs, Tw, ps, pr, N, n)
+    o = np.array([0.3, -1.0, 0.4])
+    u = (ps - pr) / np.linalg.norm(ps - pr)
+    cos_t = float(np.dot(o / np.linalg.norm(o), u))
+    for pat, a in oracle.PATTERN_ALPHA.items():
+        h = oracle.rir_list_pattern(L, [0.0] * 6, c, fs, Tw, [ps], [pr], [o], pat, N, n)[0]
+        np.testing.assert_allclose(h, (a + (1 - a) * cos_t) * h0, rtol=1e-12, atol=1e-15)
+
+
+def test_pattern_linear_in_alpha_and_omni_is_no_pattern():
+    """g is affine in alpha, so every pattern's RIR is alpha times the
+    omnidirectional RIR plus (1 - alpha) times the figure-eight one; omni is
+    bit for bit the RIR without a pattern, and flipping the orientation
+    negates the figure-eight RIR exactly."""
+    L = [3.7, 2.9, 2.3]
+    beta = [0.9, 0.8, 0.85, -0.7, 0.95, 0.6]
+    ps, pr = [[1.0, 1.1, 0.7], [2.9, 2.2, 1.5]], [[2.0, 1.4, 1.2], [0.6, 0.5, 2.0]]
+    o = [[0.2, 0.9, -0.3], [-1.0, 0.1, 0.5]]
+    c, fs, Tw, N, n = 343.0, 16000.0, 32 / 16000, [9, 9, 11], 900
+    h = {p: oracle.rir_list_pattern(L, beta, c, fs, Tw, ps, pr, o, p, N, n) for p in oracle.PATTERN_ALPHA}
+    h_plain = oracle.rir_list(L, beta, c, fs, Tw, ps, pr, N, n)
+    assert np.array_equal(h["omni"], h_plain)
+    for p, a in oracle.PATTERN_ALPHA.items():
+        np.testing.assert_allclose(h[p], a * h["omni"] + (1 - a) * h["bidirectional"], rtol=1e-9,
+                                   atol=1e-12 * np.max(np.abs(h_plain)))
+    flipped = oracle.rir_list_pattern(L, beta, c, fs, Tw, ps, pr, -np.asarray(o), "bidirectional", N, n)
+    assert np.array_equal(flipped, -h["bidirectional"])
