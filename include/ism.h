@@ -196,10 +196,31 @@ ism_status ism_simulate_noalloc(const ism_room* room, const float* pos_src, int 
 /* ------------------------------------------------------------------------- */
 /* Ragged batches: many rooms in one set of launches                         */
 /* ------------------------------------------------------------------------- */
+/* Receiver polar patterns (Section 4: "information about the polar pattern
+ * of the receivers and their orientation").  The paper gives no formula; the
+ * first-order family g(theta) = alpha + (1 - alpha) cos(theta) is used, theta
+ * being the angle between the receiver's orientation and the direction from
+ * the receiver to the image source; g multiplies the image's amplitude
+ * (eq. (4)).  alpha: OMNI 1, SUBCARDIOID 3/4, CARDIOID 1/2, HYPERCARDIOID
+ * 1/4, BIDIRECTIONAL 0. */
+typedef enum {
+    ISM_MIC_OMNI = 0,
+    ISM_MIC_SUBCARDIOID = 1,
+    ISM_MIC_CARDIOID = 2,
+    ISM_MIC_HYPERCARDIOID = 3,
+    ISM_MIC_BIDIRECTIONAL = 4
+} ism_mic_pattern;
+
 /* One independent simulation.  Meanings as in ism_simulate; pos_src,
  * pos_rcv, out and env_amp are device pointers.  env_amp may be NULL; if
  * not, it receives [n_src * n_rcv] FP32 envelope amplitudes A (eq. (8)) of
- * the diffuse tail (0 where there is no tail). */
+ * the diffuse tail (0 where there is no tail).  mic_pattern (an
+ * ism_mic_pattern, 0 = omnidirectional) applies to every receiver of the
+ * job; orient_rcv, required unless the pattern is omnidirectional, is a
+ * device pointer to [n_rcv][3] FP32 orientation vectors (any non-zero
+ * length; a zero vector is flagged ISM_DEVICE_FLAG_POSITION).  A zero-filled
+ * job struct is omnidirectional.  The gradient calls accept only
+ * omnidirectional jobs (ISM_ERR_UNSUPPORTED otherwise). */
 typedef struct {
     ism_room room;
     const float* pos_src;
@@ -211,6 +232,8 @@ typedef struct {
     uint64_t seed;
     float* out;
     float* env_amp;
+    int mic_pattern;
+    const float* orient_rcv;
 } ism_job;
 
 /* Workspace bytes for ism_simulate_batch over these jobs. */

@@ -99,7 +99,8 @@ struct WarpSmem {
 // = F amp_scale / s.  Branch free; an offset outside [-1, 31] (which the
 // binning rules out) raises *bad and contributes nothing.
 __device__ __forceinline__ void ism_delay(const float4 tx, const float4 ty, const float4 tz, int q, float amp_scale,
-                                          float* f_out, float* amp_out, int* rr_out, bool* bad)
+                                          float* f_out, float* amp_out, int* rr_out, bool* bad,
+                                          const float3 o = make_float3(0.0f, 0.0f, 0.0f), float alpha = 1.0f)
 {
     const ff s2 = ff_add(ff_add(ff{tx.x, tx.y}, ff{ty.x, ty.y}), ff{tz.x, tz.y});
     const ff sq = ff_sqrt(s2);
@@ -113,7 +114,10 @@ __device__ __forceinline__ void ism_delay(const float4 tx, const float4 ty, cons
     f = one ? __fsub_rn(f, 1.0f) : f;
     b = one ? b + 1.0f : b;
     int rr = ism_int_of_integral(b) - ISM_SB * q;
-    float amp = tx.z * ty.z * tz.z * amp_scale * ism_rcp(sq.hi);
+    const float rs = ism_rcp(sq.hi);
+    float amp = tx.z * ty.z * tz.z * amp_scale * rs;
+    if (alpha != 1.0f)   // polar pattern: cos(theta) = o . (x_n - x_r) / d, o of unit length
+        amp *= __fmaf_rn(1.0f - alpha, __fmaf_rn(o.z, tz.w, __fmaf_rn(o.y, ty.w, o.x * tx.w)) * rs, alpha);
     const bool out = rr < -1 || rr > ISM_SB - 1;
     *bad = out;
     *rr_out = out ? -1 : rr;
@@ -340,6 +344,15 @@ __global__ void __launch_bounds__(ism_acc_bins(PREC) * 32) accum_kernel(const __
     const float inv2Nw = 2.0f / J.Nw;
     const float twopi_Nw = 6.283185307179586f / J.Nw;
     const bool small_phase = J.Nw >= 16.0f;   // 2 pi f / N_w <= pi / 8
+    // receiver polar pattern: the unit orientation of this RIR's receiver
+    const float alpha = J.mic_alpha;
+    float3 orient = make_float3(0.0f, 0.0f, 0.0f);
+    if (alpha != 1.0f) {
+        const float* o = J.orient_rcv + 3 * (r % J.n_rcv);
+        const float ox = o[0], oy = o[1], oz = o[2];
+        const float inv = 1.0f / sqrtf(__fmaf_rn(ox, ox, __fmaf_rn(oy, oy, oz * oz)));
+        orient = make_float3(ox * inv, oy * inv, oz * inv);
+    }
 #pragma unroll
     for (int s = 0; s < SLOTS; ++s) {
         const int tt = lane + 32 * s;
@@ -395,7 +408,8 @@ __global__ void __launch_bounds__(ism_acc_bins(PREC) * 32) accum_kernel(const __
                         const int ix = pid & 1023, iy = (pid >> 10) & 1023, iz = pid >> 20;
                         bool bad;
                         float f, amp;
-                        ism_delay(T[ix], T[Nx + iy], T[Nx + Ny + iz], q, J.amp_scale, &f, &amp, &rr, &bad);
+                        ism_delay(T[ix], T[Nx + iy], T[Nx + Ny + iz], q, J.amp_scale, &f, &amp, &rr, &bad, orient,
+                                  alpha);
                         if (bad) atomicOr(status, (uint32_t)ISM_DEVICE_FLAG_BIN);
                         f = fminf(fmaxf(f, f_lo), f_hi);
                         rc = ism_sinc_record(f, amp, small_phase, twopi_Nw, inv2Nw);   // amp = 0 if bad
@@ -507,7 +521,8 @@ __global__ void __launch_bounds__(ism_acc_bins(PREC) * 32) accum_kernel(const __
                                 const int ix = pid & 1023, iy = (pid >> 10) & 1023, iz = pid >> 20;
                                 bool bad;
                                 float f, amp;
-                                ism_delay(T[ix], T[Nx + iy], T[Nx + Ny + iz], q, J.amp_scale, &f, &amp, &rr, &bad);
+                                ism_delay(T[ix], T[Nx + iy], T[Nx + Ny + iz], q, J.amp_scale, &f, &amp, &rr, &bad,
+                                          orient, alpha);
                                 if (bad) atomicOr(status, (uint32_t)ISM_DEVICE_FLAG_BIN);
                                 stray = rr != rr_bucket;
                                 f = fminf(fmaxf(f, f_lo), f_hi);

@@ -160,6 +160,15 @@ __global__ void __launch_bounds__(SH_WARPS * 32, 4) shell_kernel(const __grid_co
         ax[a].nlo = J.nlo[a];
         ax[a].N = J.N[a];
     }
+    // receiver polar pattern: the unit orientation of this RIR's receiver (|g| <= 1 keeps A_max a bound)
+    const float alpha = J.mic_alpha;
+    float3 orient = make_float3(0.0f, 0.0f, 0.0f);
+    if (alpha != 1.0f) {
+        const float* o = J.orient_rcv + 3 * i_rcv;
+        const float ox = o[0], oy = o[1], oz = o[2];
+        const float inv = 1.0f / sqrtf(__fmaf_rn(ox, ox, __fmaf_rn(oy, oy, oz * oz)));
+        orient = make_float3(ox * inv, oy * inv, oz * inv);
+    }
     const float sd2 = T[-J.nlo[0]].x + T[Nx - J.nlo[1]].x + T[Nx + Ny - J.nlo[2]].x;
     const bool valid = sd2 < 3.0e38f;   // +inf tables: a pair outside the room (flagged by the geometry kernel)
 
@@ -262,7 +271,7 @@ __global__ void __launch_bounds__(SH_WARPS * 32, 4) shell_kernel(const __grid_co
             }
             const int nd = max(d1 - d0, 0), nu = max(u1 - u0, 0);
             cnt = nd + nu;
-            rf = make_float4(sxy.hi, sxy.lo, tx.z * ty.z, 0.0f);
+            rf = make_float4(sxy.hi, sxy.lo, tx.z * ty.z, __fmaf_rn(orient.y, ty.w, orient.x * tx.w));
             ri = make_int4(d0, nd, u0, 0);
         }
         int inc = cnt;
@@ -310,7 +319,10 @@ __global__ void __launch_bounds__(SH_WARPS * 32, 4) shell_kernel(const __grid_co
                     const int q = (b + 1) >> 5;
                     const int ql = q - q0;
                     const int o = b - ISM_SB * q + 1;   // offset index rr + 1 in [0, 32)
-                    const float amp = cf.z * tz.z * amp_scale * ism_rcp(sq.hi);
+                    const float rs = ism_rcp(sq.hi);
+                    float amp = cf.z * tz.z * amp_scale * rs;
+                    if (alpha != 1.0f)   // polar pattern: cos(theta) = o . (x_n - x_r) / d
+                        amp *= __fmaf_rn(1.0f - alpha, __fmaf_rn(orient.z, tz.w, cf.w) * rs, alpha);
                     const float as = amp * scale_s[ql];
                     const float uu = __fmaf_rn(2.0f, f, -1.0f);
                     const float u2 = uu + uu;

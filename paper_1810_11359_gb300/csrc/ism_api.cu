@@ -96,6 +96,10 @@ ism_status validate_job(const ism_job& in, Validated& v, bool need_ptrs)
     }
     if (need_ptrs && (!j.pos_src || !j.pos_rcv || !j.out))
         return fail(ISM_ERR_INVALID_ARG, "pos_src, pos_rcv and out must be device pointers, not NULL");
+    if (j.mic_pattern < ISM_MIC_OMNI || j.mic_pattern > ISM_MIC_BIDIRECTIONAL)
+        return fail(ISM_ERR_INVALID_ARG, "mic_pattern = %d is not an ism_mic_pattern", j.mic_pattern);
+    if (need_ptrs && j.mic_pattern != ISM_MIC_OMNI && !j.orient_rcv)
+        return fail(ISM_ERR_INVALID_ARG, "a polar pattern needs orient_rcv (device pointer, [n_rcv][3])");
     v.Tw = (j.Tw > 0.0f) ? (double)j.Tw : 4e-3;
     v.Nw = window_taps(v.Tw, (double)j.fs);
     if (!(v.Nw >= 2.0)) return fail(ISM_ERR_INVALID_ARG, "window of %g taps: need Tw * fs >= 2", v.Nw);
@@ -224,6 +228,11 @@ ism_status plan(const Validated* vs, int n, ism_precision prec, bool backward, J
         J.rir_index0 = v.rir_index0;
         J.pos_src = in.pos_src;
         J.pos_rcv = in.pos_rcv;
+        {
+            static const float alpha_of[5] = {1.0f, 0.75f, 0.5f, 0.25f, 0.0f};
+            J.mic_alpha = alpha_of[in.mic_pattern];
+            J.orient_rcv = in.mic_pattern != ISM_MIC_OMNI ? in.orient_rcv : nullptr;
+        }
         J.out = in.out;
         J.env_amp = in.env_amp;
         J.rir_base = rir;
@@ -405,6 +414,7 @@ Schedule schedule(const std::vector<Validated>& vs)
                 if (j.env_amp) w.job.env_amp = j.env_amp + (long long)i0 * j.n_rcv;
             } else {
                 w.job.pos_rcv = j.pos_rcv ? j.pos_rcv + 3 * i0 : nullptr;
+                w.job.orient_rcv = j.orient_rcv ? j.orient_rcv + 3 * i0 : nullptr;
                 w.job.n_rcv = cnt;
                 w.rir_index0 = v.rir_index0 + i0;
                 if (j.env_amp) w.job.env_amp = j.env_amp + i0;
@@ -727,6 +737,8 @@ ism_status validate_grad_jobs(const ism_grad_job* jobs, int n_jobs, std::vector<
     ism_status s = validate_all(plain.data(), n_jobs, vs, false);
     if (s != ISM_OK) return s;
     for (int i = 0; i < n_jobs; ++i) {
+        if (jobs[i].job.mic_pattern != ISM_MIC_OMNI)
+            return fail(ISM_ERR_UNSUPPORTED, "job %d: gradients are for omnidirectional receivers only", i);
         if (!jobs[i].job.pos_src || !jobs[i].job.pos_rcv || !jobs[i].grad_out)
             return fail(ISM_ERR_INVALID_ARG, "job %d: pos_src, pos_rcv and grad_out must be device pointers", i);
         vs[i].grad_out = jobs[i].grad_out;
@@ -863,7 +875,11 @@ ism_status ism_backward_workspace_size(const ism_grad_job* jobs, int n_jobs, siz
     if (!bytes) return fail(ISM_ERR_INVALID_ARG, "bytes is NULL");
     if (!jobs || n_jobs < 1) return fail(ISM_ERR_INVALID_ARG, "need at least one job");
     std::vector<ism_job> plain(n_jobs);
-    for (int i = 0; i < n_jobs; ++i) plain[i] = jobs[i].job;
+    for (int i = 0; i < n_jobs; ++i) {
+        if (jobs[i].job.mic_pattern != ISM_MIC_OMNI)
+            return fail(ISM_ERR_UNSUPPORTED, "job %d: gradients are for omnidirectional receivers only", i);
+        plain[i] = jobs[i].job;
+    }
     std::vector<Validated> vs;
     ism_status s = validate_all(plain.data(), n_jobs, vs, false);
     if (s != ISM_OK) return s;

@@ -8,9 +8,12 @@
 //   S[n] = ((x_n - x_r) f_s / c)^2   (squared offset in samples^2, FP64, stored
 //                                     as a float-float pair hi + lo)
 //   F[n] = beta_0^{e0(n)} beta_1^{e1(n)}  (wall hits along that axis)
+//   D[n] = (x_n - x_r) f_s / c           (signed offset, FP32: the direction
+//                                          of arrival for polar patterns)
 // so that image (nx, ny, nz) has s^2 = Sx + Sy + Sz and weight Fx Fy Fz.  It
-// also checks that source and receiver lie strictly inside the room; a pair
-// that does not gets S = +inf everywhere, i.e. no image survives.
+// also checks that source and receiver lie strictly inside the room (and that
+// a patterned receiver has a non-zero orientation); a pair that does not gets
+// S = +inf everywhere, i.e. no image survives.
 #include <cmath>
 
 #include "ism_device.cuh"
@@ -52,6 +55,11 @@ __global__ void __launch_bounds__(128) geometry_kernel(const __grid_constant__ J
             d2 += (xs - xr) * (xs - xr);
         }
         if (!(d2 > 0.0)) ok = 0;
+        if (J.mic_alpha != 1.0f) {
+            const float* o = J.orient_rcv + 3 * i_rcv;
+            const double oo = (double)o[0] * o[0] + (double)o[1] * o[1] + (double)o[2] * o[2];
+            if (!(oo > 0.0) || !(oo < 1e300)) ok = 0;
+        }
         ok_s = ok;
         if (!ok) atomicOr(status, (uint32_t)ISM_DEVICE_FLAG_POSITION);
     }
@@ -82,7 +90,7 @@ __global__ void __launch_bounds__(128) geometry_kernel(const __grid_constant__ J
             lo = 0.0f;
             F = 0.0;
         }
-        out[e] = make_float4(hi, lo, (float)F, 0.0f);
+        out[e] = make_float4(hi, lo, (float)F, (float)u);
     }
 }
 

@@ -81,6 +81,8 @@ struct JobDev {
     uint64_t seed;
     const float* pos_src;
     const float* pos_rcv;
+    const float* orient_rcv;  // receiver orientations [n_rcv][3] (polar pattern jobs)
+    float mic_alpha;          // polar pattern g = alpha + (1 - alpha) cos(theta); 1: omnidirectional
     float* out;
     float* env_amp;
     long long img_per_rir;    // N[0] N[1] N[2]

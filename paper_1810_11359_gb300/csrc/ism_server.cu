@@ -229,6 +229,7 @@ struct ism_server {
             j.out = reinterpret_cast<float*>(d);
             j.pos_src = reinterpret_cast<const float*>(d + g256(r->out_bytes));
             j.pos_rcv = j.pos_src + 3 * r->job.n_src;
+            j.orient_rcv = r->job.mic_pattern != ISM_MIC_OMNI ? j.pos_rcv + 3 * r->job.n_rcv : nullptr;
             j.env_amp = nullptr;
             jobs.push_back(j);
         }
@@ -430,6 +431,15 @@ ism_status ism_server_submit(ism_server* s, const ism_job* job, ism_ticket* tick
         return ism_fail_message(ISM_ERR_INVALID_ARG, "pos_src, pos_rcv and out must be host pointers, not NULL");
     if (job->env_amp) return ism_fail_message(ISM_ERR_INVALID_ARG, "env_amp is not available through the server");
     if (job->n_src < 1 || job->n_rcv < 1) return ism_fail_message(ISM_ERR_INVALID_ARG, "need n_src, n_rcv >= 1");
+    const bool patterned = job->mic_pattern != ISM_MIC_OMNI;
+    if (patterned && !job->orient_rcv)
+        return ism_fail_message(ISM_ERR_INVALID_ARG, "a polar pattern needs orient_rcv (host pointer, [n_rcv][3])");
+    for (int i = 0; patterned && i < job->n_rcv; ++i) {
+        const float* o = job->orient_rcv + 3 * i;
+        const double oo = (double)o[0] * o[0] + (double)o[1] * o[1] + (double)o[2] * o[2];
+        if (!(oo > 0.0) || !(oo < 1e300))
+            return ism_fail_message(ISM_ERR_INVALID_ARG, "receiver %d has a zero or non-finite orientation", i);
+    }
     for (int i = 0; i < job->n_src; ++i)
         for (int a = 0; a < 3; ++a)
             if (!(job->pos_src[3 * i + a] > 0.0f && (double)job->pos_src[3 * i + a] < job->room.L[a]))
@@ -441,6 +451,7 @@ ism_status ism_server_submit(ism_server* s, const ism_job* job, ism_ticket* tick
     // full validation (and the workspace this job alone would need)
     ism_job probe = *job;
     probe.pos_src = probe.pos_rcv = nullptr;
+    probe.orient_rcv = nullptr;
     probe.out = nullptr;
     size_t ws1 = 0;
     ism_status v = ism_batch_workspace_size(&probe, 1, s->cfg.prec, &ws1);
@@ -450,15 +461,19 @@ ism_status ism_server_submit(ism_server* s, const ism_job* job, ism_ticket* tick
     Request* r = new Request();
     r->job = *job;
     r->out_bytes = (size_t)job->n_src * job->n_rcv * (size_t)n_S * sizeof(float);
-    r->pos_bytes = (size_t)(job->n_src + job->n_rcv) * 3 * sizeof(float);
+    const int n_vec = job->n_src + job->n_rcv + (patterned ? job->n_rcv : 0);   // positions, then orientations
+    r->pos_bytes = (size_t)n_vec * 3 * sizeof(float);
     const size_t need = g256(r->out_bytes) + g256(r->pos_bytes);
     if (need + g256(ws1) > s->dev_arena.cap() || need + 256 > s->pin_arena.cap()) {
         delete r;
         return ism_fail_message(ISM_ERR_OOM, "request needs %zu device bytes with its workspace; the budget is %zu",
                                 need + g256(ws1), s->dev_arena.cap());
     }
-    r->pos.resize((size_t)(job->n_src + job->n_rcv) * 3);
+    r->pos.resize((size_t)n_vec * 3);
     std::memcpy(r->pos.data(), job->pos_src, (size_t)job->n_src * 3 * sizeof(float));
+    if (patterned)
+        std::memcpy(r->pos.data() + 3 * (job->n_src + job->n_rcv), job->orient_rcv,
+                    (size_t)job->n_rcv * 3 * sizeof(float));
     std::memcpy(r->pos.data() + 3 * job->n_src, job->pos_rcv, (size_t)job->n_rcv * 3 * sizeof(float));
     r->t_submit = now_s();
     {

@@ -23,6 +23,8 @@ STATUS_NAMES = {0: "ISM_OK", 1: "ISM_ERR_INVALID_ARG", 2: "ISM_ERR_INFEASIBLE", 
                 4: "ISM_ERR_OOM", 5: "ISM_ERR_CUDA", 6: "ISM_ERR_TIMEOUT", 7: "ISM_ERR_DEVICE_CHECK",
                 8: "ISM_ERR_UNSUPPORTED", 9: "ISM_ERR_CANCELLED"}
 PRECISIONS = {"fp32": 0, "fp16x2": 1, "bf16x2": 2, "lut": 3, "fp32_direct": 4}
+# receiver polar patterns (ism_mic_pattern): g = alpha + (1 - alpha) cos(theta)
+MIC_PATTERNS = {"omni": 0, "subcardioid": 1, "cardioid": 2, "hypercardioid": 3, "bidirectional": 4}
 ISM_ERR_TIMEOUT_CODE = 6
 STATUS_CODES = {v: k for k, v in STATUS_NAMES.items()}
 DEVICE_FLAG_POSITION = 1
@@ -46,7 +48,8 @@ class ism_job(ctypes.Structure):
                 ("nb_img", ctypes.c_int * 3),
                 ("Tmax", ctypes.c_float), ("fs", ctypes.c_float), ("Tdiff", ctypes.c_float), ("Tw", ctypes.c_float),
                 ("seed", ctypes.c_uint64),
-                ("out", ctypes.c_void_p), ("env_amp", ctypes.c_void_p)]
+                ("out", ctypes.c_void_p), ("env_amp", ctypes.c_void_p),
+                ("mic_pattern", ctypes.c_int), ("orient_rcv", ctypes.c_void_p)]
 
 
 class ism_grad_job(ctypes.Structure):
@@ -287,11 +290,13 @@ def _workspace(ws, nbytes):
 
 
 def ism_simulate(L, beta, pos_src, pos_rcv, nb_img, Tmax, fs, Tdiff=0.0, Tw=0.0, c=343.0, prec: str = "fp32",
-                 seed: int = 0, out=None, workspace: Optional[Workspace] = None, stream=None):
+                 seed: int = 0, out=None, workspace: Optional[Workspace] = None, stream=None,
+                 mic_pattern: str = "omni", orient_rcv=None):
     """RIRs [n_src, n_rcv, n_S] (FP32 CUDA tensor) for all source/receiver pairs.
 
     pos_src/pos_rcv: [n,3] positions (CUDA FP32 tensors, or anything
-    convertible; copied to the device if needed)."""
+    convertible; copied to the device if needed).  mic_pattern / orient_rcv:
+    receiver polar pattern (a MIC_PATTERNS name) and [n_rcv,3] orientations."""
     torch = _torch()
     dev = torch.device("cuda", torch.cuda.current_device())
     ps = torch.as_tensor(pos_src, dtype=torch.float32).to(dev).reshape(-1, 3).contiguous()
@@ -299,6 +304,14 @@ def ism_simulate(L, beta, pos_src, pos_rcv, nb_img, Tmax, fs, Tdiff=0.0, Tw=0.0,
     n_S = ism_rir_length(Tmax, fs)
     if out is None:
         out = torch.empty((ps.shape[0], pr.shape[0], n_S), dtype=torch.float32, device=dev)
+    if mic_pattern != "omni":   # the pattern travels in the job struct: the batch entry point
+        orient = torch.as_tensor(orient_rcv, dtype=torch.float32).to(dev).reshape(-1, 3).contiguous()
+        if orient.shape[0] != pr.shape[0]:
+            raise ValueError("orient_rcv needs one vector per receiver")
+        job = make_job(L, beta, ps, pr, nb_img, Tmax, fs, out, Tdiff=Tdiff, Tw=Tw, c=c, seed=seed,
+                       mic_pattern=mic_pattern, orient_rcv=orient)
+        ism_simulate_batch([job], prec=prec, workspace=workspace, stream=stream)
+        return out
     nbytes = ism_workspace_size(L, beta, ps.shape[0], pr.shape[0], nb_img, Tmax, fs, Tdiff, Tw, c, prec)
     buf = _workspace(workspace, nbytes)
     r = _room(L, beta, c)
@@ -359,8 +372,9 @@ def ism_workspace_status(buf, stream=None) -> int:
 
 
 def make_job(L, beta, pos_src, pos_rcv, nb_img, Tmax, fs, out, Tdiff=0.0, Tw=0.0, c=343.0, seed=0,
-             env_amp=None) -> ism_job:
-    """An ism_job over CUDA tensors (the tensors must stay alive during the call)."""
+             env_amp=None, mic_pattern: str = "omni", orient_rcv=None) -> ism_job:
+    """An ism_job over CUDA tensors (the tensors must stay alive during the call);
+    orient_rcv: [n_rcv, 3] CUDA FP32 tensor for a polar pattern."""
     j = ism_job()
     j.room = _room(L, beta, c)
     j.pos_src = pos_src.data_ptr()
@@ -373,6 +387,8 @@ def make_job(L, beta, pos_src, pos_rcv, nb_img, Tmax, fs, out, Tdiff=0.0, Tw=0.0
     j.seed = int(seed) & (2 ** 64 - 1)
     j.out = out.data_ptr()
     j.env_amp = None if env_amp is None else env_amp.data_ptr()
+    j.mic_pattern = MIC_PATTERNS[mic_pattern]
+    j.orient_rcv = None if orient_rcv is None else orient_rcv.data_ptr()
     return j
 
 
@@ -496,7 +512,7 @@ class Server:
         self._lock = threading.Lock()
 
     def submit(self, L, beta, pos_src, pos_rcv, nb_img, Tmax, fs, Tdiff=0.0, Tw=0.0, c=343.0, seed=0,
-               out: Optional[np.ndarray] = None):
+               out: Optional[np.ndarray] = None, mic_pattern: str = "omni", orient_rcv=None):
         """Queues one room; returns (ticket, out) where `out` [n_src, n_rcv, n_S]
         FP32 receives the RIRs once the ticket is done."""
         ps = np.ascontiguousarray(np.asarray(pos_src, dtype=np.float32).reshape(-1, 3))
@@ -517,6 +533,11 @@ class Server:
         j.seed = int(seed) & (2 ** 64 - 1)
         j.out = out.ctypes.data
         j.env_amp = None
+        j.mic_pattern = MIC_PATTERNS[mic_pattern]
+        orient = None
+        if mic_pattern != "omni":
+            orient = np.ascontiguousarray(np.asarray(orient_rcv, dtype=np.float32).reshape(-1, 3))
+            j.orient_rcv = orient.ctypes.data   # copied by the server at submit
         t = ctypes.c_uint64()
         _check(load().ism_server_submit(self._h, ctypes.byref(j), ctypes.byref(t)))
         with self._lock:
