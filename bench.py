@@ -11,7 +11,7 @@ circle) in a 10 x 8 x 3.5 m room, T60 = 1.2 s, 48 kHz, image sources to
 0.3 s and the Philox diffuse tail to 1.2 s (57,600 samples per RIR); the
 line adds the HBM roofline of the tail kernel.
 
---prec fp32|fp16x2|bf16x2|lut selects the tap arithmetic of the
+--prec fp32|fp16x2|bf16x2|lut|lut_tex|fp32_direct selects the tap arithmetic of the
 accumulation kernel (the image enumeration and delays are FP32 in all).
 
 Prints one JSON line (rank 0).  `value` is RIRs/s of the whole job; the line
@@ -21,7 +21,7 @@ oracle timed on the host cores (cpu_baseline) and the SM clocks sampled
 during the timed region.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                    [--workload batched|trajectory] [--prec fp32|fp16x2|bf16x2|lut]
+                    [--workload batched|trajectory] [--prec fp32|fp16x2|bf16x2|lut|lut_tex|fp32_direct]
 
 --impl reference times the FP64 CPU oracle on a bounded sample of the same
 workload on the host cores (rank 0 only).
@@ -51,8 +51,10 @@ FMA_OPS_PER_CONTRIBUTION = 5   # FADD (j - f), 2 FFMA (window), FMUL, FFMA (accu
 OPS_PER_IMAGE = 42             # per image: the geometry of its delay and amplitude (~40), sin(pi f), the window phase
 L2_BYTES = 129 * 1024 * 1024
 DTYPES = {"fp32": "f32", "fp16x2": "f16x2 taps, f32 accumulation", "bf16x2": "bf16x2 taps, f32 accumulation",
-          "lut": "f32 windowed-sinc table, f32 accumulation", "fp32_direct": "f32 (every tap evaluated)"}
-PREC_ID = {"fp32": 0, "fp16x2": 1, "bf16x2": 2, "lut": 3, "fp32_direct": 4}
+          "lut": "f32 windowed-sinc table, f32 accumulation", "fp32_direct": "f32 (every tap evaluated)",
+          "lut_tex": "f32 windowed-sinc table through the texture unit (8-bit filter weights), f32 accumulation"}
+# tap arithmetic of the direct accumulation kernel instantiated for each form (its PREC template value)
+PREC_ID = {"fp32": 0, "fp16x2": 1, "bf16x2": 2, "lut": 3, "fp32_direct": 0, "lut_tex": 4}
 
 
 def _peaks():

@@ -77,7 +77,10 @@ typedef enum {
     ISM_PREC_FP16X2 = 1,      /* packed FP16 window and sinc, FP32 accumulation        */
     ISM_PREC_BF16X2 = 2,      /* packed BF16 window and sinc, FP32 accumulation        */
     ISM_PREC_LUT = 3,         /* FP32 windowed-sinc table (eq. (9)), FP32 lerp         */
-    ISM_PREC_FP32_DIRECT = 4  /* FP32 sin/cos/reciprocal for every image tap (eq. (6)) */
+    ISM_PREC_FP32_DIRECT = 4, /* FP32 sin/cos/reciprocal for every image tap (eq. (6)) */
+    ISM_PREC_LUT_TEX = 5      /* the same table read through the texture unit with its
+                               * hardware linear filtering (8-bit weights), as in the
+                               * paper's LUT kernel (Section 3.5)                    */
 } ism_precision;
 
 /* A shoebox room (Section 2.1).  beta is ordered x0, x1, y0, y1, z0, z1:

@@ -17,6 +17,7 @@ int ism_launch_accum(const JobTable& t, const WsPlan& p, char* ws, ism_precision
     case ISM_PREC_FP16X2: return ism_launch_accum_fp16(t, p, ws, stream, launched);
     case ISM_PREC_BF16X2: return ism_launch_accum_bf16(t, p, ws, stream, launched);
     case ISM_PREC_LUT: return ism_launch_accum_lut(t, p, ws, stream, launched);
+    case ISM_PREC_LUT_TEX: return ism_launch_accum_tex(t, p, ws, stream, launched);
     }
     *launched = 0;
     return (int)cudaErrorInvalidValue;

@@ -80,7 +80,7 @@ namespace {
 #define ISM_PAD (ISM_PIECE + 4 * ISM_NB)
 #define ISM_DUMMY 0x80000000u      // sorted-list entry that carries no image
 
-enum { PREC_FP32 = 0, PREC_FP16 = 1, PREC_BF16 = 2, PREC_LUT = 3 };
+enum { PREC_FP32 = 0, PREC_FP16 = 1, PREC_BF16 = 2, PREC_LUT = 3, PREC_TEX = 4 };
 
 struct WarpSmem {
     uint32_t sorted[ISM_PAD];      // ids sorted by plain-FP32 offset, buckets padded to 4
@@ -287,6 +287,19 @@ __device__ __forceinline__ void taps_lut(const float4 rc, const float* __restric
     }
 }
 
+// Taps of one image from the windowed-sinc table read through the texture
+// unit (the paper's own LUT path, Section 3.5): the table is a 2-D texture
+// (x = tap, y = fractional-delay phase) with hardware linear filtering along
+// y, so each tap is one filtered fetch and one FFMA with the record {A, y}.
+// The filter weight has 8 fractional bits (1/256 of a phase step).
+template <int SLOTS>
+__device__ __forceinline__ void taps_tex(const float4 rc, unsigned long long tex, int lane, float (&D)[SLOTS])
+{
+#pragma unroll
+    for (int s = 0; s < SLOTS; ++s)
+        D[s] = __fmaf_rn(rc.x, tex2D<float>((cudaTextureObject_t)tex, (float)(lane + 32 * s) + 0.5f, rc.y), D[s]);
+}
+
 template <int SLOTS, bool MASK, int PREC>
 __global__ void __launch_bounds__(ism_acc_bins(PREC) * 32) accum_kernel(const __grid_constant__ JobTable t,
                                                                   const float4* __restrict__ tbl,
@@ -305,7 +318,7 @@ __global__ void __launch_bounds__(ism_acc_bins(PREC) * 32) accum_kernel(const __
     const JobDev& J = t.j[jid];
     const bool exact = (J.Nw == (float)(2 * J.H)) && (2 * J.H == 32 * J.slots);
     if (J.slots != SLOTS || J.use_cheb) return;                // another kernel handles this job
-    if (PREC != PREC_LUT && exact == MASK) return;             // (the LUT carries its own mask)
+    if (PREC != PREC_LUT && PREC != PREC_TEX && exact == MASK) return;   // (the tables carry their own mask)
 
     const long long local = g - J.acc_cta_base;
     const int r = (int)(local / J.acc_groups);
@@ -526,7 +539,11 @@ __global__ void __launch_bounds__(ism_acc_bins(PREC) * 32) accum_kernel(const __
                                 if (bad) atomicOr(status, (uint32_t)ISM_DEVICE_FLAG_BIN);
                                 stray = rr != rr_bucket;
                                 f = fminf(fmaxf(f, f_lo), f_hi);
-                                if constexpr (PREC == PREC_LUT) {
+                                if constexpr (PREC == PREC_TEX) {
+                                    // texel row f Q, centred: the texture interpolates rows floor and + 1
+                                    rl = make_float4(amp, __fmaf_rn(f, (float)LQ, 0.5f), 0.0f, 0.0f);
+                                    if (stray) rc = ism_sinc_record(f, amp, small_phase, twopi_Nw, inv2Nw);
+                                } else if constexpr (PREC == PREC_LUT) {
                                     const float u = f * (float)LQ;        // exact: LQ is a power of two
                                     const float pf = floorf(u);
                                     const float ph = u - pf;              // exact
@@ -540,7 +557,7 @@ __global__ void __launch_bounds__(ism_acc_bins(PREC) * 32) accum_kernel(const __
                         }
                         if constexpr (PREC == PREC_FP32) {
                             W.rec[32 * h + lane] = stray ? make_float4(rc.x, 0.0f, 0.0f, 0.0f) : rc;
-                        } else if constexpr (PREC == PREC_LUT) {
+                        } else if constexpr (PREC == PREC_LUT || PREC == PREC_TEX) {
                             W.rec[32 * h + lane] = stray ? make_float4(0.0f, 0.0f, 0.0f, 0.0f) : rl;
                         } else {
                             // pack the records of lanes 2k (a) and 2k + 1 (b) into one pair
@@ -591,6 +608,13 @@ __global__ void __launch_bounds__(ism_acc_bins(PREC) * 32) accum_kernel(const __
                             taps<SLOTS, MASK>(r1, xj, nsg, Cj, Sj, tap_ok, halfNw, D2);
                             taps<SLOTS, MASK>(r2, xj, nsg, Cj, Sj, tap_ok, halfNw, D);
                             taps<SLOTS, MASK>(r3, xj, nsg, Cj, Sj, tap_ok, halfNw, D2);
+                        } else if constexpr (PREC == PREC_TEX) {
+                            const float4 r0 = W.rec[4 * g], r1 = W.rec[4 * g + 1], r2 = W.rec[4 * g + 2],
+                                         r3 = W.rec[4 * g + 3];
+                            taps_tex<SLOTS>(r0, J.lut_tex, lane, D);
+                            taps_tex<SLOTS>(r1, J.lut_tex, lane, D2);
+                            taps_tex<SLOTS>(r2, J.lut_tex, lane, D);
+                            taps_tex<SLOTS>(r3, J.lut_tex, lane, D2);
                         } else if constexpr (PREC == PREC_LUT) {
                             const float4 r0 = W.rec[4 * g], r1 = W.rec[4 * g + 1], r2 = W.rec[4 * g + 2],
                                          r3 = W.rec[4 * g + 3];
@@ -672,12 +696,12 @@ int launch_accum_prec(const JobTable& t, const WsPlan& p, char* ws, void* stream
         const JobDev& J = t.j[i];
         if (J.use_cheb) continue;
         bool exact = (J.Nw == (float)(2 * J.H)) && (2 * J.H == 32 * J.slots);
-        need[(exact || PREC == PREC_LUT) ? 0 : 1][J.slots] = true;
+        need[(exact || PREC == PREC_LUT || PREC == PREC_TEX) ? 0 : 1][J.slots] = true;
     }
     int rc = 0;
 #define ISM_L(SL)                                                                            \
     if (!rc && need[0][SL]) rc = launch_one<SL, false, PREC>(t, p, ws, s), ++*launched;      \
-    if constexpr (PREC != PREC_LUT)                                                          \
+    if constexpr (PREC != PREC_LUT && PREC != PREC_TEX)                                      \
         if (!rc && need[1][SL]) rc = launch_one<SL, true, PREC>(t, p, ws, s), ++*launched;
     ISM_L(1) ISM_L(2) ISM_L(3) ISM_L(4) ISM_L(5) ISM_L(6) ISM_L(7) ISM_L(8)
 #undef ISM_L

@@ -5,7 +5,9 @@
 #include <cstdio>
 #include <cstring>
 #include <atomic>
+#include <map>
 #include <mutex>
+#include <tuple>
 #include <string>
 #include <vector>
 
@@ -291,6 +293,8 @@ ism_status plan(const Validated* vs, int n, ism_precision prec, bool backward, J
         }
         rows += R * J.Q * 32LL * (J.slots + 1);
         if (prec == ISM_PREC_LUT) lut += (long long)(ism_lut_phases(J.slots) + 1) * 32 * J.slots;
+        // texture form: each table starts on a 512-byte boundary (texture base alignment)
+        if (prec == ISM_PREC_LUT_TEX) lut += ((long long)(ism_lut_phases(J.slots) + 1) * 32 * J.slots + 127) / 128 * 128;
         if (J.use_cheb) t.any_cheb = 1;
         else t.any_direct = 1;
         if (backward) gpart += R * J.Q * 12;
@@ -338,6 +342,7 @@ ism_status plan(const Validated* vs, int n, ism_precision prec, bool backward, J
     off = align256(off + (size_t)rows * 4);
     p.amp_off = off;
     off = align256(off + (size_t)rir * 4);
+    if (prec == ISM_PREC_LUT_TEX) off = (off + 511) & ~(size_t)511;
     p.lut_off = off;
     off = align256(off + (size_t)lut * 4);
     p.gpart_off = off;
@@ -584,6 +589,45 @@ struct StageTimer {
     }
 };
 
+// Texture objects over the windowed-sinc tables of the texture form: a 2-D
+// pitched view (x = tap, y = phase) with linear filtering, created once per
+// (device, table address, shape) and kept for the life of the process (a
+// texture object must outlive every kernel that reads it; tables reuse the
+// same workspace addresses from call to call, so the set stays small).
+bool lut_texture(float* base, int row, int rows, unsigned long long* out)
+{
+    static std::mutex mu;
+    static std::map<std::tuple<int, uintptr_t, int, int>, unsigned long long> cache;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return false;
+    const auto key = std::make_tuple(dev, (uintptr_t)base, row, rows);
+    std::lock_guard<std::mutex> g(mu);
+    auto it = cache.find(key);
+    if (it != cache.end()) {
+        *out = it->second;
+        return true;
+    }
+    cudaResourceDesc rd;
+    std::memset(&rd, 0, sizeof rd);
+    rd.resType = cudaResourceTypePitch2D;
+    rd.res.pitch2D.devPtr = base;
+    rd.res.pitch2D.desc = cudaCreateChannelDesc<float>();
+    rd.res.pitch2D.width = (size_t)row;
+    rd.res.pitch2D.height = (size_t)rows;
+    rd.res.pitch2D.pitchInBytes = (size_t)row * sizeof(float);
+    cudaTextureDesc td;
+    std::memset(&td, 0, sizeof td);
+    td.addressMode[0] = td.addressMode[1] = cudaAddressModeClamp;
+    td.filterMode = cudaFilterModeLinear;
+    td.readMode = cudaReadModeElementType;
+    td.normalizedCoords = 0;
+    cudaTextureObject_t tex = 0;
+    if (cudaCreateTextureObject(&tex, &rd, &td, nullptr) != cudaSuccess) return false;
+    cache[key] = (unsigned long long)tex;
+    *out = (unsigned long long)tex;
+    return true;
+}
+
 // The launches of one launch set, in order, on `st`.
 ism_status run_set(const std::vector<Validated>& set, ism_precision prec, size_t base, char* ws, cudaStream_t st)
 {
@@ -591,6 +635,15 @@ ism_status run_set(const std::vector<Validated>& set, ism_precision prec, size_t
     WsPlan p;
     ism_status s = plan(set.data(), (int)set.size(), prec, false, t, p, base);
     if (s != ISM_OK) return s;
+    if (prec == ISM_PREC_LUT_TEX)
+        for (int i = 0; i < t.n_jobs; ++i) {
+            JobDev& J = t.j[i];
+            float* tb = reinterpret_cast<float*>(ws + p.lut_off) + J.lut_base;
+            if (!lut_texture(tb, 32 * J.slots, ism_lut_phases(J.slots) + 1, &J.lut_tex)) {
+                cudaGetLastError();
+                return fail(ISM_ERR_CUDA, "texture object over the windowed-sinc table of job %d", i);
+            }
+        }
     void* stream = (void*)st;
     int e;
     {
@@ -774,7 +827,7 @@ ism_job make_job(const ism_room* room, const float* pos_src, int n_src, const fl
 ism_status check_prec(ism_precision prec)
 {
     if (prec != ISM_PREC_FP32 && prec != ISM_PREC_FP16X2 && prec != ISM_PREC_BF16X2 && prec != ISM_PREC_LUT &&
-        prec != ISM_PREC_FP32_DIRECT)
+        prec != ISM_PREC_FP32_DIRECT && prec != ISM_PREC_LUT_TEX)
         return fail(ISM_ERR_INVALID_ARG, "unknown precision %d", (int)prec);
     return ISM_OK;
 }

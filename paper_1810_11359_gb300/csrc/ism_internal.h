@@ -96,7 +96,8 @@ struct JobDev {
     long long tail_cta_base;  // first tail CTA of the job
     long long fin_cta_base;   // first finalize CTA of the job
     long long rows_base;      // first window row (float) of the job: [n_rir][Q][32 (slots + 1)]
-    long long lut_base;       // first entry (float) of the job's windowed-sinc table (LUT form)
+    long long lut_base;       // first entry (float) of the job's windowed-sinc table (LUT forms)
+    unsigned long long lut_tex;  // texture object over that table (texture form)
     // backward pass only
     const float* grad_out;    // dLoss/dh [n_rir][n_S]
     float* grad_beta;         // [6]
@@ -176,6 +177,7 @@ int ism_launch_accum(const JobTable& t, const WsPlan& p, char* ws, ism_precision
 int ism_launch_accum_fp16(const JobTable& t, const WsPlan& p, char* ws, void* stream, int* launched);
 int ism_launch_accum_bf16(const JobTable& t, const WsPlan& p, char* ws, void* stream, int* launched);
 int ism_launch_accum_lut(const JobTable& t, const WsPlan& p, char* ws, void* stream, int* launched);
+int ism_launch_accum_tex(const JobTable& t, const WsPlan& p, char* ws, void* stream, int* launched);
 int ism_launch_lut_tables(const JobTable& t, const WsPlan& p, char* ws, void* stream);
 int ism_launch_accum_cheb(const JobTable& t, const WsPlan& p, char* ws, void* stream, int* launched);
 int ism_launch_adjoint(const JobTable& t, const WsPlan& p, char* ws, void* stream, int* launched);

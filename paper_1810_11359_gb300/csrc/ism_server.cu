@@ -386,7 +386,7 @@ ism_status ism_server_create(const ism_server_config* cfg, ism_server** server)
     if (c.hbm_budget < ((size_t)16 << 20) || c.host_budget < ((size_t)1 << 20))
         return ism_fail_message(ISM_ERR_INVALID_ARG, "hbm_budget must be >= 16 MiB and host_budget >= 1 MiB");
     if (c.prec != ISM_PREC_FP32 && c.prec != ISM_PREC_FP16X2 && c.prec != ISM_PREC_BF16X2 && c.prec != ISM_PREC_LUT &&
-        c.prec != ISM_PREC_FP32_DIRECT)
+        c.prec != ISM_PREC_FP32_DIRECT && c.prec != ISM_PREC_LUT_TEX)
         return ism_fail_message(ISM_ERR_INVALID_ARG, "unknown precision");
     int n_dev = 0;
     if (cudaGetDeviceCount(&n_dev) != cudaSuccess || c.device < 0 || c.device >= n_dev) {

@@ -22,7 +22,7 @@ ISM_OK = 0
 STATUS_NAMES = {0: "ISM_OK", 1: "ISM_ERR_INVALID_ARG", 2: "ISM_ERR_INFEASIBLE", 3: "ISM_ERR_WORKSPACE_TOO_SMALL",
                 4: "ISM_ERR_OOM", 5: "ISM_ERR_CUDA", 6: "ISM_ERR_TIMEOUT", 7: "ISM_ERR_DEVICE_CHECK",
                 8: "ISM_ERR_UNSUPPORTED", 9: "ISM_ERR_CANCELLED"}
-PRECISIONS = {"fp32": 0, "fp16x2": 1, "bf16x2": 2, "lut": 3, "fp32_direct": 4}
+PRECISIONS = {"fp32": 0, "fp16x2": 1, "bf16x2": 2, "lut": 3, "fp32_direct": 4, "lut_tex": 5}
 # receiver polar patterns (ism_mic_pattern): g = alpha + (1 - alpha) cos(theta)
 MIC_PATTERNS = {"omni": 0, "subcardioid": 1, "cardioid": 2, "hypercardioid": 3, "bidirectional": 4}
 ISM_ERR_TIMEOUT_CODE = 6

@@ -21,8 +21,8 @@ from paper_1810_11359_gb300 import ism, workloads
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
-TOL = {"fp16x2": 2e-3, "lut": 2e-3, "bf16x2": 1e-2, "fp32_direct": 1e-5}
-PRECS = ["fp16x2", "bf16x2", "lut", "fp32_direct"]
+TOL = {"fp16x2": 2e-3, "lut": 2e-3, "bf16x2": 1e-2, "fp32_direct": 1e-5, "lut_tex": 2e-3}
+PRECS = ["fp16x2", "bf16x2", "lut", "fp32_direct", "lut_tex"]
 
 
 @pytest.fixture(scope="module", autouse=True)
