@@ -224,6 +224,37 @@ def rir_list_pattern(L, beta, c, fs, Tw, ps_list, pr_list, orient_list, pattern,
     return out
 
 
+# --------------------------------------------------------------------------- #
+# Section 4, simulating moving sources: the source signal is cut into one
+# segment per trajectory point, each segment is filtered by the RIRs of its
+# point (one per microphone) and the filtered segments are overlap-added.
+# Reading: segment p covers the samples [start_p, start_(p+1)), by default
+# start_p = floor(p n_x / n_points); the output has n_x + n_S - 1 samples.
+# --------------------------------------------------------------------------- #
+def segment_starts(n_x: int, n_points: int):
+    """Uniform segmentation: start_p = floor(p n_x / n_points), p = 0 .. n_points."""
+    return [(p * int(n_x)) // int(n_points) for p in range(int(n_points) + 1)]
+
+
+def auralize(signal, rirs, starts=None):
+    """y[m] = sum_p conv(x[start_p:start_(p+1)], h[p, m]) placed at start_p (FP64).
+
+    signal [n_x]; rirs [n_points, n_mics, n_S]; returns [n_mics, n_x + n_S - 1]."""
+    x = np.asarray(signal, dtype=np.float64).ravel()
+    h = np.asarray(rirs, dtype=np.float64)
+    n_points, n_mics, n_s = h.shape
+    if starts is None:
+        starts = segment_starts(x.size, n_points)
+    y = np.zeros((n_mics, x.size + n_s - 1), np.float64)
+    for p in range(n_points):
+        a, b = int(starts[p]), int(starts[p + 1])
+        if b <= a:
+            continue
+        for m in range(n_mics):
+            y[m, a:b + n_s - 1] += np.convolve(x[a:b], h[p, m])
+    return y
+
+
 def rir(L, beta, c, fs, Tw, ps, pr, N, n_ism, n_threads: int = 0):
     """ISM part of one RIR, eq. (5) with eq. (6)."""
     return rir_list(L, beta, c, fs, Tw, [ps], [pr], N, n_ism, n_threads)[0]
