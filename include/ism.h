@@ -377,6 +377,25 @@ ism_status ism_simulate_backward(const ism_room* room, const float* pos_src, int
 ism_status ism_diffuse_noise(uint64_t seed, uint32_t rir, uint32_t k0, int n, float* z, void* stream);
 
 /* ------------------------------------------------------------------------- */
+/* Moving sources (Section 4: a source moving along a trajectory, recorded   */
+/* by a microphone array)                                                    */
+/* ------------------------------------------------------------------------- */
+/* Cuts the source signal into one segment per trajectory point, filters each
+ * segment by the RIRs of its point (one per microphone) and overlap-adds the
+ * results:
+ *   out[m][t] = sum_p sum_{starts[p] <= s < end_p} signal[s] rirs[p][m][t - s],
+ * end_p = starts[p + 1] (n_x for the last point), 0 <= t < n_x + n_S - 1.
+ * signal: device [n_x]; rirs: device [n_points][n_mics][n_S] (the layout of
+ * ism_simulate with the trajectory points as sources and the microphones as
+ * receivers); starts: device [n_points] non-decreasing segment starts (values
+ * are clamped to [0, n_x]; samples before starts[0] are not emitted), or NULL
+ * for the uniform cut starts[p] = floor(p n_x / n_points); out: device
+ * [n_mics][n_x + n_S - 1], overwritten.  FP32 multiply-adds on the GPU in a
+ * fixed order (results are identical run to run).  No workspace. */
+ism_status ism_auralize(const float* signal, int n_x, const float* rirs, int n_points, int n_mics, int n_S,
+                        const int* starts, float* out, void* stream);
+
+/* ------------------------------------------------------------------------- */
 /* Helpers of Section 4 (FP64)                                                */
 /* ------------------------------------------------------------------------- */
 /* Eq. (7): T60 = 0.161 V / sum_i S_i (1 - beta_i^2).  Host. */

@@ -1055,6 +1055,21 @@ ism_status ism_diffuse_noise(uint64_t seed, uint32_t rir, uint32_t k0, int n, fl
     return ISM_OK;
 }
 
+ism_status ism_auralize(const float* signal, int n_x, const float* rirs, int n_points, int n_mics, int n_S,
+                        const int* starts, float* out, void* stream)
+{
+    g_last_error.clear();
+    if (!signal || !rirs || !out) return fail(ISM_ERR_INVALID_ARG, "signal, rirs and out must be device pointers");
+    if (n_x < 1 || n_points < 1 || n_mics < 1 || n_S < 1)
+        return fail(ISM_ERR_INVALID_ARG, "need n_x, n_points, n_mics, n_S >= 1");
+    if ((long long)n_x + n_S - 1 > 0x7FFFFFFFll || (long long)n_points * n_mics * (long long)n_S > (1ll << 40))
+        return fail(ISM_ERR_UNSUPPORTED, "signal or RIRs too long");
+    if (n_points > n_x) return fail(ISM_ERR_INVALID_ARG, "more trajectory points (%d) than samples (%d)", n_points, n_x);
+    int e = ism_launch_auralize(signal, n_x, rirs, n_points, n_mics, n_S, starts, out, stream);
+    if (e) return cuda_fail(e, "auralization kernel");
+    return ISM_OK;
+}
+
 ism_status ism_t60_sabine(const double L[3], const double beta[6], double* T60)
 {
     g_last_error.clear();

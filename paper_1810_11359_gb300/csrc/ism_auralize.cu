@@ -1,0 +1,171 @@
+// ism_auralize.cu -- moving sources (Section 4): the source signal is cut into
+// one segment per trajectory point, each segment is filtered by the RIRs of its
+// point (one per microphone) and the filtered segments are overlap-added:
+//   y[m][t] = sum_p sum_{s in [a_p, a_(p+1))} x[s] h[p][m][t - s].
+// The paper does this with batched FFTs; here it is a direct FP32 convolution
+// on the FMA pipe (the RIRs are long, the signal is short, and the sum has a
+// fixed order).
+//
+// One CTA owns 256 consecutive output samples and up to 8 microphones; its 4
+// warps split the segments that reach the tile round-robin and add their
+// partial sums in warp order at the end.  Lane l of a warp owns the outputs
+// T0 + 8 l + r, r = 0 .. 7, for the 8 microphones (64 accumulators).  For one
+// segment the taps k that connect it to the tile are walked in chunks of 128:
+// the chunk's taps of the 8 microphones and the signal window it needs (the
+// samples outside the segment zeroed) are staged in the warp's shared memory;
+// at tap k the lane's 8 signal values are x[T0 + 8 l + r - k], so going from k
+// to k + 1 they shift by one register and a single new value is loaded
+// (stored with a stride-9 skew so the 32 lanes' loads hit 32 banks), and the
+// 8 taps h[p][m][k] come from two broadcast 128-bit loads: 64 FFMA per three
+// shared loads.
+#include "ism_device.cuh"
+
+namespace {
+
+#define AU_R 8                       // outputs per lane
+#define AU_M 8                       // microphones per CTA
+#define AU_KC 128                    // taps per staged chunk
+#define AU_WARPS 4                   // warps per CTA (segments split round-robin)
+#define AU_TILE (32 * AU_R)          // outputs per CTA
+#define AU_XN (AU_TILE + AU_KC - 1)  // signal samples per chunk
+#define AU_XS (AU_XN + AU_XN / 8 + 8)  // skewed storage (index j + j / 8)
+
+struct AuWarp {
+    float4 h[AU_KC][AU_M / 4];       // taps of the chunk: [k][microphone]
+    float x[AU_XS];                  // signal window, skewed
+};
+
+__device__ __forceinline__ int au_skew(int j) { return j + (j >> 3); }
+
+// Segment of sample s (the largest p with a_p <= s): uniform cut when starts
+// is NULL, else a binary search over the caller's start array.
+__device__ __forceinline__ int au_segment(long long s, int n_x, int n_points, const int* starts)
+{
+    if (!starts) return (int)min((long long)n_points - 1, ((s + 1) * n_points - 1) / n_x);
+    int lo = 0, hi = n_points - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if ((long long)starts[mid] <= s) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
+}
+
+__device__ __forceinline__ int au_start(int p, int n_x, int n_points, const int* starts)
+{
+    if (!starts) return (int)(((long long)p * n_x) / n_points);
+    return min(max(starts[p], 0), n_x);
+}
+
+__global__ void __launch_bounds__(AU_WARPS * 32) auralize_kernel(const float* __restrict__ x, int n_x,
+                                                                 const float* __restrict__ h, int n_points,
+                                                                 int n_mics, int n_s,
+                                                                 const int* __restrict__ starts,
+                                                                 float* __restrict__ y, int n_out)
+{
+    extern __shared__ __align__(16) unsigned char smem[];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    AuWarp& W = reinterpret_cast<AuWarp*>(smem)[warp];
+    const long long T0 = (long long)blockIdx.x * AU_TILE;
+    const int m0 = blockIdx.y * AU_M;
+
+    float acc[AU_R][AU_M];
+#pragma unroll
+    for (int r = 0; r < AU_R; ++r)
+#pragma unroll
+        for (int m = 0; m < AU_M; ++m) acc[r][m] = 0.0f;
+
+    // samples that reach the tile: s in [T0 - n_s + 1, T0 + TILE - 1]
+    const long long s_lo = max(T0 - n_s + 1, 0ll);
+    const long long s_hi = min(T0 + AU_TILE - 1, (long long)n_x - 1);
+    if (s_lo <= s_hi) {
+        const int p_lo = au_segment(s_lo, n_x, n_points, starts);
+        const int p_hi = au_segment(s_hi, n_x, n_points, starts);
+        for (int p = p_lo + warp; p <= p_hi; p += AU_WARPS) {
+            const int a = au_start(p, n_x, n_points, starts);
+            const int b = max(a, p + 1 < n_points ? au_start(p + 1, n_x, n_points, starts) : n_x);
+            if (b <= a) continue;
+            // taps linking [a, b) to the tile
+            const long long k_lo = max(T0 - b + 1, 0ll);
+            const long long k_hi = min(T0 + AU_TILE - 1 - a, (long long)n_s - 1);
+            const float* hp = h + (long long)p * n_mics * n_s;
+            for (long long k0 = k_lo; k0 <= k_hi; k0 += AU_KC) {
+                __syncwarp();
+                // taps k0 .. k0 + KC - 1 of the 8 microphones (0 past k_hi or past the array)
+                for (int e = lane; e < AU_KC * AU_M; e += 32) {   // coalesced along the taps
+                    const int m = e / AU_KC, kk = e % AU_KC;
+                    const long long k = k0 + kk;
+                    float v = 0.0f;
+                    if (k <= k_hi && m0 + m < n_mics) v = hp[(long long)(m0 + m) * n_s + k];
+                    reinterpret_cast<float*>(&W.h[kk][0])[m] = v;
+                }
+                // signal window: x[T0 - k0 - KC + 1 + j], zero outside [a, b)
+                const long long xb = T0 - k0 - AU_KC + 1;
+                for (int j = lane; j < AU_XN; j += 32) {
+                    const long long s = xb + j;
+                    W.x[au_skew(j)] = (s >= a && s < b) ? x[s] : 0.0f;
+                }
+                __syncwarp();
+                // window of the lane at kk = 0: x[T0 + 8 l + r - k0] = window index 8 l + r + KC - 1
+                float xv[AU_R];
+#pragma unroll
+                for (int r = 0; r < AU_R; ++r) xv[r] = W.x[au_skew(AU_R * lane + r + AU_KC - 1)];
+#pragma unroll 8
+                for (int kk = 0; kk < AU_KC; ++kk) {
+                    const float4 h0 = W.h[kk][0], h1 = W.h[kk][1];
+                    const float hv[AU_M] = {h0.x, h0.y, h0.z, h0.w, h1.x, h1.y, h1.z, h1.w};
+#pragma unroll
+                    for (int r = 0; r < AU_R; ++r)
+#pragma unroll
+                        for (int m = 0; m < AU_M; ++m) acc[r][m] = __fmaf_rn(xv[r], hv[m], acc[r][m]);
+                    // next tap: the window moves one sample back
+#pragma unroll
+                    for (int r = AU_R - 1; r > 0; --r) xv[r] = xv[r - 1];
+                    const int jn = AU_R * lane + AU_KC - 2 - kk;   // >= 0 for kk <= KC - 2
+                    xv[0] = jn >= 0 ? W.x[au_skew(jn)] : 0.0f;
+                }
+            }
+        }
+    }
+
+    // partial sums of the warps, added in warp order
+    __syncthreads();
+    float* red = reinterpret_cast<float*>(smem);   // [warps][R][M][32]
+#pragma unroll
+    for (int r = 0; r < AU_R; ++r)
+#pragma unroll
+        for (int m = 0; m < AU_M; ++m) red[((warp * AU_R + r) * AU_M + m) * 32 + lane] = acc[r][m];
+    __syncthreads();
+    // thread e writes output (t, m) pairs; consecutive threads take consecutive t
+    for (int e = threadIdx.x; e < AU_TILE * AU_M; e += blockDim.x) {
+        const int m = e / AU_TILE, i = e % AU_TILE;   // i = 8 l + r
+        const int l = i / AU_R, r = i % AU_R;
+        float v = red[((0 * AU_R + r) * AU_M + m) * 32 + l];
+#pragma unroll
+        for (int w = 1; w < AU_WARPS; ++w) v += red[((w * AU_R + r) * AU_M + m) * 32 + l];
+        const long long t = T0 + i;
+        if (t < n_out && m0 + m < n_mics) y[(long long)(m0 + m) * n_out + t] = v;
+    }
+}
+
+}  // namespace
+
+size_t ism_auralize_smem()
+{
+    const size_t stage = AU_WARPS * sizeof(AuWarp);
+    const size_t red = (size_t)AU_WARPS * AU_R * AU_M * 32 * sizeof(float);
+    return stage > red ? stage : red;
+}
+
+int ism_launch_auralize(const float* x, int n_x, const float* h, int n_points, int n_mics, int n_s,
+                        const int* starts, float* y, void* stream)
+{
+    const long long n_out = (long long)n_x + n_s - 1;
+    const dim3 grid((unsigned)((n_out + AU_TILE - 1) / AU_TILE), (unsigned)((n_mics + AU_M - 1) / AU_M));
+    const size_t sm = ism_auralize_smem();
+    cudaError_t e = cudaFuncSetAttribute(auralize_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (e != cudaSuccess) return (int)e;
+    auralize_kernel<<<grid, AU_WARPS * 32, sm, (cudaStream_t)stream>>>(x, n_x, h, n_points, n_mics, n_s, starts, y,
+                                                                       (int)n_out);
+    return (int)cudaGetLastError();
+}

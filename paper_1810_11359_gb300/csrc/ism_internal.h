@@ -184,5 +184,7 @@ int ism_launch_adjoint(const JobTable& t, const WsPlan& p, char* ws, void* strea
 int ism_launch_finalize(const JobTable& t, const WsPlan& p, char* ws, void* stream);
 int ism_launch_tail(const JobTable& t, const WsPlan& p, char* ws, void* stream);
 int ism_launch_noise(uint64_t seed, uint32_t rir, uint32_t k0, int n, float* z, void* stream);
+int ism_launch_auralize(const float* x, int n_x, const float* h, int n_points, int n_mics, int n_s, const int* starts,
+                        float* y, void* stream);
 int ism_launch_beta_sabine(const double* L, const double* T60, const double* w, int negative, int n,
                            double* beta_out, int* status, void* stream);

@@ -114,6 +114,8 @@ _SIGS = {
                                              ctypes.c_void_p]),
     "ism_diffuse_noise": (ctypes.c_int, [ctypes.c_uint64, ctypes.c_uint32, ctypes.c_uint32, ctypes.c_int,
                                          ctypes.c_void_p, ctypes.c_void_p]),
+    "ism_auralize": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_int, ctypes.c_int,
+                                    ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
     "ism_t60_sabine": (ctypes.c_int, [_P(ctypes.c_double), _P(ctypes.c_double), _P(ctypes.c_double)]),
     "ism_beta_sabine": (ctypes.c_int, [_P(ctypes.c_double), ctypes.c_double, _P(ctypes.c_double), ctypes.c_int,
                                        _P(ctypes.c_double)]),
@@ -456,6 +458,31 @@ def ism_simulate_backward(L, beta, pos_src, pos_rcv, nb_img, Tmax, fs, grad_out,
     gj = make_grad_job(job, go, gb, gs, gr)
     ism_simulate_backward_batch([gj], workspace=workspace, stream=stream)
     return gb, gs, gr
+
+
+def ism_auralize(signal, rirs, starts=None, out=None, stream=None):
+    """Moving source (Section 4): signal [n_x] cut into one segment per
+    trajectory point, each filtered by its point's RIRs rirs [n_points, n_mics,
+    n_S] and overlap-added -> [n_mics, n_x + n_S - 1] (FP32 CUDA tensors).
+    starts: optional [n_points] segment starts (default: uniform cut)."""
+    torch = _torch()
+    dev = torch.device("cuda", torch.cuda.current_device())
+    x = torch.as_tensor(signal, dtype=torch.float32).to(dev).reshape(-1).contiguous()
+    h = torch.as_tensor(rirs, dtype=torch.float32).to(dev).contiguous()
+    if h.dim() != 3:
+        raise ValueError("rirs must be [n_points, n_mics, n_S]")
+    n_points, n_mics, n_s = (int(v) for v in h.shape)
+    st = None
+    if starts is not None:
+        st = torch.as_tensor(starts, dtype=torch.int32).to(dev).reshape(-1).contiguous()
+        if st.numel() < n_points:
+            raise ValueError("starts needs one entry per trajectory point")
+    if out is None:
+        out = torch.empty((n_mics, x.numel() + n_s - 1), dtype=torch.float32, device=dev)
+    _check(load().ism_auralize(ctypes.c_void_p(x.data_ptr()), int(x.numel()), ctypes.c_void_p(h.data_ptr()), n_points,
+                               n_mics, n_s, None if st is None else ctypes.c_void_p(st.data_ptr()),
+                               ctypes.c_void_p(out.data_ptr()), _stream_ptr(stream)))
+    return out
 
 
 def ism_diffuse_noise(seed: int, rir: int, k0: int, n: int, stream=None):
