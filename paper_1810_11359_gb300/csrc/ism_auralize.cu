@@ -6,36 +6,37 @@
 // on the FMA pipe (the RIRs are long, the signal is short, and the sum has a
 // fixed order).
 //
-// One CTA owns 256 consecutive output samples and up to 8 microphones; its 4
+// One CTA owns 128 consecutive output samples and up to 8 microphones; its 4
 // warps split the segments that reach the tile round-robin and add their
 // partial sums in warp order at the end.  Lane l of a warp owns the outputs
-// T0 + 8 l + r, r = 0 .. 7, for the 8 microphones (64 accumulators).  For one
+// T0 + 4 l + r, r = 0 .. 3, for the 8 microphones (32 accumulators).  For one
 // segment the taps k that connect it to the tile are walked in chunks of 128:
 // the chunk's taps of the 8 microphones and the signal window it needs (the
 // samples outside the segment zeroed) are staged in the warp's shared memory;
-// at tap k the lane's 8 signal values are x[T0 + 8 l + r - k], so going from k
+// at tap k the lane's 4 signal values are x[T0 + 4 l + r - k], so going from k
 // to k + 1 they shift by one register and a single new value is loaded
-// (stored with a stride-9 skew so the 32 lanes' loads hit 32 banks), and the
-// 8 taps h[p][m][k] come from two broadcast 128-bit loads: 64 FFMA per three
-// shared loads.
+// (stored with a stride-5 skew so the 32 lanes' loads hit 32 banks), and the
+// 8 taps h[p][m][k] come from two broadcast 128-bit loads: 32 FFMA per three
+// shared loads.  (8 outputs per lane: fewer CTAs than SM slots, 13 % of the
+// warps active, measured 10 % slower.)
 #include "ism_device.cuh"
 
 namespace {
 
-#define AU_R 8                       // outputs per lane
+#define AU_R 4                       // outputs per lane
 #define AU_M 8                       // microphones per CTA
 #define AU_KC 128                    // taps per staged chunk
 #define AU_WARPS 4                   // warps per CTA (segments split round-robin)
 #define AU_TILE (32 * AU_R)          // outputs per CTA
 #define AU_XN (AU_TILE + AU_KC - 1)  // signal samples per chunk
-#define AU_XS (AU_XN + AU_XN / 8 + 8)  // skewed storage (index j + j / 8)
+#define AU_XS (AU_XN + AU_XN / AU_R + 8)  // skewed storage (index j + j / R)
 
 struct AuWarp {
     float4 h[AU_KC][AU_M / 4];       // taps of the chunk: [k][microphone]
     float x[AU_XS];                  // signal window, skewed
 };
 
-__device__ __forceinline__ int au_skew(int j) { return j + (j >> 3); }
+__device__ __forceinline__ int au_skew(int j) { return j + j / AU_R; }
 
 // Segment of sample s (the largest p with a_p <= s): uniform cut when starts
 // is NULL, else a binary search over the caller's start array.
@@ -57,7 +58,7 @@ __device__ __forceinline__ int au_start(int p, int n_x, int n_points, const int*
     return min(max(starts[p], 0), n_x);
 }
 
-__global__ void __launch_bounds__(AU_WARPS * 32) auralize_kernel(const float* __restrict__ x, int n_x,
+__global__ void __launch_bounds__(AU_WARPS * 32, 6) auralize_kernel(const float* __restrict__ x, int n_x,
                                                                  const float* __restrict__ h, int n_points,
                                                                  int n_mics, int n_s,
                                                                  const int* __restrict__ starts,
