@@ -690,8 +690,27 @@ ism_status run_set(const std::vector<Validated>& set, ism_precision prec, size_t
     return ISM_OK;
 }
 
+// Copies of the results to host memory enqueued by run_batch: every job's
+// output region of the device buffer starting at d_base goes to the same
+// offset from h_base, on the stream that computed it, right after it.
+struct HostCopy {
+    const float* d_base;
+    float* h_base;
+};
+
+int copy_set_out(const std::vector<Validated>& set, const HostCopy* hc, cudaStream_t s)
+{
+    for (const Validated& v : set) {
+        const size_t n = (size_t)v.job.n_src * v.job.n_rcv * (size_t)v.n_S;
+        const size_t off = (size_t)(v.job.out - hc->d_base);
+        int e = (int)cudaMemcpyAsync(hc->h_base + off, v.job.out, n * sizeof(float), cudaMemcpyDeviceToHost, s);
+        if (e) return e;
+    }
+    return 0;
+}
+
 ism_status run_batch(const std::vector<Validated>& vs, ism_precision prec, void* workspace, size_t ws_bytes,
-                     void* stream)
+                     void* stream, const HostCopy* hc = nullptr)
 {
     const Schedule sc = schedule(vs);
     size_t need = 0, base1 = 0;
@@ -708,6 +727,8 @@ ism_status run_batch(const std::vector<Validated>& vs, ism_precision prec, void*
     if (sc.lanes == 1) {
         for (const auto& set : sc.sets)
             if ((s = run_set(set, prec, 0, ws, st)) != ISM_OK) return s;
+        for (const auto& set : sc.sets)
+            if (hc && (e = copy_set_out(set, hc, st))) return cuda_fail(e, "copy of the RIRs");
         return ISM_OK;
     }
     // two lanes forked from and joined back into the caller's stream; their
@@ -723,6 +744,10 @@ ism_status run_batch(const std::vector<Validated>& vs, ism_precision prec, void*
         const int lane = (int)(k % 2);
         first_err = run_set(sc.sets[k], prec, lane == 0 ? 0 : base1, ws, L->s[lane]);
     }
+    // each half's results leave for the host on its own stream while the other half computes
+    // (enqueued after every launch, so that a copy to pageable memory cannot hold up a launch)
+    for (size_t k = 0; hc && k < sc.sets.size() && first_err == ISM_OK; ++k)
+        if ((e = copy_set_out(sc.sets[k], hc, L->s[k % 2]))) first_err = cuda_fail(e, "copy of the RIRs");
     // join even after an error, so that the caller's stream orders after all work enqueued
     for (int i = 0; i < 2; ++i) {
         if ((e = (int)cudaEventRecord(L->join[i], L->s[i])) && first_err == ISM_OK) first_err = cuda_fail(e, "event");
@@ -1011,9 +1036,8 @@ ism_status ism_simulate_host(const ism_room* room, const float* pos_src, int n_s
     vs[0].job.pos_rcv = d_pos + 3 * n_src;
     vs[0].job.out = d_out;
     vs[0].job.seed = seed;
-    if ((s = run_batch(vs, prec, workspace, sim, stream)) != ISM_OK) return s;
-    if ((e = (int)cudaMemcpyAsync(out, d_out, n_out * sizeof(float), cudaMemcpyDeviceToHost, st)))
-        return cuda_fail(e, "copy of the RIRs");
+    const HostCopy hc{d_out, out};
+    if ((s = run_batch(vs, prec, workspace, sim, stream, &hc)) != ISM_OK) return s;
     if ((e = (int)cudaStreamSynchronize(st))) return cuda_fail(e, "stream synchronize");
     return ISM_OK;
 }

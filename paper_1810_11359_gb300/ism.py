@@ -394,8 +394,47 @@ def make_job(L, beta, pos_src, pos_rcv, nb_img, Tmax, fs, out, Tdiff=0.0, Tw=0.0
     return j
 
 
+def make_jobs_strided(L, beta, pos_src, pos_rcv, nb_img, Tmax, fs, out, Tdiff=0.0, Tw=0.0, c=343.0, seed=0):
+    """B jobs over batched CUDA tensors pos_src [B, S, 3], pos_rcv [B, M, 3],
+    out [B, S, M, n_S] (contiguous FP32; they must stay alive during the call):
+    one ctypes array filled through a numpy view, without per-room tensor
+    views.  L [B, 3], beta [B, 6], nb_img [B, 3] are host arrays."""
+    B = int(pos_src.shape[0])
+    S, M = int(pos_src.shape[1]), int(pos_rcv.shape[1])
+    arr = (ism_job * B)()
+    v = np.frombuffer(arr, dtype=np.dtype(ism_job), count=B)
+    v["room"]["L"] = np.asarray(L, np.float64).reshape(B, 3)
+    v["room"]["beta"] = np.asarray(beta, np.float64).reshape(B, 6).astype(np.float32)
+    v["room"]["c"] = np.float32(c)
+    idx = np.arange(B, dtype=np.uint64)
+    v["pos_src"] = np.uint64(pos_src.data_ptr()) + idx * np.uint64(S * 3 * 4)
+    v["n_src"] = S
+    v["pos_rcv"] = np.uint64(pos_rcv.data_ptr()) + idx * np.uint64(M * 3 * 4)
+    v["n_rcv"] = M
+    v["nb_img"] = np.asarray(nb_img, np.int32).reshape(B, 3)
+    v["Tmax"], v["fs"], v["Tdiff"], v["Tw"] = float(Tmax), float(fs), float(Tdiff or 0.0), float(Tw or 0.0)
+    v["seed"] = int(seed) & (2 ** 64 - 1)
+    v["out"] = np.uint64(out.data_ptr()) + idx * np.uint64(out[0].numel() * 4)
+    return arr
+
+
+def make_grad_jobs_strided(jobs, grad_out, grad_beta, grad_src, grad_rcv):
+    """ism_grad_job array for the jobs of make_jobs_strided: backward reads
+    grad_out [B, S, M, n_S] and writes grad_beta [B, 6], grad_src [B, S, 3],
+    grad_rcv [B, M, 3] (the jobs' out is not touched; it is set to grad_out)."""
+    B = len(jobs)
+    arr = (ism_grad_job * B)()
+    v = np.frombuffer(arr, dtype=np.dtype(ism_grad_job), count=B)
+    v["job"] = np.frombuffer(jobs, dtype=np.dtype(ism_job), count=B)
+    idx = np.arange(B, dtype=np.uint64)
+    for name, t in (("grad_out", grad_out), ("grad_beta", grad_beta), ("grad_src", grad_src), ("grad_rcv", grad_rcv)):
+        v[name] = np.uint64(t.data_ptr()) + idx * np.uint64(t[0].numel() * 4)
+    v["job"]["out"] = v["grad_out"]
+    return arr
+
+
 def ism_batch_workspace_size(jobs: Sequence[ism_job], prec: str = "fp32") -> int:
-    arr = (ism_job * len(jobs))(*jobs)
+    arr = jobs if isinstance(jobs, ctypes.Array) else (ism_job * len(jobs))(*jobs)
     b = ctypes.c_size_t()
     _check(load().ism_batch_workspace_size(arr, len(jobs), PRECISIONS[prec], ctypes.byref(b)))
     return b.value
@@ -403,7 +442,7 @@ def ism_batch_workspace_size(jobs: Sequence[ism_job], prec: str = "fp32") -> int
 
 def ism_simulate_batch(jobs: Sequence[ism_job], prec: str = "fp32", workspace: Optional[Workspace] = None,
                        stream=None):
-    arr = (ism_job * len(jobs))(*jobs)
+    arr = jobs if isinstance(jobs, ctypes.Array) else (ism_job * len(jobs))(*jobs)
     b = ctypes.c_size_t()
     _check(load().ism_batch_workspace_size(arr, len(jobs), PRECISIONS[prec], ctypes.byref(b)))
     buf = _workspace(workspace, b.value)
@@ -425,14 +464,14 @@ def make_grad_job(job: ism_job, grad_out, grad_beta=None, grad_src=None, grad_rc
 
 
 def ism_backward_workspace_size(gjobs: Sequence[ism_grad_job]) -> int:
-    arr = (ism_grad_job * len(gjobs))(*gjobs)
+    arr = gjobs if isinstance(gjobs, ctypes.Array) else (ism_grad_job * len(gjobs))(*gjobs)
     b = ctypes.c_size_t()
     _check(load().ism_backward_workspace_size(arr, len(gjobs), ctypes.byref(b)))
     return b.value
 
 
 def ism_simulate_backward_batch(gjobs: Sequence[ism_grad_job], workspace: Optional[Workspace] = None, stream=None):
-    arr = (ism_grad_job * len(gjobs))(*gjobs)
+    arr = gjobs if isinstance(gjobs, ctypes.Array) else (ism_grad_job * len(gjobs))(*gjobs)
     b = ctypes.c_size_t()
     _check(load().ism_backward_workspace_size(arr, len(gjobs), ctypes.byref(b)))
     buf = _workspace(workspace, b.value)

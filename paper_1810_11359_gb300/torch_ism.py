@@ -41,9 +41,8 @@ class _Spec:
 
 
 def _jobs(spec: _Spec, beta_h: np.ndarray, ps: torch.Tensor, pr: torch.Tensor, out: torch.Tensor):
-    return [ism.make_job(spec.L[b], beta_h[b], ps[b], pr[b], spec.nb_img[b], spec.Tmax, spec.fs, out[b],
-                         Tdiff=spec.Tdiff, Tw=spec.Tw, c=spec.c, seed=spec.seed)
-            for b in range(spec.L.shape[0])]
+    return ism.make_jobs_strided(spec.L, beta_h, ps, pr, spec.nb_img, spec.Tmax, spec.fs, out, Tdiff=spec.Tdiff,
+                                 Tw=spec.Tw, c=spec.c, seed=spec.seed)
 
 
 class _RoomsRIR(torch.autograd.Function):
@@ -71,8 +70,7 @@ class _RoomsRIR(torch.autograd.Function):
         gb = torch.empty((B, 6), dtype=torch.float32, device=ps.device)
         gs = torch.empty((B, S, 3), dtype=torch.float32, device=ps.device)
         gr = torch.empty((B, M, 3), dtype=torch.float32, device=ps.device)
-        gjobs = [ism.make_grad_job(j, go[b], gb[b], gs[b], gr[b])
-                 for b, j in enumerate(_jobs(spec, ctx.beta_h, ps, pr, go))]
+        gjobs = ism.make_grad_jobs_strided(_jobs(spec, ctx.beta_h, ps, pr, go), go, gb, gs, gr)
         ism.ism_simulate_backward_batch(gjobs, workspace=spec.workspace)
         dtype, device = ctx.beta_meta
         return gb.to(dtype=dtype, device=device), gs, gr, None

@@ -147,3 +147,31 @@ def test_backward_validates_like_the_forward(lib):
     assert lib.ism_simulate_backward_batch(ctypes.byref(gj), 1, None, 0, None) == 1
     gj.job.fs = -1.0
     assert lib.ism_backward_workspace_size(ctypes.byref(gj), 1, ctypes.byref(b)) == 1
+
+
+def test_strided_job_arrays_match_per_room_jobs():
+    """The vectorised job arrays of the autograd front end hold, byte for
+    byte, what make_job / make_grad_job build room by room (host tensors only
+    give the pointers here; nothing is launched)."""
+    import ctypes
+    import numpy as np
+    import torch
+    from paper_1810_11359_gb300 import ism
+    rng = np.random.default_rng(7)
+    B, S, M, n_S = 5, 2, 3, 17
+    L = rng.uniform(3, 9, (B, 3))
+    beta = rng.uniform(0.1, 0.99, (B, 6))
+    nb = rng.integers(1, 40, (B, 3)).astype(np.int32)
+    ps = torch.zeros((B, S, 3))
+    pr = torch.zeros((B, M, 3))
+    out = torch.zeros((B, S, M, n_S))
+    gb, gs, gr = torch.zeros((B, 6)), torch.zeros((B, S, 3)), torch.zeros((B, M, 3))
+    arr = ism.make_jobs_strided(L, beta, ps, pr, nb, 0.25, 16000.0, out, Tdiff=0.1, Tw=0.002, c=340.0, seed=2 ** 63 + 5)
+    garr = ism.make_grad_jobs_strided(arr, out, gb, gs, gr)
+    for b in range(B):
+        j = ism.make_job(L[b], beta[b], ps[b], pr[b], nb[b], 0.25, 16000.0, out[b], Tdiff=0.1, Tw=0.002, c=340.0,
+                         seed=2 ** 63 + 5)
+        assert bytes(arr[b]) == bytes(j)
+        g = ism.make_grad_job(j, out[b], gb[b], gs[b], gr[b])
+        assert bytes(garr[b]) == bytes(g)
+    assert ctypes.sizeof(arr) == B * ctypes.sizeof(ism.ism_job)
