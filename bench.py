@@ -166,7 +166,7 @@ def traffic_from_profiles():
         from paper_1810_11359_gb300 import build as b
         import hashlib
         h = hashlib.sha256()
-        for f in ("ism_accum_cheb.cu", "ism_accum.cuh", "ism_device.cuh", "ism_internal.h"):
+        for f in ("ism_accum_cheb.cu", "ism_shell.cuh", "ism_accum.cuh", "ism_device.cuh", "ism_internal.h"):
             h.update(open(os.path.join(b.CSRC, f), "rb").read())
         dig = h.hexdigest()[:16]
         vals = {}

@@ -23,18 +23,9 @@
 // tap reaches a sample below n_ism: b <= n_ism + 14.
 //
 // One CTA owns B = 8 consecutive bins of one RIR -- a spherical shell of
-// 256 samples around the receiver -- and enumerates the images in it itself:
-// the image coordinates along one axis increase with the index n (eq. (1)),
-// so for a grid column (ix, iy) the images whose distance falls in the shell
-// form at most two index intervals in z (below and above the receiver),
-// found in closed form from the source and receiver coordinates; the columns
-// that reach the shell form one interval in iy per row ix.  The CTA's warps
-// take the columns 32 at a time, compute each column's intervals, and then
-// process the column candidates 32 at a time (a candidate's column by binary
-// search over the warp's running counts).  Candidate intervals are widened by
-// 0.05 sample; each candidate's exact float-float delay (eq. (2)-(3), from
-// the per-axis tables) decides its bin, so every image lands in exactly one
-// CTA, the one whose bins hold its b.
+// 256 samples around the receiver -- and enumerates the images in it itself
+// (ism_shell.cuh): each candidate's exact float-float delay decides its bin,
+// so every image lands in exactly one CTA, the one whose bins hold its b.
 //
 // Fixed point.  Every image of bin q has s >= max(s_direct, 32 q - 1) (the
 // direct path is the shortest: along each axis the source's own coordinate is
@@ -58,6 +49,7 @@
 // (lane = tap) and rotates them into the bin's register window, which it
 // stores as the bin's row.
 #include "ism_accum.cuh"
+#include "ism_shell.cuh"
 
 namespace {
 
@@ -65,19 +57,8 @@ namespace {
 #define SH_WARPS 8          // warps per CTA
 #define SH_NO 32            // offsets per bin (rr = -1 .. 30)
 #define SH_RS 33            // row stride of the moment table (conflict-light atomics)
-#define SH_MARGIN 0.05f     // candidate margin (samples)
 #define CB_MAGIC 12582912.0f                       // 1.5 * 2^23
 #define CB_MAGIC_BITS 0x4B400000u                  // its bits
-
-// Smallest image index n of an axis with coordinate X(n) >= Z: X(2m) = 2 m L
-// + x_s and X(2m - 1) = 2 m L - x_s (eq. (1)); X increases with n.
-__device__ __forceinline__ int ax_first(float Z, float xs, float inv2L)
-{
-    Z = fminf(fmaxf(Z, -1e7f), 1e7f);
-    const int me = (int)ceilf((Z - xs) * inv2L);
-    const int mo = (int)ceilf((Z + xs) * inv2L);
-    return min(2 * me, 2 * mo - 1);
-}
 
 // Largest power of two 2^e with 2^e a_max <= min((1 - 2^-10) 2^22, 0.98 2^31 / n - 1):
 // no term reaches 2^22 (the FFMA rounding trick) and n terms cannot sum to 2^31.
@@ -88,21 +69,6 @@ __device__ __forceinline__ float shell_scale(float a_max, float n)
     int e = ((__float_as_int(ratio) >> 23) & 0xFF) - 127;   // floor(log2(ratio)), ratio normal
     e = max(-126, min(126, e));
     return __int_as_float((e + 127) << 23);
-}
-
-struct ShellAxis {
-    float xs, xr, inv2L, k_inv;   // source, receiver coordinate; 1 / (2 L); c / f_s (metres per sample)
-    int nlo, N;
-};
-
-// Index interval [i0, i1) (0-based, clamped to the grid) of the images of an
-// axis with X(n) - x_r in [D_lo, D_hi) (metres).
-__device__ __forceinline__ void ax_range(const ShellAxis& a, float Dlo, float Dhi, int* i0, int* i1)
-{
-    const int n0 = ax_first(a.xr + Dlo, a.xs, a.inv2L);
-    const int n1 = ax_first(a.xr + Dhi, a.xs, a.inv2L);
-    *i0 = min(max(n0 - a.nlo, 0), a.N);
-    *i1 = min(max(n1 - a.nlo, 0), a.N);
 }
 
 __global__ void __launch_bounds__(SH_WARPS * 32, 4) shell_kernel(const __grid_constant__ JobTable t,
@@ -147,20 +113,8 @@ __global__ void __launch_bounds__(SH_WARPS * 32, 4) shell_kernel(const __grid_co
     if (threadIdx.x == 0) *redo = 0;
     __syncthreads();
 
-    // geometry of the RIR
-    const int i_src = r / J.n_rcv, i_rcv = r - (r / J.n_rcv) * J.n_rcv;
-    const float kinv = J.c / J.fs;   // metres per sample
-    ShellAxis ax[3];
-#pragma unroll
-    for (int a = 0; a < 3; ++a) {
-        ax[a].xs = J.pos_src[3 * i_src + a];
-        ax[a].xr = J.pos_rcv[3 * i_rcv + a];
-        ax[a].inv2L = (float)(0.5 / J.L[a]);
-        ax[a].k_inv = kinv;
-        ax[a].nlo = J.nlo[a];
-        ax[a].N = J.N[a];
-    }
     // receiver polar pattern: the unit orientation of this RIR's receiver (|g| <= 1 keeps A_max a bound)
+    const int i_rcv = r - (r / J.n_rcv) * J.n_rcv;
     const float alpha = J.mic_alpha;
     float3 orient = make_float3(0.0f, 0.0f, 0.0f);
     if (alpha != 1.0f) {
@@ -169,15 +123,11 @@ __global__ void __launch_bounds__(SH_WARPS * 32, 4) shell_kernel(const __grid_co
         const float inv = 1.0f / sqrtf(__fmaf_rn(ox, ox, __fmaf_rn(oy, oy, oz * oz)));
         orient = make_float3(ox * inv, oy * inv, oz * inv);
     }
-    const float sd2 = T[-J.nlo[0]].x + T[Nx - J.nlo[1]].x + T[Nx + Ny - J.nlo[2]].x;
-    const bool valid = sd2 < 3.0e38f;   // +inf tables: a pair outside the room (flagged by the geometry kernel)
-
-    // exact delays b owned by this CTA: [b_lo, b_hi)
-    const int b_lo = ISM_SB * q0 - 1;
-    const int b_hi = min(ISM_SB * (q0 + nb) - 1, J.n_ism + J.H - 1);   // b <= n_ism + 14 for H = 16
-    const float s_lo = fmaxf((float)b_lo - SH_MARGIN, 0.0f);
-    const float s_hi = (float)b_hi + SH_MARGIN;
-    const float s_lo2 = s_lo * s_lo, s_hi2 = s_hi * s_hi;
+    // exact delays b owned by this CTA: [b_lo, b_hi), b <= n_ism + 14 for H = 16
+    const Shell sh = shell_setup(J, T, r, ISM_SB * q0 - 1, min(ISM_SB * (q0 + nb) - 1, J.n_ism + J.H - 1));
+    const float kinv = sh.kinv;
+    const float sd2 = sh.sd2;
+    const bool valid = sh.valid;
 
     if (threadIdx.x < SH_B) {
         // fixed-point scale of bin q0 + threadIdx.x, first from the expected number of images
@@ -203,147 +153,38 @@ __global__ void __launch_bounds__(SH_WARPS * 32, 4) shell_kernel(const __grid_co
         inv_s[threadIdx.x] = 1.0f / sc;   // exact: a power of two
         amax_s[threadIdx.x] = amax;
     }
-    // columns that reach the shell: row ix takes iy with |y - y_r| < D_y
-    for (int ix = threadIdx.x; ix < Nx; ix += blockDim.x) {
-        int w = 0, y0 = 0;
-        if (valid) {
-            const float rem = __fsub_rn(s_hi2, T[ix].x);
-            if (rem > 0.0f) {
-                const float Dy = __fadd_rn(__fmul_rn(sqrtf(rem), kinv), 1e-3f);
-                int y1;
-                ax_range(ax[1], -Dy, Dy, &y0, &y1);
-                w = max(y1 - y0, 0);
-            }
-        }
-        rowpre[ix] = w;
-        rowy0[ix] = y0;
-    }
-    __syncthreads();
-    if (warp == 0) {   // inclusive prefix over the rows
-        int carry = 0;
-        for (int base = 0; base < Nx; base += 32) {
-            const int i = base + lane;
-            int v = i < Nx ? rowpre[i] : 0;
-#pragma unroll
-            for (int o = 1; o < 32; o <<= 1) {
-                const int n = __shfl_up_sync(0xffffffffu, v, o);
-                if (lane >= o) v += n;
-            }
-            if (i < Nx) rowpre[i] = carry + v;
-            carry += __shfl_sync(0xffffffffu, v, 31);
-        }
-    }
-    __syncthreads();
-    const int n_cols = Nx > 0 ? rowpre[Nx - 1] : 0;
+    const int n_cols = shell_rows(sh, T, rowpre, rowy0);   // (synchronises the CTA)
 
     const float amp_scale = J.amp_scale;
     for (int pass = 0; pass < 2; ++pass) {
     for (int e = threadIdx.x; e < SH_B * ISM_CHEB_N * SH_RS; e += blockDim.x) S[e] = 0;
     for (int e = threadIdx.x; e < SH_B * SH_RS; e += blockDim.x) Cn[e] = 0;
     __syncthreads();
-    for (int c0 = warp * 32; c0 < n_cols; c0 += SH_WARPS * 32) {
-        // ---- the column of this lane and its candidate intervals in z
-        const int cl = c0 + lane;
-        int cnt = 0;
-        float4 rf = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
-        int4 ri = make_int4(0, 0, 0, 0);
-        if (cl < n_cols) {
-            int lo = 0, hi = Nx - 1;   // row: first ix with rowpre[ix] > cl
-            while (lo < hi) {
-                const int mid = (lo + hi) >> 1;
-                if (rowpre[mid] > cl) hi = mid;
-                else lo = mid + 1;
-            }
-            const int ix = lo;
-            const int before = ix > 0 ? rowpre[ix - 1] : 0;
-            const float4 tx = T[ix];
-            const int iy = min(rowy0[ix] + (cl - before), Ny - 1);
-            const float4 ty = T[Nx + iy];
-            const ff sxy = ff_add(ff{tx.x, tx.y}, ff{ty.x, ty.y});
-            const float sxy_p = __fadd_rn(tx.x, ty.x);
-            const float D1 = fmaxf(__fsub_rn(__fmul_rn(sqrtf(fmaxf(__fsub_rn(s_lo2, sxy_p), 0.0f)), kinv), 1e-3f), 0.0f);
-            const float D2 = __fadd_rn(__fmul_rn(sqrtf(fmaxf(__fsub_rn(s_hi2, sxy_p), 0.0f)), kinv), 1e-3f);
-            int d0 = 0, d1 = 0, u0 = 0, u1 = 0;
-            if (s_hi2 > sxy_p) {
-                ax_range(ax[2], -D2, -D1, &d0, &d1);   // below the receiver (closed-open in n)
-                ax_range(ax[2], D1, D2, &u0, &u1);     // above
-                d1 = min(d1, u0);                      // disjoint, whatever the rounding
-            }
-            const int nd = max(d1 - d0, 0), nu = max(u1 - u0, 0);
-            cnt = nd + nu;
-            rf = make_float4(sxy.hi, sxy.lo, tx.z * ty.z, __fmaf_rn(orient.y, ty.w, orient.x * tx.w));
-            ri = make_int4(d0, nd, u0, 0);
-        }
-        int inc = cnt;
+    shell_walk<SH_WARPS>(sh, T, rowpre, rowy0, n_cols, make_float2(orient.x, orient.y), Wf, Wi, Wst, warp, lane,
+                         [&](int b, float f, float s, const float4& cf, int, int, const float4& tz) {
+        const int q = (b + 1) >> 5;
+        const int ql = q - q0;
+        const int o = b - ISM_SB * q + 1;   // offset index rr + 1 in [0, 32)
+        const float rs = ism_rcp(s);
+        float amp = cf.z * tz.z * amp_scale * rs;
+        if (alpha != 1.0f)   // polar pattern: cos(theta) = o . (x_n - x_r) / d
+            amp *= __fmaf_rn(1.0f - alpha, __fmaf_rn(orient.z, tz.w, cf.w) * rs, alpha);
+        const float as = amp * scale_s[ql];
+        const float uu = __fmaf_rn(2.0f, f, -1.0f);
+        const float u2 = uu + uu;
+        int* Sb = S + ql * (ISM_CHEB_N * SH_RS) + o;
+        atomicAdd(Cn + ql * SH_RS + o, 1);
+        atomicAdd(Sb, (int)(__float_as_uint(__fadd_rn(as, CB_MAGIC)) - CB_MAGIC_BITS));
+        atomicAdd(Sb + SH_RS, (int)(__float_as_uint(__fmaf_rn(as, uu, CB_MAGIC)) - CB_MAGIC_BITS));
+        float tp = 1.0f, tc = uu;
 #pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const int n = __shfl_up_sync(0xffffffffu, inc, o);
-            if (lane >= o) inc += n;
+        for (int k = 2; k < ISM_CHEB_N; ++k) {
+            const float tn = __fmaf_rn(u2, tc, -tp);
+            atomicAdd(Sb + k * SH_RS, (int)(__float_as_uint(__fmaf_rn(as, tn, CB_MAGIC)) - CB_MAGIC_BITS));
+            tp = tc;
+            tc = tn;
         }
-        const int total = __shfl_sync(0xffffffffu, inc, 31);
-        __syncwarp();
-        Wf[lane] = rf;
-        Wi[lane] = ri;
-        Wst[lane] = inc - cnt;
-        if (lane == 31) Wst[32] = total;
-        __syncwarp();
-
-        // ---- the candidates, 32 at a time
-        for (int j0 = 0; j0 < total; j0 += 32) {
-            const int j = j0 + lane;
-            if (j < total) {
-                int lo = 0, hi = 31;   // last column o with Wst[o] <= j
-#pragma unroll
-                for (int s = 0; s < 5; ++s) {
-                    const int mid = (lo + hi + 1) >> 1;
-                    if (Wst[mid] <= j) lo = mid;
-                    else hi = mid - 1;
-                }
-                const float4 cf = Wf[lo];
-                const int4 ci = Wi[lo];
-                const int i = j - Wst[lo];
-                const int iz = i < ci.y ? ci.x + i : ci.z + (i - ci.y);
-                const float4 tz = T[Nx + Ny + iz];
-                const ff s2 = ff_add(ff{cf.x, cf.y}, ff{tz.x, tz.y});
-                const ff sq = ff_sqrt(s2);
-                float bf = floorf(sq.hi);
-                float f = __fadd_rn(__fsub_rn(sq.hi, bf), sq.lo);
-                const bool neg = f < 0.0f;   // bring f into [0, 1) (see ism_delay)
-                f = neg ? __fadd_rn(f, 1.0f) : f;
-                bf = neg ? bf - 1.0f : bf;
-                const bool one = f >= 1.0f;
-                f = one ? __fsub_rn(f, 1.0f) : f;
-                bf = one ? bf + 1.0f : bf;
-                const int b = ism_int_of_integral(fminf(bf, 4.0e6f));
-                if (b >= b_lo && b < b_hi) {
-                    const int q = (b + 1) >> 5;
-                    const int ql = q - q0;
-                    const int o = b - ISM_SB * q + 1;   // offset index rr + 1 in [0, 32)
-                    const float rs = ism_rcp(sq.hi);
-                    float amp = cf.z * tz.z * amp_scale * rs;
-                    if (alpha != 1.0f)   // polar pattern: cos(theta) = o . (x_n - x_r) / d
-                        amp *= __fmaf_rn(1.0f - alpha, __fmaf_rn(orient.z, tz.w, cf.w) * rs, alpha);
-                    const float as = amp * scale_s[ql];
-                    const float uu = __fmaf_rn(2.0f, f, -1.0f);
-                    const float u2 = uu + uu;
-                    int* Sb = S + ql * (ISM_CHEB_N * SH_RS) + o;
-                    atomicAdd(Cn + ql * SH_RS + o, 1);
-                    atomicAdd(Sb, (int)(__float_as_uint(__fadd_rn(as, CB_MAGIC)) - CB_MAGIC_BITS));
-                    atomicAdd(Sb + SH_RS, (int)(__float_as_uint(__fmaf_rn(as, uu, CB_MAGIC)) - CB_MAGIC_BITS));
-                    float tp = 1.0f, tc = uu;
-#pragma unroll
-                    for (int k = 2; k < ISM_CHEB_N; ++k) {
-                        const float tn = __fmaf_rn(u2, tc, -tp);
-                        atomicAdd(Sb + k * SH_RS,
-                                  (int)(__float_as_uint(__fmaf_rn(as, tn, CB_MAGIC)) - CB_MAGIC_BITS));
-                        tp = tc;
-                        tc = tn;
-                    }
-                }
-            }
-        }
-        __syncwarp();
-    }
+    });
     __syncthreads();
     // every sum of bin q holds at most Cn[q][o] terms of magnitude <= scale * A_max + 1/2:
     // below 2^31 means no sum can have wrapped; otherwise redo the shell with scales from

@@ -1,5 +1,7 @@
 // ism_adjoint.cu -- gradients of a loss through the image-source RIR: the
-// adjoint of eq. (1)-(6) (the paper computes forward RIRs only).
+// adjoint of eq. (1)-(6) (the paper computes forward RIRs only), per tap, for
+// windows other than exactly 32 taps (those take the fused Chebyshev adjoint
+// of ism_adjoint_cheb.cu), and the reduction of every job's gradients.
 //
 // The binned image lists of the forward pass (enumeration + counting sort)
 // are reused: one CTA per (RIR, tile of 8 delay bins), one warp per bin, as
@@ -247,8 +249,11 @@ __global__ void __launch_bounds__(ISM_ACC_WARPS * 32) adjoint_kernel(const __gri
     }
 }
 
-// Per job: bins -> RIRs (bin order), RIRs -> sources, receivers and the
-// room (index order).  One CTA per job.
+// Per job: bins -> RIRs, RIRs -> sources, receivers and the room (index
+// order).  One CTA per job.  A warp sums the Q bin records of one (RIR,
+// component): lane l adds the bins l, l + 32, ... in order, then a fixed
+// butterfly adds the lanes (lane 0's order is the result), so the per-RIR sums
+// take Q / 32 dependent loads instead of Q.
 __global__ void __launch_bounds__(256) adjoint_reduce_kernel(const __grid_constant__ JobTable t,
                                                              const float* __restrict__ gpart,
                                                              float* __restrict__ rgrad)
@@ -256,13 +261,16 @@ __global__ void __launch_bounds__(256) adjoint_reduce_kernel(const __grid_consta
     const JobDev& J = t.j[blockIdx.x];
     const long long R = J.n_rir;
     float* rg = rgrad + J.rgrad_base;
-    for (long long e = threadIdx.x; e < R * ADJ_NG; e += blockDim.x) {
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    for (long long e = warp; e < R * ADJ_NG; e += blockDim.x >> 5) {
         const long long r = e / ADJ_NG;
         const int c = (int)(e % ADJ_NG);
         const float* src = gpart + J.gpart_base + r * J.Q * ADJ_NG + c;
         float v = 0.0f;
-        for (int q = 0; q < J.Q; ++q) v += src[(long long)q * ADJ_NG];
-        rg[e] = v;
+        for (int q = lane; q < J.Q; q += 32) v += src[(long long)q * ADJ_NG];
+#pragma unroll
+        for (int m = 16; m > 0; m >>= 1) v += __shfl_xor_sync(0xffffffffu, v, m);
+        if (lane == 0) rg[e] = v;
     }
     __syncthreads();
     const int n_out = 6 + 3 * J.n_src + 3 * J.n_rcv;
@@ -304,11 +312,11 @@ int launch_adj(const JobTable& t, const WsPlan& p, char* ws, cudaStream_t s)
 int ism_launch_adjoint(const JobTable& t, const WsPlan& p, char* ws, void* stream, int* launched)
 {
     *launched = 0;
-    if (p.adj_ctas <= 0) return 0;
     cudaStream_t s = (cudaStream_t)stream;
     bool need[2][ISM_MAX_SLOTS + 1] = {};
-    for (int i = 0; i < t.n_jobs; ++i) {
+    for (int i = 0; i < t.n_jobs && p.adj_ctas > 0; ++i) {
         const JobDev& J = t.j[i];
+        if (J.adj_cheb) continue;   // the fused Chebyshev adjoint takes it
         bool exact = (J.Nw == (float)(2 * J.H)) && (2 * J.H == 32 * J.slots);
         need[exact ? 0 : 1][J.slots] = true;
     }
@@ -319,6 +327,9 @@ int ism_launch_adjoint(const JobTable& t, const WsPlan& p, char* ws, void* strea
     ISM_L(1) ISM_L(2) ISM_L(3) ISM_L(4) ISM_L(5) ISM_L(6) ISM_L(7) ISM_L(8)
 #undef ISM_L
     if (rc) return rc;
+    int fused = 0;
+    if ((rc = ism_launch_adjoint_cheb(t, p, ws, stream, &fused))) return rc;
+    *launched += fused;
     adjoint_reduce_kernel<<<(unsigned)t.n_jobs, 256, 0, s>>>(t, reinterpret_cast<const float*>(ws + p.gpart_off),
                                                              reinterpret_cast<float*>(ws + p.rgrad_off));
     ++*launched;

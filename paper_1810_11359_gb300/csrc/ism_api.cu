@@ -264,11 +264,15 @@ ism_status plan(const Validated* vs, int n, ism_precision prec, bool backward, J
             // images costs more than adding every image's taps on its own
             J.sparse = ((prec == ISM_PREC_FP32 || prec == ISM_PREC_FP32_DIRECT) && !backward && !J.use_cheb &&
                         per_bin < 128.0) ? 1 : 0;
+            // backward: a 32-tap window always takes the fused Chebyshev adjoint (an
+            // image costs two degree-8 sums there, against 32 tap derivatives)
+            J.adj_cheb = (backward && v.Nw == 32.0 && v.H == 16 && v.slots == 1) ? 1 : 0;
         }
+        const bool fused = J.use_cheb || J.adj_cheb;
         // a job takes either the fused Chebyshev CTAs (which enumerate their
         // own images) or the direct accumulation CTAs (which read the binned ids)
         J.acc_groups = J.use_cheb ? 0 : (J.Q + ism_acc_bins((int)prec) - 1) / ism_acc_bins((int)prec);
-        J.shell_groups = J.use_cheb ? (J.Q + ISM_SHELL_BINS - 1) / ISM_SHELL_BINS : 0;
+        J.shell_groups = fused ? (J.Q + ISM_SHELL_BINS - 1) / ISM_SHELL_BINS : 0;
         J.shell_cta_base = scta;
         J.grad_out = v.grad_out;
         J.grad_beta = v.grad_beta;
@@ -279,14 +283,14 @@ ism_status plan(const Validated* vs, int n, ism_precision prec, bool backward, J
         const long long R = J.n_rir;
         rir += R;
         // a fused Chebyshev job enumerates its images itself: no counts, no binned ids
-        if (!J.use_cheb) hist += R * J.Q * J.U;
+        if (!fused) hist += R * J.Q * J.U;
         int axis = in.nb_img[0] + in.nb_img[1] + in.nb_img[2];
         tbl += R * axis;
-        if (!J.use_cheb) ecta += R * ((J.U + ISM_ENUM_WARPS - 1) / ISM_ENUM_WARPS);
+        if (!fused) ecta += R * ((J.U + ISM_ENUM_WARPS - 1) / ISM_ENUM_WARPS);
         acta += R * J.acc_groups;
         scta += R * J.shell_groups;
         fcta += R * J.fin_chunks;
-        adta += R * J.n_tiles;
+        if (backward && !J.adj_cheb) adta += R * J.n_tiles;
         if (J.has_tail) {
             int blk0 = v.n_ism >> 2, blk_last = (v.n_S - 1) >> 2;
             tcta += R * ((blk_last - blk0 + 1 + ISM_TAIL_CHUNK / 4 - 1) / (ISM_TAIL_CHUNK / 4));
@@ -295,10 +299,10 @@ ism_status plan(const Validated* vs, int n, ism_precision prec, bool backward, J
         if (prec == ISM_PREC_LUT) lut += (long long)(ism_lut_phases(J.slots) + 1) * 32 * J.slots;
         // texture form: each table starts on a 512-byte boundary (texture base alignment)
         if (prec == ISM_PREC_LUT_TEX) lut += ((long long)(ism_lut_phases(J.slots) + 1) * 32 * J.slots + 127) / 128 * 128;
-        if (J.use_cheb) t.any_cheb = 1;
+        if (fused) t.any_cheb = 1;
         else t.any_direct = 1;
         if (backward) gpart += R * J.Q * 12;
-        if (!J.use_cheb) ids += R * J.img_per_rir;
+        if (!fused) ids += R * J.img_per_rir;
         if (J.Q > t.max_Q) t.max_Q = J.Q;
         if (axis > t.max_axis_sum) t.max_axis_sum = axis;
     }
@@ -338,6 +342,11 @@ ism_status plan(const Validated* vs, int n, ism_precision prec, bool backward, J
     off = align256(off + (size_t)ids * 4);
     p.tbl_off = off;
     off = align256(off + (size_t)tbl * 16);
+    p.dtbl_off = 0;
+    if (backward) {
+        p.dtbl_off = off;
+        off = align256(off + (size_t)tbl * 16);
+    }
     p.rows_off = off;
     off = align256(off + (size_t)rows * 4);
     p.amp_off = off;
@@ -756,8 +765,10 @@ ism_status run_batch(const std::vector<Validated>& vs, ism_precision prec, void*
     return first_err;
 }
 
-// Backward pass: the forward's geometry, enumeration and binning, then the
-// adjoint kernel and its fixed-order reductions.
+// Backward pass: the forward's geometry; for 32-tap windows the fused
+// Chebyshev adjoint (which enumerates its own images), for other windows the
+// forward's enumeration and binning and the per-tap adjoint; then the
+// fixed-order reductions.
 ism_status run_backward(const std::vector<Validated>& vs, void* workspace, size_t ws_bytes, void* stream)
 {
     size_t need = 0;
@@ -787,7 +798,7 @@ ism_status run_backward(const std::vector<Validated>& vs, void* workspace, size_
             if ((e = ism_launch_enum(t, p, ws, false, stream))) return cuda_fail(e, "enumeration (count) kernel");
             tm.done(p.enum_ctas > 0);
         }
-        {
+        if (p.hist_total > 0) {
             StageTimer tm(ISM_STAGE_SCAN, st);
             if ((e = ism_launch_scan(p, ws, stream))) return cuda_fail(e, "scan kernels");
             tm.done(3);

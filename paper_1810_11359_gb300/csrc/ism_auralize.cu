@@ -12,13 +12,15 @@
 // T0 + 4 l + r, r = 0 .. 3, for the 8 microphones (32 accumulators).  For one
 // segment the taps k that connect it to the tile are walked in chunks of 128:
 // the chunk's taps of the 8 microphones and the signal window it needs (the
-// samples outside the segment zeroed) are staged in the warp's shared memory;
-// at tap k the lane's 4 signal values are x[T0 + 4 l + r - k], so going from k
-// to k + 1 they shift by one register and a single new value is loaded
-// (stored with a stride-5 skew so the 32 lanes' loads hit 32 banks), and the
-// 8 taps h[p][m][k] come from two broadcast 128-bit loads: 32 FFMA per three
-// shared loads.  (8 outputs per lane: fewer CTAs than SM slots, 13 % of the
-// warps active, measured 10 % slower.)
+// samples outside the segment zeroed) are staged in the warp's shared memory.
+// The taps go in groups of 4: for taps k .. k + 3 the lane's 16 products need
+// the 7 signal values x[T0 + 4 l - k - 3 .. T0 + 4 l - k + 3], two aligned
+// float4 of the window of which the later one is the previous group's earlier
+// one, so a group costs one 128-bit signal load (the 32 lanes read 512
+// contiguous bytes) and eight broadcast 128-bit tap loads (h[p][m][k] for the
+// 8 microphones, two per tap) for 128 FFMA; every shared address is the
+// lane's base plus a constant.  (8 outputs per lane: fewer CTAs than SM
+// slots, 13 % of the warps active, measured 10 % slower.)
 #include "ism_device.cuh"
 
 namespace {
@@ -28,15 +30,14 @@ namespace {
 #define AU_KC 128                    // taps per staged chunk
 #define AU_WARPS 4                   // warps per CTA (segments split round-robin)
 #define AU_TILE (32 * AU_R)          // outputs per CTA
-#define AU_XN (AU_TILE + AU_KC - 1)  // signal samples per chunk
-#define AU_XS (AU_XN + AU_XN / AU_R + 8)  // skewed storage (index j + j / R)
+#define AU_XN (AU_TILE + AU_KC)      // signal samples per chunk (the last one is never used)
+
+static_assert(AU_R == 4 && AU_KC % 4 == 0, "the signal window is read as float4 groups of 4 taps");
 
 struct AuWarp {
     float4 h[AU_KC][AU_M / 4];       // taps of the chunk: [k][microphone]
-    float x[AU_XS];                  // signal window, skewed
+    float4 x[AU_XN / 4];             // signal window
 };
-
-__device__ __forceinline__ int au_skew(int j) { return j + j / AU_R; }
 
 // Segment of sample s (the largest p with a_p <= s): uniform cut when starts
 // is NULL, else a binary search over the caller's start array.
@@ -102,28 +103,31 @@ __global__ void __launch_bounds__(AU_WARPS * 32, 6) auralize_kernel(const float*
                 }
                 // signal window: x[T0 - k0 - KC + 1 + j], zero outside [a, b)
                 const long long xb = T0 - k0 - AU_KC + 1;
+                float* xw = reinterpret_cast<float*>(W.x);
                 for (int j = lane; j < AU_XN; j += 32) {
                     const long long s = xb + j;
-                    W.x[au_skew(j)] = (s >= a && s < b) ? x[s] : 0.0f;
+                    xw[j] = (s >= a && s < b) ? x[s] : 0.0f;
                 }
                 __syncwarp();
-                // window of the lane at kk = 0: x[T0 + 8 l + r - k0] = window index 8 l + r + KC - 1
-                float xv[AU_R];
+                // output r of the lane at tap kk reads window index 4 l + r + KC - 1 - kk; for the
+                // group kk = 4 g + u that is element 3 + r - u of {xa, xb4}, xa = float4 at
+                // 4 l + KC - 4 - 4 g, xb4 = the next float4 (the previous group's xa)
+                const float4* xl = W.x + lane + (AU_KC - 4) / 4;
+                float4 xb4 = xl[1];
+#pragma unroll 2
+                for (int g = 0; g < AU_KC / 4; ++g) {
+                    const float4 xa = xl[-g];
+                    const float v[8] = {xa.x, xa.y, xa.z, xa.w, xb4.x, xb4.y, xb4.z, xb4.w};
 #pragma unroll
-                for (int r = 0; r < AU_R; ++r) xv[r] = W.x[au_skew(AU_R * lane + r + AU_KC - 1)];
-#pragma unroll 8
-                for (int kk = 0; kk < AU_KC; ++kk) {
-                    const float4 h0 = W.h[kk][0], h1 = W.h[kk][1];
-                    const float hv[AU_M] = {h0.x, h0.y, h0.z, h0.w, h1.x, h1.y, h1.z, h1.w};
+                    for (int u = 0; u < 4; ++u) {
+                        const float4 h0 = W.h[4 * g + u][0], h1 = W.h[4 * g + u][1];
+                        const float hv[AU_M] = {h0.x, h0.y, h0.z, h0.w, h1.x, h1.y, h1.z, h1.w};
 #pragma unroll
-                    for (int r = 0; r < AU_R; ++r)
+                        for (int r = 0; r < AU_R; ++r)
 #pragma unroll
-                        for (int m = 0; m < AU_M; ++m) acc[r][m] = __fmaf_rn(xv[r], hv[m], acc[r][m]);
-                    // next tap: the window moves one sample back
-#pragma unroll
-                    for (int r = AU_R - 1; r > 0; --r) xv[r] = xv[r - 1];
-                    const int jn = AU_R * lane + AU_KC - 2 - kk;   // >= 0 for kk <= KC - 2
-                    xv[0] = jn >= 0 ? W.x[au_skew(jn)] : 0.0f;
+                            for (int m = 0; m < AU_M; ++m) acc[r][m] = __fmaf_rn(v[3 + r - u], hv[m], acc[r][m]);
+                    }
+                    xb4 = xa;
                 }
             }
         }

@@ -10,7 +10,9 @@
 //   F[n] = beta_0^{e0(n)} beta_1^{e1(n)}  (wall hits along that axis)
 //   D[n] = (x_n - x_r) f_s / c           (signed offset, FP32: the direction
 //                                          of arrival for polar patterns)
-// so that image (nx, ny, nz) has s^2 = Sx + Sy + Sz and weight Fx Fy Fz.  It
+// so that image (nx, ny, nz) has s^2 = Sx + Sy + Sz and weight Fx Fy Fz.  For
+// the backward pass it also tabulates dF/dbeta_0, dF/dbeta_1 (product form,
+// valid at beta = 0) and d x_n / d x_s = +-1 (even / odd n).  It
 // also checks that source and receiver lie strictly inside the room (and that
 // a patterned receiver has a non-zero orientation); a pair that does not gets
 // S = +inf everywhere, i.e. no image survives.
@@ -32,7 +34,7 @@ __device__ double dpow_int(double b, int e)
 }
 
 __global__ void __launch_bounds__(128) geometry_kernel(const __grid_constant__ JobTable t, float4* tbl,
-                                                       uint32_t* status)
+                                                       float4* dtbl, uint32_t* status)
 {
     const long long g = blockIdx.x;  // one CTA per RIR of the launch set
     const int jid = ism_find_job(t, g, [](const JobDev& j) { return j.rir_base; });
@@ -82,7 +84,8 @@ __global__ void __launch_bounds__(128) geometry_kernel(const __grid_constant__ J
         int an = n < 0 ? -n : n;
         int e0 = even ? an / 2 : (n - 1 < 0 ? 1 - n : n - 1) / 2;
         int e1 = even ? an / 2 : (n + 1 < 0 ? -(n + 1) : n + 1) / 2;
-        double F = dpow_int((double)J.beta[2 * a], e0) * dpow_int((double)J.beta[2 * a + 1], e1);
+        const double b0 = (double)J.beta[2 * a], b1 = (double)J.beta[2 * a + 1];
+        double F = dpow_int(b0, e0) * dpow_int(b1, e1);
         float hi = (float)S;
         float lo = (float)(S - (double)hi);
         if (!ok_s) {
@@ -91,6 +94,12 @@ __global__ void __launch_bounds__(128) geometry_kernel(const __grid_constant__ J
             F = 0.0;
         }
         out[e] = make_float4(hi, lo, (float)F, (float)u);
+        if (dtbl) {
+            const double d0 = e0 > 0 ? (double)e0 * dpow_int(b0, e0 - 1) * dpow_int(b1, e1) : 0.0;
+            const double d1 = e1 > 0 ? (double)e1 * dpow_int(b0, e0) * dpow_int(b1, e1 - 1) : 0.0;
+            dtbl[J.tbl_base + (long long)r * n_axis + e] =
+                make_float4(ok_s ? (float)d0 : 0.0f, ok_s ? (float)d1 : 0.0f, even ? 1.0f : -1.0f, 0.0f);
+        }
     }
 }
 
@@ -131,7 +140,8 @@ int ism_launch_geometry(const JobTable& t, const WsPlan& p, char* ws, void* stre
     long long n_rir = p.rir_total;
     if (n_rir <= 0) return 0;
     geometry_kernel<<<(unsigned)n_rir, 128, 0, (cudaStream_t)stream>>>(
-        t, reinterpret_cast<float4*>(ws + p.tbl_off), reinterpret_cast<uint32_t*>(ws + p.status_off));
+        t, reinterpret_cast<float4*>(ws + p.tbl_off), p.dtbl_off ? reinterpret_cast<float4*>(ws + p.dtbl_off) : nullptr,
+        reinterpret_cast<uint32_t*>(ws + p.status_off));
     return (int)cudaGetLastError();
 }
 

@@ -77,6 +77,7 @@ struct JobDev {
     int use_cheb;             // FP32 accumulation through Chebyshev moments (32-tap window)
     int shell_groups;         // fused Chebyshev CTAs per RIR (ISM_SHELL_BINS bins each; 0 otherwise)
     int sparse;               // direct FP32 form, few images per bin: no sort, each image's taps added at once
+    int adj_cheb;             // backward: fused Chebyshev adjoint (32-tap window; shell_groups CTAs per RIR)
     int rir_index0;           // RIR index of the job's first RIR in its caller's job (noise counter)
     uint64_t seed;
     const float* pos_src;
@@ -126,6 +127,7 @@ struct WsPlan {
     size_t part_off;       // uint32 [n_scan_blocks + 1]
     size_t ids_off;        // uint32 [ids_total]
     size_t tbl_off;        // float4 [tbl_total]
+    size_t dtbl_off;       // float4 [tbl_total] (backward): dF/dbeta_lo, dF/dbeta_hi, d x_n / d x_s per axis index
     size_t rows_off;       // float  [rows_total]: per-bin window rows of the accumulation
     size_t amp_off;        // float  [rir_total]
     size_t lut_off;        // float  [lut_total]: polyphase windowed-sinc tables (LUT form)
@@ -181,6 +183,7 @@ int ism_launch_accum_tex(const JobTable& t, const WsPlan& p, char* ws, void* str
 int ism_launch_lut_tables(const JobTable& t, const WsPlan& p, char* ws, void* stream);
 int ism_launch_accum_cheb(const JobTable& t, const WsPlan& p, char* ws, void* stream, int* launched);
 int ism_launch_adjoint(const JobTable& t, const WsPlan& p, char* ws, void* stream, int* launched);
+int ism_launch_adjoint_cheb(const JobTable& t, const WsPlan& p, char* ws, void* stream, int* launched);
 int ism_launch_finalize(const JobTable& t, const WsPlan& p, char* ws, void* stream);
 int ism_launch_tail(const JobTable& t, const WsPlan& p, char* ws, void* stream);
 int ism_launch_noise(uint64_t seed, uint32_t rir, uint32_t k0, int n, float* z, void* stream);

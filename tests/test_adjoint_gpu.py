@@ -208,3 +208,98 @@ def test_tail_samples_carry_no_gradient():
         assert np.array_equal(x, y)
     ref = oracle_grads(L, beta, ps, pr, N, n_ism, fs, Tw, g0)
     check(a, ref, "with tail")
+
+
+def _grad_job(L, beta, ps, pr, N, Tmax, fs, Tw, g, keep):
+    ps_t = torch.as_tensor(np.asarray(ps, np.float32)).cuda()
+    pr_t = torch.as_tensor(np.asarray(pr, np.float32)).cuda()
+    go = torch.as_tensor(np.asarray(g, np.float32)).cuda()
+    gb = torch.empty(6, device="cuda")
+    gs = torch.empty((ps_t.shape[0], 3), device="cuda")
+    gr = torch.empty((pr_t.shape[0], 3), device="cuda")
+    keep.append((ps_t, pr_t, go))
+    job = ism.make_job(L, beta, ps_t, pr_t, N, Tmax, fs, go, Tw=Tw)
+    return ism.make_grad_job(job, go, gb, gs, gr), (gb, gs, gr)
+
+
+def test_mixed_window_batch_matches_single_calls_and_oracle():
+    """One backward call over a 32-tap job (fused Chebyshev adjoint), a 6-tap
+    job and a 110.25-tap job (per-tap adjoint over binned ids): each job's
+    gradients are bitwise those of its own call, and within the bound of the
+    oracle."""
+    L = np.array([4.1, 3.3, 2.7])
+    beta = np.array([0.85, 0.9, 0.8, 0.75, 0.95, 0.7], np.float32)
+    ps = np.array([[1.0, 1.1, 0.7], [2.9, 2.2, 1.5]], np.float32)
+    pr = np.array([[2.0, 1.4, 1.2], [0.6, 0.5, 2.0]], np.float32)
+    cases = [(16000.0, 32 / 16000), (16000.0, 6 / 16000), (8000.0, 110.25 / 8000)]
+    Tmax = 0.0617
+    keep, gjobs, outs, gs_in, meta = [], [], [], [], []
+    for k, (fs, Tw) in enumerate(cases):
+        N = oracle.nb_img_from_t(Tmax, L, 343.0, Tw)
+        n = oracle.n_samples(f32(Tmax), fs)
+        g = np.random.default_rng(20 + k).standard_normal((2, 2, n)).astype(np.float32)
+        gj, o = _grad_job(L, beta, ps, pr, N, Tmax, fs, Tw, g, keep)
+        gjobs.append(gj)
+        outs.append(o)
+        gs_in.append(g)
+        meta.append((fs, Tw, N, n))
+    ism.ism_simulate_backward_batch(gjobs)
+    torch.cuda.synchronize()
+    for k, (fs, Tw, N, n) in enumerate(meta):
+        got = tuple(x.cpu().numpy() for x in outs[k])
+        single = gpu_grads(L, beta, ps, pr, N, Tmax, fs, Tw, gs_in[k])
+        for x, y in zip(got, single):
+            assert np.array_equal(x.view(np.uint32), y.view(np.uint32)), (fs, Tw)
+        check(got, oracle_grads(L, beta, ps, pr, N, n, fs, Tw, gs_in[k]), f"mixed batch fs={fs} Nw={Tw * fs}")
+
+
+@pytest.mark.parametrize("case", ["cube_centre", "near_walls", "shared_xy"])
+def test_fused_adjoint_edge_geometries(case):
+    """Geometries that stress the shell enumeration of the fused adjoint: a
+    cube with the receiver at its centre (images on a near-cubic lattice, many
+    per integer delay), source and receiver 1 cm from walls, and a pair that
+    shares x and y (the images of a column straddle the receiver)."""
+    fs, Tw = 16000.0, 32 / 16000
+    if case == "cube_centre":
+        L = np.array([3.0, 3.0, 3.0])
+        ps = np.array([[0.75, 1.1, 2.2]], np.float32)
+        pr = np.array([[1.5, 1.5, 1.5]], np.float32)
+    elif case == "near_walls":
+        L = np.array([4.0, 3.5, 2.8])
+        ps = np.array([[0.01, 3.49, 1.4]], np.float32)
+        pr = np.array([[3.99, 0.01, 2.79]], np.float32)
+    else:
+        L = np.array([5.0, 4.0, 3.0])
+        ps = np.array([[2.0, 1.5, 0.6]], np.float32)
+        pr = np.array([[2.0, 1.5, 2.4]], np.float32)
+    beta = np.array([0.92, 0.88, 0.9, 0.85, 0.8, 0.95], np.float32)
+    Tmax = 0.09
+    N = oracle.nb_img_from_t(Tmax, L, 343.0, Tw)
+    n = oracle.n_samples(f32(Tmax), fs)
+    g = np.random.default_rng(31).standard_normal((1, 1, n)).astype(np.float32)
+    got = gpu_grads(L, beta, ps, pr, N, Tmax, fs, Tw, g)
+    check(got, oracle_grads(L, beta, ps, pr, N, n, fs, Tw, g), case)
+
+
+def test_backward_batch_invariance():
+    """A room's gradients do not depend on the other rooms of the batch (the
+    fused adjoint's sums have a fixed order per RIR)."""
+    rooms = workloads.differentiation_rooms(4)
+    n_S = oracle.n_samples(f32(0.4), 16000.0)
+    g_all = np.random.default_rng(33).standard_normal((4, n_S)).astype(np.float32)
+    keep, gjobs, outs = [], [], []
+    for b, r in enumerate(rooms):
+        beta = ism.ism_beta_sabine(r.L, r.rt60)
+        N = ism.ism_nb_img_from_t(r.Tmax, r.L, r.c, r.window())
+        gj, o = _grad_job(r.L, beta, r.pos_src, r.pos_rcv, N, r.Tmax, r.fs, r.window(), g_all[b], keep)
+        gjobs.append(gj)
+        outs.append(o)
+    ism.ism_simulate_backward_batch(gjobs)
+    torch.cuda.synchronize()
+    for b in (0, 3):
+        r = rooms[b]
+        beta = ism.ism_beta_sabine(r.L, r.rt60)
+        N = ism.ism_nb_img_from_t(r.Tmax, r.L, r.c, r.window())
+        single = gpu_grads(r.L, beta, r.pos_src, r.pos_rcv, N, r.Tmax, r.fs, r.window(), g_all[b][None, None])
+        for x, y in zip((o.cpu().numpy() for o in outs[b]), single):
+            assert np.array_equal(x.reshape(-1).view(np.uint32), y.reshape(-1).view(np.uint32))
