@@ -78,12 +78,9 @@ __global__ void __launch_bounds__(SH_WARPS * 32, 4) shell_kernel(const __grid_co
 {
     constexpr int WIN = 64;   // 32 (SLOTS + 1), SLOTS = 1
     extern __shared__ __align__(16) unsigned char smem[];
-    const long long g = blockIdx.x;
-    const int jid = ism_find_job(t, g, [](const JobDev& j) { return j.shell_cta_base; });
+    int jid, r, grp;
+    if (!shell_cta(t, blockIdx.x, &jid, &r, &grp)) return;   // CTA-uniform
     const JobDev& J = t.j[jid];
-    const long long local = g - J.shell_cta_base;
-    const int r = (int)(local / J.shell_groups);
-    const int grp = J.shell_groups - 1 - (int)(local % J.shell_groups);  // densest (latest) shells first
     const int q0 = grp * SH_B;
     const int nb = min(SH_B, J.Q - q0);
     const int Nx = J.N[0], Ny = J.N[1], Nz = J.N[2];
@@ -138,14 +135,13 @@ __global__ void __launch_bounds__(SH_WARPS * 32, 4) shell_kernel(const __grid_co
             const float slo = fmaxf(fmaxf(sqrtf(sd2) * (1.0f - 1.0f / 1024.0f), (float)(ISM_SB * q) - 1.0f), 1e-30f);
             float bmax = 0.0f;
             for (int w = 0; w < 6; ++w) bmax = fmaxf(bmax, fabsf(J.beta[w]));
-            const double Lmax = fmax(J.L[0], fmax(J.L[1], J.L[2]));
-            const int h = max(0, (int)floorf(slo * kinv / (float)Lmax - 3.0f));
+            const int h = max(0, (int)floorf(slo * kinv / J.Lmax - 3.0f));
             const float decay = (h == 0) ? 1.0f : (bmax > 0.0f ? exp2f((float)h * log2f(bmax)) : 0.0f);
             amax = J.amp_scale / slo * decay * 1.001f;
             // images per integer delay at s: 4 pi s^2 / (k^3 V) (one image per volume V)
             const float shi = (float)(ISM_SB * q + ISM_SB);
             const float k = 1.0f / kinv;
-            const float vol = (float)(J.L[0] * J.L[1] * J.L[2]);
+            const float vol = J.vol;
             const float n_est = 4.0f * (12.566371f * shi * shi / (k * k * k * vol)) + 64.0f;
             sc = shell_scale(amax, n_est);
         }

@@ -22,8 +22,6 @@
 // butterfly per warp, the bins of an RIR in bin order, and the RIRs of a
 // source, receiver or room in index order: no atomics, bit-identical from
 // run to run.
-#include <cmath>
-
 #include "ism_device.cuh"
 
 namespace {
@@ -40,20 +38,10 @@ struct AdjRec {
     float4 q1;  // dA / d beta_w, w = 4, 5
 };
 
-__device__ double adj_pow_int(double b, int e)
-{
-    double r = 1.0;
-    while (e > 0) {
-        if (e & 1) r *= b;
-        b *= b;
-        e >>= 1;
-    }
-    return r;
-}
-
 template <int SLOTS, bool MASK>
 __global__ void __launch_bounds__(ISM_ACC_WARPS * 32) adjoint_kernel(const __grid_constant__ JobTable t,
                                                                       const float4* __restrict__ tbl,
+                                                                      const float4* __restrict__ dtbl,
                                                                       const uint32_t* __restrict__ hist,
                                                                       const uint32_t* __restrict__ ids,
                                                                       float* __restrict__ gpart,
@@ -73,7 +61,6 @@ __global__ void __launch_bounds__(ISM_ACC_WARPS * 32) adjoint_kernel(const __gri
     const int Nx = J.N[0], Ny = J.N[1], Nz = J.N[2];
     const int n_axis = Nx + Ny + Nz;
     const int H = J.H;
-    const int i_src = r / J.n_rcv, i_rcv = r % J.n_rcv;
 
     const int axis_pad = (t.max_axis_sum + 1) & ~1;
     float4* T = reinterpret_cast<float4*>(smem);      // S_hi, S_lo, F (forward tables)
@@ -81,23 +68,12 @@ __global__ void __launch_bounds__(ISM_ACC_WARPS * 32) adjoint_kernel(const __gri
     float* gw_all = reinterpret_cast<float*>(X + axis_pad);          // [warp][WIN]
     AdjRec* rec_all = reinterpret_cast<AdjRec*>(gw_all + ISM_ACC_WARPS * WIN);  // [warp][ADJ_CHUNK]
 
+    // forward tables and the geometry kernel's backward tables (x_n - x_r, dF/dbeta, d x_n / d x_s)
     const float4* Tg = tbl + J.tbl_base + (long long)r * n_axis;
+    const float4* Xg = dtbl + J.tbl_base + (long long)r * n_axis;
     for (int e = threadIdx.x; e < n_axis; e += blockDim.x) {
         T[e] = Tg[e];
-        // eq. (1) and eq. (4) per axis index, FP64
-        const int a = (e < Nx) ? 0 : ((e < Nx + Ny) ? 1 : 2);
-        const int i = e - (a == 0 ? 0 : (a == 1 ? Nx : Nx + Ny));
-        const int n = J.nlo[a] + i;
-        const bool even = (n % 2) == 0;
-        const double xs = (double)J.pos_src[3 * i_src + a], xr = (double)J.pos_rcv[3 * i_rcv + a];
-        const double xn = even ? (double)n * J.L[a] + xs : (double)(n + 1) * J.L[a] - xs;
-        const int an = n < 0 ? -n : n;
-        const int e0 = even ? an / 2 : (n - 1 < 0 ? 1 - n : n - 1) / 2;
-        const int e1 = even ? an / 2 : (n + 1 < 0 ? -(n + 1) : n + 1) / 2;
-        const double b0 = (double)J.beta[2 * a], b1 = (double)J.beta[2 * a + 1];
-        const double d0 = e0 > 0 ? (double)e0 * adj_pow_int(b0, e0 - 1) * adj_pow_int(b1, e1) : 0.0;
-        const double d1 = e1 > 0 ? (double)e1 * adj_pow_int(b0, e0) * adj_pow_int(b1, e1 - 1) : 0.0;
-        X[e] = make_float4((float)(xn - xr), (float)d0, (float)d1, even ? 1.0f : -1.0f);
+        X[e] = Xg[e];
     }
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -301,7 +277,8 @@ int launch_adj(const JobTable& t, const WsPlan& p, char* ws, cudaStream_t s)
                                          (int)sm);
     if (e != cudaSuccess) return (int)e;
     adjoint_kernel<SLOTS, MASK><<<(unsigned)p.adj_ctas, ISM_ACC_WARPS * 32, sm, s>>>(
-        t, reinterpret_cast<const float4*>(ws + p.tbl_off), reinterpret_cast<const uint32_t*>(ws + p.hist_off),
+        t, reinterpret_cast<const float4*>(ws + p.tbl_off), reinterpret_cast<const float4*>(ws + p.dtbl_off),
+        reinterpret_cast<const uint32_t*>(ws + p.hist_off),
         reinterpret_cast<const uint32_t*>(ws + p.ids_off), reinterpret_cast<float*>(ws + p.gpart_off),
         reinterpret_cast<uint32_t*>(ws + p.status_off));
     return (int)cudaGetLastError();

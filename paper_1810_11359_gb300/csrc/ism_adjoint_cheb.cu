@@ -36,7 +36,7 @@ namespace {
 
 #define SA_B ISM_SHELL_BINS   // delay bins per CTA
 #define SA_WARPS 8            // warps per CTA (one per bin for the tables)
-#define SA_RS 33              // row stride of the Gamma table
+#define SA_GV 3               // float4 per Gamma row (9 terms + 3 pad)
 #define SA_NG 12              // gradient components: dp_r[3], dp_s[3], dbeta[6]
 
 __global__ void __launch_bounds__(SA_WARPS * 32, 3) shell_adjoint_kernel(const __grid_constant__ JobTable t,
@@ -45,12 +45,9 @@ __global__ void __launch_bounds__(SA_WARPS * 32, 3) shell_adjoint_kernel(const _
                                                                           float* __restrict__ gpart)
 {
     extern __shared__ __align__(16) unsigned char smem[];
-    const long long g = blockIdx.x;
-    const int jid = ism_find_job(t, g, [](const JobDev& j) { return j.shell_cta_base; });
+    int jid, r, grp;
+    if (!shell_cta(t, blockIdx.x, &jid, &r, &grp)) return;   // CTA-uniform
     const JobDev& J = t.j[jid];
-    const long long local = g - J.shell_cta_base;
-    const int r = (int)(local / J.shell_groups);
-    const int grp = J.shell_groups - 1 - (int)(local % J.shell_groups);  // densest (latest) shells first
     const int q0 = grp * SA_B;
     const int nb = min(SA_B, J.Q - q0);
     const int Nx = J.N[0], Ny = J.N[1];
@@ -61,9 +58,9 @@ __global__ void __launch_bounds__(SA_WARPS * 32, 3) shell_adjoint_kernel(const _
     // warp sums | row prefix | per-warp column records
     const int axis_pad = (t.max_axis_sum + 1) & ~1;
     float4* T = reinterpret_cast<float4*>(smem);
-    float4* X = T + axis_pad;                                   // dF/dbeta_lo, dF/dbeta_hi, d x_n / d x_s
-    float* Gam = reinterpret_cast<float*>(X + axis_pad);        // [bin][i][SA_RS]
-    float* gw = Gam + SA_B * ISM_CHEB_N * SA_RS;                // [bin][64]
+    float4* X = T + axis_pad;                                   // x_n - x_r, dF/dbeta_lo, dF/dbeta_hi, d x_n / d x_s
+    float4* Gam = X + axis_pad;                                 // [bin][offset][SA_GV]: Gamma_0..8
+    float* gw = reinterpret_cast<float*>(Gam + SA_B * 32 * SA_GV);   // [bin][64]
     float* red = gw + SA_B * 64;                                // [warp][SA_NG]
     int* rowpre = reinterpret_cast<int*>(red + SA_WARPS * SA_NG);
     int* rowy0 = rowpre + ((t.max_axis_sum + 4) & ~3);
@@ -96,8 +93,10 @@ __global__ void __launch_bounds__(SA_WARPS * 32, 3) shell_adjoint_kernel(const _
 #pragma unroll
             for (int i = 0; i < ISM_CHEB_N; ++i) acc[i] = __fmaf_rn(t.cheb[tt * ISM_CHEB_N + i], gk, acc[i]);
         }
-#pragma unroll
-        for (int i = 0; i < ISM_CHEB_N; ++i) Gam[(warp * ISM_CHEB_N + i) * SA_RS + lane] = acc[i];
+        float4* row = Gam + (warp * 32 + lane) * SA_GV;
+        row[0] = make_float4(acc[0], acc[1], acc[2], acc[3]);
+        row[1] = make_float4(acc[4], acc[5], acc[6], acc[7]);
+        row[2] = make_float4(acc[8], 0.0f, 0.0f, 0.0f);
     }
 
     // exact delays b owned by this CTA: [b_lo, b_hi), b <= n_ism + 14 (later taps miss [0, n_ism))
@@ -114,18 +113,20 @@ __global__ void __launch_bounds__(SA_WARPS * 32, 3) shell_adjoint_kernel(const _
                          [&](int b, float f, float s, const float4& cf, int ixy, int iz, const float4& tz) {
         const int q = (b + 1) >> 5;
         const int o = b - ISM_SB * q + 1;   // offset index rr + 1 in [0, 32)
-        const float* Gb = Gam + (q - q0) * (ISM_CHEB_N * SA_RS) + o;
+        const float4* Gr = Gam + ((q - q0) * 32 + o) * SA_GV;
+        const float4 g0 = Gr[0], g1 = Gr[1], g2 = Gr[2];
+        const float Gb[ISM_CHEB_N] = {g0.x, g0.y, g0.z, g0.w, g1.x, g1.y, g1.z, g1.w, g2.x};
         // ga = sum_i Gamma_i T_i(u), gd = sum_i Gamma_i T_i'(u)
         const float uu = __fmaf_rn(2.0f, f, -1.0f);
         const float u2 = uu + uu;
-        float ga = __fmaf_rn(Gb[SA_RS], uu, Gb[0]);
-        float gd = Gb[SA_RS];
+        float ga = __fmaf_rn(Gb[1], uu, Gb[0]);
+        float gd = Gb[1];
         float tp = 1.0f, tc = uu, dp = 0.0f, dc = 1.0f;
 #pragma unroll
         for (int i = 2; i < ISM_CHEB_N; ++i) {
             const float tn = __fmaf_rn(u2, tc, -tp);
             const float dn = __fmaf_rn(u2, dc, __fmaf_rn(2.0f, tc, -dp));   // T_i' = 2 T_(i-1) + 2 u T_(i-1)' - T_(i-2)'
-            const float gi = Gb[i * SA_RS];
+            const float gi = Gb[i];
             ga = __fmaf_rn(gi, tn, ga);
             gd = __fmaf_rn(gi, dn, gd);
             tp = tc;
@@ -144,17 +145,17 @@ __global__ void __launch_bounds__(SA_WARPS * 32, 3) shell_adjoint_kernel(const _
         G[0] = __fmaf_rn(-cr, tx.w, G[0]);
         G[1] = __fmaf_rn(-cr, ty.w, G[1]);
         G[2] = __fmaf_rn(-cr, tz.w, G[2]);
-        G[3] = __fmaf_rn(cr, xx.z * tx.w, G[3]);
-        G[4] = __fmaf_rn(cr, xy.z * ty.w, G[4]);
-        G[5] = __fmaf_rn(cr, xz.z * tz.w, G[5]);
+        G[3] = __fmaf_rn(cr, xx.w * tx.w, G[3]);
+        G[4] = __fmaf_rn(cr, xy.w * ty.w, G[4]);
+        G[5] = __fmaf_rn(cr, xz.w * tz.w, G[5]);
         const float gs = ga * amp_scale * rs;                // ga / (4 pi d)
         const float Fyz = ty.z * tz.z, Fxz = tx.z * tz.z, Fxy = cf.z;
-        G[6] = __fmaf_rn(gs, xx.x * Fyz, G[6]);
-        G[7] = __fmaf_rn(gs, xx.y * Fyz, G[7]);
-        G[8] = __fmaf_rn(gs, xy.x * Fxz, G[8]);
-        G[9] = __fmaf_rn(gs, xy.y * Fxz, G[9]);
-        G[10] = __fmaf_rn(gs, xz.x * Fxy, G[10]);
-        G[11] = __fmaf_rn(gs, xz.y * Fxy, G[11]);
+        G[6] = __fmaf_rn(gs, xx.y * Fyz, G[6]);
+        G[7] = __fmaf_rn(gs, xx.z * Fyz, G[7]);
+        G[8] = __fmaf_rn(gs, xy.y * Fxz, G[8]);
+        G[9] = __fmaf_rn(gs, xy.z * Fxz, G[9]);
+        G[10] = __fmaf_rn(gs, xz.y * Fxy, G[10]);
+        G[11] = __fmaf_rn(gs, xz.z * Fxy, G[11]);
     });
 
     // lanes (fixed butterfly; lane 0's order), then warps in order
@@ -179,7 +180,7 @@ size_t shell_adjoint_smem(const JobTable& t)
 {
     const size_t axis_pad = (size_t)((t.max_axis_sum + 1) & ~1);
     const size_t rows = (size_t)((t.max_axis_sum + 4) & ~3);
-    return 2 * axis_pad * sizeof(float4) + (size_t)SA_B * ISM_CHEB_N * SA_RS * sizeof(float) +
+    return 2 * axis_pad * sizeof(float4) + (size_t)SA_B * 32 * SA_GV * sizeof(float4) +
            (size_t)SA_B * 64 * sizeof(float) + (size_t)SA_WARPS * SA_NG * sizeof(float) + 2 * rows * sizeof(int) +
            (size_t)SA_WARPS * 32 * (sizeof(float4) + sizeof(int4)) + (size_t)SA_WARPS * 33 * sizeof(int);
 }

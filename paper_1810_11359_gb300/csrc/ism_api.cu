@@ -166,7 +166,7 @@ ism_status plan(const Validated* vs, int n, ism_precision prec, bool backward, J
     for (int i = 0; i < n; ++i)
         set_cols += (long long)vs[i].job.nb_img[0] * vs[i].job.nb_img[1] * vs[i].job.n_src * vs[i].job.n_rcv;
     long long rir = 0, hist = 0, tbl = 0, ecta = 0, acta = 0, adta = 0, tcta = 0, fcta = 0, rows = 0, ids = 0, lut = 0,
-              gpart = 0, scta = 0;
+              gpart = 0, srir = 0, scta = 0;
     for (int i = 0; i < n; ++i) {
         const Validated& v = vs[i];
         const ism_job& in = v.job;
@@ -214,6 +214,10 @@ ism_status plan(const Validated* vs, int n, ism_precision prec, bool backward, J
             J.U = (int)((cols + cpu - 1) / cpu);
         }
         J.inv_kLz = (float)(1.0 / (k * in.room.L[2]));
+        for (int a = 0; a < 3; ++a) J.inv2L[a] = (float)(0.5 / in.room.L[a]);
+        J.kinv = in.room.c / in.fs;   // FP32 division, as the kernels did it
+        J.Lmax = (float)std::max(in.room.L[0], std::max(in.room.L[1], in.room.L[2]));
+        J.vol = (float)(in.room.L[0] * in.room.L[1] * in.room.L[2]);
 
         J.n_tiles = (J.Q + ISM_TILE_BINS - 1) / ISM_TILE_BINS;
         double s_cut = (double)v.n_ism - 1.0 + (double)v.H + 0.5;
@@ -273,6 +277,7 @@ ism_status plan(const Validated* vs, int n, ism_precision prec, bool backward, J
         // own images) or the direct accumulation CTAs (which read the binned ids)
         J.acc_groups = J.use_cheb ? 0 : (J.Q + ism_acc_bins((int)prec) - 1) / ism_acc_bins((int)prec);
         J.shell_groups = fused ? (J.Q + ISM_SHELL_BINS - 1) / ISM_SHELL_BINS : 0;
+        J.shell_rir_base = srir;
         J.shell_cta_base = scta;
         J.grad_out = v.grad_out;
         J.grad_beta = v.grad_beta;
@@ -288,7 +293,9 @@ ism_status plan(const Validated* vs, int n, ism_precision prec, bool backward, J
         tbl += R * axis;
         if (!fused) ecta += R * ((J.U + ISM_ENUM_WARPS - 1) / ISM_ENUM_WARPS);
         acta += R * J.acc_groups;
+        if (fused) srir += R;
         scta += R * J.shell_groups;
+        if (J.shell_groups > t.shell_gmax) t.shell_gmax = J.shell_groups;
         fcta += R * J.fin_chunks;
         if (backward && !J.adj_cheb) adta += R * J.n_tiles;
         if (J.has_tail) {
@@ -312,7 +319,7 @@ ism_status plan(const Validated* vs, int n, ism_precision prec, bool backward, J
     if (ids >= 0xFFFFFFFFll)
         return fail(ISM_ERR_UNSUPPORTED, "%lld images in one launch set exceed 2^32; split the batch", ids);
     if (rir > 0x7FFFFFFFll || ecta > 0x7FFFFFFFll || acta > 0x7FFFFFFFll || adta > 0x7FFFFFFFll ||
-        tcta > 0x7FFFFFFFll || fcta > 0x7FFFFFFFll || scta > 0x7FFFFFFFll)
+        tcta > 0x7FFFFFFFll || fcta > 0x7FFFFFFFll || srir * (long long)t.shell_gmax > 0x7FFFFFFFll)
         return fail(ISM_ERR_UNSUPPORTED, "launch set too large; split the batch");
     p.hist_total = hist;
     p.ids_total = ids;
@@ -327,7 +334,11 @@ ism_status plan(const Validated* vs, int n, ism_precision prec, bool backward, J
     p.rgrad_total = backward ? rir * 12 : 0;
     p.enum_ctas = ecta;
     p.acc_ctas = acta;
-    p.shell_ctas = scta;
+    t.shell_rirs = srir;
+    // shell-rank order when the jobs' shell counts are alike (at most 1/8 of the
+    // rank-major grid would be CTAs past their job's shells), else job-major
+    t.shell_rank_major = (srir * (long long)t.shell_gmax * 7 <= scta * 8) ? 1 : 0;
+    p.shell_ctas = t.shell_rank_major ? srir * t.shell_gmax : scta;
     p.adj_ctas = adta;
     p.tail_ctas = tcta;
     p.fin_ctas = fcta;

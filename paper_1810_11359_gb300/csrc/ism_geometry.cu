@@ -11,8 +11,9 @@
 //   D[n] = (x_n - x_r) f_s / c           (signed offset, FP32: the direction
 //                                          of arrival for polar patterns)
 // so that image (nx, ny, nz) has s^2 = Sx + Sy + Sz and weight Fx Fy Fz.  For
-// the backward pass it also tabulates dF/dbeta_0, dF/dbeta_1 (product form,
-// valid at beta = 0) and d x_n / d x_s = +-1 (even / odd n).  It
+// the backward pass it also tabulates x_n - x_r (metres), dF/dbeta_0,
+// dF/dbeta_1 (product form, valid at beta = 0) and d x_n / d x_s = +-1
+// (even / odd n).  It
 // also checks that source and receiver lie strictly inside the room (and that
 // a patterned receiver has a non-zero orientation); a pair that does not gets
 // S = +inf everywhere, i.e. no image survives.
@@ -97,8 +98,8 @@ __global__ void __launch_bounds__(128) geometry_kernel(const __grid_constant__ J
         if (dtbl) {
             const double d0 = e0 > 0 ? (double)e0 * dpow_int(b0, e0 - 1) * dpow_int(b1, e1) : 0.0;
             const double d1 = e1 > 0 ? (double)e1 * dpow_int(b0, e0) * dpow_int(b1, e1 - 1) : 0.0;
-            dtbl[J.tbl_base + (long long)r * n_axis + e] =
-                make_float4(ok_s ? (float)d0 : 0.0f, ok_s ? (float)d1 : 0.0f, even ? 1.0f : -1.0f, 0.0f);
+            dtbl[J.tbl_base + (long long)r * n_axis + e] = make_float4(
+                (float)(m * J.L[a] + off), ok_s ? (float)d0 : 0.0f, ok_s ? (float)d1 : 0.0f, even ? 1.0f : -1.0f);
         }
     }
 }

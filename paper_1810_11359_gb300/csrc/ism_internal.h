@@ -66,6 +66,9 @@ struct JobDev {
     int U;                    // enumeration units (warps) per RIR
     int cols_per_unit;        // grid columns (ix, iy) per enumeration unit
     float inv_kLz;            // 1 / ((f_s / c) L_z): samples -> z cells
+    float inv2L[3];           // 1 / (2 L) per axis (rounded from FP64 on the host: no FP64 in the kernels)
+    float kinv;               // c / f_s: metres per sample
+    float Lmax, vol;          // longest side, volume (FP32)
     int acc_groups;           // accumulation CTAs per RIR (groups of ISM_ACC_BPC bins)
     int fin_chunk;            // samples per finalize CTA (>= the envelope-fit window)
     int fin_chunks;           // finalize CTAs per RIR (chunk 0 holds the last samples)
@@ -92,7 +95,8 @@ struct JobDev {
     long long tbl_base;       // first table entry (float4) of the job
     long long enum_cta_base;  // first enumeration CTA of the job
     long long acc_cta_base;   // first accumulation CTA of the job
-    long long shell_cta_base; // first fused Chebyshev CTA of the job
+    long long shell_rir_base; // first RIR of the job among the launch set's fused RIRs
+    long long shell_cta_base; // first fused CTA of the job (job-major order)
     long long adj_cta_base;   // first adjoint CTA of the job
     long long tail_cta_base;  // first tail CTA of the job
     long long fin_cta_base;   // first finalize CTA of the job
@@ -114,6 +118,9 @@ struct JobTable {
     int max_axis_sum;
     int any_cheb;                      // some job accumulates through Chebyshev moments
     int any_direct;                    // some job reads delay-binned image ids
+    int shell_gmax;                    // most shells of a fused RIR
+    int shell_rank_major;              // fused CTAs ordered by shell rank (shell_gmax x shell_rirs) or by job
+    long long shell_rirs;              // RIRs of the fused jobs
     float cheb[32 * ISM_CHEB_N];       // Chebyshev coefficients of the 32 tap functions (32-tap window)
     JobDev j[ISM_MAX_JOBS];
 };

@@ -47,6 +47,31 @@ __device__ __forceinline__ void ax_range(const ShellAxis& a, float Dlo, float Dh
     *i1 = min(max(n1 - a.nlo, 0), a.N);
 }
 
+// CTA g of a fused launch -> (job, RIR, shell).  When the jobs' shell counts
+// are alike the CTAs are ordered by the shell's rank from the outside over all
+// fused RIRs of the launch set: every RIR's outermost (densest, since the
+// images per delay grow as s^2) shell first, so the lightest shells fill the
+// end of the launch; false for a CTA past its job's shells.  Otherwise they go
+// job by job, RIR by RIR, densest shell first.
+__device__ __forceinline__ bool shell_cta(const JobTable& t, long long g, int* jid, int* r, int* grp)
+{
+    if (!t.shell_rank_major) {
+        const int j = ism_find_job(t, g, [](const JobDev& d) { return d.shell_cta_base; });
+        const long long local = g - t.j[j].shell_cta_base;
+        *jid = j;
+        *r = (int)(local / t.j[j].shell_groups);
+        *grp = t.j[j].shell_groups - 1 - (int)(local % t.j[j].shell_groups);
+        return true;
+    }
+    const long long k = g / t.shell_rirs;   // rank from the outside
+    const long long rr = g - k * t.shell_rirs;
+    const int j = ism_find_job(t, rr, [](const JobDev& d) { return d.shell_rir_base; });
+    *jid = j;
+    *r = (int)(rr - t.j[j].shell_rir_base);
+    *grp = t.j[j].shell_groups - 1 - (int)k;
+    return *grp >= 0;
+}
+
 // What a CTA needs to walk the shell [b_lo, b_hi) of integer delays of RIR r.
 struct Shell {
     ShellAxis ax[3];
@@ -62,12 +87,12 @@ __device__ __forceinline__ Shell shell_setup(const JobDev& J, const float4* T, i
 {
     Shell sh;
     const int i_src = r / J.n_rcv, i_rcv = r - (r / J.n_rcv) * J.n_rcv;
-    sh.kinv = J.c / J.fs;
+    sh.kinv = J.kinv;
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
         sh.ax[a].xs = J.pos_src[3 * i_src + a];
         sh.ax[a].xr = J.pos_rcv[3 * i_rcv + a];
-        sh.ax[a].inv2L = (float)(0.5 / J.L[a]);
+        sh.ax[a].inv2L = J.inv2L[a];
         sh.ax[a].nlo = J.nlo[a];
         sh.ax[a].N = J.N[a];
     }
