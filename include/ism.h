@@ -298,6 +298,12 @@ ism_status ism_server_create(const ism_server_config* cfg, ism_server** server);
  * never fit the budget is rejected with ISM_ERR_OOM. */
 ism_status ism_server_submit(ism_server* server, const ism_job* job, ism_ticket* ticket);
 
+/* Queues n_jobs requests in one call (jobs[k] as for ism_server_submit;
+ * tickets: n_jobs entries).  Every job is checked before any is queued: on an
+ * error nothing is queued and the message names the job.  The requests enter
+ * the queue together, in array order, with one submission time. */
+ism_status ism_server_submit_batch(ism_server* server, const ism_job* jobs, int n_jobs, ism_ticket* tickets);
+
 /* *done = 1 if the request has finished (successfully or not), else 0. */
 ism_status ism_server_poll(ism_server* server, ism_ticket ticket, int* done);
 

@@ -71,7 +71,7 @@ __device__ __forceinline__ float shell_scale(float a_max, float n)
     return __int_as_float((e + 127) << 23);
 }
 
-__global__ void __launch_bounds__(SH_WARPS * 32, 4) shell_kernel(const __grid_constant__ JobTable t,
+__global__ void __launch_bounds__(SH_WARPS * 32, 5) shell_kernel(const __grid_constant__ JobTable t,
                                                                   const float4* __restrict__ tbl,
                                                                   float* __restrict__ rows,
                                                                   uint32_t* __restrict__ status)
@@ -248,6 +248,9 @@ int ism_launch_accum_cheb(const JobTable& t, const WsPlan& p, char* ws, void* st
     if (p.shell_ctas <= 0 || !t.any_cheb) return 0;
     const size_t sm = shell_smem(t);
     cudaError_t e = cudaFuncSetAttribute(shell_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (e != cudaSuccess) return (int)e;
+    // all of the unified L1 as shared memory: 5 CTAs of ~27 KB per SM
+    e = cudaFuncSetAttribute(shell_kernel, cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxShared);
     if (e != cudaSuccess) return (int)e;
     shell_kernel<<<(unsigned)p.shell_ctas, SH_WARPS * 32, sm, (cudaStream_t)stream>>>(
         t, reinterpret_cast<const float4*>(ws + p.tbl_off), reinterpret_cast<float*>(ws + p.rows_off),

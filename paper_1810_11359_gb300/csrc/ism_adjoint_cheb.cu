@@ -39,7 +39,7 @@ namespace {
 #define SA_GV 3               // float4 per Gamma row (9 terms + 3 pad)
 #define SA_NG 12              // gradient components: dp_r[3], dp_s[3], dbeta[6]
 
-__global__ void __launch_bounds__(SA_WARPS * 32, 3) shell_adjoint_kernel(const __grid_constant__ JobTable t,
+__global__ void __launch_bounds__(SA_WARPS * 32, 4) shell_adjoint_kernel(const __grid_constant__ JobTable t,
                                                                           const float4* __restrict__ tbl,
                                                                           const float4* __restrict__ dtbl,
                                                                           float* __restrict__ gpart)
@@ -193,6 +193,9 @@ int ism_launch_adjoint_cheb(const JobTable& t, const WsPlan& p, char* ws, void* 
     if (p.shell_ctas <= 0) return 0;
     const size_t sm = shell_adjoint_smem(t);
     cudaError_t e = cudaFuncSetAttribute(shell_adjoint_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (e != cudaSuccess) return (int)e;
+    e = cudaFuncSetAttribute(shell_adjoint_kernel, cudaFuncAttributePreferredSharedMemoryCarveout,
+                             cudaSharedmemCarveoutMaxShared);   // 4 CTAs of ~32 KB per SM
     if (e != cudaSuccess) return (int)e;
     shell_adjoint_kernel<<<(unsigned)p.shell_ctas, SA_WARPS * 32, sm, (cudaStream_t)stream>>>(
         t, reinterpret_cast<const float4*>(ws + p.tbl_off), reinterpret_cast<const float4*>(ws + p.dtbl_off),

@@ -254,8 +254,11 @@ ism_status plan(const Validated* vs, int n, ism_precision prec, bool backward, J
         J.rows_base = rows;
         J.lut_base = lut;
         // Chebyshev moments pay off when a delay bin holds enough images to
-        // amortise the expansion of its 33 offsets: estimate the images in
-        // reach per bin from the sphere of radius n_ism + H samples
+        // amortise the expansion of its 33 offsets and the shell's enumeration
+        // set-up: estimate the images in reach per bin from the sphere of radius
+        // n_ism + H samples.  Measured crossover: 64 (the 16 kHz serving mix and
+        // training rooms gain down to ~16 per bin, the 48 kHz array with ~36 per
+        // bin is 1.5x faster in the direct form)
         {
             const double reach = ((double)v.n_ism + v.H) / k;                     // metres
             const double vol = in.room.L[0] * in.room.L[1] * in.room.L[2];
@@ -263,7 +266,7 @@ ism_status plan(const Validated* vs, int n, ism_precision prec, bool backward, J
                                              4.18879020478639 * reach * reach * reach / vol);
             const double per_bin = in_reach / (double)((v.n_ism + v.H) / ISM_SB + 1);
             J.use_cheb = (prec == ISM_PREC_FP32 && !backward && v.Nw == 32.0 && v.H == 16 && v.slots == 1 &&
-                          per_bin >= 256.0) ? 1 : 0;
+                          per_bin >= 64.0) ? 1 : 0;
             // sparse bins: sorting by offset and padding each offset to a group of 4
             // images costs more than adding every image's taps on its own
             J.sparse = ((prec == ISM_PREC_FP32 || prec == ISM_PREC_FP32_DIRECT) && !backward && !J.use_cheb &&

@@ -371,6 +371,69 @@ struct ism_server {
     }
 };
 
+namespace {
+
+// Checks one job (arguments as for ism_simulate, host positions strictly
+// inside the room, a budget it can fit) and builds its request with copies of
+// its positions; nothing is queued.
+ism_status prepare_request(ism_server* s, const ism_job* job, Request** out)
+{
+    *out = nullptr;
+    if (!job) return ism_fail_message(ISM_ERR_INVALID_ARG, "NULL job");
+    if (!job->pos_src || !job->pos_rcv || !job->out)
+        return ism_fail_message(ISM_ERR_INVALID_ARG, "pos_src, pos_rcv and out must be host pointers, not NULL");
+    if (job->env_amp) return ism_fail_message(ISM_ERR_INVALID_ARG, "env_amp is not available through the server");
+    if (job->n_src < 1 || job->n_rcv < 1) return ism_fail_message(ISM_ERR_INVALID_ARG, "need n_src, n_rcv >= 1");
+    const bool patterned = job->mic_pattern != ISM_MIC_OMNI;
+    if (patterned && !job->orient_rcv)
+        return ism_fail_message(ISM_ERR_INVALID_ARG, "a polar pattern needs orient_rcv (host pointer, [n_rcv][3])");
+    for (int i = 0; patterned && i < job->n_rcv; ++i) {
+        const float* o = job->orient_rcv + 3 * i;
+        const double oo = (double)o[0] * o[0] + (double)o[1] * o[1] + (double)o[2] * o[2];
+        if (!(oo > 0.0) || !(oo < 1e300))
+            return ism_fail_message(ISM_ERR_INVALID_ARG, "receiver %d has a zero or non-finite orientation", i);
+    }
+    for (int i = 0; i < job->n_src; ++i)
+        for (int a = 0; a < 3; ++a)
+            if (!(job->pos_src[3 * i + a] > 0.0f && (double)job->pos_src[3 * i + a] < job->room.L[a]))
+                return ism_fail_message(ISM_ERR_INVALID_ARG, "source %d lies outside the room", i);
+    for (int i = 0; i < job->n_rcv; ++i)
+        for (int a = 0; a < 3; ++a)
+            if (!(job->pos_rcv[3 * i + a] > 0.0f && (double)job->pos_rcv[3 * i + a] < job->room.L[a]))
+                return ism_fail_message(ISM_ERR_INVALID_ARG, "receiver %d lies outside the room", i);
+    // full validation (and the workspace this job alone would need)
+    ism_job probe = *job;
+    probe.pos_src = probe.pos_rcv = nullptr;
+    probe.orient_rcv = nullptr;
+    probe.out = nullptr;
+    size_t ws1 = 0;
+    ism_status v = ism_batch_workspace_size(&probe, 1, s->cfg.prec, &ws1);
+    if (v != ISM_OK) return v;
+    int n_S = 0;
+    if ((v = ism_rir_length(job->Tmax, job->fs, &n_S)) != ISM_OK) return v;
+    Request* r = new Request();
+    r->job = *job;
+    r->out_bytes = (size_t)job->n_src * job->n_rcv * (size_t)n_S * sizeof(float);
+    const int n_vec = job->n_src + job->n_rcv + (patterned ? job->n_rcv : 0);   // positions, then orientations
+    r->pos_bytes = (size_t)n_vec * 3 * sizeof(float);
+    const size_t need = g256(r->out_bytes) + g256(r->pos_bytes);
+    if (need + g256(ws1) > s->dev_arena.cap() || need + 256 > s->pin_arena.cap()) {
+        delete r;
+        return ism_fail_message(ISM_ERR_OOM, "request needs %zu device bytes with its workspace; the budget is %zu",
+                                need + g256(ws1), s->dev_arena.cap());
+    }
+    r->pos.resize((size_t)n_vec * 3);
+    std::memcpy(r->pos.data(), job->pos_src, (size_t)job->n_src * 3 * sizeof(float));
+    if (patterned)
+        std::memcpy(r->pos.data() + 3 * (job->n_src + job->n_rcv), job->orient_rcv,
+                    (size_t)job->n_rcv * 3 * sizeof(float));
+    std::memcpy(r->pos.data() + 3 * job->n_src, job->pos_rcv, (size_t)job->n_rcv * 3 * sizeof(float));
+    *out = r;
+    return ISM_OK;
+}
+
+}  // namespace
+
 extern "C" {
 
 ism_status ism_server_create(const ism_server_config* cfg, ism_server** server)
@@ -427,66 +490,40 @@ ism_status ism_server_create(const ism_server_config* cfg, ism_server** server)
 ism_status ism_server_submit(ism_server* s, const ism_job* job, ism_ticket* ticket)
 {
     if (!s || !job || !ticket) return ism_fail_message(ISM_ERR_INVALID_ARG, "NULL argument");
-    if (!job->pos_src || !job->pos_rcv || !job->out)
-        return ism_fail_message(ISM_ERR_INVALID_ARG, "pos_src, pos_rcv and out must be host pointers, not NULL");
-    if (job->env_amp) return ism_fail_message(ISM_ERR_INVALID_ARG, "env_amp is not available through the server");
-    if (job->n_src < 1 || job->n_rcv < 1) return ism_fail_message(ISM_ERR_INVALID_ARG, "need n_src, n_rcv >= 1");
-    const bool patterned = job->mic_pattern != ISM_MIC_OMNI;
-    if (patterned && !job->orient_rcv)
-        return ism_fail_message(ISM_ERR_INVALID_ARG, "a polar pattern needs orient_rcv (host pointer, [n_rcv][3])");
-    for (int i = 0; patterned && i < job->n_rcv; ++i) {
-        const float* o = job->orient_rcv + 3 * i;
-        const double oo = (double)o[0] * o[0] + (double)o[1] * o[1] + (double)o[2] * o[2];
-        if (!(oo > 0.0) || !(oo < 1e300))
-            return ism_fail_message(ISM_ERR_INVALID_ARG, "receiver %d has a zero or non-finite orientation", i);
+    return ism_server_submit_batch(s, job, 1, ticket);
+}
+
+ism_status ism_server_submit_batch(ism_server* s, const ism_job* jobs, int n_jobs, ism_ticket* tickets)
+{
+    if (!s || !jobs || !tickets || n_jobs < 1) return ism_fail_message(ISM_ERR_INVALID_ARG, "NULL argument or no job");
+    std::vector<Request*> rs((size_t)n_jobs, nullptr);
+    for (int k = 0; k < n_jobs; ++k) {
+        ism_status v = prepare_request(s, jobs + k, &rs[k]);
+        if (v != ISM_OK) {
+            for (Request* r : rs) delete r;
+            if (n_jobs > 1) {
+                const std::string m = ism_last_error_message();
+                return ism_fail_message(v, "job %d: %s", k, m.c_str());
+            }
+            return v;
+        }
     }
-    for (int i = 0; i < job->n_src; ++i)
-        for (int a = 0; a < 3; ++a)
-            if (!(job->pos_src[3 * i + a] > 0.0f && (double)job->pos_src[3 * i + a] < job->room.L[a]))
-                return ism_fail_message(ISM_ERR_INVALID_ARG, "source %d lies outside the room", i);
-    for (int i = 0; i < job->n_rcv; ++i)
-        for (int a = 0; a < 3; ++a)
-            if (!(job->pos_rcv[3 * i + a] > 0.0f && (double)job->pos_rcv[3 * i + a] < job->room.L[a]))
-                return ism_fail_message(ISM_ERR_INVALID_ARG, "receiver %d lies outside the room", i);
-    // full validation (and the workspace this job alone would need)
-    ism_job probe = *job;
-    probe.pos_src = probe.pos_rcv = nullptr;
-    probe.orient_rcv = nullptr;
-    probe.out = nullptr;
-    size_t ws1 = 0;
-    ism_status v = ism_batch_workspace_size(&probe, 1, s->cfg.prec, &ws1);
-    if (v != ISM_OK) return v;
-    int n_S = 0;
-    if ((v = ism_rir_length(job->Tmax, job->fs, &n_S)) != ISM_OK) return v;
-    Request* r = new Request();
-    r->job = *job;
-    r->out_bytes = (size_t)job->n_src * job->n_rcv * (size_t)n_S * sizeof(float);
-    const int n_vec = job->n_src + job->n_rcv + (patterned ? job->n_rcv : 0);   // positions, then orientations
-    r->pos_bytes = (size_t)n_vec * 3 * sizeof(float);
-    const size_t need = g256(r->out_bytes) + g256(r->pos_bytes);
-    if (need + g256(ws1) > s->dev_arena.cap() || need + 256 > s->pin_arena.cap()) {
-        delete r;
-        return ism_fail_message(ISM_ERR_OOM, "request needs %zu device bytes with its workspace; the budget is %zu",
-                                need + g256(ws1), s->dev_arena.cap());
-    }
-    r->pos.resize((size_t)n_vec * 3);
-    std::memcpy(r->pos.data(), job->pos_src, (size_t)job->n_src * 3 * sizeof(float));
-    if (patterned)
-        std::memcpy(r->pos.data() + 3 * (job->n_src + job->n_rcv), job->orient_rcv,
-                    (size_t)job->n_rcv * 3 * sizeof(float));
-    std::memcpy(r->pos.data() + 3 * job->n_src, job->pos_rcv, (size_t)job->n_rcv * 3 * sizeof(float));
-    r->t_submit = now_s();
+    const double t = now_s();
     {
         std::lock_guard<std::mutex> g(s->mu);
         if (s->stopping) {
-            delete r;
+            for (Request* r : rs) delete r;
             return ism_fail_message(ISM_ERR_CANCELLED, "the server is shutting down");
         }
-        r->id = s->next_id++;
-        s->table[r->id] = r;
-        s->queue.push_back(r);
-        ++s->st.submitted;
-        *ticket = r->id;
+        for (int k = 0; k < n_jobs; ++k) {
+            Request* r = rs[k];
+            r->t_submit = t;
+            r->id = s->next_id++;
+            s->table[r->id] = r;
+            s->queue.push_back(r);
+            ++s->st.submitted;
+            tickets[k] = r->id;
+        }
     }
     s->cv_launch.notify_one();
     return ISM_OK;

@@ -100,6 +100,7 @@ _SIGS = {
                                           ctypes.c_void_p]),
     "ism_server_create": (ctypes.c_int, [_P(ism_server_config), _P(ctypes.c_void_p)]),
     "ism_server_submit": (ctypes.c_int, [ctypes.c_void_p, _P(ism_job), _P(ctypes.c_uint64)]),
+    "ism_server_submit_batch": (ctypes.c_int, [ctypes.c_void_p, _P(ism_job), ctypes.c_int, _P(ctypes.c_uint64)]),
     "ism_server_poll": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_uint64, _P(ctypes.c_int)]),
     "ism_server_wait": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_uint64, ctypes.c_double, _P(ctypes.c_double)]),
     "ism_server_stats_read": (ctypes.c_int, [ctypes.c_void_p, _P(ism_server_stats)]),
@@ -609,6 +610,52 @@ class Server:
         with self._lock:
             self._outs[t.value] = out
         return t.value, out
+
+    def submit_many(self, reqs, outs=None):
+        """Queues omnidirectional requests in one ism_server_submit_batch call.
+        reqs: dicts with L, beta, pos_src, pos_rcv, nb_img, Tmax, fs and
+        optionally Tdiff, Tw, c, seed.  outs: one FP32 array per request (or
+        None: views of one new block).  Returns [(ticket, out)]."""
+        n = len(reqs)
+        if n == 0:
+            return []
+        arr = (ism_job * n)()
+        v = np.frombuffer(arr, dtype=np.dtype(ism_job), count=n)
+        v["room"]["L"] = np.array([r["L"] for r in reqs], np.float64).reshape(n, 3)
+        v["room"]["beta"] = np.array([r["beta"] for r in reqs], np.float64).reshape(n, 6).astype(np.float32)
+        v["room"]["c"] = [float(r.get("c", 343.0)) for r in reqs]
+        ps = [np.asarray(r["pos_src"], np.float32).reshape(-1, 3) for r in reqs]
+        pr = [np.asarray(r["pos_rcv"], np.float32).reshape(-1, 3) for r in reqs]
+        ns = np.array([a.shape[0] for a in ps], np.int64)
+        nr = np.array([a.shape[0] for a in pr], np.int64)
+        # every request's positions in one host block (the server copies them in the call)
+        pos = np.concatenate([x for a, b in zip(ps, pr) for x in (a.ravel(), b.ravel())])
+        off = np.concatenate([[0], np.cumsum(3 * (ns + nr))[:-1]]).astype(np.uint64)
+        base = np.uint64(pos.ctypes.data)
+        v["pos_src"] = base + off * np.uint64(4)
+        v["pos_rcv"] = base + (off + np.uint64(3) * ns.astype(np.uint64)) * np.uint64(4)
+        v["n_src"], v["n_rcv"] = ns, nr
+        v["nb_img"] = np.array([r["nb_img"] for r in reqs], np.int32).reshape(n, 3)
+        for f, d in (("Tmax", None), ("fs", None), ("Tdiff", 0.0), ("Tw", 0.0)):
+            v[f] = [float(r[f] if d is None else (r.get(f) or d)) for r in reqs]
+        v["seed"] = [int(r.get("seed", 0)) & (2 ** 64 - 1) for r in reqs]
+        lens = {}
+        n_S = np.array([lens.setdefault((r["Tmax"], r["fs"]), ism_rir_length(r["Tmax"], r["fs"])) for r in reqs],
+                       np.int64)
+        sizes = ns * nr * n_S
+        if outs is None:
+            block = np.empty(int(sizes.sum()), np.float32)
+            cuts = np.cumsum(sizes)[:-1]
+            outs = [b.reshape(a, c, m) for b, a, c, m in zip(np.split(block, cuts), ns, nr, n_S)]
+        for o, sz in zip(outs, sizes):
+            assert o.dtype == np.float32 and o.flags["C_CONTIGUOUS"] and o.size == sz
+        v["out"] = [o.ctypes.data for o in outs]
+        t = (ctypes.c_uint64 * n)()
+        _check(load().ism_server_submit_batch(self._h, arr, n, t))
+        with self._lock:
+            for k in range(n):
+                self._outs[t[k]] = outs[k]
+        return list(zip(list(t), outs))
 
     def poll(self, ticket: int) -> bool:
         d = ctypes.c_int()

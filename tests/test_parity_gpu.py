@@ -256,6 +256,29 @@ def test_host_entry_matches_device_entry():
     assert np.array_equal(dev.view(np.uint32), host.view(np.uint32))
 
 
+@pytest.mark.parametrize("pinned", [True, False])
+def test_host_entry_large_result_in_pieces_matches_device_entry(pinned):
+    """A 118 MB result (the 48 kHz array workload: 64 source points x 8
+    microphones, 1.2 s with a diffuse tail) into a pinned or a pageable host
+    buffer: bitwise the device entry point's RIRs."""
+    room = workloads.trajectory_array()
+    beta = ism.ism_beta_sabine(room.L, room.rt60)
+    N = ism.ism_nb_img_from_t(room.Tdiff, room.L, room.c, room.window())
+    n_S = ism.ism_rir_length(room.Tmax, room.fs)
+    ps = torch.as_tensor(room.pos_src).cuda()
+    pr = torch.as_tensor(room.pos_rcv).cuda()
+    dev = torch.empty((ps.shape[0], pr.shape[0], n_S), device="cuda")
+    ism.ism_simulate(room.L, beta, ps, pr, N, room.Tmax, room.fs, Tdiff=room.Tdiff, Tw=room.window(), seed=room.seed,
+                     out=dev)
+    out = torch.empty((ps.shape[0], pr.shape[0], n_S), dtype=torch.float32)
+    if pinned:
+        out = out.pin_memory()
+    out.numpy()[:] = np.nan
+    host = ism.ism_simulate_host(room.L, beta, room.pos_src, room.pos_rcv, N, room.Tmax, room.fs, Tdiff=room.Tdiff,
+                                 Tw=room.window(), seed=room.seed, out=out.numpy())
+    assert np.array_equal(dev.cpu().numpy().view(np.uint32), host.view(np.uint32))
+
+
 def test_sabine_on_device_fp64():
     rooms = workloads.serving_requests(64, seed=9)
     L = torch.tensor(np.stack([r.room.L for r in rooms]), dtype=torch.float64, device="cuda")

@@ -173,3 +173,22 @@ def test_destroy_with_queued_requests_returns():
     for a in reqs:
         submit(srv, a)
     srv.close()        # finishes what is on the GPU, cancels the rest, joins its threads
+
+
+def test_batch_submit_matches_alone_and_is_all_or_nothing():
+    """ism_server_submit_batch: 60 requests in one call give, bitwise, each
+    request's RIRs computed alone; a call with one bad job (a receiver outside
+    its room) queues none of its jobs and names the bad one."""
+    reqs = [request_args(r.room) for r in workloads.serving_requests(60, seed=12, feasible=feasible)]
+    ref = [alone(a) for a in reqs]
+    with ism.Server(hbm_budget=2 << 30, max_inflight=3, max_batch=16) as srv:
+        got = srv.submit_many(reqs)
+        for (t, out), r in zip(got, ref):
+            assert srv.wait(t) > 0
+            assert np.array_equal(out.view(np.uint32), r.view(np.uint32))
+        before = srv.stats()["submitted"]
+        bad = [dict(a) for a in reqs[:5]]
+        bad[3]["pos_rcv"] = np.array([[-1.0, 1.0, 1.0]], np.float32)
+        with pytest.raises(ism.IsmError, match="job 3"):
+            srv.submit_many(bad)
+        assert srv.stats()["submitted"] == before
