@@ -99,6 +99,7 @@ struct Request {
     std::vector<float> pos;      // n_src * 3 source then n_rcv * 3 receiver coordinates
     size_t out_bytes = 0, pos_bytes = 0;
     size_t dev_off = 0, pin_off = 0;
+    bool direct = false;         // out is page-locked: results go there without staging
     bool admitted = false, done = false;
     ism_status status = ISM_OK;
     std::string message;
@@ -149,9 +150,14 @@ struct ism_server {
     {
         if (!r->admitted) return;
         dev_arena.release(r->dev_off, g256(r->out_bytes) + g256(r->pos_bytes));
-        pin_arena.release(r->pin_off, g256(r->out_bytes) + g256(r->pos_bytes));
+        pin_arena.release(r->pin_off, pin_bytes(r));
         r->admitted = false;
     }
+
+    // Staging bytes of a request in the pinned pool: [results | positions], or
+    // the positions alone when the results go straight to a page-locked `out`.
+    static size_t pin_bytes(const Request* r) { return (r->direct ? 0 : g256(r->out_bytes)) + g256(r->pos_bytes); }
+    static size_t pin_pos(const Request* r) { return r->pin_off + (r->direct ? 0 : g256(r->out_bytes)); }
 
     // Admits requests from the head of the queue into a batch (lock held).
     // Returns nullptr when nothing can start now.
@@ -170,7 +176,7 @@ struct ism_server {
             const size_t need = g256(r->out_bytes) + g256(r->pos_bytes);
             size_t doff = 0, poff = 0;
             if (!dev_arena.alloc(need, &doff)) break;
-            if (!pin_arena.alloc(need, &poff)) {
+            if (!pin_arena.alloc(pin_bytes(r), &poff)) {
                 dev_arena.release(doff, need);
                 break;
             }
@@ -241,7 +247,7 @@ struct ism_server {
     {
         cudaStream_t s = streams[b->stream];
         for (Request* r : b->reqs) {
-            char* h = pin + r->pin_off + g256(r->out_bytes);
+            char* h = pin + pin_pos(r);
             std::memcpy(h, r->pos.data(), r->pos_bytes);
             if (cudaMemcpyAsync(dev + r->dev_off + g256(r->out_bytes), h, r->pos_bytes, cudaMemcpyHostToDevice, s) !=
                 cudaSuccess) {
@@ -261,8 +267,8 @@ struct ism_server {
             return ISM_ERR_CUDA;
         }
         for (Request* r : b->reqs)
-            if (cudaMemcpyAsync(pin + r->pin_off, dev + r->dev_off, r->out_bytes, cudaMemcpyDeviceToHost, s) !=
-                cudaSuccess) {
+            if (cudaMemcpyAsync(r->direct ? static_cast<void*>(r->job.out) : static_cast<void*>(pin + r->pin_off),
+                                dev + r->dev_off, r->out_bytes, cudaMemcpyDeviceToHost, s) != cudaSuccess) {
                 *msg = "result copy failed";
                 return ISM_ERR_CUDA;
             }
@@ -357,7 +363,8 @@ struct ism_server {
                     msg = "device check flags set";
                 }
                 if (s == ISM_OK)
-                    for (Request* r : b->reqs) std::memcpy(r->job.out, pin + r->pin_off, r->out_bytes);
+                    for (Request* r : b->reqs)
+                        if (!r->direct) std::memcpy(r->job.out, pin + r->pin_off, r->out_bytes);
                 res.emplace_back(s, msg);
             }
             lk.lock();
@@ -428,6 +435,9 @@ ism_status prepare_request(ism_server* s, const ism_job* job, Request** out)
         std::memcpy(r->pos.data() + 3 * (job->n_src + job->n_rcv), job->orient_rcv,
                     (size_t)job->n_rcv * 3 * sizeof(float));
     std::memcpy(r->pos.data() + 3 * job->n_src, job->pos_rcv, (size_t)job->n_rcv * 3 * sizeof(float));
+    cudaPointerAttributes attr{};
+    r->direct = cudaPointerGetAttributes(&attr, job->out) == cudaSuccess && attr.type == cudaMemoryTypeHost;
+    cudaGetLastError();   // a pageable pointer may leave an error behind on older drivers
     *out = r;
     return ISM_OK;
 }

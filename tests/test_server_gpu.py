@@ -186,6 +186,12 @@ def test_batch_submit_matches_alone_and_is_all_or_nothing():
         for (t, out), r in zip(got, ref):
             assert srv.wait(t) > 0
             assert np.array_equal(out.view(np.uint32), r.view(np.uint32))
+        # page-locked result buffers: the server copies into them directly
+        pinned = [torch.full(r.shape, float("nan")).pin_memory() for r in ref]
+        got = srv.submit_many(reqs, outs=[o.numpy() for o in pinned])
+        for (t, out), r in zip(got, ref):
+            srv.wait(t)
+            assert np.array_equal(out.view(np.uint32), r.view(np.uint32))
         before = srv.stats()["submitted"]
         bad = [dict(a) for a in reqs[:5]]
         bad[3]["pos_rcv"] = np.array([[-1.0, 1.0, 1.0]], np.float32)
