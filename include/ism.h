@@ -169,6 +169,8 @@ ism_status ism_host_workspace_size(const ism_room* room, int n_src, int n_rcv, c
  * bitwise OR of ISM_DEVICE_FLAG_* values. */
 #define ISM_DEVICE_FLAG_POSITION 1u   /* a source/receiver outside the room or coincident */
 #define ISM_DEVICE_FLAG_BIN 2u        /* an image delay fell outside its bin (internal)    */
+#define ISM_DEVICE_FLAG_BETA 4u       /* a reflection coefficient read from device memory
+                                         (ism_job.beta_dev) was not finite or had |beta| > 1 */
 ism_status ism_workspace_status(const void* workspace, void* stream, uint32_t* flags);
 
 /* Same computation as ism_simulate without a workspace argument, for callers
@@ -223,7 +225,17 @@ typedef enum {
  * device pointer to [n_rcv][3] FP32 orientation vectors (any non-zero
  * length; a zero vector is flagged ISM_DEVICE_FLAG_POSITION).  A zero-filled
  * job struct is omnidirectional.  The gradient calls accept only
- * omnidirectional jobs (ISM_ERR_UNSUPPORTED otherwise). */
+ * omnidirectional jobs (ISM_ERR_UNSUPPORTED otherwise).
+ * beta_dev (may be NULL): a device pointer to the job's 6 reflection
+ * coefficients (the order of room.beta).  When set, the kernels read the
+ * coefficients there and room.beta is ignored, so a caller whose
+ * coefficients live on the GPU (an optimiser updating them) needs no copy to
+ * the host and no synchronisation; they are checked on the device (a
+ * non-finite value or |beta| > 1 flags ISM_DEVICE_FLAG_BETA and the job's
+ * pairs get no image), and the Sabine T60 of the diffuse tail (eq. (7)) is
+ * computed on the device with the host's FP64 operations, so the results are
+ * bitwise those of the same coefficients in room.beta.  Not accepted by the
+ * server (whose jobs are host-side). */
 typedef struct {
     ism_room room;
     const float* pos_src;
@@ -237,6 +249,7 @@ typedef struct {
     float* env_amp;
     int mic_pattern;
     const float* orient_rcv;
+    const float* beta_dev;
 } ism_job;
 
 /* Workspace bytes for ism_simulate_batch over these jobs. */

@@ -134,7 +134,7 @@ __global__ void __launch_bounds__(SH_WARPS * 32, 5) shell_kernel(const __grid_co
         if (q < J.Q && valid) {
             const float slo = fmaxf(fmaxf(sqrtf(sd2) * (1.0f - 1.0f / 1024.0f), (float)(ISM_SB * q) - 1.0f), 1e-30f);
             float bmax = 0.0f;
-            for (int w = 0; w < 6; ++w) bmax = fmaxf(bmax, fabsf(J.beta[w]));
+            for (int w = 0; w < 6; ++w) bmax = fmaxf(bmax, fabsf(ism_job_beta(J, w)));
             const int h = max(0, (int)floorf(slo * kinv / J.Lmax - 3.0f));
             const float decay = (h == 0) ? 1.0f : (bmax > 0.0f ? exp2f((float)h * log2f(bmax)) : 0.0f);
             amax = J.amp_scale / slo * decay * 1.001f;

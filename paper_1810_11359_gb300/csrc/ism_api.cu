@@ -82,7 +82,7 @@ ism_status validate_job(const ism_job& in, Validated& v, bool need_ptrs)
         if (!(j.room.L[a] > 0.0) || !isfin(j.room.L[a]))
             return fail(ISM_ERR_INVALID_ARG, "room size L[%d] = %g must be finite and > 0", a, j.room.L[a]);
     for (int w = 0; w < 6; ++w)
-        if (!isfin(j.room.beta[w]) || std::fabs(j.room.beta[w]) > 1.0f)
+        if (!j.beta_dev && (!isfin(j.room.beta[w]) || std::fabs(j.room.beta[w]) > 1.0f))
             return fail(ISM_ERR_INVALID_ARG, "beta[%d] = %g must satisfy |beta| <= 1", w, (double)j.room.beta[w]);
     if (!(j.room.c > 0.0f)) j.room.c = 343.0f;
     if (!isfin(j.room.c)) return fail(ISM_ERR_INVALID_ARG, "speed of sound must be finite");
@@ -177,6 +177,8 @@ ism_status plan(const Validated* vs, int n, ism_precision prec, bool backward, J
             J.nlo[a] = -(in.nb_img[a] / 2);
         }
         for (int w = 0; w < 6; ++w) J.beta[w] = in.room.beta[w];
+        J.beta_dev = in.beta_dev;
+        J.g2_c = 6.0 * std::log2(10.0);
         J.c = in.room.c;
         J.fs = in.fs;
         J.Nw = (float)v.Nw;
@@ -226,7 +228,7 @@ ism_status plan(const Validated* vs, int n, ism_precision prec, bool backward, J
         double beta_d[6];
         for (int w = 0; w < 6; ++w) beta_d[w] = in.room.beta[w];
         double T60 = t60_of(in.room.L, beta_d);
-        J.g2 = std::isfinite(T60) ? (float)(6.0 * std::log2(10.0) / ((double)in.fs * T60)) : 0.0f;
+        J.g2 = std::isfinite(T60) ? (float)(J.g2_c / ((double)in.fs * T60)) : 0.0f;   // (device: ism_job_g2)
         int W = (int)std::ceil(ISM_FIT_WINDOW_S * (double)in.fs - 1e-9);
         J.W_env = W < v.n_ism ? W : v.n_ism;
         J.vec4 = (v.n_S % 4 == 0) && (((uintptr_t)in.out & 15u) == 0);

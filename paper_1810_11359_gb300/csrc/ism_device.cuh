@@ -24,6 +24,32 @@ __device__ __forceinline__ int ism_find_job(const JobTable& t, long long cta, F 
     return lo;
 }
 
+// Reflection coefficient w of a job: from device memory when the caller keeps
+// the coefficients there, else from the job table.
+__device__ __forceinline__ float ism_job_beta(const JobDev& J, int w) { return J.beta_dev ? J.beta_dev[w] : J.beta[w]; }
+
+// g2 = 6 log2(10) / (f_s T60), the log2 of the power decay per sample of the
+// diffuse tail (eq. (7)-(8)).  For coefficients in device memory T60 comes
+// from the Sabine formula evaluated here with the host's FP64 operations in
+// the host's order, each rounded on its own (no contraction), so the value is
+// bitwise the one the host computes from the same coefficients.
+__device__ __forceinline__ float ism_job_g2(const JobDev& J)
+{
+    if (!J.beta_dev) return J.g2;
+    const double L0 = J.L[0], L1 = J.L[1], L2 = J.L[2];
+    const double S[6] = {__dmul_rn(L1, L2), __dmul_rn(L1, L2), __dmul_rn(L0, L2),
+                         __dmul_rn(L0, L2), __dmul_rn(L0, L1), __dmul_rn(L0, L1)};
+    double den = 0.0;
+    for (int i = 0; i < 6; ++i) {
+        const double b = (double)J.beta_dev[i];
+        den = __dadd_rn(den, __dmul_rn(S[i], __dsub_rn(1.0, __dmul_rn(b, b))));
+    }
+    if (!(den > 0.0)) return 0.0f;
+    const double T60 = __ddiv_rn(__dmul_rn(__dmul_rn(__dmul_rn(0.161, L0), L1), L2), den);
+    if (!(T60 < 1.0e300)) return 0.0f;
+    return (float)__ddiv_rn(J.g2_c, __dmul_rn((double)J.fs, T60));
+}
+
 // ---------------------------------------------------------------------------
 // Float-float (unevaluated sum hi + lo) arithmetic on correctly rounded FP32
 // operations (Dekker / Knuth two-sum).  Intrinsics keep the compiler from

@@ -46,9 +46,15 @@ __global__ void __launch_bounds__(128) geometry_kernel(const __grid_constant__ J
     const float* pr = J.pos_rcv + 3 * i_rcv;
 
     __shared__ int ok_s;
-    __shared__ double ps_s[3], pr_s[3];
+    __shared__ double ps_s[3], pr_s[3], beta_s[6];
     if (threadIdx.x == 0) {
-        int ok = 1;
+        int ok = 1, ok_beta = 1;
+        for (int w = 0; w < 6; ++w) {
+            const float b = ism_job_beta(J, w);   // checked on the host unless it lives on the device
+            beta_s[w] = (double)b;
+            if (J.beta_dev && !(fabsf(b) <= 1.0f)) ok_beta = 0;
+        }
+        if (!ok_beta) atomicOr(status, (uint32_t)ISM_DEVICE_FLAG_BETA);
         double d2 = 0.0;
         for (int a = 0; a < 3; ++a) {
             double xs = ps[a], xr = pr[a];
@@ -63,7 +69,7 @@ __global__ void __launch_bounds__(128) geometry_kernel(const __grid_constant__ J
             const double oo = (double)o[0] * o[0] + (double)o[1] * o[1] + (double)o[2] * o[2];
             if (!(oo > 0.0) || !(oo < 1e300)) ok = 0;
         }
-        ok_s = ok;
+        ok_s = ok && ok_beta;
         if (!ok) atomicOr(status, (uint32_t)ISM_DEVICE_FLAG_POSITION);
     }
     __syncthreads();
@@ -85,7 +91,7 @@ __global__ void __launch_bounds__(128) geometry_kernel(const __grid_constant__ J
         int an = n < 0 ? -n : n;
         int e0 = even ? an / 2 : (n - 1 < 0 ? 1 - n : n - 1) / 2;
         int e1 = even ? an / 2 : (n + 1 < 0 ? -(n + 1) : n + 1) / 2;
-        const double b0 = (double)J.beta[2 * a], b1 = (double)J.beta[2 * a + 1];
+        const double b0 = beta_s[2 * a], b1 = beta_s[2 * a + 1];
         double F = dpow_int(b0, e0) * dpow_int(b1, e1);
         float hi = (float)S;
         float lo = (float)(S - (double)hi);

@@ -52,6 +52,8 @@
 struct JobDev {
     double L[3];
     float beta[6];
+    const float* beta_dev;    // reflection coefficients in device memory (NULL: beta)
+    double g2_c;              // 6 log2(10): numerator of g2 (device-side T60)
     float c, fs, Nw;          // Nw = Tw * fs taps (real)
     float kfs_hi, kfs_lo;     // fs / c as a float-float pair
     float amp_scale;          // (fs / c) / (4 pi): A = F / (4 pi d) = F * amp_scale / s

@@ -390,6 +390,8 @@ ism_status prepare_request(ism_server* s, const ism_job* job, Request** out)
     if (!job->pos_src || !job->pos_rcv || !job->out)
         return ism_fail_message(ISM_ERR_INVALID_ARG, "pos_src, pos_rcv and out must be host pointers, not NULL");
     if (job->env_amp) return ism_fail_message(ISM_ERR_INVALID_ARG, "env_amp is not available through the server");
+    if (job->beta_dev)
+        return ism_fail_message(ISM_ERR_INVALID_ARG, "beta_dev is not available through the server (host jobs)");
     if (job->n_src < 1 || job->n_rcv < 1) return ism_fail_message(ISM_ERR_INVALID_ARG, "need n_src, n_rcv >= 1");
     const bool patterned = job->mic_pattern != ISM_MIC_OMNI;
     if (patterned && !job->orient_rcv)

@@ -50,11 +50,15 @@ __global__ void __launch_bounds__(256) finalize_kernel(const __grid_constant__ J
     __shared__ float red[256];
     float A = 0.0f;
     if (J.has_tail && J.W_env > 0) {
+        __shared__ float g2_s;
+        if (threadIdx.x == 0) g2_s = ism_job_g2(J);
+        __syncthreads();
+        const float g2 = g2_s;
         const int k0 = J.n_ism - J.W_env;
         float acc = 0.0f;
         for (int k = k0 + (int)threadIdx.x; k < J.n_ism; k += blockDim.x) {
             float h = out[k];
-            acc += h * h * exp2f(-J.g2 * (float)(J.n_ism - k));
+            acc += h * h * exp2f(-g2 * (float)(J.n_ism - k));
         }
         red[threadIdx.x] = acc;
         __syncthreads();
@@ -82,7 +86,10 @@ __global__ void __launch_bounds__(256) tail_kernel(const __grid_constant__ JobTa
     const int r = (int)(local / per_rir);
     const int c = (int)(local % per_rir);
     const float sqA = sqrtf(amp[J.rir_base + r]);
-    const float hg = 0.5f * J.g2;
+    __shared__ float g2_s;
+    if (threadIdx.x == 0) g2_s = ism_job_g2(J);
+    __syncthreads();
+    const float hg = 0.5f * g2_s;
     float* out = J.out + (long long)r * J.n_S;
     for (int i = 0; i < ISM_TAIL_CHUNK / 4 / 256; ++i) {
         int blk = blk0 + c * (ISM_TAIL_CHUNK / 4) + i * 256 + (int)threadIdx.x;

@@ -26,6 +26,9 @@ PRECISIONS = {"fp32": 0, "fp16x2": 1, "bf16x2": 2, "lut": 3, "fp32_direct": 4, "
 # receiver polar patterns (ism_mic_pattern): g = alpha + (1 - alpha) cos(theta)
 MIC_PATTERNS = {"omni": 0, "subcardioid": 1, "cardioid": 2, "hypercardioid": 3, "bidirectional": 4}
 ISM_ERR_TIMEOUT_CODE = 6
+ISM_DEVICE_FLAG_POSITION = 1   # include/ism.h ISM_DEVICE_FLAG_*
+ISM_DEVICE_FLAG_BIN = 2
+ISM_DEVICE_FLAG_BETA = 4
 STATUS_CODES = {v: k for k, v in STATUS_NAMES.items()}
 DEVICE_FLAG_POSITION = 1
 DEVICE_FLAG_BIN = 2
@@ -49,7 +52,7 @@ class ism_job(ctypes.Structure):
                 ("Tmax", ctypes.c_float), ("fs", ctypes.c_float), ("Tdiff", ctypes.c_float), ("Tw", ctypes.c_float),
                 ("seed", ctypes.c_uint64),
                 ("out", ctypes.c_void_p), ("env_amp", ctypes.c_void_p),
-                ("mic_pattern", ctypes.c_int), ("orient_rcv", ctypes.c_void_p)]
+                ("mic_pattern", ctypes.c_int), ("orient_rcv", ctypes.c_void_p), ("beta_dev", ctypes.c_void_p)]
 
 
 class ism_grad_job(ctypes.Structure):
@@ -326,6 +329,10 @@ def ism_simulate(L, beta, pos_src, pos_rcv, nb_img, Tmax, fs, Tdiff=0.0, Tw=0.0,
     return out
 
 
+_host_sizes = {}     # (arguments) -> host-entry workspace bytes (the sizing call plans the whole call)
+_lanes_setting = [2]
+
+
 def ism_simulate_host(L, beta, pos_src, pos_rcv, nb_img, Tmax, fs, Tdiff=0.0, Tw=0.0, c=343.0, prec: str = "fp32",
                       seed: int = 0, out: Optional[np.ndarray] = None, workspace: Optional[Workspace] = None,
                       stream=None) -> np.ndarray:
@@ -333,14 +340,25 @@ def ism_simulate_host(L, beta, pos_src, pos_rcv, nb_img, Tmax, fs, Tdiff=0.0, Tw
     the copies happen inside the library call (synchronous)."""
     ps = np.ascontiguousarray(np.asarray(pos_src, dtype=np.float32).reshape(-1, 3))
     pr = np.ascontiguousarray(np.asarray(pos_rcv, dtype=np.float32).reshape(-1, 3))
-    n_S = ism_rir_length(Tmax, fs)
+    r = _room(L, beta, c)
+    nb = _nb(nb_img)
+    key = (bytes(r), bytes(nb), ps.shape[0], pr.shape[0], float(Tmax), float(fs), float(Tdiff or 0.0),
+           float(Tw or 0.0), prec, _lanes_setting[0])
+    sized = _host_sizes.get(key)
+    if sized is None:
+        b = ctypes.c_size_t()
+        _check(load().ism_host_workspace_size(ctypes.byref(r), int(ps.shape[0]), int(pr.shape[0]), nb, float(Tmax),
+                                              float(fs), float(Tdiff or 0.0), float(Tw or 0.0), PRECISIONS[prec],
+                                              ctypes.byref(b)))
+        if len(_host_sizes) > 256:
+            _host_sizes.clear()
+        sized = _host_sizes[key] = (b.value, ism_rir_length(Tmax, fs))
+    nbytes, n_S = sized
     if out is None:
         out = np.empty((ps.shape[0], pr.shape[0], n_S), dtype=np.float32)
-    nbytes = ism_host_workspace_size(L, beta, ps.shape[0], pr.shape[0], nb_img, Tmax, fs, Tdiff, Tw, c, prec)
     buf = _workspace(workspace, nbytes)
-    r = _room(L, beta, c)
     _check(load().ism_simulate_host(ctypes.byref(r), ctypes.c_void_p(ps.ctypes.data), int(ps.shape[0]),
-                                    ctypes.c_void_p(pr.ctypes.data), int(pr.shape[0]), _nb(nb_img), float(Tmax),
+                                    ctypes.c_void_p(pr.ctypes.data), int(pr.shape[0]), nb, float(Tmax),
                                     float(fs), float(Tdiff or 0.0), float(Tw or 0.0), PRECISIONS[prec],
                                     int(seed) & (2 ** 64 - 1), ctypes.c_void_p(out.ctypes.data),
                                     ctypes.c_void_p(buf.data_ptr()), int(buf.numel()), _stream_ptr(stream)))
@@ -377,9 +395,12 @@ def ism_workspace_status(buf, stream=None) -> int:
 def make_job(L, beta, pos_src, pos_rcv, nb_img, Tmax, fs, out, Tdiff=0.0, Tw=0.0, c=343.0, seed=0,
              env_amp=None, mic_pattern: str = "omni", orient_rcv=None) -> ism_job:
     """An ism_job over CUDA tensors (the tensors must stay alive during the call);
-    orient_rcv: [n_rcv, 3] CUDA FP32 tensor for a polar pattern."""
+    orient_rcv: [n_rcv, 3] CUDA FP32 tensor for a polar pattern; beta: 6 host
+    values, or a contiguous FP32 CUDA tensor of 6 read in place (beta_dev)."""
     j = ism_job()
-    j.room = _room(L, beta, c)
+    on_device = hasattr(beta, "data_ptr")
+    j.room = _room(L, [0.0] * 6 if on_device else beta, c)
+    j.beta_dev = beta.data_ptr() if on_device else None
     j.pos_src = pos_src.data_ptr()
     j.n_src = int(pos_src.shape[0])
     j.pos_rcv = pos_rcv.data_ptr()
@@ -399,13 +420,18 @@ def make_jobs_strided(L, beta, pos_src, pos_rcv, nb_img, Tmax, fs, out, Tdiff=0.
     """B jobs over batched CUDA tensors pos_src [B, S, 3], pos_rcv [B, M, 3],
     out [B, S, M, n_S] (contiguous FP32; they must stay alive during the call):
     one ctypes array filled through a numpy view, without per-room tensor
-    views.  L [B, 3], beta [B, 6], nb_img [B, 3] are host arrays."""
+    views.  L [B, 3], nb_img [B, 3] are host arrays; beta [B, 6] is a host
+    array or a contiguous FP32 CUDA tensor (read by the kernels in place:
+    ism_job.beta_dev)."""
     B = int(pos_src.shape[0])
     S, M = int(pos_src.shape[1]), int(pos_rcv.shape[1])
     arr = (ism_job * B)()
     v = np.frombuffer(arr, dtype=np.dtype(ism_job), count=B)
     v["room"]["L"] = np.asarray(L, np.float64).reshape(B, 3)
-    v["room"]["beta"] = np.asarray(beta, np.float64).reshape(B, 6).astype(np.float32)
+    if hasattr(beta, "data_ptr"):
+        v["beta_dev"] = np.uint64(beta.data_ptr()) + np.arange(B, dtype=np.uint64) * np.uint64(24)
+    else:
+        v["room"]["beta"] = np.asarray(beta, np.float64).reshape(B, 6).astype(np.float32)
     v["room"]["c"] = np.float32(c)
     idx = np.arange(B, dtype=np.uint64)
     v["pos_src"] = np.uint64(pos_src.data_ptr()) + idx * np.uint64(S * 3 * 4)
@@ -540,6 +566,7 @@ def ism_set_lanes(n_lanes: int):
     """1: every launch on the caller's stream; 2 (default): large calls run
     as two halves on two internal streams."""
     _check(load().ism_set_lanes(int(n_lanes)))
+    _lanes_setting[0] = int(n_lanes)
 
 
 def ism_profile_enable(enable: bool = True):

@@ -14,6 +14,9 @@ Shapes: one room -- L [3], beta [6], pos_src [S, 3], pos_rcv [M, 3] ->
 h [S, M, n_S]; B rooms -- L [B, 3], beta [B, 6], pos_src [B, S, 3],
 pos_rcv [B, M, 3] -> h [B, S, M, n_S].  All rooms share Tmax, fs, Tdiff and
 Tw.  The samples of a diffuse tail (k >= ceil(Tdiff fs)) carry no gradient.
+A CUDA beta is read by the kernels in place (ism_job.beta_dev): a training
+step then never waits for the GPU; a CPU beta is copied into the job structs
+(and its gradient back to the host, which waits for the backward pass).
 """
 from __future__ import annotations
 
@@ -40,8 +43,9 @@ class _Spec:
     workspace: Optional[ism.Workspace]
 
 
-def _jobs(spec: _Spec, beta_h: np.ndarray, ps: torch.Tensor, pr: torch.Tensor, out: torch.Tensor):
-    return ism.make_jobs_strided(spec.L, beta_h, ps, pr, spec.nb_img, spec.Tmax, spec.fs, out, Tdiff=spec.Tdiff,
+def _jobs(spec: _Spec, beta, ps: torch.Tensor, pr: torch.Tensor, out: torch.Tensor):
+    # beta: [B, 6] host array, or FP32 CUDA tensor read in place (ism_job.beta_dev)
+    return ism.make_jobs_strided(spec.L, beta, ps, pr, spec.nb_img, spec.Tmax, spec.fs, out, Tdiff=spec.Tdiff,
                                  Tw=spec.Tw, c=spec.c, seed=spec.seed)
 
 
@@ -52,11 +56,14 @@ class _RoomsRIR(torch.autograd.Function):
         n_S = ism.ism_rir_length(spec.Tmax, spec.fs)
         ps = pos_src.detach().float().contiguous()
         pr = pos_rcv.detach().float().contiguous()
-        beta_h = beta.detach().double().cpu().numpy().reshape(B, 6)
+        if beta.is_cuda:   # read in place by the kernels: no copy to the host, no synchronisation
+            beta_k = beta.detach().to(device=ps.device, dtype=torch.float32).reshape(B, 6).contiguous()
+        else:
+            beta_k = beta.detach().double().numpy().reshape(B, 6)
         out = torch.empty((B, S, M, n_S), dtype=torch.float32, device=ps.device)
-        ism.ism_simulate_batch(_jobs(spec, beta_h, ps, pr, out), prec=spec.prec, workspace=spec.workspace)
+        ism.ism_simulate_batch(_jobs(spec, beta_k, ps, pr, out), prec=spec.prec, workspace=spec.workspace)
         ctx.spec = spec
-        ctx.beta_h = beta_h
+        ctx.beta_k = beta_k
         ctx.beta_meta = (beta.dtype, beta.device)
         ctx.save_for_backward(ps, pr)
         return out
@@ -70,7 +77,7 @@ class _RoomsRIR(torch.autograd.Function):
         gb = torch.empty((B, 6), dtype=torch.float32, device=ps.device)
         gs = torch.empty((B, S, 3), dtype=torch.float32, device=ps.device)
         gr = torch.empty((B, M, 3), dtype=torch.float32, device=ps.device)
-        gjobs = ism.make_grad_jobs_strided(_jobs(spec, ctx.beta_h, ps, pr, go), go, gb, gs, gr)
+        gjobs = ism.make_grad_jobs_strided(_jobs(spec, ctx.beta_k, ps, pr, go), go, gb, gs, gr)
         ism.ism_simulate_backward_batch(gjobs, workspace=spec.workspace)
         dtype, device = ctx.beta_meta
         return gb.to(dtype=dtype, device=device), gs, gr, None

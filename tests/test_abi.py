@@ -175,3 +175,39 @@ def test_strided_job_arrays_match_per_room_jobs():
         g = ism.make_grad_job(j, out[b], gb[b], gs[b], gr[b])
         assert bytes(garr[b]) == bytes(g)
     assert ctypes.sizeof(arr) == B * ctypes.sizeof(ism.ism_job)
+
+
+def test_binding_struct_layouts_match_the_header(tmp_path):
+    """The ctypes structs of the binding have the sizes and field offsets the
+    C compiler gives the structs of include/ism.h (a C program built here
+    prints them)."""
+    import ctypes
+    import os
+    import shutil
+    import subprocess
+    import pytest
+    from paper_1810_11359_gb300 import ism
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    structs = {"ism_room": ism.ism_room, "ism_job": ism.ism_job, "ism_grad_job": ism.ism_grad_job,
+               "ism_server_config": ism.ism_server_config, "ism_server_stats": ism.ism_server_stats}
+    lines = ["#include <stdio.h>", "#include <stddef.h>", '#include "ism.h"', "int main(void) {"]
+    for name, cls in structs.items():
+        lines.append(f'printf("{name} size %zu\\n", sizeof({name}));')
+        for f in cls._fields_:
+            lines.append(f'printf("{name} {f[0]} %zu\\n", offsetof({name}, {f[0]}));')
+    lines += ["return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    inc = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include")
+    subprocess.run([cc, "-std=c99", "-I", inc, str(src), "-o", str(exe)], check=True)
+    got = {}
+    for line in subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.splitlines():
+        name, field, val = line.split()
+        got[(name, field)] = int(val)
+    for name, cls in structs.items():
+        assert got[(name, "size")] == ctypes.sizeof(cls), name
+        for f in cls._fields_:
+            assert got[(name, f[0])] == getattr(cls, f[0]).offset, (name, f[0])
