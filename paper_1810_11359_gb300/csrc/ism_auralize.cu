@@ -12,14 +12,17 @@
 // T0 + 4 l + r, r = 0 .. 3, for the 8 microphones (32 accumulators).  For one
 // segment the taps k that connect it to the tile are walked in chunks of 128:
 // the chunk's taps of the 8 microphones and the signal window it needs (the
-// samples outside the segment zeroed) are staged in the warp's shared memory.
-// The taps go in groups of 4: for taps k .. k + 3 the lane's 16 products need
-// the 7 signal values x[T0 + 4 l - k - 3 .. T0 + 4 l - k + 3], two aligned
-// float4 of the window of which the later one is the previous group's earlier
-// one, so a group costs one 128-bit signal load (the 32 lanes read 512
-// contiguous bytes) and eight broadcast 128-bit tap loads (h[p][m][k] for the
-// 8 microphones, two per tap) for 128 FFMA; every shared address is the
-// lane's base plus a constant.  (8 outputs per lane: fewer CTAs than SM
+// samples outside the segment zeroed) are staged in the warp's shared memory,
+// the taps as [microphone][k] rows copied with 128-bit loads when every RIR
+// row starts on a 16-byte boundary (n_S a multiple of 4; the chunk's first
+// tap rounded down to a multiple of 4 -- the extra taps meet zeroed signal
+// samples), else one float at a time.  The taps go in groups of 4: for taps
+// k .. k + 3 the lane's 16 products need the 7 signal values
+// x[T0 + 4 l - k - 3 .. T0 + 4 l - k + 3], two aligned float4 of the window of
+// which the later one is the previous group's earlier one, so a group costs
+// one 128-bit signal load (the 32 lanes read 512 contiguous bytes) and eight
+// broadcast 128-bit tap loads (taps k .. k + 3 of each microphone) for 128
+// FFMA; every shared address is the lane's base plus a constant.  (8 outputs per lane: fewer CTAs than SM
 // slots, 13 % of the warps active, measured 10 % slower.)
 #include "ism_device.cuh"
 
@@ -35,7 +38,7 @@ namespace {
 static_assert(AU_R == 4 && AU_KC % 4 == 0, "the signal window is read as float4 groups of 4 taps");
 
 struct AuWarp {
-    float4 h[AU_KC][AU_M / 4];       // taps of the chunk: [k][microphone]
+    float4 h[AU_M][AU_KC / 4];       // taps of the chunk: [microphone][k / 4]
     float4 x[AU_XN / 4];             // signal window
 };
 
@@ -59,6 +62,7 @@ __device__ __forceinline__ int au_start(int p, int n_x, int n_points, const int*
     return min(max(starts[p], 0), n_x);
 }
 
+template <bool VEC>   // 128-bit tap staging (16-byte aligned RIR rows)
 __global__ void __launch_bounds__(AU_WARPS * 32, 6) auralize_kernel(const float* __restrict__ x, int n_x,
                                                                  const float* __restrict__ h, int n_points,
                                                                  int n_mics, int n_s,
@@ -87,19 +91,30 @@ __global__ void __launch_bounds__(AU_WARPS * 32, 6) auralize_kernel(const float*
             const int a = au_start(p, n_x, n_points, starts);
             const int b = max(a, p + 1 < n_points ? au_start(p + 1, n_x, n_points, starts) : n_x);
             if (b <= a) continue;
-            // taps linking [a, b) to the tile
-            const long long k_lo = max(T0 - b + 1, 0ll);
+            // taps linking [a, b) to the tile (the vector form starts on a multiple of 4)
+            const long long k_lo = VEC ? (max(T0 - b + 1, 0ll) & ~3ll) : max(T0 - b + 1, 0ll);
             const long long k_hi = min(T0 + AU_TILE - 1 - a, (long long)n_s - 1);
             const float* hp = h + (long long)p * n_mics * n_s;
             for (long long k0 = k_lo; k0 <= k_hi; k0 += AU_KC) {
                 __syncwarp();
                 // taps k0 .. k0 + KC - 1 of the 8 microphones (0 past k_hi or past the array)
-                for (int e = lane; e < AU_KC * AU_M; e += 32) {   // coalesced along the taps
-                    const int m = e / AU_KC, kk = e % AU_KC;
-                    const long long k = k0 + kk;
-                    float v = 0.0f;
-                    if (k <= k_hi && m0 + m < n_mics) v = hp[(long long)(m0 + m) * n_s + k];
-                    reinterpret_cast<float*>(&W.h[kk][0])[m] = v;
+                if (VEC) {
+                    for (int e = lane; e < AU_M * AU_KC / 4; e += 32) {   // 32 lanes: 512 contiguous bytes
+                        const int m = e / (AU_KC / 4), kq = e % (AU_KC / 4);
+                        const long long k = k0 + 4 * kq;   // k0 % 4 == 0 and n_s % 4 == 0: k .. k + 3 < n_s
+                        float4 v = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+                        if (k <= k_hi && m0 + m < n_mics)
+                            v = *reinterpret_cast<const float4*>(hp + (long long)(m0 + m) * n_s + k);
+                        W.h[m][kq] = v;
+                    }
+                } else {
+                    for (int e = lane; e < AU_KC * AU_M; e += 32) {   // coalesced along the taps
+                        const int m = e / AU_KC, kk = e % AU_KC;
+                        const long long k = k0 + kk;
+                        float v = 0.0f;
+                        if (k <= k_hi && m0 + m < n_mics) v = hp[(long long)(m0 + m) * n_s + k];
+                        reinterpret_cast<float*>(&W.h[m][0])[kk] = v;
+                    }
                 }
                 // signal window: x[T0 - k0 - KC + 1 + j], zero outside [a, b)
                 const long long xb = T0 - k0 - AU_KC + 1;
@@ -114,19 +129,28 @@ __global__ void __launch_bounds__(AU_WARPS * 32, 6) auralize_kernel(const float*
                 // 4 l + KC - 4 - 4 g, xb4 = the next float4 (the previous group's xa)
                 const float4* xl = W.x + lane + (AU_KC - 4) / 4;
                 float4 xb4 = xl[1];
+                // the groups that hold taps <= k_hi (the last chunk of a segment is partial)
+                const int ng = (int)min((long long)(AU_KC / 4), (k_hi - k0) / 4 + 1);
 #pragma unroll 2
-                for (int g = 0; g < AU_KC / 4; ++g) {
+                for (int g = 0; g < ng; ++g) {
                     const float4 xa = xl[-g];
                     const float v[8] = {xa.x, xa.y, xa.z, xa.w, xb4.x, xb4.y, xb4.z, xb4.w};
+                    float hv[AU_M][4];   // taps 4 g .. 4 g + 3 of each microphone
 #pragma unroll
-                    for (int u = 0; u < 4; ++u) {
-                        const float4 h0 = W.h[4 * g + u][0], h1 = W.h[4 * g + u][1];
-                        const float hv[AU_M] = {h0.x, h0.y, h0.z, h0.w, h1.x, h1.y, h1.z, h1.w};
+                    for (int m = 0; m < AU_M; ++m) {
+                        const float4 hm = W.h[m][g];
+                        hv[m][0] = hm.x;
+                        hv[m][1] = hm.y;
+                        hv[m][2] = hm.z;
+                        hv[m][3] = hm.w;
+                    }
+#pragma unroll
+                    for (int u = 0; u < 4; ++u)
 #pragma unroll
                         for (int r = 0; r < AU_R; ++r)
 #pragma unroll
-                            for (int m = 0; m < AU_M; ++m) acc[r][m] = __fmaf_rn(v[3 + r - u], hv[m], acc[r][m]);
-                    }
+                            for (int m = 0; m < AU_M; ++m)
+                                acc[r][m] = __fmaf_rn(v[3 + r - u], hv[m][u], acc[r][m]);
                     xb4 = xa;
                 }
             }
@@ -168,9 +192,11 @@ int ism_launch_auralize(const float* x, int n_x, const float* h, int n_points, i
     const long long n_out = (long long)n_x + n_s - 1;
     const dim3 grid((unsigned)((n_out + AU_TILE - 1) / AU_TILE), (unsigned)((n_mics + AU_M - 1) / AU_M));
     const size_t sm = ism_auralize_smem();
-    cudaError_t e = cudaFuncSetAttribute(auralize_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    // 128-bit tap rows when every row starts on a 16-byte boundary
+    const bool vec = (n_s % 4 == 0) && (((uintptr_t)h & 15u) == 0);
+    auto kern = vec ? auralize_kernel<true> : auralize_kernel<false>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (e != cudaSuccess) return (int)e;
-    auralize_kernel<<<grid, AU_WARPS * 32, sm, (cudaStream_t)stream>>>(x, n_x, h, n_points, n_mics, n_s, starts, y,
-                                                                       (int)n_out);
+    kern<<<grid, AU_WARPS * 32, sm, (cudaStream_t)stream>>>(x, n_x, h, n_points, n_mics, n_s, starts, y, (int)n_out);
     return (int)cudaGetLastError();
 }

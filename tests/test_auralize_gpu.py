@@ -43,11 +43,12 @@ def run(x, h, starts=None):
 
 
 @pytest.mark.parametrize("n_x,n_points,n_mics,n_s", [(1000, 7, 3, 300), (257, 1, 9, 1), (4099, 64, 8, 517),
-                                                     (300, 300, 2, 129), (50, 3, 1, 2000)])
+                                                     (300, 300, 2, 129), (50, 3, 1, 2000), (1500, 11, 9, 1024)])
 def test_random_shapes_against_oracle(n_x, n_points, n_mics, n_s):
-    """Ragged sizes: tails of the 256-output tiles and 128-tap chunks, mic groups
+    """Ragged sizes: tails of the 128-output tiles and 128-tap chunks, mic groups
     of 8 plus a remainder, one segment, one sample per segment, RIRs longer
-    than the signal."""
+    than the signal; RIR lengths that are multiples of 4 take the 128-bit tap
+    staging, the others the scalar one."""
     rng = np.random.default_rng(n_x + n_points)
     x = rng.normal(size=n_x).astype(np.float32)
     h = rng.normal(size=(n_points, n_mics, n_s)).astype(np.float32)
