@@ -351,7 +351,7 @@ def run_serving(args):
         return {"requests": n, "rirs": rirs, "seconds": dur, "rirs_per_s": rirs / dur, "requests_per_s": n / dur,
                 "p50_ms": _pct(lat, 50) * 1e3, "p99_ms": _pct(lat, 99) * 1e3, "max_ms": max(lat) * 1e3}
 
-    srv = ism.Server(hbm_budget=8 << 30, max_inflight=3, max_batch=32, prec=args.prec)
+    srv = ism.Server(hbm_budget=8 << 30, max_inflight=6, max_batch=32, prec=args.prec)
     warm = prepared(None)[:300]
     run(srv, warm)
     sat_reqs = prepared(None)
@@ -368,7 +368,7 @@ def run_serving(args):
         "ms_per_step": sat["seconds"] * 1e3, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": DTYPES[args.prec], "data": "synthetic (seeded serving stream)",
         "config": {"workload": "serving_3-10m_rt0.2-1.0_1-16rcv_16k", "requests_per_pattern": args.requests,
-                   "hbm_budget_bytes": 8 << 30, "max_inflight": 3, "max_batch": 32,
+                   "hbm_budget_bytes": 8 << 30, "max_inflight": 6, "max_batch": 32,
                    "latency": "arrival to RIRs in the caller's host buffer (client submit delay + server time)",
                    "client": "arrived requests handed over in one ism_server_submit_batch call, "
                              "page-locked result buffers"},
