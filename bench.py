@@ -571,8 +571,8 @@ def main():
     if rank == 0 or world == 1:
         __graft_entry__.build()
     if world > 1:
+        torch.cuda.set_device(local_rank)   # before the process group, so NCCL binds this rank's GPU
         dist.init_process_group("nccl")
-        torch.cuda.set_device(local_rank)
         dist.barrier()
         __graft_entry__.build()
     else:
