@@ -165,6 +165,34 @@ def test_batch_equals_separate_calls_bitwise():
         assert np.array_equal(out.cpu().numpy().view(np.uint32), alone.view(np.uint32))
 
 
+@pytest.mark.parametrize("order", ["alike", "different"])
+def test_fused_and_direct_jobs_in_one_set_equal_separate_calls(order):
+    """One launch set mixing fused jobs (dense rooms) and a direct job (a sparse
+    48 kHz room) between them: with the fused jobs' shell counts alike the
+    fused CTAs go by shell rank over all their RIRs, with different counts job
+    by job; either way every job's RIRs are bitwise those of its own call."""
+    dense = [(np.array([4.0, 3.5, 2.8]), [[1.1, 2.4, 1.3]], [[2.9, 0.8, 1.7], [0.7, 3.0, 2.2]]),
+             (np.array([3.6, 4.2, 2.9]), [[2.5, 1.0, 0.9]], [[0.9, 3.1, 2.0]])]
+    Tmax_dense = [0.2, 0.2] if order == "alike" else [0.2, 0.35]
+    sparse = (np.array([10.0, 8.0, 3.5]), [[2.0, 3.0, 1.2]], [[7.5, 5.0, 1.6], [7.6, 5.1, 1.6]])
+    specs = [(dense[0], Tmax_dense[0], 16000.0), (sparse, 0.05, 48000.0), (dense[1], Tmax_dense[1], 16000.0)]
+    jobs, keep, refs = [], [], []
+    for (L, src, rcv), Tmax, fs in specs:
+        beta = oracle.beta_sabine(L, 0.5)
+        Tw = 32 / fs
+        N = oracle.nb_img_from_t(Tmax, L, 343.0, Tw)
+        refs.append(lib_run(L, beta, src, rcv, N, Tmax, fs, Tw=Tw))
+        ps = torch.as_tensor(np.asarray(src, np.float32)).cuda()
+        pr = torch.as_tensor(np.asarray(rcv, np.float32)).cuda()
+        out = torch.full(refs[-1].shape, float("nan"), device="cuda")
+        keep.append((ps, pr, out))
+        jobs.append(ism.make_job(L, beta, ps, pr, N, Tmax, fs, out, Tw=Tw))
+    ism.ism_simulate_batch(jobs)
+    torch.cuda.synchronize()
+    for (ps, pr, out), ref in zip(keep, refs):
+        assert np.array_equal(out.cpu().numpy().view(np.uint32), ref.view(np.uint32))
+
+
 def test_batched_config_full_size_sampled_rirs():
     """The 128-RIR 6 x 5 x 3 m workload at full size, in the bench's launch;
     four RIRs compared in full against the oracle."""
