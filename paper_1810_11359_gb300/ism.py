@@ -329,7 +329,7 @@ def ism_simulate(L, beta, pos_src, pos_rcv, nb_img, Tmax, fs, Tdiff=0.0, Tw=0.0,
     return out
 
 
-_host_sizes = {}     # (arguments) -> host-entry workspace bytes (the sizing call plans the whole call)
+_host_sizes = {}     # (arguments) -> (room struct, nb, host-entry workspace bytes, RIR length)
 _lanes_setting = [2]
 
 
@@ -338,22 +338,24 @@ def ism_simulate_host(L, beta, pos_src, pos_rcv, nb_img, Tmax, fs, Tdiff=0.0, Tw
                       stream=None) -> np.ndarray:
     """Same as ism_simulate from host (numpy) positions into a host array;
     the copies happen inside the library call (synchronous)."""
-    ps = np.ascontiguousarray(np.asarray(pos_src, dtype=np.float32).reshape(-1, 3))
-    pr = np.ascontiguousarray(np.asarray(pos_rcv, dtype=np.float32).reshape(-1, 3))
-    r = _room(L, beta, c)
-    nb = _nb(nb_img)
-    key = (bytes(r), bytes(nb), ps.shape[0], pr.shape[0], float(Tmax), float(fs), float(Tdiff or 0.0),
-           float(Tw or 0.0), prec, _lanes_setting[0])
-    sized = _host_sizes.get(key)
-    if sized is None:
+    ps = np.ascontiguousarray(pos_src, dtype=np.float32).reshape(-1, 3)
+    pr = np.ascontiguousarray(pos_rcv, dtype=np.float32).reshape(-1, 3)
+    # the room struct, images per axis, workspace bytes and RIR length of these arguments
+    key = (np.asarray(L, np.float64).tobytes(), np.asarray(beta, np.float64).tobytes(),
+           np.asarray(nb_img, np.int64).tobytes(), ps.shape[0], pr.shape[0], float(Tmax), float(fs),
+           float(Tdiff or 0.0), float(Tw or 0.0), float(c), prec, _lanes_setting[0])
+    hit = _host_sizes.get(key)
+    if hit is None:
+        r = _room(L, beta, c)
+        nb = _nb(nb_img)
         b = ctypes.c_size_t()
         _check(load().ism_host_workspace_size(ctypes.byref(r), int(ps.shape[0]), int(pr.shape[0]), nb, float(Tmax),
                                               float(fs), float(Tdiff or 0.0), float(Tw or 0.0), PRECISIONS[prec],
                                               ctypes.byref(b)))
         if len(_host_sizes) > 256:
             _host_sizes.clear()
-        sized = _host_sizes[key] = (b.value, ism_rir_length(Tmax, fs))
-    nbytes, n_S = sized
+        hit = _host_sizes[key] = (r, nb, b.value, ism_rir_length(Tmax, fs))
+    r, nb, nbytes, n_S = hit
     if out is None:
         out = np.empty((ps.shape[0], pr.shape[0], n_S), dtype=np.float32)
     buf = _workspace(workspace, nbytes)
