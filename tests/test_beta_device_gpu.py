@@ -6,7 +6,8 @@ must be bitwise the one of the same coefficients passed in room.beta: the
 fused FP32 form, the direct form with a diffuse tail, the gradients, and the
 autograd front end with a CUDA beta.  A coefficient outside [-1, 1] in device
 memory is flagged by the geometry kernel (ISM_DEVICE_FLAG_BETA) and its job
-gets no image.
+gets no image.  With the training state on the device a whole training step
+can be captured in a CUDA graph; a replay is bitwise the eager step.
 """
 import numpy as np
 import pytest
@@ -115,3 +116,45 @@ def test_autograd_with_cuda_beta_matches_cpu_beta():
         got.append([h.detach().cpu().numpy(), beta.grad.cpu().numpy(), ps.grad.cpu().numpy(), pr.grad.cpu().numpy()])
     for a, b in zip(*got):
         assert np.array_equal(a.view(np.uint32), b.view(np.uint32))
+
+
+def test_training_step_captured_in_a_cuda_graph_matches_eager():
+    """The library makes no synchronous call and no allocation inside its
+    calls, so a whole training step (forward batch, loss, autograd backward
+    through the adjoint) can be captured in a CUDA graph; a replay gives
+    bitwise the eager step's loss and gradients."""
+    from paper_1810_11359_gb300 import torch_ism
+    rooms = workloads.differentiation_rooms(70)   # two launch sets of jobs
+    L = np.stack([r.L for r in rooms])
+    beta0 = np.stack([ism.ism_beta_sabine(r.L, r.rt60) for r in rooms]).astype(np.float32)
+    Tw = rooms[0].window()
+    nb = np.stack([ism.ism_nb_img_from_t(0.4, r.L, 343.0, Tw) for r in rooms])
+    beta = torch.tensor(beta0, device="cuda", requires_grad=True)
+    ps = torch.tensor(np.stack([r.pos_src for r in rooms]), device="cuda", requires_grad=True)
+    pr = torch.tensor(np.stack([r.pos_rcv for r in rooms]), device="cuda", requires_grad=True)
+    target = torch.randn((70, 1, 1, ism.ism_rir_length(0.4, 16000.0)), device="cuda") * 1e-3
+    ws = ism.Workspace()
+
+    def step():
+        h = torch_ism.rir(L, beta, ps, pr, 0.4, 16000.0, Tw=Tw, nb_img=nb, workspace=ws)
+        loss = ((h - target) ** 2).sum()
+        beta.grad = ps.grad = pr.grad = None
+        loss.backward()
+        return loss
+
+    side = torch.cuda.Stream()
+    side.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(side):
+        for _ in range(3):
+            eager_loss = step()
+    torch.cuda.current_stream().wait_stream(side)
+    torch.cuda.synchronize()
+    eager = [eager_loss.detach().clone(), beta.grad.clone(), ps.grad.clone(), pr.grad.clone()]
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph):
+        g_loss = step()
+    for _ in range(2):
+        graph.replay()
+    torch.cuda.synchronize()
+    for a, b in zip(eager, [g_loss, beta.grad, ps.grad, pr.grad]):
+        assert torch.equal(a, b)
