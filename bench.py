@@ -476,8 +476,12 @@ def run_differentiation(args, world, rank, dist):
         loss_h = float(g_loss.item())
         walls.append(time.perf_counter() - w0)
     wall = sum(walls) / len(walls)
+    from paper_1810_11359_gb300 import replicas
+    ms = replicas.max_over_ranks(ms, device=dev)           # the slowest rank's step (replicas)
+    wall = replicas.max_over_ranks(wall, device=dev)
     line = {
-        "metric": METRIC, "value": B / (ms * 1e-3), "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "metric": METRIC, "value": replicas.whole_job_rate(B, world, ms * 1e-3), "unit": UNIT, "n_gpus": world,
+        "steps": args.steps,
         "warmup": max(args.warmup, 3), "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32", "data": "synthetic (seeded rooms and perturbed targets)",
         "config": {"workload": "differentiation_256rooms_4-8m_rt0.3-0.8_16k_0.4s", "rooms_per_step": B,
@@ -488,7 +492,8 @@ def run_differentiation(args, world, rank, dist):
         "library_device_ms_per_step": dev_ms,
         "stage_ms_per_step": {k: v[0] / args.steps for k, v in prof.items()},
         "gpu_launches": int(sum(v[1] for v in prof.values())),
-        "e2e": {"value": B / wall, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 4,
+        "e2e": {"value": replicas.whole_job_rate(B, world, wall), "unit": UNIT, "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 4,
                 "ms_per_step": wall * 1e3,
                 "entry": "torch_ism.rir + loss.backward() captured in a CUDA graph, training state on "
                          "the device, loss read to the host after every replay"},
@@ -552,8 +557,11 @@ def run_moving_source(args, world, rank, dist):
     peak_tops = n_sm * 128 * sm_mhz * 1e6 / 1e12
     macs = pr.shape[0] * x.numel() * n_s
     rirs = ps.shape[0] * pr.shape[0]
+    from paper_1810_11359_gb300 import replicas
+    ms = replicas.max_over_ranks(ms, device=dev)           # the slowest rank's step (replicas)
     line = {
-        "metric": METRIC, "value": rirs / (ms * 1e-3), "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "metric": METRIC, "value": replicas.whole_job_rate(rirs, world, ms * 1e-3), "unit": UNIT, "n_gpus": world,
+        "steps": args.steps,
         "warmup": max(args.warmup, 3), "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32", "data": "synthetic (seeded trajectory and source signal)",
         "config": {"workload": "moving_source_10x8x3.5_rt1.2_64x8_48k_1.2s_signal1.2s", "rirs_per_step": rirs,
