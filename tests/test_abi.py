@@ -211,3 +211,38 @@ def test_binding_struct_layouts_match_the_header(tmp_path):
         assert got[(name, "size")] == ctypes.sizeof(cls), name
         for f in cls._fields_:
             assert got[(name, f[0])] == getattr(cls, f[0]).offset, (name, f[0])
+
+
+def test_plan_takes_the_fused_form_for_dense_rooms_only():
+    """Host-side planning (no GPU needed): a dense 32-tap room takes the fused
+    kernel, which needs no image-id buffer, so its FP32 workspace is a small
+    fraction of the per-tap form's; the sparse 48 kHz array (~36 images per
+    delay bin) takes the direct form in both cases (same workspace); a backward
+    call over a 32-tap window takes the fused adjoint (no ids either), over a
+    6-tap window the per-tap adjoint over binned ids."""
+    from paper_1810_11359_gb300 import ism
+    L = [6.0, 5.0, 3.0]
+    beta = ism.ism_beta_sabine(L, 0.6)
+    N = ism.ism_nb_img_from_t(0.6, L, 343.0, 32 / 16000)
+    fused = ism.ism_workspace_size(L, beta, 4, 32, N, 0.6, 16000.0, Tw=32 / 16000, prec="fp32")
+    direct = ism.ism_workspace_size(L, beta, 4, 32, N, 0.6, 16000.0, Tw=32 / 16000, prec="fp32_direct")
+    ids = 128 * int(np.prod(N)) * 4
+    assert fused < direct / 10 and direct > ids
+    L2 = [10.0, 8.0, 3.5]
+    b2 = ism.ism_beta_sabine(L2, 1.2)
+    N2 = ism.ism_nb_img_from_t(0.3, L2, 343.0, 32 / 48000)
+    a = ism.ism_workspace_size(L2, b2, 64, 8, N2, 1.2, 48000.0, Tdiff=0.3, Tw=32 / 48000, prec="fp32")
+    b = ism.ism_workspace_size(L2, b2, 64, 8, N2, 1.2, 48000.0, Tdiff=0.3, Tw=32 / 48000, prec="fp32_direct")
+    assert a == b and a > 512 * int(np.prod(N2)) * 4
+    # backward: host tensors only lend the pointers the host-side checks look at
+    import torch
+    ps, pr = torch.ones((1, 3)), torch.ones((1, 3))
+    sizes = []
+    for Tw in (32 / 16000, 6 / 16000):
+        N3 = ism.ism_nb_img_from_t(0.4, L, 343.0, Tw)
+        go = torch.zeros(ism.ism_rir_length(0.4, 16000.0))
+        job = ism.make_job(L, beta, ps, pr, N3, 0.4, 16000.0, go, Tw=Tw)
+        gj = ism.make_grad_job(job, go, torch.zeros(6), torch.zeros((1, 3)), torch.zeros((1, 3)))
+        sizes.append((ism.ism_backward_workspace_size([gj]), int(np.prod(N3)) * 4))
+    (fused_b, _), (direct_b, ids_b) = sizes
+    assert fused_b < ids_b and direct_b > ids_b
