@@ -23,7 +23,12 @@
  *     device; "host" pointers are ordinary host memory.
  *   - Work is enqueued on `stream` (a cudaStream_t passed as void*; NULL is
  *     the legacy default stream) and the call returns after the launches:
- *     results are ready when the stream reaches that point.
+ *     results are ready when the stream reaches that point.  Apart from
+ *     ism_simulate_host, ism_workspace_status and the server's waits, no call
+ *     waits for the device, and internal streams fork from and join back into
+ *     `stream` through events, so the device-pointer calls can be captured in
+ *     a CUDA graph on `stream` (once each kernel has been launched outside a
+ *     capture) and replayed.
  *   - Every call returns an ism_status.  No C++ exception crosses the ABI.
  *     On an error the outputs are not written; ism_last_error_message()
  *     describes the last error of the calling thread.
