@@ -154,8 +154,10 @@ ism_status ism_simulate(const ism_room* room, const float* pos_src, int n_src, c
                         size_t ws_bytes, void* stream);
 
 /* Same computation from HOST buffers: copies pos_src/pos_rcv to the device,
- * runs ism_simulate and copies the RIRs back into host `out`
- * ([n_src][n_rcv][n_S] FP32).  Positions are validated on the host first
+ * runs ism_simulate and delivers the RIRs into host `out`
+ * ([n_src][n_rcv][n_S] FP32): a page-locked `out` is written by the kernels
+ * directly over the host link, any other host memory receives a copy of the
+ * device result.  Positions are validated on the host first
  * (ISM_ERR_INVALID_ARG if one lies outside the room).  Synchronous: returns
  * when `out` holds the result.  The workspace is device memory as above. */
 ism_status ism_simulate_host(const ism_room* room, const float* pos_src, int n_src,

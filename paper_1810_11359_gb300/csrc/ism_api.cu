@@ -1063,8 +1063,15 @@ ism_status ism_simulate_host(const ism_room* room, const float* pos_src, int n_s
     vs[0].job.pos_rcv = d_pos + 3 * n_src;
     vs[0].job.out = d_out;
     vs[0].job.seed = seed;
+    // a page-locked `out` is written by the kernels themselves (over the host link, as the
+    // RIRs are finished); other host memory receives a copy of the device result
+    cudaPointerAttributes attr{};
+    const bool direct = cudaPointerGetAttributes(&attr, out) == cudaSuccess && attr.type == cudaMemoryTypeHost &&
+                        attr.devicePointer != nullptr;
+    cudaGetLastError();   // a pageable pointer may leave an error behind on older drivers
+    if (direct) vs[0].job.out = static_cast<float*>(attr.devicePointer);
     const HostCopy hc{d_out, out};
-    if ((s = run_batch(vs, prec, workspace, sim, stream, &hc)) != ISM_OK) return s;
+    if ((s = run_batch(vs, prec, workspace, sim, stream, direct ? nullptr : &hc)) != ISM_OK) return s;
     if ((e = (int)cudaStreamSynchronize(st))) return cuda_fail(e, "stream synchronize");
     return ISM_OK;
 }
