@@ -312,8 +312,9 @@ ism_status ism_server_create(const ism_server_config* cfg, ism_server** server);
 /* Queues one request.  job->pos_src and job->pos_rcv are HOST pointers, copied
  * before this returns; job->out is a HOST pointer of n_src * n_rcv * n_S FP32
  * that the server writes before the request is reported done (it must stay
- * valid until then; page-locked memory receives the results by DMA straight
- * from the device, other memory through the server's staging pool);
+ * valid until then; page-locked memory is written by the kernels directly
+ * over the host link, other memory through a device buffer and the
+ * server's staging pool);
  * job->env_amp must be NULL.  The job is validated here
  * (arguments as for ism_simulate, positions strictly inside the room):
  * errors return at once and no ticket is issued.  A request whose memory can

@@ -99,7 +99,8 @@ struct Request {
     std::vector<float> pos;      // n_src * 3 source then n_rcv * 3 receiver coordinates
     size_t out_bytes = 0, pos_bytes = 0;
     size_t dev_off = 0, pin_off = 0;
-    bool direct = false;         // out is page-locked: results go there without staging
+    bool direct = false;         // out is page-locked: the kernels write the results there
+    float* out_dev = nullptr;    // its device-side address (direct requests)
     bool admitted = false, done = false;
     ism_status status = ISM_OK;
     std::string message;
@@ -149,7 +150,7 @@ struct ism_server {
     void release_request(Request* r)
     {
         if (!r->admitted) return;
-        dev_arena.release(r->dev_off, g256(r->out_bytes) + g256(r->pos_bytes));
+        dev_arena.release(r->dev_off, dev_bytes(r));
         pin_arena.release(r->pin_off, pin_bytes(r));
         r->admitted = false;
     }
@@ -158,6 +159,10 @@ struct ism_server {
     // the positions alone when the results go straight to a page-locked `out`.
     static size_t pin_bytes(const Request* r) { return (r->direct ? 0 : g256(r->out_bytes)) + g256(r->pos_bytes); }
     static size_t pin_pos(const Request* r) { return r->pin_off + (r->direct ? 0 : g256(r->out_bytes)); }
+    // Device bytes of a request: [results | positions], or the positions alone when the
+    // kernels write the results straight into a page-locked `out`.
+    static size_t dev_bytes(const Request* r) { return (r->direct ? 0 : g256(r->out_bytes)) + g256(r->pos_bytes); }
+    static size_t dev_pos(const Request* r) { return r->dev_off + (r->direct ? 0 : g256(r->out_bytes)); }
 
     // Admits requests from the head of the queue into a batch (lock held).
     // Returns nullptr when nothing can start now.
@@ -173,7 +178,7 @@ struct ism_server {
         Batch* b = new Batch();
         while (!queue.empty() && (int)b->reqs.size() < cfg.max_batch) {
             Request* r = queue.front();
-            const size_t need = g256(r->out_bytes) + g256(r->pos_bytes);
+            const size_t need = dev_bytes(r);
             size_t doff = 0, poff = 0;
             if (!dev_arena.alloc(need, &doff)) break;
             if (!pin_arena.alloc(pin_bytes(r), &poff)) {
@@ -231,9 +236,8 @@ struct ism_server {
         std::vector<ism_job> jobs;
         for (Request* r : b->reqs) {
             ism_job j = r->job;
-            char* d = dev + r->dev_off;
-            j.out = reinterpret_cast<float*>(d);
-            j.pos_src = reinterpret_cast<const float*>(d + g256(r->out_bytes));
+            j.out = r->direct ? r->out_dev : reinterpret_cast<float*>(dev + r->dev_off);
+            j.pos_src = reinterpret_cast<const float*>(dev + dev_pos(r));
             j.pos_rcv = j.pos_src + 3 * r->job.n_src;
             j.orient_rcv = r->job.mic_pattern != ISM_MIC_OMNI ? j.pos_rcv + 3 * r->job.n_rcv : nullptr;
             j.env_amp = nullptr;
@@ -249,7 +253,7 @@ struct ism_server {
         for (Request* r : b->reqs) {
             char* h = pin + pin_pos(r);
             std::memcpy(h, r->pos.data(), r->pos_bytes);
-            if (cudaMemcpyAsync(dev + r->dev_off + g256(r->out_bytes), h, r->pos_bytes, cudaMemcpyHostToDevice, s) !=
+            if (cudaMemcpyAsync(dev + dev_pos(r), h, r->pos_bytes, cudaMemcpyHostToDevice, s) !=
                 cudaSuccess) {
                 *msg = "position copy failed";
                 return ISM_ERR_CUDA;
@@ -267,8 +271,8 @@ struct ism_server {
             return ISM_ERR_CUDA;
         }
         for (Request* r : b->reqs)
-            if (cudaMemcpyAsync(r->direct ? static_cast<void*>(r->job.out) : static_cast<void*>(pin + r->pin_off),
-                                dev + r->dev_off, r->out_bytes, cudaMemcpyDeviceToHost, s) != cudaSuccess) {
+            if (!r->direct && cudaMemcpyAsync(pin + r->pin_off, dev + r->dev_off, r->out_bytes, cudaMemcpyDeviceToHost,
+                                              s) != cudaSuccess) {
                 *msg = "result copy failed";
                 return ISM_ERR_CUDA;
             }
@@ -438,7 +442,9 @@ ism_status prepare_request(ism_server* s, const ism_job* job, Request** out)
                     (size_t)job->n_rcv * 3 * sizeof(float));
     std::memcpy(r->pos.data() + 3 * job->n_src, job->pos_rcv, (size_t)job->n_rcv * 3 * sizeof(float));
     cudaPointerAttributes attr{};
-    r->direct = cudaPointerGetAttributes(&attr, job->out) == cudaSuccess && attr.type == cudaMemoryTypeHost;
+    r->direct = cudaPointerGetAttributes(&attr, job->out) == cudaSuccess && attr.type == cudaMemoryTypeHost &&
+                attr.devicePointer != nullptr;
+    r->out_dev = r->direct ? static_cast<float*>(attr.devicePointer) : nullptr;
     cudaGetLastError();   // a pageable pointer may leave an error behind on older drivers
     *out = r;
     return ISM_OK;
