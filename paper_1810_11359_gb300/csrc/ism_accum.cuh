@@ -673,9 +673,9 @@ int launch_one(const JobTable& t, const WsPlan& p, char* ws, cudaStream_t s)
         PREC == PREC_LUT ? (size_t)(ism_lut_phases(SLOTS) + 1) * 32 * SLOTS * sizeof(float) : 0;
     size_t sm = (size_t)((t.max_axis_sum + 1) & ~1) * sizeof(float4) + lut_bytes + BPC * sizeof(WarpSmem) +
                 (size_t)t.max_axis_sum * sizeof(float);
-    cudaError_t e = cudaFuncSetAttribute(accum_kernel<SLOTS, MASK, PREC>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    if (e != cudaSuccess) return (int)e;
+    static std::atomic<unsigned long long> opened{0};
+    int rc = ism_open_smem((const void*)accum_kernel<SLOTS, MASK, PREC>, &opened);
+    if (rc) return rc;
     accum_kernel<SLOTS, MASK, PREC><<<(unsigned)p.acc_ctas, BPC * 32, sm, s>>>(
         t, reinterpret_cast<const float4*>(ws + p.tbl_off), reinterpret_cast<const uint32_t*>(ws + p.hist_off),
         reinterpret_cast<const uint32_t*>(ws + p.ids_off), reinterpret_cast<const float*>(ws + p.lut_off),

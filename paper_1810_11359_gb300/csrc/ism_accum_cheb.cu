@@ -247,10 +247,12 @@ int ism_launch_accum_cheb(const JobTable& t, const WsPlan& p, char* ws, void* st
     *launched = 0;
     if (p.shell_ctas <= 0 || !t.any_cheb) return 0;
     const size_t sm = shell_smem(t);
-    cudaError_t e = cudaFuncSetAttribute(shell_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    if (e != cudaSuccess) return (int)e;
+    static std::atomic<unsigned long long> opened{0};
+    int rc = ism_open_smem((const void*)shell_kernel, &opened);
+    if (rc) return rc;
     // all of the unified L1 as shared memory: 5 CTAs of ~27 KB per SM
-    e = cudaFuncSetAttribute(shell_kernel, cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxShared);
+    cudaError_t e = cudaFuncSetAttribute(shell_kernel, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                         cudaSharedmemCarveoutMaxShared);
     if (e != cudaSuccess) return (int)e;
     shell_kernel<<<(unsigned)p.shell_ctas, SH_WARPS * 32, sm, (cudaStream_t)stream>>>(
         t, reinterpret_cast<const float4*>(ws + p.tbl_off), reinterpret_cast<float*>(ws + p.rows_off),

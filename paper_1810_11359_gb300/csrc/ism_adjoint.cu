@@ -273,9 +273,9 @@ int launch_adj(const JobTable& t, const WsPlan& p, char* ws, cudaStream_t s)
     const size_t axis_pad = (size_t)((t.max_axis_sum + 1) & ~1);
     const size_t sm = 2 * axis_pad * sizeof(float4) + (size_t)ISM_ACC_WARPS * 32 * (SLOTS + 1) * sizeof(float) +
                       (size_t)ISM_ACC_WARPS * ADJ_CHUNK * sizeof(AdjRec);
-    cudaError_t e = cudaFuncSetAttribute(adjoint_kernel<SLOTS, MASK>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)sm);
-    if (e != cudaSuccess) return (int)e;
+    static std::atomic<unsigned long long> opened{0};
+    int rc = ism_open_smem((const void*)adjoint_kernel<SLOTS, MASK>, &opened);
+    if (rc) return rc;
     adjoint_kernel<SLOTS, MASK><<<(unsigned)p.adj_ctas, ISM_ACC_WARPS * 32, sm, s>>>(
         t, reinterpret_cast<const float4*>(ws + p.tbl_off), reinterpret_cast<const float4*>(ws + p.dtbl_off),
         reinterpret_cast<const uint32_t*>(ws + p.hist_off),

@@ -192,10 +192,11 @@ int ism_launch_adjoint_cheb(const JobTable& t, const WsPlan& p, char* ws, void* 
     *launched = 0;
     if (p.shell_ctas <= 0) return 0;
     const size_t sm = shell_adjoint_smem(t);
-    cudaError_t e = cudaFuncSetAttribute(shell_adjoint_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    if (e != cudaSuccess) return (int)e;
-    e = cudaFuncSetAttribute(shell_adjoint_kernel, cudaFuncAttributePreferredSharedMemoryCarveout,
-                             cudaSharedmemCarveoutMaxShared);   // 4 CTAs of ~32 KB per SM
+    static std::atomic<unsigned long long> opened{0};
+    int rc = ism_open_smem((const void*)shell_adjoint_kernel, &opened);
+    if (rc) return rc;
+    cudaError_t e = cudaFuncSetAttribute(shell_adjoint_kernel, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                         cudaSharedmemCarveoutMaxShared);   // 4 CTAs of ~32 KB per SM
     if (e != cudaSuccess) return (int)e;
     shell_adjoint_kernel<<<(unsigned)p.shell_ctas, SA_WARPS * 32, sm, (cudaStream_t)stream>>>(
         t, reinterpret_cast<const float4*>(ws + p.tbl_off), reinterpret_cast<const float4*>(ws + p.dtbl_off),

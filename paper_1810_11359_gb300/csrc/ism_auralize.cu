@@ -195,8 +195,9 @@ int ism_launch_auralize(const float* x, int n_x, const float* h, int n_points, i
     // 128-bit tap rows when every row starts on a 16-byte boundary
     const bool vec = (n_s % 4 == 0) && (((uintptr_t)h & 15u) == 0);
     auto kern = vec ? auralize_kernel<true> : auralize_kernel<false>;
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    if (e != cudaSuccess) return (int)e;
+    static std::atomic<unsigned long long> opened[2] = {{0}, {0}};
+    const int rc = ism_open_smem((const void*)kern, &opened[vec ? 1 : 0]);
+    if (rc) return rc;
     kern<<<grid, AU_WARPS * 32, sm, (cudaStream_t)stream>>>(x, n_x, h, n_points, n_mics, n_s, starts, y, (int)n_out);
     return (int)cudaGetLastError();
 }

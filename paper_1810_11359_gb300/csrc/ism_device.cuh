@@ -1,6 +1,7 @@
 // ism_device.cuh -- device helpers shared by the libism kernels.
 #pragma once
 
+#include <atomic>
 #include <cstdint>
 #include <cuda_runtime.h>
 
@@ -22,6 +23,30 @@ __device__ __forceinline__ int ism_find_job(const JobTable& t, long long cta, F 
         else hi = mid - 1;
     }
     return lo;
+}
+
+// A kernel's dynamic shared-memory limit is process-wide, so a limit set to
+// each launch's own need could be lowered by another host thread launching
+// the same kernel between this thread's set and its launch (which would then
+// fail).  Instead the limit is raised once per device to the device's opt-in
+// maximum less the kernel's static shared memory; `done` holds one bit per
+// device (one flag per kernel).
+inline int ism_open_smem(const void* kernel, std::atomic<unsigned long long>* done)
+{
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return (int)e;
+    const unsigned long long bit = 1ull << (dev & 63);
+    if (done->load(std::memory_order_acquire) & bit) return 0;
+    int mx = 0;
+    if ((e = cudaDeviceGetAttribute(&mx, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev)) != cudaSuccess) return (int)e;
+    cudaFuncAttributes fa{};
+    if ((e = cudaFuncGetAttributes(&fa, kernel)) != cudaSuccess) return (int)e;   // static + dynamic <= opt-in
+    if ((e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  mx - (int)fa.sharedSizeBytes)) != cudaSuccess)
+        return (int)e;
+    done->fetch_or(bit, std::memory_order_release);
+    return 0;
 }
 
 // Reflection coefficient w of a job: from device memory when the caller keeps

@@ -287,14 +287,13 @@ int ism_launch_enum(const JobTable& t, const WsPlan& p, char* ws, bool scatter, 
     auto* idsp = reinterpret_cast<uint32_t*>(ws + p.ids_off);
     auto* st = reinterpret_cast<uint32_t*>(ws + p.status_off);
     cudaStream_t s = (cudaStream_t)stream;
-    cudaError_t e;
+    static std::atomic<unsigned long long> opened[2] = {{0}, {0}};
+    int rc;
     if (scatter) {
-        e = cudaFuncSetAttribute(enum_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-        if (e != cudaSuccess) return (int)e;
+        if ((rc = ism_open_smem((const void*)enum_kernel<true>, &opened[1]))) return rc;
         enum_kernel<true><<<(unsigned)p.enum_ctas, ISM_ENUM_WARPS * 32, sm, s>>>(t, tbl, hist, idsp, st);
     } else {
-        e = cudaFuncSetAttribute(enum_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-        if (e != cudaSuccess) return (int)e;
+        if ((rc = ism_open_smem((const void*)enum_kernel<false>, &opened[0]))) return rc;
         enum_kernel<false><<<(unsigned)p.enum_ctas, ISM_ENUM_WARPS * 32, sm, s>>>(t, tbl, hist, idsp, st);
     }
     return (int)cudaGetLastError();
