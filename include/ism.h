@@ -37,6 +37,12 @@
  *     Tdiff <= 0 or Tdiff >= Tmax means no diffuse tail (n_ism = n_S).
  *   - The window length Tw is in seconds (eq. (6)); N_w = Tw fs taps.
  *     Tw <= 0 selects the paper's typical 4 ms.
+ *   - The library keeps per-device state for the life of the process: the
+ *     kernels' raised shared-memory limits, two internal streams and three
+ *     events per host thread and device, texture objects of the LUT tables
+ *     and the allocation-free entry point's scratch address.  It does not
+ *     survive cudaDeviceReset() or the release of a device's primary
+ *     context; after either, use it from a new process.
  */
 #ifndef ISM_H
 #define ISM_H
@@ -121,9 +127,9 @@ ism_status ism_workspace_size(const ism_room* room, int n_src, int n_rcv, const 
                               size_t* bytes);
 
 /* ------------------------------------------------------------------------- */
-/* Forward simulation (Section 4: "room dimensions, reflection coefficients, */
-/* source and receiver positions, images per dimension, RIR duration, time   */
-/* to switch to the diffuse model, sampling frequency" -> 3-D tensor)        */
+/* Forward simulation (the library call of Section 4: the room, its walls'   */
+/* coefficients, the positions, the image counts, the RIR length, the switch */
+/* time to the diffuse model and the sampling rate -> a 3-D tensor)          */
 /* ------------------------------------------------------------------------- */
 /* RIRs for all n_src x n_rcv pairs.
  *   room      host, see ism_room.
@@ -185,21 +191,34 @@ ism_status ism_workspace_status(const void* workspace, void* stream, uint32_t* f
  * worker thread that must not block on the allocator, code inside a
  * framework that owns every device allocation, embedded uses that cannot
  * keep a workspace).  The paper has no counterpart: it is a deployment
- * variant of the same launches.
- *   Scratch: a fixed 64 MiB area that the library reserves in device memory
- *   when it is loaded; every device that loads the library holds it until
- *   the process exits.  No call here allocates or frees device memory.
+ * variant of the same launches, with bitwise the same results.
+ *   Scratch: a fixed 64 MiB area in device memory (a file-scope __device__
+ *   array of the library); every device on which it has been set up holds it
+ *   until the process exits.  This entry point never calls cudaMalloc or
+ *   cudaFree.
+ *   Set-up, once per device: the first call on a device looks up the area's
+ *   device address (cudaGetSymbolAddress) with that device current.  With
+ *   CUDA's lazy module loading (the default) that lookup is also when the
+ *   driver loads the library's device code and reserves the 64 MiB, so the
+ *   first call on each device can block, and can fail (ISM_ERR_CUDA, e.g.
+ *   out of memory); later calls cannot fail that way.  The first call whose
+ *   simulation is large enough to run as two halves (see ism_set_lanes) also
+ *   creates, once per host thread and device, two internal streams and three
+ *   events.  A real-time caller should therefore make one warm-up call at
+ *   set-up on each device and each host thread it will call from, outside
+ *   its real-time path, and before any stream capture.
  *   Limit: a simulation needing more scratch than 64 MiB (ism_workspace_size)
  *   is rejected with ISM_ERR_UNSUPPORTED and nothing is launched.
- *   Set-up: the first call on each device looks up the area's device address
- *   (cudaGetSymbolAddress) with that device current; make that first call
- *   before any stream capture.
  *   Sharing: every call uses the same area and leaves its contents behind;
  *   the kernels reset what they need.  Two calls whose work overlaps on the
  *   GPU (different streams without ordering between them, or different host
  *   threads) race on the area and corrupt each other's results: order them.
- * Arguments, layout and errors are those of ism_simulate; ism_workspace_status
- * is not available for this entry point. */
+ *   Checks: the device-side flags of ism_workspace_status live in the area,
+ *   whose address callers never see, so they are not reported here: a source
+ *   or receiver outside the room, or a source on a receiver, silently gives
+ *   an all-zero RIR.  Callers of this entry point range-check their device
+ *   positions themselves.
+ * Arguments, layout and errors are otherwise those of ism_simulate. */
 ism_status ism_simulate_noalloc(const ism_room* room, const float* pos_src, int n_src,
                                 const float* pos_rcv, int n_rcv, const int nb_img[3], float Tmax,
                                 float fs, float Tdiff, float Tw, ism_precision prec, uint64_t seed,
@@ -208,8 +227,8 @@ ism_status ism_simulate_noalloc(const ism_room* room, const float* pos_src, int 
 /* ------------------------------------------------------------------------- */
 /* Ragged batches: many rooms in one set of launches                         */
 /* ------------------------------------------------------------------------- */
-/* Receiver polar patterns (Section 4: "information about the polar pattern
- * of the receivers and their orientation").  The paper gives no formula; the
+/* Receiver polar patterns and orientations (Section 4 lists them among the
+ * inputs of the library call).  The paper gives no formula; the
  * first-order family g(theta) = alpha + (1 - alpha) cos(theta) is used, theta
  * being the angle between the receiver's orientation and the direction from
  * the receiver to the image source; g multiplies the image's amplitude

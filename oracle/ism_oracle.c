@@ -19,7 +19,7 @@
  *   - eq. (8) prints exp(log10(T60/20)(t - t0)), which is not a 60 dB decay in
  *     T60; the envelope used is the Sabine one it is meant to express:
  *     power falls by 60 dB in T60 seconds.
- *   - the envelope amplitude A "estimated from the early reflections" is the
+ *   - the envelope amplitude A, fitted to the image-source part (Section 2.2), is the
  *     detrended power of the last 20 ms of the image-source part.
  *   - the noise is logistic with unit variance driven by Philox4x32-10.
  *
@@ -401,7 +401,7 @@ void oracle_noise(uint64_t seed, uint32_t rir, uint32_t k0, int n, float* z)
         z[i] = oracle_logistic_f32(oracle_uniform_f32(oracle_noise_word(seed, rir, k0 + (uint32_t)i)));
 }
 
-/* Envelope amplitude at t0 = n_ism/f_s "estimated from the early reflections"
+/* Envelope amplitude at t0 = n_ism/f_s, fitted to the image-source part (Section 2.2)
  * (Section 2.2): mean of h[k]^2 10^(-6 (t0 - t_k)/T60) over the last
  * W = ceil(0.02 f_s) image-source samples, i.e. the ISM power brought forward
  * to t0 along the 60 dB/T60 decay of eq. (8) (earlier samples carry more

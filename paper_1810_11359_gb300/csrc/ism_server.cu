@@ -441,11 +441,22 @@ ism_status prepare_request(ism_server* s, const ism_job* job, Request** out)
         std::memcpy(r->pos.data() + 3 * (job->n_src + job->n_rcv), job->orient_rcv,
                     (size_t)job->n_rcv * 3 * sizeof(float));
     std::memcpy(r->pos.data() + 3 * job->n_src, job->pos_rcv, (size_t)job->n_rcv * 3 * sizeof(float));
-    cudaPointerAttributes attr{};
-    r->direct = cudaPointerGetAttributes(&attr, job->out) == cudaSuccess && attr.type == cudaMemoryTypeHost &&
-                attr.devicePointer != nullptr;
-    r->out_dev = r->direct ? static_cast<float*>(attr.devicePointer) : nullptr;
-    cudaGetLastError();   // a pageable pointer may leave an error behind on older drivers
+    // The kernels run on the server's device, so a page-locked `out` is written directly only
+    // if it has an address there: it is looked up with that device current (memory pinned in
+    // another device's context without the portable flag has none and takes the staging copy).
+    int prev = -1;
+    if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+    if (prev == s->cfg.device || cudaSetDevice(s->cfg.device) == cudaSuccess) {
+        cudaPointerAttributes attr{};
+        void* dp = nullptr;
+        if (cudaPointerGetAttributes(&attr, job->out) == cudaSuccess && attr.type == cudaMemoryTypeHost &&
+            cudaHostGetDevicePointer(&dp, static_cast<void*>(job->out), 0) == cudaSuccess && dp != nullptr) {
+            r->direct = true;
+            r->out_dev = static_cast<float*>(dp);
+        }
+        if (prev >= 0 && prev != s->cfg.device) cudaSetDevice(prev);
+    }
+    cudaGetLastError();   // a pageable or foreign pointer leaves an error behind
     *out = r;
     return ISM_OK;
 }

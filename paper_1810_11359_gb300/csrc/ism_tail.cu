@@ -3,8 +3,8 @@
 // Section 2.2 ("Diffuse reverberation") models the late RIR as logistic
 // noise whose power follows the Sabine decay: 60 dB in T60 (eq. (7)) from
 // the end of the image-source part t0 = n_ism / f_s (eq. (8), whose printed
-// exponent log10(T60/20) is read as this decay).  The amplitude A is
-// "estimated from the early reflections": here the mean over the last
+// exponent log10(T60/20) is read as this decay).  Section 2.2 leaves the
+// amplitude A to be fitted to the image-source part; here it is the mean over the last
 // W = ceil(0.02 f_s) image-source samples of h[k]^2 2^(-g2 (n_ism - k)),
 // g2 = 6 log2(10) / (f_s T60), i.e. their power brought forward to t0 along
 // the same decay.  The tail is h[k] = z_k sqrt(A) 2^(-g2 (k - n_ism) / 2).

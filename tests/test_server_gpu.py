@@ -186,7 +186,7 @@ def test_batch_submit_matches_alone_and_is_all_or_nothing():
         for (t, out), r in zip(got, ref):
             assert srv.wait(t) > 0
             assert np.array_equal(out.view(np.uint32), r.view(np.uint32))
-        # page-locked result buffers: the server copies into them directly
+        # page-locked result buffers: the kernels write the RIRs into them directly
         pinned = [torch.full(r.shape, float("nan")).pin_memory() for r in ref]
         got = srv.submit_many(reqs, outs=[o.numpy() for o in pinned])
         for (t, out), r in zip(got, ref):
