@@ -14,6 +14,9 @@ Functions map one to one onto passages of the paper (Diaz-Guerra et al.,
 * ``nb_img_from_t``, ``att2t_sabine`` -- Section 4 helpers
 * ``noise`` / ``tail`` / ``envelope_amp`` -- Section 2.2 "Diffuse reverberation",
   eq. (8) read as a 60 dB decay over T60, Philox4x32-10 driven logistic noise
+* ``lj_energy`` / ``envelope_amp_lj`` / ``tail_lj`` -- the Lehmann-Johansson
+  energy-decay envelope that Section 2.2 cites (a reading: the energy arrival
+  rate of the image lattice, averaged over directions)
 * ``rir_grad``          -- derivative of eq. (1)-(6) (not in the paper)
 * ``simulate``          -- the library call of Section 4 (ISM up to Tdiff, tail after)
 
@@ -110,6 +113,10 @@ def _load():
         lib.oracle_tail.restype = None
         lib.oracle_tail.argtypes = [ctypes.c_uint64, ctypes.c_uint32, D, ctypes.c_int, ctypes.c_int,
                                     D, D, Dp]
+        lib.oracle_lj_energy.restype = D
+        lib.oracle_lj_energy.argtypes = [Dp, Dp, D, D, Dp, Dp, ctypes.c_int]
+        lib.oracle_lj_energy_many.restype = None
+        lib.oracle_lj_energy_many.argtypes = [Dp, Dp, D, Dp, ctypes.c_int, Dp, Dp, ctypes.c_int, Dp]
         lib.oracle_rir_grad.restype = None
         lib.oracle_rir_grad.argtypes = [Dp, Dp, D, D, D, Dp, Dp, Ip, ctypes.c_int, Dp, Dp, Dp, Dp]
         lib.oracle_max_threads.restype = ctypes.c_int
@@ -347,6 +354,65 @@ def tail(seed: int, rir: int, A: float, n_ism: int, n_s: int, fs: float, T60: fl
 
 
 # --------------------------------------------------------------------------- #
+# Lehmann-Johansson energy-decay envelope (Section 2.2 cites it; a reading)
+# --------------------------------------------------------------------------- #
+LJ_NODES = 96   # Gauss-Legendre nodes per angle (quadrature error < 1e-11 while c t sum_a -ln(rho_a) / L_a < 300)
+
+
+def _gauss_legendre(n):
+    x, w = np.polynomial.legendre.leggauss(int(n))
+    return np.ascontiguousarray(x), np.ascontiguousarray(w)
+
+
+def lj_energy(L, beta, c, t, nodes: int = LJ_NODES):
+    """E(t): the energy arriving at time t from the images of the room, relative
+    to t = 0 (the average over directions of prod_a rho_a^(c t |u_a| / L_a),
+    rho_a = |beta_a0 beta_a1|).  t: scalar or array (seconds)."""
+    x, w = _gauss_legendre(nodes)
+    tt = np.ascontiguousarray(np.atleast_1d(np.asarray(t, np.float64)))
+    out = np.zeros(tt.shape[0], np.float64)
+    _load().oracle_lj_energy_many(_dp(_d(L, 3)), _dp(_d(beta, 6)), float(c), _dp(tt), int(tt.shape[0]), _dp(x),
+                                  _dp(w), int(nodes), _dp(out))
+    return out if np.ndim(t) else float(out[0])
+
+
+def envelope_amp_lj(h_ism, n_ism: int, fs: float, L, beta, c, nodes: int = LJ_NODES) -> float:
+    """Envelope amplitude at t0 = n_ism / fs for the Lehmann-Johansson decay: the
+    mean over the last W = ceil(0.02 fs) image-source samples of
+    h[k]^2 E(t0) / E(t_k) (their power brought forward to t0 along the same
+    decay; 0 if E(t0) = 0)."""
+    h = np.asarray(h_ism, np.float64)
+    W = min(int(math.ceil(0.02 * fs)), int(n_ism))
+    if W <= 0:
+        return 0.0
+    k = np.arange(n_ism - W, n_ism)
+    E = lj_energy(L, beta, c, np.concatenate([[n_ism / fs], k / fs]), nodes)
+    if not E[0] > 0.0:
+        return 0.0
+    acc = 0.0
+    for i in range(W):   # fixed order, one sample at a time
+        acc += h[k[i]] ** 2 * (E[0] / E[1 + i])
+    return acc / W
+
+
+def tail_lj(seed: int, rir: int, A: float, n_ism: int, n_s: int, fs: float, L, beta, c, ks=None,
+            nodes: int = LJ_NODES) -> np.ndarray:
+    """The diffuse tail with the Lehmann-Johansson envelope: h[k] = z_k sqrt(A E(t_k) / E(t0))
+    for n_ism <= k < n_s (z_k the noise of ``noise``); returns h[0:n_s] with zeros
+    below n_ism, or, when ``ks`` lists sample indices, the tail at those samples only."""
+    ks_arr = np.arange(n_ism, n_s) if ks is None else np.asarray(ks, np.int64)
+    E = lj_energy(L, beta, c, np.concatenate([[n_ism / fs], ks_arr / fs]), nodes)
+    z = np.array([noise(seed, rir, int(k), 1)[0] for k in ks_arr], np.float64) if ks is not None else \
+        noise(seed, rir, n_ism, n_s - n_ism).astype(np.float64)
+    env = np.zeros_like(E[1:]) if not E[0] > 0.0 else np.sqrt(A * E[1:] / E[0])
+    if ks is not None:
+        return z * env
+    h = np.zeros(int(n_s), np.float64)
+    h[n_ism:] = z * env
+    return h
+
+
+# --------------------------------------------------------------------------- #
 # Gradient (not in the paper): derivative of eq. (1)-(6)
 # --------------------------------------------------------------------------- #
 def rir_grad(L, beta, c, fs, Tw, ps, pr, N, n_ism, g):
@@ -373,7 +439,7 @@ def n_samples(T: float, fs: float) -> int:
 
 
 def simulate(L, beta, c, fs, pos_src, pos_rcv, N, Tmax, Tdiff=None, Tw=None, seed: int = 0,
-             pairs=None, n_threads: int = 0, env_amp=None):
+             pairs=None, n_threads: int = 0, env_amp=None, envelope: str = "sabine"):
     """RIRs for all (source, receiver) pairs, [n_src, n_rcv, n_S] FP64.
 
     ISM (eq. (5)-(6)) for samples k < n_ism = ceil(Tdiff fs), diffuse tail
@@ -381,7 +447,8 @@ def simulate(L, beta, c, fs, pos_src, pos_rcv, N, Tmax, Tdiff=None, Tw=None, see
     + i_rcv keys the noise.  ``pairs`` restricts the work to a list of
     (i_src, i_rcv); the result is then [len(pairs), n_S].  ``env_amp`` maps an
     RIR index to an externally supplied envelope amplitude (for comparing tails
-    given the same A).
+    given the same A).  ``envelope``: "sabine" (eq. (7)-(8)) or "lj" (the
+    Lehmann-Johansson energy decay, ``lj_energy``).
     """
     ps_all = np.asarray(pos_src, dtype=np.float64).reshape(-1, 3)
     pr_all = np.asarray(pos_rcv, dtype=np.float64).reshape(-1, 3)
@@ -404,6 +471,10 @@ def simulate(L, beta, c, fs, pos_src, pos_rcv, N, Tmax, Tdiff=None, Tw=None, see
         T60 = t60_sabine(L, beta)
         for idx, (i, j) in enumerate(pairs):
             r = i * n_rcv + j
+            if envelope == "lj":
+                A = envelope_amp_lj(h_ism[idx], n_ism, fs, L, beta, c) if env_amp is None else float(env_amp[r])
+                out[idx, n_ism:] = tail_lj(seed, r, A, n_ism, n_S, fs, L, beta, c)[n_ism:]
+                continue
             A = envelope_amp(h_ism[idx], n_ism, fs, T60) if env_amp is None else float(env_amp[r])
             out[idx, n_ism:] = tail(seed, r, A, n_ism, n_S, fs, T60)[n_ism:]
     if len(pairs) == ps_all.shape[0] * n_rcv and pairs == [(i, j) for i in range(ps_all.shape[0])

@@ -401,7 +401,7 @@ void oracle_noise(uint64_t seed, uint32_t rir, uint32_t k0, int n, float* z)
         z[i] = oracle_logistic_f32(oracle_uniform_f32(oracle_noise_word(seed, rir, k0 + (uint32_t)i)));
 }
 
-/* Envelope amplitude at t0 = n_ism/f_s, fitted to the image-source part (Section 2.2)
+/* Envelope amplitude at t0 = n_ism/f_s, fitted to the image-source part
  * (Section 2.2): mean of h[k]^2 10^(-6 (t0 - t_k)/T60) over the last
  * W = ceil(0.02 f_s) image-source samples, i.e. the ISM power brought forward
  * to t0 along the 60 dB/T60 decay of eq. (8) (earlier samples carry more
@@ -435,6 +435,52 @@ void oracle_tail(uint64_t seed, uint32_t rir, double A, int n_ism, int n_s, doub
         float z = oracle_logistic_f32(oracle_uniform_f32(oracle_noise_word(seed, rir, (uint32_t)k)));
         h[k] = (double)z * oracle_envelope_sqrt(A, k, n_ism, fs, T60);
     }
+}
+
+/* ------------------------------------------------------------------------- */
+/* Energy-decay envelope after Lehmann and Johansson, which Section 2.2 cites */
+/* as the more faithful (and costlier) alternative to the Sabine exponential. */
+/* The paper gives no formula; the reading taken (parity pinned by closed     */
+/* forms and by the energy decay of the images themselves, see the tests):    */
+/* the images of a shoebox room fill space with density 1/V; an image at     */
+/* distance r in direction u is reached through about r |u_a| / L_a          */
+/* reflections on the two walls of axis a, half on each, so it carries the   */
+/* energy prod_a rho_a^(r |u_a| / L_a) / (4 pi r)^2 with rho_a =             */
+/* |beta_a0 beta_a1| (eq. (4) squared).  The r^2 growth of a shell cancels    */
+/* the spreading, and the energy arriving at time t = r / c is proportional   */
+/* to the average over directions                                             */
+/*   E(t) = (1 / 4 pi) oint prod_a rho_a^(c t |u_a| / L_a) dOmega.            */
+/* |u_a| is the same in all eight octants, so the average is taken over one:  */
+/* theta, phi in [0, pi/2], u = (sin t cos p, sin t sin p, cos t), dOmega =   */
+/* sin t dt dp, weight 8 / (4 pi) = 2 / pi, with the product quadrature rule  */
+/* whose n nodes x[i] and weights w[i] on [-1, 1] the caller supplies.        */
+/* ------------------------------------------------------------------------- */
+double oracle_lj_energy(const double L[3], const double beta[6], double c, double t, const double* x,
+                        const double* w, int n)
+{
+    double rho[3];
+    for (int a = 0; a < 3; ++a) rho[a] = fabs(beta[2 * a] * beta[2 * a + 1]);
+    const double h = 0.25 * ORACLE_PI;   /* [-1, 1] -> [0, pi/2]: angle = (x + 1) pi / 4 */
+    double acc = 0.0;
+    for (int i = 0; i < n; ++i) {
+        const double th = (x[i] + 1.0) * h;
+        for (int j = 0; j < n; ++j) {
+            const double ph = (x[j] + 1.0) * h;
+            const double u[3] = {sin(th) * cos(ph), sin(th) * sin(ph), cos(th)};
+            double f = 1.0;
+            for (int a = 0; a < 3; ++a) f *= pow(rho[a], c * t * u[a] / L[a]);
+            acc += w[i] * h * w[j] * h * sin(th) * f;
+        }
+    }
+    return acc * 2.0 / ORACLE_PI;
+}
+
+/* E(t) at several times (t[m], m < n_t). */
+void oracle_lj_energy_many(const double L[3], const double beta[6], double c, const double* t, int n_t,
+                           const double* x, const double* w, int n, double* out)
+{
+#pragma omp parallel for schedule(dynamic, 4)
+    for (int m = 0; m < n_t; ++m) out[m] = oracle_lj_energy(L, beta, c, t[m], x, w, n);
 }
 
 /* ------------------------------------------------------------------------- */

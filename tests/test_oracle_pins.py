@@ -328,6 +328,108 @@ def test_envelope_amp_on_exact_exponential():
 
 
 # --------------------------------------------------------------------------- #
+# Lehmann-Johansson energy-decay envelope (Section 2.2 cites it; a reading)
+# --------------------------------------------------------------------------- #
+def test_lj_energy_rigid_walls_do_not_decay():
+    """|beta| = 1 on every wall: no image loses energy, E(t) = 1 at all times."""
+    for beta in ([1, 1, 1, 1, 1, 1], [-1, 1, 1, -1, -1, -1]):
+        np.testing.assert_allclose(oracle.lj_energy([5.0, 4.0, 3.0], beta, 343.0, [0.0, 0.05, 0.7, 3.0]), 1.0,
+                                   rtol=1e-13)
+
+
+@pytest.mark.parametrize("axis", [0, 1, 2])
+def test_lj_energy_one_absorbing_axis_closed_form(axis):
+    """Only the walls of one axis absorb (rho = |b0 b1| < 1): |u_a| is uniform on
+    [0, 1] over the sphere, so E(t) = int_0^1 rho^(k mu) dmu = (1 - e^-K) / K with
+    K = -ln(rho) c t / L_a."""
+    L = [4.3, 3.1, 2.6]
+    beta = [1.0] * 6
+    beta[2 * axis], beta[2 * axis + 1] = 0.6, -0.85
+    rho = 0.6 * 0.85
+    for t in (0.01, 0.1, 0.45, 1.3):
+        K = -math.log(rho) * 343.0 * t / L[axis]
+        assert oracle.lj_energy(L, beta, 343.0, t) == pytest.approx((1 - math.exp(-K)) / K, rel=1e-11)
+
+
+def test_lj_energy_depends_on_wall_products_and_axis_symmetry():
+    """The energy of an image depends on the two walls of an axis through their
+    product only (each is hit half of the time), and the directional average
+    does not prefer an axis: permuting the axes with their walls changes nothing."""
+    L = [6.0, 5.0, 3.0]
+    a = oracle.lj_energy(L, [0.5, 0.8, 0.9, 0.7, 0.6, 0.95], 343.0, [0.05, 0.3])
+    b = oracle.lj_energy(L, [0.8, 0.5, -0.7, -0.9, 0.95, 0.6], 343.0, [0.05, 0.3])
+    c = oracle.lj_energy(L, [math.sqrt(0.4)] * 2 + [math.sqrt(0.63)] * 2 + [math.sqrt(0.57)] * 2, 343.0, [0.05, 0.3])
+    np.testing.assert_allclose(a, b, rtol=1e-12)
+    np.testing.assert_allclose(a, c, rtol=1e-12)
+    d = oracle.lj_energy([3.0, 6.0, 5.0], [0.6, 0.95, 0.5, 0.8, 0.9, 0.7], 343.0, [0.05, 0.3])
+    np.testing.assert_allclose(a, d, rtol=1e-11)
+
+
+def test_lj_energy_initial_decay_is_eyring():
+    """For short times E(t) ~ 1 - t c sum_a (-ln rho_a) <|u_a|> / L_a with <|u_a|> = 1/2 over
+    the sphere; with one absorption alpha on every wall (rho = 1 - alpha) that is
+    Eyring's energy decay rate c S (-ln(1 - alpha)) / (4 V)."""
+    L = np.array([7.0, 5.0, 3.2])
+    alpha = 0.3
+    b = math.sqrt(1 - alpha)
+    V = float(np.prod(L))
+    S = 2 * (L[0] * L[1] + L[1] * L[2] + L[0] * L[2])
+    rate = 343.0 * S * (-math.log(1 - alpha)) / (4 * V)
+    h = 1e-6
+    slope = (oracle.lj_energy(L, [b] * 6, 343.0, h) - oracle.lj_energy(L, [b] * 6, 343.0, 0.0)) / h
+    assert slope == pytest.approx(-rate, rel=1e-4)
+    # and it falls monotonically, log-convex (a mixture of exponentials)
+    t = np.linspace(0.0, 1.0, 41)
+    E = oracle.lj_energy(L, [b] * 6, 343.0, t)
+    assert np.all(np.diff(E) < 0)
+    assert np.all(np.diff(np.log(E), 2) >= -1e-12)
+
+
+def test_lj_energy_follows_the_energy_decay_of_the_images():
+    """Brute force: the energy sum A_n^2 of the images whose delay falls in each
+    20 ms window (eq. (1)-(4), enumerated by the oracle) decays with the slope
+    of E(t) within 2 %, and its level is c / (4 pi V) E(t) on average within 10 %;
+    the Sabine exponential misses the slope of this room with unequal walls by
+    more than 25 %."""
+    L = np.array([5.0, 4.0, 3.0])
+    beta = np.array([0.9, 0.85, 0.95, 0.8, 0.7, 0.9])
+    c, T = 343.0, 0.6
+    N = oracle.nb_img_from_t(T, L, c, 0.0)
+    im = oracle.enumerate_images(L, beta, c, [1.2, 1.7, 1.1], [3.9, 2.2, 1.8], N)
+    edges = np.arange(0.02, T, 0.02)
+    E_img = np.histogram(im["tau"], bins=edges, weights=im["A"] ** 2)[0] / np.diff(edges)
+    mid = 0.5 * (edges[1:] + edges[:-1])
+    pred = c / (4 * math.pi * np.prod(L)) * oracle.lj_energy(L, beta, c, mid)
+    sel = (mid > 0.05) & (mid < 0.56)
+    s_img = np.polyfit(mid[sel], np.log(E_img[sel]), 1)[0]
+    s_lj = np.polyfit(mid[sel], np.log(pred[sel]), 1)[0]
+    assert s_lj == pytest.approx(s_img, rel=0.02)
+    assert math.exp(np.mean(np.log(E_img[sel] / pred[sel]))) == pytest.approx(1.0, abs=0.1)
+    s_sabine = -6 * math.log(10) / oracle.t60_sabine(L, beta)
+    assert abs(s_sabine / s_img - 1) > 0.25
+
+
+def test_lj_envelope_amp_and_tail_level():
+    """If the image-source part already follows the decay E(t), the amplitude
+    fit returns its level at t0; the tail continues it: mean z^2 E(t) / E(t0) A."""
+    L, beta, c, fs, n_ism = [6.0, 5.0, 3.0], [0.9, 0.8, 0.85, 0.9, 0.7, 0.95], 343.0, 8000.0, 1600
+    k = np.arange(n_ism)
+    E = oracle.lj_energy(L, beta, c, np.concatenate([[n_ism / fs], k / fs]))
+    A0 = 2e-3
+    h = np.sqrt(A0 * E[1:] / E[0])
+    assert oracle.envelope_amp_lj(h, n_ism, fs, L, beta, c) == pytest.approx(A0, rel=1e-12)
+    n_s = 8000
+    rirs = np.stack([oracle.tail_lj(3, r, A0, n_ism, n_s, fs, L, beta, c)[n_ism:] for r in range(8)])
+    Et = oracle.lj_energy(L, beta, c, np.arange(n_ism, n_s) / fs) / E[0]
+    ratio = np.mean(rirs ** 2, axis=0) / (A0 * Et)   # unit-variance noise: mean 1
+    assert np.mean(ratio) == pytest.approx(1.0, abs=0.03)
+    # the noise is the bit-exact stream of the Sabine tail, only the envelope differs
+    z = oracle.noise(3, 5, n_ism, 50).astype(np.float64)
+    np.testing.assert_allclose(oracle.tail_lj(3, 5, A0, n_ism, n_s, fs, L, beta, c, ks=np.arange(n_ism, n_ism + 50)),
+                               z * np.sqrt(A0 * Et[:50]), rtol=1e-14)
+
+
+# --------------------------------------------------------------------------- #
 # Gradient: FP64 central finite differences of the oracle's own forward
 # --------------------------------------------------------------------------- #
 def test_gradient_matches_central_differences():
