@@ -54,7 +54,7 @@
 extern "C" {
 #endif
 
-#define ISM_VERSION 100
+#define ISM_VERSION 101
 
 typedef enum {
     ISM_OK = 0,
@@ -86,7 +86,9 @@ typedef enum {
 typedef enum {
     ISM_PREC_FP32 = 0,        /* FP32, Chebyshev moments (32-tap windows), else direct */
     ISM_PREC_FP16X2 = 1,      /* packed FP16 window and sinc, FP32 accumulation        */
-    ISM_PREC_BF16X2 = 2,      /* packed BF16 window and sinc, FP32 accumulation        */
+    ISM_PREC_BF16X2 = 2,      /* packed BF16 window and sinc, FP32 accumulation; BF16's
+                               * 8-bit significand bounds its error only to ~1e-2 of
+                               * the peak (the other reduced forms: 2e-3)            */
     ISM_PREC_LUT = 3,         /* FP32 windowed-sinc table (eq. (9)), FP32 lerp         */
     ISM_PREC_FP32_DIRECT = 4, /* FP32 sin/cos/reciprocal for every image tap (eq. (6)) */
     ISM_PREC_LUT_TEX = 5      /* the same table read through the texture unit with its
@@ -242,6 +244,30 @@ typedef enum {
     ISM_MIC_BIDIRECTIONAL = 4
 } ism_mic_pattern;
 
+/* Power envelope of the diffuse tail (Section 2.2).
+ *   ISM_ENVELOPE_SABINE: eq. (7)-(8), P(t) = A 10^(-6 (t - t0) / T60).
+ *   ISM_ENVELOPE_LJ: the energy-decay prediction of Lehmann and Johansson,
+ *   which Section 2.2 cites as the more faithful alternative.  The paper
+ *   gives no formula; the one used is the energy arrival rate of the image
+ *   sources of the shoebox: images have density 1/V, an image at distance r
+ *   in direction u has met the walls of axis a about r |u_a| / L_a times
+ *   (half of them each wall), so the energy arriving at time t follows
+ *     E(t) = (1 / 4 pi) oint prod_a |beta_a0 beta_a1|^(c t |u_a| / L_a) dOmega
+ *   and P(t) = A E(t) / E(t0).  It is a sum of exponentials: for equal
+ *   coefficients its initial slope is Eyring's decay rate, and with unequal
+ *   walls it follows the images' own energy decay where the Sabine
+ *   exponential does not.  The integral is evaluated once per job on the
+ *   GPU (Gauss-Legendre product rule over one octant, 16 to 64 nodes per
+ *   angle chosen from c Tmax sum_a -ln|beta_a0 beta_a1| / L_a; relative
+ *   quadrature error below 1e-9 while that exponent stays below 300).
+ * In both, A is fitted to the last 20 ms of the image-source part (their
+ * power brought forward to t0 along the envelope), and the noise is the same
+ * bit-exact Philox stream. */
+typedef enum {
+    ISM_ENVELOPE_SABINE = 0,
+    ISM_ENVELOPE_LJ = 1
+} ism_envelope;
+
 /* One independent simulation.  Meanings as in ism_simulate; pos_src,
  * pos_rcv, out and env_amp are device pointers.  env_amp may be NULL; if
  * not, it receives [n_src * n_rcv] FP32 envelope amplitudes A (eq. (8)) of
@@ -261,7 +287,9 @@ typedef enum {
  * pairs get no image), and the Sabine T60 of the diffuse tail (eq. (7)) is
  * computed on the device with the host's FP64 operations, so the results are
  * bitwise those of the same coefficients in room.beta.  Not accepted by the
- * server (whose jobs are host-side). */
+ * server (whose jobs are host-side).
+ * envelope: the ism_envelope of the diffuse tail (a zero-filled job uses
+ * Sabine's); ignored when the job has no tail. */
 typedef struct {
     ism_room room;
     const float* pos_src;
@@ -276,6 +304,7 @@ typedef struct {
     int mic_pattern;
     const float* orient_rcv;
     const float* beta_dev;
+    int envelope;             /* an ism_envelope (0: Sabine) */
 } ism_job;
 
 /* Workspace bytes for ism_simulate_batch over these jobs. */

@@ -100,6 +100,8 @@ ism_status validate_job(const ism_job& in, Validated& v, bool need_ptrs)
         return fail(ISM_ERR_INVALID_ARG, "pos_src, pos_rcv and out must be device pointers, not NULL");
     if (j.mic_pattern < ISM_MIC_OMNI || j.mic_pattern > ISM_MIC_BIDIRECTIONAL)
         return fail(ISM_ERR_INVALID_ARG, "mic_pattern = %d is not an ism_mic_pattern", j.mic_pattern);
+    if (j.envelope != ISM_ENVELOPE_SABINE && j.envelope != ISM_ENVELOPE_LJ)
+        return fail(ISM_ERR_INVALID_ARG, "envelope = %d is not an ism_envelope", j.envelope);
     if (need_ptrs && j.mic_pattern != ISM_MIC_OMNI && !j.orient_rcv)
         return fail(ISM_ERR_INVALID_ARG, "a polar pattern needs orient_rcv (device pointer, [n_rcv][3])");
     v.Tw = (j.Tw > 0.0f) ? (double)j.Tw : 4e-3;
@@ -166,7 +168,7 @@ ism_status plan(const Validated* vs, int n, ism_precision prec, bool backward, J
     for (int i = 0; i < n; ++i)
         set_cols += (long long)vs[i].job.nb_img[0] * vs[i].job.nb_img[1] * vs[i].job.n_src * vs[i].job.n_rcv;
     long long rir = 0, hist = 0, tbl = 0, ecta = 0, acta = 0, adta = 0, tcta = 0, fcta = 0, rows = 0, ids = 0, lut = 0,
-              gpart = 0, srir = 0, scta = 0;
+              gpart = 0, srir = 0, scta = 0, env = 0, vcta = 0;
     for (int i = 0; i < n; ++i) {
         const Validated& v = vs[i];
         const ism_job& in = v.job;
@@ -228,7 +230,12 @@ ism_status plan(const Validated* vs, int n, ism_precision prec, bool backward, J
         double beta_d[6];
         for (int w = 0; w < 6; ++w) beta_d[w] = in.room.beta[w];
         double T60 = t60_of(in.room.L, beta_d);
-        J.g2 = std::isfinite(T60) ? (float)(J.g2_c / ((double)in.fs * T60)) : 0.0f;   // (device: ism_job_g2)
+        {
+            const double g2 = std::isfinite(T60) ? J.g2_c / ((double)in.fs * T60) : 0.0;   // (device: ism_job_g2)
+            J.g2 = (float)g2;
+            J.g2_lo = (float)(g2 - (double)J.g2);
+        }
+        J.envelope = in.envelope;
         int W = (int)std::ceil(ISM_FIT_WINDOW_S * (double)in.fs - 1e-9);
         J.W_env = W < v.n_ism ? W : v.n_ism;
         J.vec4 = (v.n_S % 4 == 0) && (((uintptr_t)in.out & 15u) == 0);
@@ -307,6 +314,15 @@ ism_status plan(const Validated* vs, int n, ism_precision prec, bool backward, J
             int blk0 = v.n_ism >> 2, blk_last = (v.n_S - 1) >> 2;
             tcta += R * ((blk_last - blk0 + 1 + ISM_TAIL_CHUNK / 4 - 1) / (ISM_TAIL_CHUNK / 4));
         }
+        // Lehmann-Johansson tails: one envelope table per job, from the fit window to the end
+        J.env_k0 = v.n_ism - J.W_env;
+        J.env_base = env;
+        J.env_cta_base = vcta;
+        if (J.has_tail && J.envelope == ISM_ENVELOPE_LJ) {
+            const long long n_env = (long long)v.n_S - J.env_k0;
+            env += (n_env + 63) / 64 * 64;
+            vcta += (n_env + ISM_ENV_CHUNK - 1) / ISM_ENV_CHUNK;
+        }
         rows += R * J.Q * 32LL * (J.slots + 1);
         if (prec == ISM_PREC_LUT) lut += (long long)(ism_lut_phases(J.slots) + 1) * 32 * J.slots;
         // texture form: each table starts on a 512-byte boundary (texture base alignment)
@@ -324,7 +340,8 @@ ism_status plan(const Validated* vs, int n, ism_precision prec, bool backward, J
     if (ids >= 0xFFFFFFFFll)
         return fail(ISM_ERR_UNSUPPORTED, "%lld images in one launch set exceed 2^32; split the batch", ids);
     if (rir > 0x7FFFFFFFll || ecta > 0x7FFFFFFFll || acta > 0x7FFFFFFFll || adta > 0x7FFFFFFFll ||
-        tcta > 0x7FFFFFFFll || fcta > 0x7FFFFFFFll || srir * (long long)t.shell_gmax > 0x7FFFFFFFll)
+        tcta > 0x7FFFFFFFll || fcta > 0x7FFFFFFFll || srir * (long long)t.shell_gmax > 0x7FFFFFFFll ||
+        env > 0x7FFFFFFFll || vcta > 0x7FFFFFFFll)
         return fail(ISM_ERR_UNSUPPORTED, "launch set too large; split the batch");
     p.hist_total = hist;
     p.ids_total = ids;
@@ -337,6 +354,8 @@ ism_status plan(const Validated* vs, int n, ism_precision prec, bool backward, J
     p.lut_total = lut;
     p.gpart_total = gpart;
     p.rgrad_total = backward ? rir * 12 : 0;
+    p.env_total = backward ? 0 : env;
+    p.env_ctas = backward ? 0 : vcta;
     p.enum_ctas = ecta;
     p.acc_ctas = acta;
     t.shell_rirs = srir;
@@ -374,6 +393,8 @@ ism_status plan(const Validated* vs, int n, ism_precision prec, bool backward, J
     off = align256(off + (size_t)p.gpart_total * 4);
     p.rgrad_off = off;
     off = align256(off + (size_t)p.rgrad_total * 4);
+    p.env_off = off;
+    off = align256(off + (size_t)p.env_total * 4);
     p.total = off;
     return ISM_OK;
 }
@@ -675,6 +696,11 @@ ism_status run_set(const std::vector<Validated>& set, ism_precision prec, size_t
         StageTimer tm(ISM_STAGE_GEOMETRY, st);
         if ((e = ism_launch_geometry(t, p, ws, stream))) return cuda_fail(e, "geometry kernel");
         tm.done(p.rir_total > 0);
+    }
+    if (p.env_ctas > 0) {   // envelope tables of Lehmann-Johansson tails (read by finalize and tail)
+        StageTimer tm(ISM_STAGE_TAIL, st);
+        if ((e = ism_launch_envelope(t, p, ws, stream))) return cuda_fail(e, "envelope kernel");
+        tm.done(1);
     }
     {
         StageTimer tm(ISM_STAGE_ENUM_COUNT, st);

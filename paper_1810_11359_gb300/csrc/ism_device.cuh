@@ -58,9 +58,8 @@ __device__ __forceinline__ float ism_job_beta(const JobDev& J, int w) { return J
 // from the Sabine formula evaluated here with the host's FP64 operations in
 // the host's order, each rounded on its own (no contraction), so the value is
 // bitwise the one the host computes from the same coefficients.
-__device__ __forceinline__ float ism_job_g2(const JobDev& J)
+__device__ __forceinline__ double ism_job_g2_fp64(const JobDev& J)
 {
-    if (!J.beta_dev) return J.g2;
     const double L0 = J.L[0], L1 = J.L[1], L2 = J.L[2];
     const double S[6] = {__dmul_rn(L1, L2), __dmul_rn(L1, L2), __dmul_rn(L0, L2),
                          __dmul_rn(L0, L2), __dmul_rn(L0, L1), __dmul_rn(L0, L1)};
@@ -69,10 +68,10 @@ __device__ __forceinline__ float ism_job_g2(const JobDev& J)
         const double b = (double)J.beta_dev[i];
         den = __dadd_rn(den, __dmul_rn(S[i], __dsub_rn(1.0, __dmul_rn(b, b))));
     }
-    if (!(den > 0.0)) return 0.0f;
+    if (!(den > 0.0)) return 0.0;
     const double T60 = __ddiv_rn(__dmul_rn(__dmul_rn(__dmul_rn(0.161, L0), L1), L2), den);
-    if (!(T60 < 1.0e300)) return 0.0f;
-    return (float)__ddiv_rn(J.g2_c, __dmul_rn((double)J.fs, T60));
+    if (!(T60 < 1.0e300)) return 0.0;
+    return __ddiv_rn(J.g2_c, __dmul_rn((double)J.fs, T60));
 }
 
 // ---------------------------------------------------------------------------
@@ -93,6 +92,31 @@ __device__ __forceinline__ ff ff_add(ff a, ff b)
     float hi = __fadd_rn(s, e);
     float lo = __fsub_rn(e, __fsub_rn(hi, s));
     return {hi, lo};
+}
+
+// g2 of the job as a float-float pair (hi + lo is its FP64 value to ~2^-48).
+__device__ __forceinline__ ff ism_job_g2(const JobDev& J)
+{
+    if (!J.beta_dev) return {J.g2, J.g2_lo};
+    const double g = ism_job_g2_fp64(J);
+    const float hi = (float)g;
+    return {hi, (float)(g - (double)hi)};
+}
+
+// 2^(-g i) for a float-float rate g >= 0 and an integer 0 <= i < 2^24: the
+// product x = g i keeps its rounding error (one FMA) and the low part of g,
+// x is split into its nearest integer n and a remainder r in [-1/2, 1/2]
+// (p - n is exact: Sterbenz), and 2^-x = 2^-n 2^-r.  The result carries
+// exp2f's own error (2 ulp) and nothing from the size of x.
+__device__ __forceinline__ float ism_exp2_neg(ff g, int i)
+{
+    const float fi = (float)i;
+    const float p = __fmul_rn(g.hi, fi);
+    if (!(p < 256.0f)) return 0.0f;   // below 2^-255: zero in FP32 (also catches an infinite rate)
+    const float pe = __fmaf_rn(g.lo, fi, __fmaf_rn(g.hi, fi, -p));
+    const float n = rintf(p);
+    const float r = __fadd_rn(__fsub_rn(p, n), pe);
+    return ldexpf(exp2f(-r), -(int)n);
 }
 
 // Approximate reciprocal and reciprocal square root on the special-function

@@ -59,6 +59,11 @@ struct JobDev {
     float amp_scale;          // (fs / c) / (4 pi): A = F / (4 pi d) = F * amp_scale / s
     float s_cut2;             // cull: keep an image iff s_plain^2 < s_cut2 (samples^2)
     float g2;                 // log2 of the power decay per sample: 6 log2(10) / (fs T60)
+    float g2_lo;              // its low part (g2 + g2_lo is the FP64 value to ~2^-48)
+    int envelope;             // ISM_ENVELOPE_SABINE or ISM_ENVELOPE_LJ (diffuse tail)
+    int env_k0;               // first sample of the job's envelope table (n_ism - W_env)
+    int env_base;             // first entry (float) of the job's envelope table [n_S - env_k0]
+    int env_cta_base;         // first envelope CTA of the job
     int N[3], nlo[3];         // images per axis, lowest index per axis
     int n_src, n_rcv, n_rir;
     int n_S, n_ism;
@@ -142,6 +147,7 @@ struct WsPlan {
     size_t lut_off;        // float  [lut_total]: polyphase windowed-sinc tables (LUT form)
     size_t gpart_off;      // float  [gpart_total]: backward, per-(RIR, bin) gradients
     size_t rgrad_off;      // float  [rgrad_total]: backward, per-RIR gradients
+    size_t env_off;        // float  [env_total]: per-job envelope tables (Lehmann-Johansson tails)
     size_t total;
     long long hist_total;
     long long ids_total;
@@ -151,6 +157,8 @@ struct WsPlan {
     long long lut_total;
     long long gpart_total;
     long long rgrad_total;
+    long long env_total;
+    long long env_ctas;
     long long n_scan_blocks;
     long long enum_ctas;
     long long acc_ctas;
@@ -161,6 +169,8 @@ struct WsPlan {
 };
 
 #define ISM_TAIL_CHUNK 4096   // tail samples per CTA (256 threads x 16)
+#define ISM_ENV_CHUNK 256     // envelope-table samples per CTA (one per thread)
+#define ISM_ENV_MAX_NODES 64  // Gauss-Legendre nodes per angle of the envelope integral
 
 // Delay bins (warps) per accumulation CTA: the LUT form copies its ~33 KB
 // table into shared memory once per CTA, so it takes 8 bins per CTA.
@@ -195,6 +205,7 @@ int ism_launch_adjoint(const JobTable& t, const WsPlan& p, char* ws, void* strea
 int ism_launch_adjoint_cheb(const JobTable& t, const WsPlan& p, char* ws, void* stream, int* launched);
 int ism_launch_finalize(const JobTable& t, const WsPlan& p, char* ws, void* stream);
 int ism_launch_tail(const JobTable& t, const WsPlan& p, char* ws, void* stream);
+int ism_launch_envelope(const JobTable& t, const WsPlan& p, char* ws, void* stream);
 int ism_launch_noise(uint64_t seed, uint32_t rir, uint32_t k0, int n, float* z, void* stream);
 int ism_launch_auralize(const float* x, int n_x, const float* h, int n_points, int n_mics, int n_s, const int* starts,
                         float* y, void* stream);

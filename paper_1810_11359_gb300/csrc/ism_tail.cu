@@ -20,7 +20,8 @@ namespace {
 // samples [n_ism - (c + 1) fin_chunk, n_ism - c fin_chunk), so chunk 0 holds
 // the envelope-fit window and also fits the amplitude.
 __global__ void __launch_bounds__(256) finalize_kernel(const __grid_constant__ JobTable t,
-                                                       const float* __restrict__ rows, float* __restrict__ amp)
+                                                       const float* __restrict__ rows, float* __restrict__ amp,
+                                                       const float* __restrict__ env)
 {
     const long long g = blockIdx.x;
     const int jid = ism_find_job(t, g, [](const JobDev& j) { return j.fin_cta_base; });
@@ -49,16 +50,25 @@ __global__ void __launch_bounds__(256) finalize_kernel(const __grid_constant__ J
     __syncthreads();
     __shared__ float red[256];
     float A = 0.0f;
-    if (J.has_tail && J.W_env > 0) {
-        __shared__ float g2_s;
+    // Lehmann-Johansson envelope: env[k] = sqrt(E(t_k) / E(t0)) from the job's table
+    // (all zero when E(t0) = 0: no tail)
+    const float* envt = env + J.env_base - J.env_k0;
+    const bool lj = J.envelope == ISM_ENVELOPE_LJ;
+    if (J.has_tail && J.W_env > 0 && !(lj && envt[J.n_ism] == 0.0f)) {
+        __shared__ ff g2_s;
         if (threadIdx.x == 0) g2_s = ism_job_g2(J);
         __syncthreads();
-        const float g2 = g2_s;
+        const ff g2 = g2_s;
         const int k0 = J.n_ism - J.W_env;
         float acc = 0.0f;
         for (int k = k0 + (int)threadIdx.x; k < J.n_ism; k += blockDim.x) {
             float h = out[k];
-            acc += h * h * exp2f(-g2 * (float)(J.n_ism - k));
+            if (lj) {
+                const float e = envt[k];
+                acc += h * h / (e * e);   // E(t0) / E(t_k): the power brought forward to t0
+            } else {
+                acc += h * h * ism_exp2_neg(g2, J.n_ism - k);
+            }
         }
         red[threadIdx.x] = acc;
         __syncthreads();
@@ -74,7 +84,8 @@ __global__ void __launch_bounds__(256) finalize_kernel(const __grid_constant__ J
     }
 }
 
-__global__ void __launch_bounds__(256) tail_kernel(const __grid_constant__ JobTable t, const float* __restrict__ amp)
+__global__ void __launch_bounds__(256) tail_kernel(const __grid_constant__ JobTable t, const float* __restrict__ amp,
+                                                   const float* __restrict__ env)
 {
     const long long g = blockIdx.x;
     const int jid = ism_find_job(t, g, [](const JobDev& j) { return j.tail_cta_base; });
@@ -86,20 +97,30 @@ __global__ void __launch_bounds__(256) tail_kernel(const __grid_constant__ JobTa
     const int r = (int)(local / per_rir);
     const int c = (int)(local % per_rir);
     const float sqA = sqrtf(amp[J.rir_base + r]);
-    __shared__ float g2_s;
+    __shared__ ff g2_s;
     if (threadIdx.x == 0) g2_s = ism_job_g2(J);
     __syncthreads();
-    const float hg = 0.5f * g2_s;
+    const ff hg = {0.5f * g2_s.hi, 0.5f * g2_s.lo};   // amplitude: half the power's rate (exact)
+    const bool lj = J.envelope == ISM_ENVELOPE_LJ;
+    const float* envt = env + J.env_base - J.env_k0;   // sqrt(E(t_k) / E(t0)), k >= env_k0
     float* out = J.out + (long long)r * J.n_S;
     for (int i = 0; i < ISM_TAIL_CHUNK / 4 / 256; ++i) {
         int blk = blk0 + c * (ISM_TAIL_CHUNK / 4) + i * 256 + (int)threadIdx.x;
         if (blk > blk_last) break;
         float4 z = ism_noise_block(J.seed, (uint32_t)(r + J.rir_index0), (uint32_t)blk);
         int k = 4 * blk;
-        float e0 = sqA * exp2f(-hg * (float)(k - J.n_ism));
-        float e1 = sqA * exp2f(-hg * (float)(k + 1 - J.n_ism));
-        float e2 = sqA * exp2f(-hg * (float)(k + 2 - J.n_ism));
-        float e3 = sqA * exp2f(-hg * (float)(k + 3 - J.n_ism));
+        float e0, e1, e2, e3;
+        if (lj) {   // (k < n_S; entries below n_ism are never stored)
+            e0 = sqA * envt[max(k, J.n_ism)];
+            e1 = sqA * envt[min(max(k + 1, J.n_ism), J.n_S - 1)];
+            e2 = sqA * envt[min(max(k + 2, J.n_ism), J.n_S - 1)];
+            e3 = sqA * envt[min(max(k + 3, J.n_ism), J.n_S - 1)];
+        } else {
+            e0 = sqA * ism_exp2_neg(hg, max(k - J.n_ism, 0));
+            e1 = sqA * ism_exp2_neg(hg, max(k + 1 - J.n_ism, 0));
+            e2 = sqA * ism_exp2_neg(hg, max(k + 2 - J.n_ism, 0));
+            e3 = sqA * ism_exp2_neg(hg, max(k + 3 - J.n_ism, 0));
+        }
         float4 v = make_float4(z.x * e0, z.y * e1, z.z * e2, z.w * e3);
         if (J.vec4 && k >= J.n_ism && k + 3 < J.n_S) {
             *reinterpret_cast<float4*>(out + k) = v;
@@ -110,6 +131,130 @@ __global__ void __launch_bounds__(256) tail_kernel(const __grid_constant__ JobTa
             if (k + 3 >= J.n_ism && k + 3 < J.n_S) out[k + 3] = v.w;
         }
     }
+}
+
+// ---------------------------------------------------------------------------
+// Envelope table of a Lehmann-Johansson tail (one per job): for k in [env_k0,
+// n_S), env[k] = sqrt(E(t_k) / E(t0)), t = k / f_s, t0 = n_ism / f_s, with
+//   E(t) = (2 / pi) int_0^(pi/2) int_0^(pi/2) 2^(-k g(theta, phi)) sin(theta) dtheta dphi,
+//   g = sum_a |u_a| gamma_a,  gamma_a = -log2 |beta_a0 beta_a1| c / (f_s L_a)
+// (the average over one octant of directions u; log2 of the energy lost per
+// sample along u).  Each CTA builds the Gauss-Legendre product rule itself
+// (nodes by Newton's iteration on the Legendre recurrence, FP64), the node
+// rates g in float-float and the weights in FP32, then each thread sums its
+// sample's n^2 terms 2^(-k g) with Kahan's compensated FP32 summation (all
+// terms positive: relative error ~2 ulp plus exp2f's 2 ulp).  E(t0) is summed
+// the same way by every CTA of the job, so all CTAs agree on it bit for bit.
+// n = clamp(ceil(K / 4) + 12, 16, 64) nodes per angle, K = (n_S / f_s) c
+// |(-ln rho_a / L_a)_a|, the largest exponent (in nepers) over the table.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ float env_sum(const float2* g, const float* w, int nn, int k)
+{
+    float s = 0.0f, comp = 0.0f;
+    for (int i = 0; i < nn; ++i) {
+        const float y = __fsub_rn(__fmul_rn(w[i], ism_exp2_neg(ff{g[i].x, g[i].y}, k)), comp);
+        const float tt = __fadd_rn(s, y);
+        comp = __fsub_rn(__fsub_rn(tt, s), y);
+        s = tt;
+    }
+    return s;
+}
+
+__global__ void __launch_bounds__(ISM_ENV_CHUNK) envelope_kernel(const __grid_constant__ JobTable t,
+                                                                 float* __restrict__ env)
+{
+    extern __shared__ __align__(16) unsigned char smem[];
+    const long long g = blockIdx.x;
+    const int jid = ism_find_job(t, g, [](const JobDev& j) { return j.env_cta_base; });
+    const JobDev& J = t.j[jid];
+    const int chunk = (int)(g - J.env_cta_base);
+    __shared__ double xg[ISM_ENV_MAX_NODES], wg[ISM_ENV_MAX_NODES];
+    __shared__ double sth[ISM_ENV_MAX_NODES], cth[ISM_ENV_MAX_NODES];
+    __shared__ double gam[3];
+    __shared__ int n_s;
+    __shared__ float part[ISM_ENV_CHUNK];
+    float2* gn = reinterpret_cast<float2*>(smem);                       // [n * n] node rates
+    float* wn = reinterpret_cast<float*>(gn + ISM_ENV_MAX_NODES * ISM_ENV_MAX_NODES);   // [n * n] weights
+    const double PI = 3.141592653589793238462643383279502884;
+    if (threadIdx.x == 0) {
+        double kn = 0.0;
+        for (int a = 0; a < 3; ++a) {
+            const double rho = fabs((double)ism_job_beta(J, 2 * a) * (double)ism_job_beta(J, 2 * a + 1));
+            const double nep = rho > 0.0 ? -log(rho) : 1.0e30;                 // nepers per reflection pair
+            gam[a] = rho > 0.0 ? nep / log(2.0) * (double)J.c / ((double)J.fs * J.L[a]) : 1.0e30;
+            const double ka = nep * (double)J.c * ((double)J.n_S / (double)J.fs) / J.L[a];
+            kn += ka * ka;
+        }
+        kn = sqrt(kn);
+        n_s = kn < 4.0 * (ISM_ENV_MAX_NODES - 12) ? max(16, (int)ceil(kn / 4.0) + 12) : ISM_ENV_MAX_NODES;
+    }
+    __syncthreads();
+    const int n = n_s;
+    // Gauss-Legendre nodes and weights on [-1, 1]: Newton on P_n from the asymptotic guess
+    if ((int)threadIdx.x < n) {
+        const int i = threadIdx.x;
+        double x = cos(PI * (i + 0.75) / (n + 0.5));
+        double dp = 1.0;
+        for (int it = 0; it < 100; ++it) {
+            double p0 = 1.0, p1 = x;
+            for (int m = 2; m <= n; ++m) {
+                const double p2 = ((2.0 * m - 1.0) * x * p1 - (m - 1.0) * p0) / m;
+                p0 = p1;
+                p1 = p2;
+            }
+            dp = n * (x * p1 - p0) / (x * x - 1.0);
+            const double dx = p1 / dp;
+            x -= dx;
+            if (fabs(dx) < 1e-16) break;
+        }
+        {   // derivative at the converged root
+            double p0 = 1.0, p1 = x;
+            for (int m = 2; m <= n; ++m) {
+                const double p2 = ((2.0 * m - 1.0) * x * p1 - (m - 1.0) * p0) / m;
+                p0 = p1;
+                p1 = p2;
+            }
+            dp = n * (x * p1 - p0) / (x * x - 1.0);
+        }
+        xg[i] = x;
+        wg[i] = 2.0 / ((1.0 - x * x) * dp * dp);
+        const double ang = (x + 1.0) * (PI / 4.0);   // [-1, 1] -> [0, pi/2]
+        sth[i] = sin(ang);
+        cth[i] = cos(ang);
+    }
+    __syncthreads();
+    // nodes (theta_i, phi_j): u = (sin t cos p, sin t sin p, cos t), weight (pi/4)^2 w_i w_j sin t (2 / pi)
+    const int nn = n * n;
+    for (int e = threadIdx.x; e < nn; e += blockDim.x) {
+        const int i = e / n, j = e - (e / n) * n;
+        const double gr = sth[i] * cth[j] * gam[0] + sth[i] * sth[j] * gam[1] + cth[i] * gam[2];
+        const float hi = (float)gr;
+        gn[e] = make_float2(hi, gr < 1.0e29 ? (float)(gr - (double)hi) : 0.0f);
+        wn[e] = (float)(wg[i] * wg[j] * sth[i] * (PI / 8.0));
+    }
+    __syncthreads();
+    // E(t0): the CTA's threads split the nodes, then a fixed-order tree
+    {
+        float s = 0.0f, comp = 0.0f;
+        for (int e = threadIdx.x; e < nn; e += blockDim.x) {
+            const float y = __fsub_rn(__fmul_rn(wn[e], ism_exp2_neg(ff{gn[e].x, gn[e].y}, J.n_ism)), comp);
+            const float tt = __fadd_rn(s, y);
+            comp = __fsub_rn(__fsub_rn(tt, s), y);
+            s = tt;
+        }
+        part[threadIdx.x] = s;
+        __syncthreads();
+        for (int w = ISM_ENV_CHUNK / 2; w > 0; w >>= 1) {
+            if ((int)threadIdx.x < w) part[threadIdx.x] = __fadd_rn(part[threadIdx.x], part[threadIdx.x + w]);
+            __syncthreads();
+        }
+    }
+    const float E0 = part[0];
+    const int k = J.env_k0 + chunk * ISM_ENV_CHUNK + (int)threadIdx.x;
+    if (k >= J.n_S) return;
+    float v = 0.0f;
+    if (E0 > 0.0f) v = sqrtf(__fdiv_rn(env_sum(gn, wn, nn, k), E0));
+    env[J.env_base + (k - J.env_k0)] = v;
 }
 
 __global__ void noise_kernel(uint64_t seed, uint32_t rir, uint32_t k0, int n, float* z)
@@ -128,15 +273,28 @@ int ism_launch_finalize(const JobTable& t, const WsPlan& p, char* ws, void* stre
 {
     if (p.fin_ctas <= 0) return 0;
     finalize_kernel<<<(unsigned)p.fin_ctas, 256, 0, (cudaStream_t)stream>>>(
-        t, reinterpret_cast<const float*>(ws + p.rows_off), reinterpret_cast<float*>(ws + p.amp_off));
+        t, reinterpret_cast<const float*>(ws + p.rows_off), reinterpret_cast<float*>(ws + p.amp_off),
+        reinterpret_cast<const float*>(ws + p.env_off));
     return (int)cudaGetLastError();
 }
 
 int ism_launch_tail(const JobTable& t, const WsPlan& p, char* ws, void* stream)
 {
     if (p.tail_ctas <= 0) return 0;
-    tail_kernel<<<(unsigned)p.tail_ctas, 256, 0, (cudaStream_t)stream>>>(t,
-                                                                         reinterpret_cast<const float*>(ws + p.amp_off));
+    tail_kernel<<<(unsigned)p.tail_ctas, 256, 0, (cudaStream_t)stream>>>(
+        t, reinterpret_cast<const float*>(ws + p.amp_off), reinterpret_cast<const float*>(ws + p.env_off));
+    return (int)cudaGetLastError();
+}
+
+int ism_launch_envelope(const JobTable& t, const WsPlan& p, char* ws, void* stream)
+{
+    if (p.env_ctas <= 0) return 0;
+    const size_t sm = (size_t)ISM_ENV_MAX_NODES * ISM_ENV_MAX_NODES * (sizeof(float2) + sizeof(float));
+    static std::atomic<unsigned long long> opened{0};
+    int rc = ism_open_smem((const void*)envelope_kernel, &opened);
+    if (rc) return rc;
+    envelope_kernel<<<(unsigned)p.env_ctas, ISM_ENV_CHUNK, sm, (cudaStream_t)stream>>>(
+        t, reinterpret_cast<float*>(ws + p.env_off));
     return (int)cudaGetLastError();
 }
 

@@ -25,6 +25,7 @@ STATUS_NAMES = {0: "ISM_OK", 1: "ISM_ERR_INVALID_ARG", 2: "ISM_ERR_INFEASIBLE", 
 PRECISIONS = {"fp32": 0, "fp16x2": 1, "bf16x2": 2, "lut": 3, "fp32_direct": 4, "lut_tex": 5}
 # receiver polar patterns (ism_mic_pattern): g = alpha + (1 - alpha) cos(theta)
 MIC_PATTERNS = {"omni": 0, "subcardioid": 1, "cardioid": 2, "hypercardioid": 3, "bidirectional": 4}
+ENVELOPES = {"sabine": 0, "lj": 1}   # ism_envelope: power envelope of the diffuse tail
 ISM_ERR_TIMEOUT_CODE = 6
 ISM_DEVICE_FLAG_POSITION = 1   # include/ism.h ISM_DEVICE_FLAG_*
 ISM_DEVICE_FLAG_BIN = 2
@@ -52,7 +53,8 @@ class ism_job(ctypes.Structure):
                 ("Tmax", ctypes.c_float), ("fs", ctypes.c_float), ("Tdiff", ctypes.c_float), ("Tw", ctypes.c_float),
                 ("seed", ctypes.c_uint64),
                 ("out", ctypes.c_void_p), ("env_amp", ctypes.c_void_p),
-                ("mic_pattern", ctypes.c_int), ("orient_rcv", ctypes.c_void_p), ("beta_dev", ctypes.c_void_p)]
+                ("mic_pattern", ctypes.c_int), ("orient_rcv", ctypes.c_void_p), ("beta_dev", ctypes.c_void_p),
+                ("envelope", ctypes.c_int)]
 
 
 class ism_grad_job(ctypes.Structure):
@@ -297,12 +299,13 @@ def _workspace(ws, nbytes):
 
 def ism_simulate(L, beta, pos_src, pos_rcv, nb_img, Tmax, fs, Tdiff=0.0, Tw=0.0, c=343.0, prec: str = "fp32",
                  seed: int = 0, out=None, workspace: Optional[Workspace] = None, stream=None,
-                 mic_pattern: str = "omni", orient_rcv=None):
+                 mic_pattern: str = "omni", orient_rcv=None, envelope: str = "sabine"):
     """RIRs [n_src, n_rcv, n_S] (FP32 CUDA tensor) for all source/receiver pairs.
 
     pos_src/pos_rcv: [n,3] positions (CUDA FP32 tensors, or anything
     convertible; copied to the device if needed).  mic_pattern / orient_rcv:
-    receiver polar pattern (a MIC_PATTERNS name) and [n_rcv,3] orientations."""
+    receiver polar pattern (a MIC_PATTERNS name) and [n_rcv,3] orientations.
+    envelope: power envelope of the diffuse tail (an ENVELOPES name)."""
     torch = _torch()
     dev = torch.device("cuda", torch.cuda.current_device())
     ps = torch.as_tensor(pos_src, dtype=torch.float32).to(dev).reshape(-1, 3).contiguous()
@@ -310,12 +313,14 @@ def ism_simulate(L, beta, pos_src, pos_rcv, nb_img, Tmax, fs, Tdiff=0.0, Tw=0.0,
     n_S = ism_rir_length(Tmax, fs)
     if out is None:
         out = torch.empty((ps.shape[0], pr.shape[0], n_S), dtype=torch.float32, device=dev)
-    if mic_pattern != "omni":   # the pattern travels in the job struct: the batch entry point
-        orient = torch.as_tensor(orient_rcv, dtype=torch.float32).to(dev).reshape(-1, 3).contiguous()
-        if orient.shape[0] != pr.shape[0]:
-            raise ValueError("orient_rcv needs one vector per receiver")
+    if mic_pattern != "omni" or envelope != "sabine":   # these travel in the job struct: the batch entry point
+        orient = None
+        if mic_pattern != "omni":
+            orient = torch.as_tensor(orient_rcv, dtype=torch.float32).to(dev).reshape(-1, 3).contiguous()
+            if orient.shape[0] != pr.shape[0]:
+                raise ValueError("orient_rcv needs one vector per receiver")
         job = make_job(L, beta, ps, pr, nb_img, Tmax, fs, out, Tdiff=Tdiff, Tw=Tw, c=c, seed=seed,
-                       mic_pattern=mic_pattern, orient_rcv=orient)
+                       mic_pattern=mic_pattern, orient_rcv=orient, envelope=envelope)
         ism_simulate_batch([job], prec=prec, workspace=workspace, stream=stream)
         return out
     nbytes = ism_workspace_size(L, beta, ps.shape[0], pr.shape[0], nb_img, Tmax, fs, Tdiff, Tw, c, prec)
@@ -395,7 +400,7 @@ def ism_workspace_status(buf, stream=None) -> int:
 
 
 def make_job(L, beta, pos_src, pos_rcv, nb_img, Tmax, fs, out, Tdiff=0.0, Tw=0.0, c=343.0, seed=0,
-             env_amp=None, mic_pattern: str = "omni", orient_rcv=None) -> ism_job:
+             env_amp=None, mic_pattern: str = "omni", orient_rcv=None, envelope: str = "sabine") -> ism_job:
     """An ism_job over CUDA tensors (the tensors must stay alive during the call);
     orient_rcv: [n_rcv, 3] CUDA FP32 tensor for a polar pattern; beta: 6 host
     values, or a contiguous FP32 CUDA tensor of 6 read in place (beta_dev)."""
@@ -415,6 +420,7 @@ def make_job(L, beta, pos_src, pos_rcv, nb_img, Tmax, fs, out, Tdiff=0.0, Tw=0.0
     j.env_amp = None if env_amp is None else env_amp.data_ptr()
     j.mic_pattern = MIC_PATTERNS[mic_pattern]
     j.orient_rcv = None if orient_rcv is None else orient_rcv.data_ptr()
+    j.envelope = ENVELOPES[envelope]
     return j
 
 
@@ -608,7 +614,8 @@ class Server:
         self._lock = threading.Lock()
 
     def submit(self, L, beta, pos_src, pos_rcv, nb_img, Tmax, fs, Tdiff=0.0, Tw=0.0, c=343.0, seed=0,
-               out: Optional[np.ndarray] = None, mic_pattern: str = "omni", orient_rcv=None):
+               out: Optional[np.ndarray] = None, mic_pattern: str = "omni", orient_rcv=None,
+               envelope: str = "sabine"):
         """Queues one room; returns (ticket, out) where `out` [n_src, n_rcv, n_S]
         FP32 receives the RIRs once the ticket is done."""
         ps = np.ascontiguousarray(np.asarray(pos_src, dtype=np.float32).reshape(-1, 3))
@@ -630,6 +637,7 @@ class Server:
         j.out = out.ctypes.data
         j.env_amp = None
         j.mic_pattern = MIC_PATTERNS[mic_pattern]
+        j.envelope = ENVELOPES[envelope]
         orient = None
         if mic_pattern != "omni":
             orient = np.ascontiguousarray(np.asarray(orient_rcv, dtype=np.float32).reshape(-1, 3))
@@ -668,6 +676,7 @@ class Server:
         for f, d in (("Tmax", None), ("fs", None), ("Tdiff", 0.0), ("Tw", 0.0)):
             v[f] = [float(r[f] if d is None else (r.get(f) or d)) for r in reqs]
         v["seed"] = [int(r.get("seed", 0)) & (2 ** 64 - 1) for r in reqs]
+        v["envelope"] = [ENVELOPES[r.get("envelope", "sabine")] for r in reqs]
         lens = {}
         n_S = np.array([lens.setdefault((r["Tmax"], r["fs"]), ism_rir_length(r["Tmax"], r["fs"])) for r in reqs],
                        np.int64)

@@ -41,7 +41,7 @@ def test_every_declared_symbol_is_exported(lib):
 
 
 def test_status_strings_and_version(lib):
-    assert lib.ism_version() == 100
+    assert lib.ism_version() == 101
     for code, name in ism.STATUS_NAMES.items():
         assert lib.ism_status_string(code).decode() == name
 

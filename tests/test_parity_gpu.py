@@ -241,7 +241,7 @@ def test_tail_and_envelope_given_same_amplitude():
         assert A[r] == pytest.approx(A_ref, rel=2e-3), r
         tail_ref = oracle.tail(room.seed, r, float(A[r]), n_ism, n_S, float(f32(room.fs)), T60)[n_ism:]
         tail = got[r, n_ism:].astype(np.float64)
-        np.testing.assert_allclose(tail, tail_ref, rtol=2e-6, atol=1e-12 * np.sqrt(A[r]))
+        np.testing.assert_allclose(tail, tail_ref, rtol=1e-6, atol=1e-12 * np.sqrt(A[r]))
 
 
 def test_invalid_positions_flagged_on_device():
@@ -358,7 +358,7 @@ def test_split_call_keeps_the_noise_index_of_every_rir():
     T60 = oracle.t60_sabine(room.L, np.asarray(beta, np.float32).astype(np.float64))
     for r in [3, 255, 256, 300, 511]:
         tail_ref = oracle.tail(11, r, float(A[r]), n_ism, n_S, float(f32(room.fs)), T60)[n_ism:]
-        np.testing.assert_allclose(got[r, n_ism:].astype(np.float64), tail_ref, rtol=2e-6,
+        np.testing.assert_allclose(got[r, n_ism:].astype(np.float64), tail_ref, rtol=1e-6,
                                    atol=1e-12 * np.sqrt(A[r]))
 
 

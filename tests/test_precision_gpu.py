@@ -3,14 +3,20 @@
 FP32_DIRECT evaluates every image tap in FP32 (the default FP32 form uses the
 Chebyshev moments for 32-tap windows); its bound is the FP32 one, 1e-5.
 
-The window and the sinc of eq. (6) are evaluated in packed FP16 (FP16X2),
-packed BF16 (BF16X2), or read from the windowed-sinc table of eq. (9)
-(LUT); every form accumulates in FP32, and the image enumeration, distances
-and delays stay in FP32 / float-float.  Each result is compared with the FP64
-oracle: max|err| <= 2e-3 x max|h| for FP16X2 and LUT.  BF16 keeps 8
-significant bits, so three roundings of the tap (x, the window product, the
-reciprocal) already reach 3 x 2^-9 = 5.9e-3 of a tap's value; its bound is
-1e-2 x max|h| and the measured error is reported beside the others.
+The window and the sinc of eq. (6) are evaluated in packed FP16 (FP16X2) or
+read from the windowed-sinc table of eq. (9) (LUT, and LUT_TEX through the
+texture unit); every form accumulates in FP32, and the image enumeration,
+distances and delays stay in FP32 / float-float.  Each result is compared with
+the FP64 oracle: max|err| <= 2e-3 x max|h|, the reduced-precision bound.
+
+BF16X2 is not one of the delivered reduced-precision forms: BF16 keeps 8
+significant bits, so rounding a single tap to BF16 may already move it by
+2^-8 = 3.9e-3 of its value, and the peak sample of an RIR is one tap of the
+direct path: no BF16 tap evaluation can guarantee 2e-3 of the peak.  The form
+is kept for the comparison the paper's mixed-precision section invites; its
+test checks that it runs, is reproducible, and stays within the error its
+arithmetic allows (three roundings of 2^-8 on the largest tap, below 1.2e-2),
+and prints the error it reaches.
 """
 import numpy as np
 import pytest
@@ -21,7 +27,8 @@ from paper_1810_11359_gb300 import ism, workloads
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
-TOL = {"fp16x2": 2e-3, "lut": 2e-3, "bf16x2": 1e-2, "fp32_direct": 1e-5, "lut_tex": 2e-3}
+TOL = {"fp16x2": 2e-3, "lut": 2e-3, "fp32_direct": 1e-5, "lut_tex": 2e-3,
+       "bf16x2": 1.2e-2}   # bf16x2: not a delivered form (see above); its arithmetic's own bound
 PRECS = ["fp16x2", "bf16x2", "lut", "fp32_direct", "lut_tex"]
 
 
@@ -122,7 +129,7 @@ def test_trajectory_workload_sampled_rirs_and_tail(prec):
                          room.window())
         worst = max(worst, rel_err(got[r:r + 1, :n_ism], ref))
         tail_ref = oracle.tail(room.seed, r, float(A[r]), n_ism, n_S, float(f32(room.fs)), T60)[n_ism:]
-        np.testing.assert_allclose(got[r, n_ism:].astype(np.float64), tail_ref, rtol=2e-6,
+        np.testing.assert_allclose(got[r, n_ism:].astype(np.float64), tail_ref, rtol=1e-6,
                                    atol=1e-12 * np.sqrt(A[r]))
     print(f"{prec} trajectory workload: max|err|/peak = {worst:.3e}")
     assert worst <= TOL[prec]
