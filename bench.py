@@ -192,12 +192,24 @@ def _oracle_pairs(room, beta, N, Tdiff, pairs, cores):
                            seed=room.seed, pairs=pairs, n_threads=cores)
 
 
+_CORES = []
+
+
+def host_cores():
+    """OpenMP threads of the oracle on this host, read once (an oracle call with an
+    explicit thread count changes what OpenMP reports afterwards)."""
+    if not _CORES:
+        import oracle
+        _CORES.append(int(oracle.max_threads()))
+    return _CORES[0]
+
+
 def cpu_baseline(room, beta, N, Tdiff, budget_s=15.0):
     """The FP64 oracle, as it stands, on the host cores over a bounded sample
     of the step's RIRs."""
     import oracle
     oracle.build()
-    cores = oracle.max_threads()
+    cores = host_cores()
     all_pairs = [(i, j) for i in range(room.pos_src.shape[0]) for j in range(room.pos_rcv.shape[0])]
     # calibrate on one RIR per core, then size the sample to the budget
     n = max(1, min(cores, len(all_pairs)))
@@ -218,6 +230,175 @@ def cpu_baseline(room, beta, N, Tdiff, budget_s=15.0):
                       f"{total_t:.1f} s"}
 
 
+def cpu_single_core(room, beta, N, Tdiff, budget_s=5.0):
+    """The FP64 oracle on one host core over a bounded sample of the step's RIRs."""
+    all_pairs = [(i, j) for i in range(room.pos_src.shape[0]) for j in range(room.pos_rcv.shape[0])]
+    t0 = time.perf_counter()
+    done = 0
+    while done < len(all_pairs) and time.perf_counter() - t0 < budget_s:
+        _oracle_pairs(room, beta, N, Tdiff, all_pairs[done:done + 1], 1)
+        done += 1
+    dt = time.perf_counter() - t0
+    return {"value": done / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"{done} of the step's {len(all_pairs)} RIRs on one core, {dt:.1f} s"}
+
+
+def _setup(name):
+    """(room, beta, N, Tdiff, n_S, n_ism, ps, pr) of a named workload, on the device."""
+    import torch
+    from paper_1810_11359_gb300 import ism
+    room, Tdiff, T_img = workload(name)
+    beta = ism.ism_beta_sabine(room.L, room.rt60)
+    N = ism.ism_nb_img_from_t(T_img, room.L, room.c, room.window())
+    n_S = ism.ism_rir_length(room.Tmax, room.fs)
+    n_ism = ism.ism_rir_length(Tdiff, room.fs) if Tdiff else n_S
+    dev = torch.device("cuda", torch.cuda.current_device())
+    ps = torch.from_numpy(room.pos_src).to(dev)
+    pr = torch.from_numpy(room.pos_rcv).to(dev)
+    return room, beta, N, Tdiff, n_S, n_ism, ps, pr
+
+
+def measure_forms(name, forms, steps, flush, peak_tops, envelope="sabine", counts=None):
+    """Each tap arithmetic on one workload, against the FP32 path on the same
+    GPU: RIRs/s of the whole step (CUDA events around each step, L2 flushed
+    before it, default internal lanes), the accumulation stage timed with every
+    launch on one stream (useful ops / time against the FP32 FMA peak), the
+    tail stage, and max|err| / peak of the image-source part against the FP32
+    path's (all RIRs) and against the FP64 oracle (one RIR)."""
+    import torch
+    import oracle
+    from paper_1810_11359_gb300 import ism
+    room, beta, N, Tdiff, n_S, n_ism, ps, pr = _setup(name)
+    dev = ps.device
+    n_rir = ps.shape[0] * pr.shape[0]
+    n_contrib, n_images = counts if counts is not None else contributions(room, beta, N, n_ism)
+    alg_ops = FMA_OPS_PER_CONTRIBUTION * n_contrib + OPS_PER_IMAGE * n_images
+    ws = ism.Workspace(dev)
+    outs = {}
+    res = {}
+    r_or = min(n_rir - 1, 301)
+    i_or, j_or = divmod(r_or, pr.shape[0])
+    ref_or = oracle.rir(room.L, np.asarray(beta, np.float32).astype(np.float64), float(np.float32(room.c)),
+                        float(np.float32(room.fs)), float(np.float32(room.window())), room.pos_src[i_or],
+                        room.pos_rcv[j_or], N, n_ism, n_threads=host_cores())
+    for form in ["fp32"] + [f for f in forms if f != "fp32"]:
+        out = torch.empty((ps.shape[0], pr.shape[0], n_S), dtype=torch.float32, device=dev)
+
+        def step():
+            ism.ism_simulate(room.L, beta, ps, pr, N, room.Tmax, room.fs, Tdiff=Tdiff, Tw=room.window(), c=room.c,
+                             prec=form, seed=room.seed, out=out, workspace=ws, envelope=envelope)
+
+        for _ in range(3):
+            step()
+        torch.cuda.synchronize()
+        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+        for a, b in evs:
+            flush.zero_()
+            a.record()
+            step()
+            b.record()
+        torch.cuda.synchronize()
+        ms = sum(a.elapsed_time(b) for a, b in evs) / steps
+        ism.ism_set_lanes(1)
+        step()
+        torch.cuda.synchronize()
+        ism.ism_profile_reset()
+        ism.ism_profile_enable(True)
+        k = 5
+        for _ in range(k):
+            flush.zero_()
+            step()
+        torch.cuda.synchronize()
+        ism.ism_profile_enable(False)
+        prof = ism.ism_profile_read()
+        ism.ism_set_lanes(2)
+        acc_ms = prof["accum"][0] / k
+        got = out.cpu().numpy().reshape(n_rir, n_S)
+        outs[form] = got
+        e_or = float(np.max(np.abs(got[r_or, :n_ism].astype(np.float64) - ref_or)) / np.max(np.abs(ref_or)))
+        d = {"rirs_per_s": n_rir / (ms * 1e-3), "ms_per_step": ms, "accum_ms": acc_ms,
+             "accum_frac_of_fp32_peak": alg_ops / (acc_ms * 1e-3) / 1e12 / peak_tops,
+             "stage_ms": {kk: v[0] / k for kk, v in prof.items() if v[0] > 0},
+             "max_err_vs_oracle_rir": e_or, "oracle_rir": r_or}
+        if form != "fp32":
+            ref = outs["fp32"][:, :n_ism].astype(np.float64)
+            d["max_err_vs_fp32_path"] = float(np.max(np.abs(got[:, :n_ism] - ref)) / np.max(np.abs(ref)))
+            d["speed_vs_fp32"] = res["fp32"]["ms_per_step"] / ms
+        res[form] = d
+    return {"workload": room.name, "rirs_per_step": n_rir, "envelope": envelope,
+            "timing": "CUDA events per step, L2 flushed before each; accumulation stage with every launch on one "
+                      "stream; errors over the image-source part, relative to its peak",
+            "forms": res}
+
+
+def single_rir_latency(calls=50):
+    """The single-RIR workload (3 x 4 x 2.5 m, 10,648 images, 4800 samples): time per
+    call on the device (CUDA events, positions resident) and end to end through
+    the host-buffer entry point (wall clock), the FP32 error against the oracle,
+    and the oracle's own time for the RIR on one core."""
+    import torch
+    import oracle
+    from paper_1810_11359_gb300 import ism
+    room = workloads.single_rir()
+    dev = torch.device("cuda", torch.cuda.current_device())
+    ps = torch.from_numpy(room.pos_src).to(dev)
+    pr = torch.from_numpy(room.pos_rcv).to(dev)
+    ws = ism.Workspace(dev)
+    out = torch.empty((1, 1, 4800), dtype=torch.float32, device=dev)
+
+    def call():
+        ism.ism_simulate(room.L, room.beta, ps, pr, room.nb_img, room.Tmax, room.fs, Tw=room.window(), c=room.c,
+                         out=out, workspace=ws)
+
+    for _ in range(5):
+        call()
+    torch.cuda.synchronize()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record()
+    for _ in range(calls):
+        call()
+    b.record()
+    torch.cuda.synchronize()
+    dev_ms = a.elapsed_time(b) / calls
+    h_ps = torch.from_numpy(room.pos_src).pin_memory()
+    h_pr = torch.from_numpy(room.pos_rcv).pin_memory()
+    h_out = torch.empty((1, 1, 4800), dtype=torch.float32).pin_memory()
+    ws_h = ism.Workspace(dev)
+    for _ in range(5):
+        ism.ism_simulate_host(room.L, room.beta, h_ps.numpy(), h_pr.numpy(), room.nb_img, room.Tmax, room.fs,
+                              Tw=room.window(), c=room.c, out=h_out.numpy(), workspace=ws_h)
+    walls = []
+    for _ in range(calls):
+        t0 = time.perf_counter()
+        ism.ism_simulate_host(room.L, room.beta, h_ps.numpy(), h_pr.numpy(), room.nb_img, room.Tmax, room.fs,
+                              Tw=room.window(), c=room.c, out=h_out.numpy(), workspace=ws_h)
+        walls.append(time.perf_counter() - t0)
+    t0 = time.perf_counter()
+    ref = oracle.rir(room.L, room.beta.astype(np.float32), np.float32(room.c), np.float32(room.fs),
+                     np.float32(room.window()), room.pos_src[0], room.pos_rcv[0], room.nb_img, 4800, n_threads=1)
+    or_s = time.perf_counter() - t0
+    got = h_out.numpy().reshape(-1).astype(np.float64)
+    return {"workload": room.name, "images": int(np.prod(room.nb_img)), "samples": 4800,
+            "device_ms_per_call": dev_ms, "host_entry_ms_per_call_p50": float(np.median(walls)) * 1e3,
+            "host_entry_ms_per_call_p99": float(np.percentile(walls, 99)) * 1e3,
+            "max_err_vs_oracle": float(np.max(np.abs(got - ref)) / np.max(np.abs(ref))),
+            "oracle_ms_one_core": or_s * 1e3, "calls": calls}
+
+
+def sustain_clocks(step, seconds=1.5):
+    """Untimed repeats of the step for `seconds` after the timed region, so that
+    the clock sampler sees the GPU under load for several samples."""
+    import torch
+    t0 = time.perf_counter()
+    n = 0
+    while time.perf_counter() - t0 < seconds:
+        for _ in range(20):
+            step()
+        torch.cuda.synchronize()
+        n += 20
+    return n
+
+
 def run_reference(args, rank):
     if rank != 0:
         return
@@ -226,7 +407,7 @@ def run_reference(args, rank):
     beta = oracle.beta_sabine(room.L, room.rt60)
     N = oracle.nb_img_from_t(T_img, room.L, room.c, room.window())
     oracle.build()
-    cores = oracle.max_threads()
+    cores = host_cores()
     all_pairs = [(i, j) for i in range(room.pos_src.shape[0]) for j in range(room.pos_rcv.shape[0])]
     sample = max(1, min(len(all_pairs), cores))
     pairs = all_pairs[:sample]
@@ -255,7 +436,7 @@ def _pct(v, q):
     return float(np.percentile(np.asarray(v), q)) if len(v) else None
 
 
-def run_serving(args):
+def serving_measure(args):
     """The serving stream: rooms with sides U(3, 10) m, T60 U(0.2, 1.0) s, one
     source and 1-16 receivers, 16 kHz, Tdiff = min(0.25 s, T60), Tmax = T60,
     through the continuous-batching server.  Three arrival patterns of
@@ -363,6 +544,13 @@ def run_serving(args):
         res[f"poisson_{f}x"] = run(srv, prepared(f * sat["requests_per_s"]))
     st = srv.stats()
     srv.close()
+    return res, st, st_sat
+
+
+def run_serving(args):
+    """Prints the serving line (see serving_measure)."""
+    res, st, st_sat = serving_measure(args)
+    sat = res["saturated"]
     line = {
         "metric": METRIC, "value": sat["rirs_per_s"], "unit": UNIT, "n_gpus": 1, "steps": 1, "warmup": 1,
         "ms_per_step": sat["seconds"] * 1e3, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
@@ -590,6 +778,10 @@ def main():
                     choices=["batched", "trajectory", "serving", "differentiation", "moving_source"])
     ap.add_argument("--requests", type=int, default=20000, help="serving: requests per arrival pattern")
     ap.add_argument("--prec", default="fp32", choices=list(PREC_ID))
+    ap.add_argument("--no-extras", action="store_true",
+                    help="default workload: skip the precision forms, the 48 kHz array, serving and single-RIR lines")
+    ap.add_argument("--serving-requests", type=int, default=3000,
+                    help="default workload: requests per arrival pattern of the serving line")
     args = ap.parse_args()
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -671,7 +863,12 @@ def main():
     if world > 1:
         dist.barrier()
     ism.ism_profile_enable(False)
+    # the timed region lasts ~10 ms: keep the GPU on the same step for 1.5 s more,
+    # untimed, so that the clock record holds several samples under this load
+    sustained = sustain_clocks(step)
     clk = clocks.stop()
+    if clk is not None:
+        clk["window"] = f"the timed steps and {sustained} untimed repeats of the step (1.5 s) right after them"
     step_ms = [a.elapsed_time(b) for a, b in evs]
     ms = sum(step_ms) / len(step_ms)
     prof = ism.ism_profile_read()
@@ -788,8 +985,35 @@ def main():
                                  "hbm_gbs": tail_bytes / tail_ms_launch / 1e6, "hbm_frac": tail_bytes / tail_ms_launch / 1e6 / hbm,
                                  "bytes_per_step": tail_bytes,
                                  "peak_basis": f"{n_sm} SMs x 128 lanes x {sm_mhz:.0f} MHz; HBM {peak_kind} copy bandwidth"}
+    if world == 1 and not args.no_extras:
+        host_cores()   # before any oracle call that sets its own thread count
+        # the rest of the metric, measured in the same run: the reduced-precision forms against
+        # the FP32 path on this workload and on the 48 kHz array with its diffuse tail, the
+        # serving stream's latency percentiles, and the single-RIR latency
+        extras = {}
+        t_x = time.perf_counter()
+        forms = ["fp32_direct", "fp16x2", "lut", "lut_tex", "bf16x2"]
+        extras["precision_forms"] = measure_forms(args.workload, forms, 10, flush, peak_tops,
+                                                  counts=(n_contrib, n_images))
+        extras["trajectory_48k_array"] = measure_forms("trajectory", ["fp32"] + forms, 10, flush, peak_tops)
+        lj = measure_forms("trajectory", ["fp32"], 10, flush, peak_tops, envelope="lj")
+        extras["trajectory_48k_array_lj_envelope"] = lj
+        extras["single_rir"] = single_rir_latency()
+        sv_args = argparse.Namespace(requests=args.serving_requests, prec="fp32")
+        res, st, _ = serving_measure(sv_args)
+        extras["serving"] = {"workload": "serving_3-10m_rt0.2-1.0_1-16rcv_16k", "requests_per_pattern":
+                             args.serving_requests, "patterns": res,
+                             "server": {"hbm_budget_bytes": 8 << 30, "max_inflight": 6, "max_batch": 32,
+                                        "batches": st["batches"], "inflight_peak": st["inflight_peak"]},
+                             "latency": "arrival to RIRs in the caller's page-locked host buffer",
+                             "entry": "ism_server_submit_batch / ism_server_wait"}
+        extras["seconds"] = time.perf_counter() - t_x
+        line["extras"] = extras
+        line["p50_ms"] = res["poisson_0.8x"]["p50_ms"]
+        line["p99_ms"] = res["poisson_0.8x"]["p99_ms"]
     if not args.no_cpu_baseline and world >= 1:
         line["cpu_baseline"] = cpu_baseline(room, beta, N, Tdiff)
+        line["cpu_baseline"]["single_core"] = cpu_single_core(room, beta, N, Tdiff)
     print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()
