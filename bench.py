@@ -716,11 +716,12 @@ def run_moving_source(args, world, rank, dist):
     h = torch.empty((ps.shape[0], pr.shape[0], n_s), dtype=torch.float32, device=dev)
     y = torch.empty((pr.shape[0], x.numel() + n_s - 1), dtype=torch.float32, device=dev)
     ws = ism.Workspace(dev)
+    ws_au = ism.Workspace(dev)
 
     def step():
         ism.ism_simulate(room.L, beta, ps, pr, N, room.Tmax, room.fs, room.Tdiff, room.window(), seed=room.seed,
                          out=h, workspace=ws)
-        ism.ism_auralize(x, h, out=y)
+        ism.ism_auralize(x, h, out=y, method="auto", workspace=ws_au)
 
     for _ in range(max(args.warmup, 3)):
         step()
@@ -734,17 +735,41 @@ def run_moving_source(args, world, rank, dist):
         ism.ism_simulate(room.L, beta, ps, pr, N, room.Tmax, room.fs, room.Tdiff, room.window(), seed=room.seed,
                          out=h, workspace=ws)
         m.record()
-        ism.ism_auralize(x, h, out=y)
+        ism.ism_auralize(x, h, out=y, method="auto", workspace=ws_au)
         b.record()
     torch.cuda.synchronize()
     ms = sum(a.elapsed_time(b) for a, _, b in evs) / len(evs)
     au_ms = sum(m.elapsed_time(b) for _, m, b in evs) / len(evs)
+    # the direct form on the same RIRs, for comparison
+    y_d = torch.empty_like(y)
+    for _ in range(2):
+        ism.ism_auralize(x, h, out=y_d)
+    torch.cuda.synchronize()
+    ed = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    for a, b in ed:
+        flush.zero_()
+        a.record()
+        ism.ism_auralize(x, h, out=y_d)
+        b.record()
+    torch.cuda.synchronize()
+    direct_ms = sum(a.elapsed_time(b) for a, b in ed) / len(ed)
+    fft_vs_direct = float((y - y_d).abs().max() / y_d.abs().max())
     peaks, peak_kind = _peaks()
     sm_mhz = float(peaks.get("sm_max_mhz", 2070.0))
     n_sm = torch.cuda.get_device_properties(dev).multi_processor_count
     peak_tops = n_sm * 128 * sm_mhz * 1e6 / 1e12
     macs = pr.shape[0] * x.numel() * n_s
     rirs = ps.shape[0] * pr.shape[0]
+    # the FFT form's own work: one length-N complex DFT per segment, per point and
+    # microphone pair and per pair's inverse (5 N log2 N flops each, the radix-2
+    # count), and one complex multiply-add (8 flops) per point, pair and bin
+    n_out = x.numel() + n_s - 1
+    logN = max(4, int(math.ceil(math.log2(n_out))))
+    Nf = 1 << logN
+    pairs = (pr.shape[0] + 1) // 2
+    n_dft = ps.shape[0] * (1 + pairs) + pairs
+    fft_flops = 5.0 * Nf * logN * n_dft + 8.0 * ps.shape[0] * pairs * Nf
+    peak_tflops = 2.0 * peak_tops
     from paper_1810_11359_gb300 import replicas
     ms = replicas.max_over_ranks(ms, device=dev)           # the slowest rank's step (replicas)
     line = {
@@ -757,11 +782,20 @@ def run_moving_source(args, world, rank, dist):
                    "l2": "flushed between timed steps (256 MB write)"},
         "seconds_of_audio_per_sec": (x.numel() / room.fs) / (ms * 1e-3),
         "auralize_ms_per_step": au_ms,
-        "roofline": {"bound": "alu", "kernel": "auralize_kernel", "achieved": macs / (au_ms * 1e-3) / 1e12,
-                     "peak": peak_tops, "unit": "T multiply-adds/s (FP32 FMA pipe)",
-                     "frac": macs / (au_ms * 1e-3) / 1e12 / peak_tops, "useful_macs_per_step": macs,
-                     "peak_basis": f"{n_sm} SMs x 128 FP32 lanes x {sm_mhz:.0f} MHz ({peak_kind} max SM clock)",
+        "auralize_method": "fft (automatic choice)",
+        "direct_form_ms": direct_ms,
+        "fft_speedup_vs_direct": direct_ms / au_ms,
+        "fft_vs_direct_max_err_rel_peak": fft_vs_direct,
+        "roofline": {"bound": "alu", "kernel": "af_cols_kernel + af_rows_kernel + af_icols_kernel (FFT form)",
+                     "achieved": fft_flops / (au_ms * 1e-3) / 1e12, "peak": peak_tflops, "unit": "TFLOP/s (FP32)",
+                     "frac": fft_flops / (au_ms * 1e-3) / 1e12 / peak_tflops, "flops_per_step": fft_flops,
+                     "dft_length": Nf, "dfts_per_step": n_dft,
+                     "peak_basis": f"{n_sm} SMs x 128 FP32 lanes x 2 flops x {sm_mhz:.0f} MHz ({peak_kind} max SM "
+                                   f"clock); flops counted as 5 N log2 N per complex DFT",
                      "traffic": None},
+        "direct_roofline": {"bound": "alu", "kernel": "auralize_kernel", "achieved": macs / (direct_ms * 1e-3) / 1e12,
+                            "peak": peak_tops, "unit": "T multiply-adds/s (FP32 FMA pipe)",
+                            "frac": macs / (direct_ms * 1e-3) / 1e12 / peak_tops, "useful_macs_per_step": macs},
     }
     if rank == 0:
         print(json.dumps(line), flush=True)

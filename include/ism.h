@@ -472,6 +472,39 @@ ism_status ism_diffuse_noise(uint64_t seed, uint32_t rir, uint32_t k0, int n, fl
 ism_status ism_auralize(const float* signal, int n_x, const float* rirs, int n_points, int n_mics, int n_S,
                         const int* starts, float* out, void* stream);
 
+/* The same filtering with a choice of method and a caller-owned workspace.
+ * The paper filters with batched FFTs and overlap-add; ISM_AURALIZE_FFT does
+ * it in the frequency domain with FFTs written for this library (FP32,
+ * four-step: length-N DFTs, N the power of two >= n_x + n_S - 1, at most 2^20, split
+ * as N = R C into shared-memory DFTs of R and C points).  Two microphones
+ * share one complex sequence (real and imaginary parts), the segment
+ * spectra X_p times the pair spectra are summed over the points in ascending
+ * order (the overlap-add, in the frequency domain), and one inverse DFT per
+ * pair gives both outputs; results are identical run to run.  Its error is
+ * that of an FP32 FFT: a few 1e-7 of the largest sum |x| * |h|, spread over
+ * all outputs.  ISM_AURALIZE_DIRECT is ism_auralize (no workspace).
+ * ISM_AURALIZE_AUTO takes the FFT form when its operation count is less than
+ * half the direct form's (n_mics n_x n_S multiply-adds) and the workspace
+ * holds at least one chunk, else the direct form.
+ *   workspace  device, 256-byte aligned, >= ism_auralize_workspace_size()
+ *              bytes for the FFT form (scratch; may be NULL for DIRECT);
+ *              a larger workspace processes more points per chunk.
+ * Other arguments, layout and errors as ism_auralize; ISM_ERR_UNSUPPORTED if
+ * the FFT form is asked for an output longer than 2^20 samples. */
+typedef enum {
+    ISM_AURALIZE_AUTO = 0,
+    ISM_AURALIZE_DIRECT = 1,
+    ISM_AURALIZE_FFT = 2
+} ism_auralize_method;
+
+/* Workspace bytes of ism_auralize_ex for this method (0 when it takes the
+ * direct form).  Host only. */
+ism_status ism_auralize_workspace_size(int n_x, int n_points, int n_mics, int n_S, int method, size_t* bytes);
+
+ism_status ism_auralize_ex(const float* signal, int n_x, const float* rirs, int n_points, int n_mics, int n_S,
+                           const int* starts, float* out, int method, void* workspace, size_t ws_bytes,
+                           void* stream);
+
 /* ------------------------------------------------------------------------- */
 /* Helpers of Section 4 (FP64)                                                */
 /* ------------------------------------------------------------------------- */

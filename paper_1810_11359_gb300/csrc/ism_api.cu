@@ -1154,6 +1154,88 @@ ism_status ism_auralize(const float* signal, int n_x, const float* rirs, int n_p
     return ISM_OK;
 }
 
+// Operation counts deciding the automatic choice of ism_auralize_ex: the
+// direct form does n_mics n_x n_S multiply-adds; the FFT form about 4 N log2 N
+// lane operations per length-N DFT (one per segment, one per microphone pair
+// and point, one inverse per pair) and 4 per product of spectra.
+static bool auralize_fft_pays(int n_x, int n_points, int n_mics, int n_S)
+{
+    const long long n_out = (long long)n_x + n_S - 1;
+    int logN = 4;
+    while ((1ll << logN) < n_out) ++logN;
+    if (logN > 20) return false;
+    const double N = (double)(1ll << logN);
+    const double pairs = (double)((n_mics + 1) / 2);
+    const double fft = ((double)n_points * (1.0 + pairs) + pairs) * 4.0 * N * logN + (double)n_points * pairs * 4.0 * N;
+    const double direct = (double)n_mics * (double)n_x * (double)n_S;
+    return direct > 2.0 * fft;
+}
+
+static ism_status auralize_args(const float* signal, int n_x, const float* rirs, int n_points, int n_mics, int n_S,
+                                float* out)
+{
+    if (!signal || !rirs || !out) return fail(ISM_ERR_INVALID_ARG, "signal, rirs and out must be device pointers");
+    if (n_x < 1 || n_points < 1 || n_mics < 1 || n_S < 1)
+        return fail(ISM_ERR_INVALID_ARG, "need n_x, n_points, n_mics, n_S >= 1");
+    if ((long long)n_x + n_S - 1 > 0x7FFFFFFFll || (long long)n_points * n_mics * (long long)n_S > (1ll << 40))
+        return fail(ISM_ERR_UNSUPPORTED, "signal or RIRs too long");
+    if (n_points > n_x) return fail(ISM_ERR_INVALID_ARG, "more trajectory points (%d) than samples (%d)", n_points, n_x);
+    return ISM_OK;
+}
+
+ism_status ism_auralize_workspace_size(int n_x, int n_points, int n_mics, int n_S, int method, size_t* bytes)
+{
+    g_last_error.clear();
+    if (!bytes) return fail(ISM_ERR_INVALID_ARG, "bytes must not be NULL");
+    *bytes = 0;
+    if (n_x < 1 || n_points < 1 || n_mics < 1 || n_S < 1)
+        return fail(ISM_ERR_INVALID_ARG, "need n_x, n_points, n_mics, n_S >= 1");
+    if (method < ISM_AURALIZE_AUTO || method > ISM_AURALIZE_FFT)
+        return fail(ISM_ERR_INVALID_ARG, "method = %d is not an ism_auralize_method", method);
+    const bool fft = method == ISM_AURALIZE_FFT ||
+                     (method == ISM_AURALIZE_AUTO && auralize_fft_pays(n_x, n_points, n_mics, n_S));
+    if (!fft) return ISM_OK;
+    AfPlan pl;
+    size_t need = 0;
+    if (ism_auralize_fft_plan(n_x, n_points, n_mics, n_S, 0, &pl, &need))
+        return fail(ISM_ERR_UNSUPPORTED, "output of %lld samples exceeds the FFT form's 2^20",
+                    (long long)n_x + n_S - 1);
+    *bytes = need;
+    return ISM_OK;
+}
+
+ism_status ism_auralize_ex(const float* signal, int n_x, const float* rirs, int n_points, int n_mics, int n_S,
+                           const int* starts, float* out, int method, void* workspace, size_t ws_bytes, void* stream)
+{
+    g_last_error.clear();
+    ism_status st = auralize_args(signal, n_x, rirs, n_points, n_mics, n_S, out);
+    if (st != ISM_OK) return st;
+    if (method < ISM_AURALIZE_AUTO || method > ISM_AURALIZE_FFT)
+        return fail(ISM_ERR_INVALID_ARG, "method = %d is not an ism_auralize_method", method);
+    bool fft = method == ISM_AURALIZE_FFT;
+    AfPlan pl;
+    size_t need = 0;
+    if (method == ISM_AURALIZE_AUTO && auralize_fft_pays(n_x, n_points, n_mics, n_S) && workspace &&
+        ism_auralize_fft_plan(n_x, n_points, n_mics, n_S, ws_bytes, &pl, &need) == 0)
+        fft = true;
+    if (fft) {
+        if (!workspace) return fail(ISM_ERR_INVALID_ARG, "the FFT form needs a workspace");
+        if (((uintptr_t)workspace & 255u) != 0) return fail(ISM_ERR_INVALID_ARG, "workspace must be 256-byte aligned");
+        const int r = ism_auralize_fft_plan(n_x, n_points, n_mics, n_S, ws_bytes, &pl, &need);
+        if (r == -1)
+            return fail(ISM_ERR_UNSUPPORTED, "output of %lld samples exceeds the FFT form's 2^20",
+                        (long long)n_x + n_S - 1);
+        if (r == -2)
+            return fail(ISM_ERR_WORKSPACE_TOO_SMALL, "workspace of %zu bytes holds no chunk of the FFT form", ws_bytes);
+        int e = ism_launch_auralize_fft(signal, rirs, starts, out, pl, static_cast<char*>(workspace), stream);
+        if (e) return cuda_fail(e, "auralization (FFT) kernels");
+        return ISM_OK;
+    }
+    int e = ism_launch_auralize(signal, n_x, rirs, n_points, n_mics, n_S, starts, out, stream);
+    if (e) return cuda_fail(e, "auralization kernel");
+    return ISM_OK;
+}
+
 ism_status ism_t60_sabine(const double L[3], const double beta[6], double* T60)
 {
     g_last_error.clear();

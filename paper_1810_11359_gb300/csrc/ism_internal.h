@@ -185,6 +185,19 @@ __host__ __device__ constexpr int ism_lut_phases(int slots)
     return slots <= 1 ? 256 : slots == 2 ? 128 : slots <= 4 ? 64 : 32;
 }
 
+// Plan of the FFT form of the moving-source filtering (ism_auralize_fft.cu).
+struct AfPlan {
+    int N, logN, R, logR, C, logC;   // DFT length N = R C (powers of two)
+    int n_x, P, M, n_S, n_out, n_pairs;
+    int pc;             // trajectory points per chunk
+    int cb;             // columns per CTA, column pass
+    int cb3;            // columns per CTA, inverse column pass
+    int rb;             // rows per CTA, row pass
+    int npg;            // microphone pairs per CTA of the row pass
+    int n_pg;           // microphone-pair groups of the row pass
+    int n_grp;          // point groups of the row pass (partial spectra summed in group order)
+};
+
 // Sets the calling thread's ism_last_error_message() and returns s.
 ism_status ism_fail_message(ism_status s, const char* fmt, ...);
 
@@ -209,5 +222,8 @@ int ism_launch_envelope(const JobTable& t, const WsPlan& p, char* ws, void* stre
 int ism_launch_noise(uint64_t seed, uint32_t rir, uint32_t k0, int n, float* z, void* stream);
 int ism_launch_auralize(const float* x, int n_x, const float* h, int n_points, int n_mics, int n_s, const int* starts,
                         float* y, void* stream);
+int ism_auralize_fft_plan(int n_x, int n_points, int n_mics, int n_S, size_t ws_bytes, AfPlan* out, size_t* need);
+int ism_launch_auralize_fft(const float* x, const float* h, const int* starts, float* y, const AfPlan& pl, char* ws,
+                            void* stream);
 int ism_launch_beta_sabine(const double* L, const double* T60, const double* w, int negative, int n,
                            double* beta_out, int* status, void* stream);

@@ -168,7 +168,7 @@ __global__ void __launch_bounds__(ISM_ENV_CHUNK) envelope_kernel(const __grid_co
     const int jid = ism_find_job(t, g, [](const JobDev& j) { return j.env_cta_base; });
     const JobDev& J = t.j[jid];
     const int chunk = (int)(g - J.env_cta_base);
-    __shared__ double xg[ISM_ENV_MAX_NODES], wg[ISM_ENV_MAX_NODES];
+    __shared__ double wg[ISM_ENV_MAX_NODES];
     __shared__ double sth[ISM_ENV_MAX_NODES], cth[ISM_ENV_MAX_NODES];
     __shared__ double gam[3];
     __shared__ int n_s;
@@ -216,7 +216,6 @@ __global__ void __launch_bounds__(ISM_ENV_CHUNK) envelope_kernel(const __grid_co
             }
             dp = n * (x * p1 - p0) / (x * x - 1.0);
         }
-        xg[i] = x;
         wg[i] = 2.0 / ((1.0 - x * x) * dp * dp);
         const double ang = (x + 1.0) * (PI / 4.0);   // [-1, 1] -> [0, pi/2]
         sth[i] = sin(ang);

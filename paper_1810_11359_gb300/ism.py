@@ -122,6 +122,11 @@ _SIGS = {
                                          ctypes.c_void_p, ctypes.c_void_p]),
     "ism_auralize": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_int, ctypes.c_int,
                                     ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
+    "ism_auralize_workspace_size": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                                   ctypes.c_int, _P(ctypes.c_size_t)]),
+    "ism_auralize_ex": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_int, ctypes.c_int,
+                                       ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p,
+                                       ctypes.c_size_t, ctypes.c_void_p]),
     "ism_t60_sabine": (ctypes.c_int, [_P(ctypes.c_double), _P(ctypes.c_double), _P(ctypes.c_double)]),
     "ism_beta_sabine": (ctypes.c_int, [_P(ctypes.c_double), ctypes.c_double, _P(ctypes.c_double), ctypes.c_int,
                                        _P(ctypes.c_double)]),
@@ -534,11 +539,24 @@ def ism_simulate_backward(L, beta, pos_src, pos_rcv, nb_img, Tmax, fs, grad_out,
     return gb, gs, gr
 
 
-def ism_auralize(signal, rirs, starts=None, out=None, stream=None):
+AURALIZE_METHODS = {"auto": 0, "direct": 1, "fft": 2}
+
+
+def ism_auralize_workspace_size(n_x: int, n_points: int, n_mics: int, n_s: int, method: str = "auto") -> int:
+    b = ctypes.c_size_t()
+    _check(load().ism_auralize_workspace_size(int(n_x), int(n_points), int(n_mics), int(n_s),
+                                              AURALIZE_METHODS[method], ctypes.byref(b)))
+    return int(b.value)
+
+
+def ism_auralize(signal, rirs, starts=None, out=None, stream=None, method: Optional[str] = None,
+                 workspace: Optional[Workspace] = None):
     """Moving source (Section 4): signal [n_x] cut into one segment per
     trajectory point, each filtered by its point's RIRs rirs [n_points, n_mics,
     n_S] and overlap-added -> [n_mics, n_x + n_S - 1] (FP32 CUDA tensors).
-    starts: optional [n_points] segment starts (default: uniform cut)."""
+    starts: optional [n_points] segment starts (default: uniform cut).
+    method: None calls ism_auralize (direct form, no workspace); "auto",
+    "direct" or "fft" call ism_auralize_ex with a workspace."""
     torch = _torch()
     dev = torch.device("cuda", torch.cuda.current_device())
     x = torch.as_tensor(signal, dtype=torch.float32).to(dev).reshape(-1).contiguous()
@@ -553,6 +571,15 @@ def ism_auralize(signal, rirs, starts=None, out=None, stream=None):
             raise ValueError("starts needs one entry per trajectory point")
     if out is None:
         out = torch.empty((n_mics, x.numel() + n_s - 1), dtype=torch.float32, device=dev)
+    if method is not None:
+        nbytes = ism_auralize_workspace_size(x.numel(), n_points, n_mics, n_s, method)
+        buf = _workspace(workspace, nbytes) if nbytes else None
+        _check(load().ism_auralize_ex(ctypes.c_void_p(x.data_ptr()), int(x.numel()), ctypes.c_void_p(h.data_ptr()),
+                                      n_points, n_mics, n_s, None if st is None else ctypes.c_void_p(st.data_ptr()),
+                                      ctypes.c_void_p(out.data_ptr()), AURALIZE_METHODS[method],
+                                      None if buf is None else ctypes.c_void_p(buf.data_ptr()),
+                                      0 if buf is None else int(buf.numel()), _stream_ptr(stream)))
+        return out
     _check(load().ism_auralize(ctypes.c_void_p(x.data_ptr()), int(x.numel()), ctypes.c_void_p(h.data_ptr()), n_points,
                                n_mics, n_s, None if st is None else ctypes.c_void_p(st.data_ptr()),
                                ctypes.c_void_p(out.data_ptr()), _stream_ptr(stream)))
