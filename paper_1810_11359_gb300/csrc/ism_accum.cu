@@ -6,14 +6,15 @@ int ism_launch_accum(const JobTable& t, const WsPlan& p, char* ws, ism_precision
                      int* launched)
 {
     switch (prec) {
-    case ISM_PREC_FP32: {
-        int a = 0, b = 0;
+    case ISM_PREC_FP32:
+    case ISM_PREC_FP32_DIRECT: {
+        int a = 0, b = 0, c = 0;
         int rc = ism_launch_accum_cheb(t, p, ws, stream, &a);
-        if (!rc) rc = launch_accum_prec<PREC_FP32>(t, p, ws, stream, &b);
-        *launched = a + b;
+        if (!rc) rc = ism_launch_accum_shell_direct(t, p, ws, stream, &b);
+        if (!rc) rc = launch_accum_prec<PREC_FP32>(t, p, ws, stream, &c);
+        *launched = a + b + c;
         return rc;
     }
-    case ISM_PREC_FP32_DIRECT: return launch_accum_prec<PREC_FP32>(t, p, ws, stream, launched);
     case ISM_PREC_FP16X2: return ism_launch_accum_fp16(t, p, ws, stream, launched);
     case ISM_PREC_BF16X2: return ism_launch_accum_bf16(t, p, ws, stream, launched);
     case ISM_PREC_LUT: return ism_launch_accum_lut(t, p, ws, stream, launched);

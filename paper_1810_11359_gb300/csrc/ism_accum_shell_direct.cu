@@ -1,0 +1,188 @@
+// ism_accum_shell_direct.cu -- FP32 accumulation of eq. (5) with every tap of
+// eq. (6) evaluated, for a 32-tap window, fused with the enumeration of the
+// images (Section 2.1) it accumulates.
+//
+// The Chebyshev form (ism_accum_cheb.cu) pays for the expansion of every
+// occupied integer delay; with few images per delay bin (the 48 kHz array:
+// ~36 per bin) evaluating each image's 32 taps is cheaper.  Before this kernel
+// such jobs went through an enumeration count, a scan and a scatter of image
+// ids into delay bins; here the CTA that owns a shell of delay bins of one
+// RIR enumerates the shell's images itself (ism_shell.cuh, as the Chebyshev
+// form does) and adds their taps at once, so no ids, counts or sorts exist.
+// The shells are 32 bins thick (1024 samples) when the bins hold few images:
+// visiting the grid columns that reach a shell is what thickness amortises;
+// dense rooms take 8 bins, so that their RIRs still split into many CTAs.
+// The candidates of every chunk of columns are split evenly over the CTA's
+// warps (ism_shell.cuh, shell_walk_cta), so no warp waits for another.
+//
+// Each lane that finds an image computes its record {f, P, P cos phi,
+// P sin phi} (the factorised windowed sinc of ism_accum.cuh: P = A sin(pi f) /
+// (2 pi), phi = 2 pi f / N_w) and the position of its first tap in the
+// shell's window (32 B + 32 samples from 32 q0 - 16, B bins) and stages
+// them in the warp's shared memory.  After every batch of 32 candidates the warp takes the
+// staged images in lane order, and lane t adds tap t of each -- sigma_t
+// (t - 15 - f) by one FFMA, the window by two, one reciprocal and one product --
+// to its warp's window of the shell in shared memory (consecutive lanes,
+// consecutive addresses).  The order in which a warp adds its images is a
+// function of the geometry alone (ism_shell.cuh), so the warp windows are the same in every
+// run; at the end they are summed in warp order.  No atomics: the output is
+// bit-identical from run to run.
+//
+// The shell's window is written as the bins' window rows of the finalize
+// kernel (64 samples from 32 q - 16, summed per sample with the previous
+// bin's row): each bin's row holds the window's values on its first 32
+// samples and zeros on the rest, except the last bin of the shell, whose
+// upper half holds the 32 samples that spill into the next shell.
+#include "ism_accum.cuh"
+#include "ism_shell.cuh"
+
+namespace {
+
+#define SD_B ISM_SD_BINS             // delay bins per CTA, at most
+#define SD_WARPS 8                   // warps per CTA
+#define SD_WIN (32 * SD_B + 32)      // samples of the shell's window (taps of b in [32 q0 - 1, 32 (q0 + SD_B) - 1))
+
+__global__ void __launch_bounds__(SD_WARPS * 32, 4) shell_direct_kernel(const __grid_constant__ JobTable t,
+                                                                        const float4* __restrict__ tbl,
+                                                                        float* __restrict__ rows)
+{
+    constexpr int WIN = 64;   // window row of a bin: 32 (SLOTS + 1), SLOTS = 1
+    extern __shared__ __align__(16) unsigned char smem[];
+    // CTA -> (job, RIR, shell): job by job, RIR by RIR, outermost (densest) shell first
+    const long long g = blockIdx.x;
+    const int jid = ism_find_job(t, g, [](const JobDev& d) { return (long long)d.sd_cta_base; });
+    const JobDev& J = t.j[jid];
+    const long long local = g - J.sd_cta_base;
+    const int r = (int)(local / J.shell_groups);
+    const int grp = J.shell_groups - 1 - (int)(local % J.shell_groups);
+    const int B = J.shell_direct;   // bins per shell: 8 (dense rooms) or 32 (sparse ones)
+    const int q0 = grp * B;
+    const int nb = min(B, J.Q - q0);
+    const int Nx = J.N[0], Ny = J.N[1], Nz = J.N[2];
+    const int n_axis = Nx + Ny + Nz;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+
+    // shared memory: axis tables | row prefix | per-warp column records | per-warp windows |
+    // per-warp staged images
+    float4* T = reinterpret_cast<float4*>(smem);
+    int* rowpre = reinterpret_cast<int*>(smem + (size_t)((t.max_axis_sum + 1) & ~1) * sizeof(float4));
+    int* rowy0 = rowpre + ((t.max_axis_sum + 4) & ~3);
+    float4* recf = reinterpret_cast<float4*>(rowy0 + ((t.max_axis_sum + 4) & ~3));
+    int4* reci = reinterpret_cast<int4*>(recf + SD_WARPS * 32);
+    int* st = reinterpret_cast<int*>(reci + SD_WARPS * 32);            // [warps][33]
+    float* win_all = reinterpret_cast<float*>(st + SD_WARPS * 33);     // [warps][SD_WIN]
+    float4* stage_all = reinterpret_cast<float4*>(win_all + SD_WARPS * SD_WIN);   // [warps][32]
+    int* spos_all = reinterpret_cast<int*>(stage_all + SD_WARPS * 32);            // [warps][32]
+    int* wtot = spos_all + SD_WARPS * 32;                                          // [warps]
+    float* win = win_all + warp * SD_WIN;
+    float4* stage = stage_all + warp * 32;
+    int* spos = spos_all + warp * 32;
+
+    const float4* Tg = tbl + J.tbl_base + (long long)r * n_axis;
+    for (int e = threadIdx.x; e < n_axis; e += blockDim.x) T[e] = Tg[e];
+    for (int e = threadIdx.x; e < SD_WARPS * SD_WIN; e += blockDim.x) win_all[e] = 0.0f;
+    spos[lane] = -1;
+    __syncthreads();
+
+    // receiver polar pattern: the unit orientation of this RIR's receiver
+    const int i_rcv = r - (r / J.n_rcv) * J.n_rcv;
+    const float alpha = J.mic_alpha;
+    float3 orient = make_float3(0.0f, 0.0f, 0.0f);
+    if (alpha != 1.0f) {
+        const float* o = J.orient_rcv + 3 * i_rcv;
+        const float ox = o[0], oy = o[1], oz = o[2];
+        const float inv = 1.0f / sqrtf(__fmaf_rn(ox, ox, __fmaf_rn(oy, oy, oz * oz)));
+        orient = make_float3(ox * inv, oy * inv, oz * inv);
+    }
+    // lane constants of tap t = lane, j = t - 15 (see ism_accum.cuh)
+    const int j = lane - 15;
+    const float sg = (j & 1) ? 1.0f : -1.0f;   // (-1)^(j+1)
+    const float xj = sg * (float)j, nsg = -sg;
+    float Sj, Cj;
+    sincospif((float)j * (2.0f / 32.0f), &Sj, &Cj);
+    const float twopi_Nw = 6.283185307179586f / 32.0f, inv2Nw = 2.0f / 32.0f;
+
+    const int W0 = ISM_SB * q0 - 16;   // first sample of the shell's window
+    const Shell sh = shell_setup(J, T, r, ISM_SB * q0 - 1, min(ISM_SB * (q0 + nb) - 1, J.n_ism + J.H - 1));
+    const int n_cols = shell_rows(sh, T, rowpre, rowy0);   // (synchronises the CTA)
+    const float amp_scale = J.amp_scale;
+
+    shell_walk_cta<SD_WARPS>(
+        sh, T, rowpre, rowy0, n_cols, make_float2(orient.x, orient.y), recf, reci, st, wtot, warp, lane,
+        [&](int b, float f, float s, const float4& cf, int, int, const float4& tz) {
+            const float rs = ism_rcp(s);
+            float amp = cf.z * tz.z * amp_scale * rs;
+            if (alpha != 1.0f)   // polar pattern: cos(theta) = o . (x_n - x_r) / d
+                amp *= __fmaf_rn(1.0f - alpha, __fmaf_rn(orient.z, tz.w, cf.w) * rs, alpha);
+            f = fmaxf(f, 0x1p-60f);   // keeps j - f away from 0 (the reciprocal of the tap j = 0)
+            stage[lane] = ism_sinc_record(f, amp, true, twopi_Nw, inv2Nw);
+            spos[lane] = b - 15 - W0;   // window position of tap 0, in [0, 32 nb - 1)
+        },
+        [&]() {
+            __syncwarp();
+            unsigned m = __ballot_sync(0xffffffffu, spos[lane] >= 0);
+            while (m) {   // the staged images in lane order
+                const int l = __ffs(m) - 1;
+                m &= m - 1;
+                const float4 rc = stage[l];
+                const int p = spos[l];
+                const float x = __fmaf_rn(nsg, rc.x, xj);
+                const float w = __fmaf_rn(Cj, rc.z, __fmaf_rn(Sj, rc.w, rc.y));
+                win[p + lane] += w * ism_rcp(x);
+            }
+            __syncwarp();
+            spos[lane] = -1;
+            __syncwarp();
+        });
+    __syncthreads();
+
+    // the bins' rows: the warps' windows summed in warp order
+    for (int ql = warp; ql < nb; ql += SD_WARPS) {
+        const int q = q0 + ql;
+        float* row = rows + J.rows_base + ((long long)r * J.Q + q) * WIN;
+        {
+            const int p = 32 * ql + lane;   // lower half: samples 32 q - 16 + lane
+            float v = win_all[p];
+#pragma unroll
+            for (int w = 1; w < SD_WARPS; ++w) v += win_all[w * SD_WIN + p];
+            row[lane] = v;
+        }
+        {
+            float v = 0.0f;
+            if (ql == nb - 1) {   // the samples that spill into the next shell
+                const int p = 32 * nb + lane;
+                v = win_all[p];
+#pragma unroll
+                for (int w = 1; w < SD_WARPS; ++w) v += win_all[w * SD_WIN + p];
+            }
+            row[32 + lane] = v;
+        }
+    }
+}
+
+size_t shell_direct_smem(const JobTable& t)
+{
+    return (size_t)((t.max_axis_sum + 1) & ~1) * sizeof(float4) + 2 * (size_t)((t.max_axis_sum + 4) & ~3) * sizeof(int) +
+           (size_t)SD_WARPS * 32 * (sizeof(float4) + sizeof(int4)) + (size_t)SD_WARPS * 33 * sizeof(int) +
+           (size_t)SD_WARPS * SD_WIN * sizeof(float) + (size_t)SD_WARPS * 32 * (sizeof(float4) + sizeof(int)) +
+           SD_WARPS * sizeof(int);
+}
+
+}  // namespace
+
+int ism_launch_accum_shell_direct(const JobTable& t, const WsPlan& p, char* ws, void* stream, int* launched)
+{
+    *launched = 0;
+    if (p.sd_ctas <= 0) return 0;
+    const size_t sm = shell_direct_smem(t);
+    static std::atomic<unsigned long long> opened{0};
+    int rc = ism_open_smem((const void*)shell_direct_kernel, &opened);
+    if (rc) return rc;
+    cudaError_t e = cudaFuncSetAttribute(shell_direct_kernel, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                         cudaSharedmemCarveoutMaxShared);
+    if (e != cudaSuccess) return (int)e;
+    shell_direct_kernel<<<(unsigned)p.sd_ctas, SD_WARPS * 32, sm, (cudaStream_t)stream>>>(
+        t, reinterpret_cast<const float4*>(ws + p.tbl_off), reinterpret_cast<float*>(ws + p.rows_off));
+    *launched = 1;
+    return (int)cudaGetLastError();
+}

@@ -168,7 +168,7 @@ ism_status plan(const Validated* vs, int n, ism_precision prec, bool backward, J
     for (int i = 0; i < n; ++i)
         set_cols += (long long)vs[i].job.nb_img[0] * vs[i].job.nb_img[1] * vs[i].job.n_src * vs[i].job.n_rcv;
     long long rir = 0, hist = 0, tbl = 0, ecta = 0, acta = 0, adta = 0, tcta = 0, fcta = 0, rows = 0, ids = 0, lut = 0,
-              gpart = 0, srir = 0, scta = 0, env = 0, vcta = 0;
+              gpart = 0, srir = 0, scta = 0, env = 0, vcta = 0, sdc = 0;
     for (int i = 0; i < n; ++i) {
         const Validated& v = vs[i];
         const ism_job& in = v.job;
@@ -283,14 +283,22 @@ ism_status plan(const Validated* vs, int n, ism_precision prec, bool backward, J
             // backward: a 32-tap window always takes the fused Chebyshev adjoint (an
             // image costs two degree-8 sums there, against 32 tap derivatives)
             J.adj_cheb = (backward && v.Nw == 32.0 && v.H == 16 && v.slots == 1) ? 1 : 0;
+            // the other FP32 forward jobs with a 32-tap window: every tap evaluated, the
+            // images enumerated by the CTA that accumulates them (no ids, no sort)
+            // (the value is the shell's thickness in bins: 32 for sparse bins, 8 for dense ones)
+            J.shell_direct = (!backward && !J.use_cheb && (prec == ISM_PREC_FP32 || prec == ISM_PREC_FP32_DIRECT) &&
+                              v.Nw == 32.0 && v.H == 16 && v.slots == 1) ? (per_bin < 64.0 ? ISM_SD_BINS : 8) : 0;
         }
-        const bool fused = J.use_cheb || J.adj_cheb;
-        // a job takes either the fused Chebyshev CTAs (which enumerate their
-        // own images) or the direct accumulation CTAs (which read the binned ids)
-        J.acc_groups = J.use_cheb ? 0 : (J.Q + ism_acc_bins((int)prec) - 1) / ism_acc_bins((int)prec);
-        J.shell_groups = fused ? (J.Q + ISM_SHELL_BINS - 1) / ISM_SHELL_BINS : 0;
+        const bool cheb = J.use_cheb || J.adj_cheb;
+        const bool fused = cheb || J.shell_direct;
+        // a job takes the fused Chebyshev CTAs or the fused direct CTAs (both enumerate
+        // their own images), or the direct accumulation CTAs (which read the binned ids)
+        J.acc_groups = (J.use_cheb || J.shell_direct) ? 0 : (J.Q + ism_acc_bins((int)prec) - 1) / ism_acc_bins((int)prec);
+        J.shell_groups = cheb ? (J.Q + ISM_SHELL_BINS - 1) / ISM_SHELL_BINS
+                              : (J.shell_direct ? (J.Q + J.shell_direct - 1) / J.shell_direct : 0);
         J.shell_rir_base = srir;
         J.shell_cta_base = scta;
+        J.sd_cta_base = (int)sdc;
         J.grad_out = v.grad_out;
         J.grad_beta = v.grad_beta;
         J.grad_src = v.grad_src;
@@ -305,9 +313,12 @@ ism_status plan(const Validated* vs, int n, ism_precision prec, bool backward, J
         tbl += R * axis;
         if (!fused) ecta += R * ((J.U + ISM_ENUM_WARPS - 1) / ISM_ENUM_WARPS);
         acta += R * J.acc_groups;
-        if (fused) srir += R;
-        scta += R * J.shell_groups;
-        if (J.shell_groups > t.shell_gmax) t.shell_gmax = J.shell_groups;
+        if (cheb) {
+            srir += R;
+            scta += R * J.shell_groups;
+            if (J.shell_groups > t.shell_gmax) t.shell_gmax = J.shell_groups;
+        }
+        if (J.shell_direct) sdc += R * J.shell_groups;
         fcta += R * J.fin_chunks;
         if (backward && !J.adj_cheb) adta += R * J.n_tiles;
         if (J.has_tail) {
@@ -327,8 +338,8 @@ ism_status plan(const Validated* vs, int n, ism_precision prec, bool backward, J
         if (prec == ISM_PREC_LUT) lut += (long long)(ism_lut_phases(J.slots) + 1) * 32 * J.slots;
         // texture form: each table starts on a 512-byte boundary (texture base alignment)
         if (prec == ISM_PREC_LUT_TEX) lut += ((long long)(ism_lut_phases(J.slots) + 1) * 32 * J.slots + 127) / 128 * 128;
-        if (fused) t.any_cheb = 1;
-        else t.any_direct = 1;
+        if (cheb) t.any_cheb = 1;
+        else if (!fused) t.any_direct = 1;
         if (backward) gpart += R * J.Q * 12;
         if (!fused) ids += R * J.img_per_rir;
         if (J.Q > t.max_Q) t.max_Q = J.Q;
@@ -341,7 +352,8 @@ ism_status plan(const Validated* vs, int n, ism_precision prec, bool backward, J
         return fail(ISM_ERR_UNSUPPORTED, "%lld images in one launch set exceed 2^32; split the batch", ids);
     if (rir > 0x7FFFFFFFll || ecta > 0x7FFFFFFFll || acta > 0x7FFFFFFFll || adta > 0x7FFFFFFFll ||
         tcta > 0x7FFFFFFFll || fcta > 0x7FFFFFFFll || srir * (long long)t.shell_gmax > 0x7FFFFFFFll ||
-        env > 0x7FFFFFFFll || vcta > 0x7FFFFFFFll)
+        env > 0x7FFFFFFFll || vcta > 0x7FFFFFFFll || sdc > 0x7FFFFFFFll || gpart > 0x7FFFFFFFll ||
+        rir * 12 > 0x7FFFFFFFll || lut > 0x7FFFFFFFll)
         return fail(ISM_ERR_UNSUPPORTED, "launch set too large; split the batch");
     p.hist_total = hist;
     p.ids_total = ids;
@@ -364,6 +376,7 @@ ism_status plan(const Validated* vs, int n, ism_precision prec, bool backward, J
     t.shell_rank_major = (srir * (long long)t.shell_gmax * 7 <= scta * 8) ? 1 : 0;
     p.shell_ctas = t.shell_rank_major ? srir * t.shell_gmax : scta;
     p.adj_ctas = adta;
+    p.sd_ctas = sdc;
     p.tail_ctas = tcta;
     p.fin_ctas = fcta;
     size_t off = base;

@@ -46,6 +46,7 @@
 #define ISM_FIT_WINDOW_S 0.02     // envelope fit: last 20 ms of the ISM part
 #define ISM_CHEB_N 9              // Chebyshev terms of a tap function (degree 8)
 #define ISM_SHELL_BINS 8          // delay bins per CTA of the fused Chebyshev accumulation
+#define ISM_SD_BINS 32            // delay bins per CTA of the fused direct accumulation
 
 // Device-side description of one job.  Everything the kernels need is here
 // so that a whole launch set takes its jobs as one kernel parameter.
@@ -59,11 +60,6 @@ struct JobDev {
     float amp_scale;          // (fs / c) / (4 pi): A = F / (4 pi d) = F * amp_scale / s
     float s_cut2;             // cull: keep an image iff s_plain^2 < s_cut2 (samples^2)
     float g2;                 // log2 of the power decay per sample: 6 log2(10) / (fs T60)
-    float g2_lo;              // its low part (g2 + g2_lo is the FP64 value to ~2^-48)
-    int envelope;             // ISM_ENVELOPE_SABINE or ISM_ENVELOPE_LJ (diffuse tail)
-    int env_k0;               // first sample of the job's envelope table (n_ism - W_env)
-    int env_base;             // first entry (float) of the job's envelope table [n_S - env_k0]
-    int env_cta_base;         // first envelope CTA of the job
     int N[3], nlo[3];         // images per axis, lowest index per axis
     int n_src, n_rcv, n_rir;
     int n_S, n_ism;
@@ -108,15 +104,26 @@ struct JobDev {
     long long tail_cta_base;  // first tail CTA of the job
     long long fin_cta_base;   // first finalize CTA of the job
     long long rows_base;      // first window row (float) of the job: [n_rir][Q][32 (slots + 1)]
-    long long lut_base;       // first entry (float) of the job's windowed-sinc table (LUT forms)
-    unsigned long long lut_tex;  // texture object over that table (texture form)
+    // (the fields above keep their places: the register allocation of the fused kernels
+    // follows the layout of what they read; the ones below are read elsewhere)
+    unsigned long long lut_tex;  // texture object over the job's windowed-sinc table (texture form)
     // backward pass only
     const float* grad_out;    // dLoss/dh [n_rir][n_S]
     float* grad_beta;         // [6]
     float* grad_src;          // [n_src][3]
     float* grad_rcv;          // [n_rcv][3]
-    long long gpart_base;     // first per-(RIR, bin) gradient record (x 12 floats)
-    long long rgrad_base;     // first per-RIR gradient (float; 12 per RIR)
+    int gpart_base;           // first per-(RIR, bin) gradient record (x 12 floats); below 2^31
+    int rgrad_base;           // first per-RIR gradient (float; 12 per RIR)
+    int lut_base;             // first entry (float) of the job's windowed-sinc table (LUT forms)
+    // diffuse tail
+    float g2_lo;              // low part of g2 (g2 + g2_lo is the FP64 value to ~2^-48)
+    int envelope;             // ISM_ENVELOPE_SABINE or ISM_ENVELOPE_LJ
+    int env_k0;               // first sample of the job's envelope table (n_ism - W_env)
+    int env_base;             // first entry (float) of the job's envelope table [n_S - env_k0]
+    int env_cta_base;         // first envelope CTA of the job
+    // fused direct form (a 32-tap window, every tap evaluated, images enumerated per shell)
+    int shell_direct;         // its bins per CTA (0: not this form)
+    int sd_cta_base;          // first CTA of the job in its launch (shell_groups CTAs per RIR)
 };
 
 struct JobTable {
@@ -163,6 +170,7 @@ struct WsPlan {
     long long enum_ctas;
     long long acc_ctas;
     long long shell_ctas;
+    long long sd_ctas;     // CTAs of the fused direct form (shell_direct jobs)
     long long adj_ctas;
     long long tail_ctas;
     long long fin_ctas;
@@ -214,6 +222,7 @@ int ism_launch_accum_lut(const JobTable& t, const WsPlan& p, char* ws, void* str
 int ism_launch_accum_tex(const JobTable& t, const WsPlan& p, char* ws, void* stream, int* launched);
 int ism_launch_lut_tables(const JobTable& t, const WsPlan& p, char* ws, void* stream);
 int ism_launch_accum_cheb(const JobTable& t, const WsPlan& p, char* ws, void* stream, int* launched);
+int ism_launch_accum_shell_direct(const JobTable& t, const WsPlan& p, char* ws, void* stream, int* launched);
 int ism_launch_adjoint(const JobTable& t, const WsPlan& p, char* ws, void* stream, int* launched);
 int ism_launch_adjoint_cheb(const JobTable& t, const WsPlan& p, char* ws, void* stream, int* launched);
 int ism_launch_finalize(const JobTable& t, const WsPlan& p, char* ws, void* stream);

@@ -149,6 +149,76 @@ __device__ __forceinline__ int shell_rows(const Shell& sh, const float4* T, int*
     return Nx > 0 ? rowpre[Nx - 1] : 0;
 }
 
+// Column cl of the shell (cl < n_cols): its candidate intervals in z and its
+// record.  cnt = candidates; rf = {S_xy hi, S_xy lo, F_x F_y, o_x D_x + o_y D_y};
+// ri = {first z index below, count below, first z index above, ix | iy << 16}.
+__device__ __forceinline__ int shell_column(const Shell& sh, const float4* T, const int* rowpre, const int* rowy0,
+                                            int cl, float2 orient_xy, float4* rf_out, int4* ri_out)
+{
+    const int Nx = sh.Nx, Ny = sh.Ny;
+    int lo = 0, hi = Nx - 1;   // row: first ix with rowpre[ix] > cl
+    while (lo < hi) {
+        const int mid = (lo + hi) >> 1;
+        if (rowpre[mid] > cl) hi = mid;
+        else lo = mid + 1;
+    }
+    const int ix = lo;
+    const int before = ix > 0 ? rowpre[ix - 1] : 0;
+    const float4 tx = T[ix];
+    const int iy = min(rowy0[ix] + (cl - before), Ny - 1);
+    const float4 ty = T[Nx + iy];
+    const ff sxy = ff_add(ff{tx.x, tx.y}, ff{ty.x, ty.y});
+    const float sxy_p = __fadd_rn(tx.x, ty.x);
+    const float D1 =
+        fmaxf(__fsub_rn(__fmul_rn(sqrtf(fmaxf(__fsub_rn(sh.s_lo2, sxy_p), 0.0f)), sh.kinv), 1e-3f), 0.0f);
+    const float D2 = __fadd_rn(__fmul_rn(sqrtf(fmaxf(__fsub_rn(sh.s_hi2, sxy_p), 0.0f)), sh.kinv), 1e-3f);
+    int d0 = 0, d1 = 0, u0 = 0, u1 = 0;
+    if (sh.s_hi2 > sxy_p) {
+        ax_range(sh.ax[2], -D2, -D1, &d0, &d1);   // below the receiver (closed-open in n)
+        ax_range(sh.ax[2], D1, D2, &u0, &u1);     // above
+        d1 = min(d1, u0);                         // disjoint, whatever the rounding
+    }
+    const int nd = max(d1 - d0, 0), nu = max(u1 - u0, 0);
+    *rf_out = make_float4(sxy.hi, sxy.lo, tx.z * ty.z, __fmaf_rn(orient_xy.y, ty.w, orient_xy.x * tx.w));
+    *ri_out = make_int4(d0, nd, u0, ix | (iy << 16));
+    return nd + nu;
+}
+
+// Candidate i of a column (record cf, ci): its exact float-float delay; calls
+// on_image(b, f, s, cf, ixy, iz, tz) if its integer delay b lies in [b_lo, b_hi).
+template <class F>
+__device__ __forceinline__ void shell_candidate(const Shell& sh, const float4* T, const float4& cf, const int4& ci,
+                                                int i, F& on_image)
+{
+    const int iz = i < ci.y ? ci.x + i : ci.z + (i - ci.y);
+    const float4 tz = T[sh.Nx + sh.Ny + iz];
+    const ff s2 = ff_add(ff{cf.x, cf.y}, ff{tz.x, tz.y});
+    const ff sq = ff_sqrt(s2);
+    float bf = floorf(sq.hi);
+    float f = __fadd_rn(__fsub_rn(sq.hi, bf), sq.lo);
+    const bool neg = f < 0.0f;   // bring f into [0, 1) (see ism_delay)
+    f = neg ? __fadd_rn(f, 1.0f) : f;
+    bf = neg ? bf - 1.0f : bf;
+    const bool one = f >= 1.0f;
+    f = one ? __fsub_rn(f, 1.0f) : f;
+    bf = one ? bf + 1.0f : bf;
+    const int b = ism_int_of_integral(fminf(bf, 4.0e6f));
+    if (b >= sh.b_lo && b < sh.b_hi) on_image(b, f, sq.hi, cf, ci.w, iz, tz);
+}
+
+// Last index o in [0, 31] with W[o] <= j (W non-decreasing, W[0] = 0 <= j).
+__device__ __forceinline__ int shell_find(const int* W, int j)
+{
+    int lo = 0, hi = 31;
+#pragma unroll
+    for (int s = 0; s < 5; ++s) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (W[mid] <= j) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
+}
+
 // The images of the shell, for the calling warp's share of the columns
 // (chunks c0 = warp * 32 + k * 32 WARPS).  For each image with integer delay
 // b in [b_lo, b_hi) lane calls
@@ -163,41 +233,13 @@ __device__ __forceinline__ void shell_walk(const Shell& sh, const float4* T, con
                                            int n_cols, float2 orient_xy, float4* Wf, int4* Wi, int* Wst, int warp,
                                            int lane, F&& on_image)
 {
-    const int Nx = sh.Nx, Ny = sh.Ny;
     for (int c0 = warp * 32; c0 < n_cols; c0 += WARPS * 32) {
         // ---- the column of this lane and its candidate intervals in z
         const int cl = c0 + lane;
         int cnt = 0;
         float4 rf = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
         int4 ri = make_int4(0, 0, 0, 0);
-        if (cl < n_cols) {
-            int lo = 0, hi = Nx - 1;   // row: first ix with rowpre[ix] > cl
-            while (lo < hi) {
-                const int mid = (lo + hi) >> 1;
-                if (rowpre[mid] > cl) hi = mid;
-                else lo = mid + 1;
-            }
-            const int ix = lo;
-            const int before = ix > 0 ? rowpre[ix - 1] : 0;
-            const float4 tx = T[ix];
-            const int iy = min(rowy0[ix] + (cl - before), Ny - 1);
-            const float4 ty = T[Nx + iy];
-            const ff sxy = ff_add(ff{tx.x, tx.y}, ff{ty.x, ty.y});
-            const float sxy_p = __fadd_rn(tx.x, ty.x);
-            const float D1 =
-                fmaxf(__fsub_rn(__fmul_rn(sqrtf(fmaxf(__fsub_rn(sh.s_lo2, sxy_p), 0.0f)), sh.kinv), 1e-3f), 0.0f);
-            const float D2 = __fadd_rn(__fmul_rn(sqrtf(fmaxf(__fsub_rn(sh.s_hi2, sxy_p), 0.0f)), sh.kinv), 1e-3f);
-            int d0 = 0, d1 = 0, u0 = 0, u1 = 0;
-            if (sh.s_hi2 > sxy_p) {
-                ax_range(sh.ax[2], -D2, -D1, &d0, &d1);   // below the receiver (closed-open in n)
-                ax_range(sh.ax[2], D1, D2, &u0, &u1);     // above
-                d1 = min(d1, u0);                         // disjoint, whatever the rounding
-            }
-            const int nd = max(d1 - d0, 0), nu = max(u1 - u0, 0);
-            cnt = nd + nu;
-            rf = make_float4(sxy.hi, sxy.lo, tx.z * ty.z, __fmaf_rn(orient_xy.y, ty.w, orient_xy.x * tx.w));
-            ri = make_int4(d0, nd, u0, ix | (iy << 16));
-        }
+        if (cl < n_cols) cnt = shell_column(sh, T, rowpre, rowy0, cl, orient_xy, &rf, &ri);
         int inc = cnt;
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
@@ -216,32 +258,70 @@ __device__ __forceinline__ void shell_walk(const Shell& sh, const float4* T, con
         for (int j0 = 0; j0 < total; j0 += 32) {
             const int j = j0 + lane;
             if (j < total) {
-                int lo = 0, hi = 31;   // last column o with Wst[o] <= j
-#pragma unroll
-                for (int s = 0; s < 5; ++s) {
-                    const int mid = (lo + hi + 1) >> 1;
-                    if (Wst[mid] <= j) lo = mid;
-                    else hi = mid - 1;
-                }
-                const float4 cf = Wf[lo];
-                const int4 ci = Wi[lo];
-                const int i = j - Wst[lo];
-                const int iz = i < ci.y ? ci.x + i : ci.z + (i - ci.y);
-                const float4 tz = T[Nx + Ny + iz];
-                const ff s2 = ff_add(ff{cf.x, cf.y}, ff{tz.x, tz.y});
-                const ff sq = ff_sqrt(s2);
-                float bf = floorf(sq.hi);
-                float f = __fadd_rn(__fsub_rn(sq.hi, bf), sq.lo);
-                const bool neg = f < 0.0f;   // bring f into [0, 1) (see ism_delay)
-                f = neg ? __fadd_rn(f, 1.0f) : f;
-                bf = neg ? bf - 1.0f : bf;
-                const bool one = f >= 1.0f;
-                f = one ? __fsub_rn(f, 1.0f) : f;
-                bf = one ? bf + 1.0f : bf;
-                const int b = ism_int_of_integral(fminf(bf, 4.0e6f));
-                if (b >= sh.b_lo && b < sh.b_hi) on_image(b, f, sq.hi, cf, ci.w, iz, tz);
+                const int o = shell_find(Wst, j);
+                shell_candidate(sh, T, Wf[o], Wi[o], j - Wst[o], on_image);
             }
         }
         __syncwarp();
+    }
+}
+
+// The images of the shell for the whole CTA, the candidates of every chunk of
+// WARPS x 32 columns split evenly over the warps: warp w takes the chunk's
+// candidates [w C / WARPS, (w + 1) C / WARPS) in ascending order, 32 at a time
+// (candidate c by lane c mod 32), so every warp has the same work whatever the
+// columns hold, and which warp and lane meet an image is a function of the
+// geometry alone.  on_image as for shell_walk; on_batch() is called by every
+// warp (converged) after each batch of 32 candidates.  Every thread of the
+// CTA calls it.  Wf, Wi: [WARPS x 32] column records; Wst: [WARPS][33] warp
+// prefixes; wtot: [WARPS].
+template <int WARPS, class F, class G>
+__device__ __forceinline__ void shell_walk_cta(const Shell& sh, const float4* T, const int* rowpre, const int* rowy0,
+                                               int n_cols, float2 orient_xy, float4* Wf, int4* Wi, int* Wst,
+                                               int* wtot, int warp, int lane, F&& on_image, G&& on_batch)
+{
+    for (int c0 = 0; c0 < n_cols; c0 += WARPS * 32) {
+        const int cl = c0 + warp * 32 + lane;
+        int cnt = 0;
+        float4 rf = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+        int4 ri = make_int4(0, 0, 0, 0);
+        if (cl < n_cols) cnt = shell_column(sh, T, rowpre, rowy0, cl, orient_xy, &rf, &ri);
+        int inc = cnt;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int n = __shfl_up_sync(0xffffffffu, inc, o);
+            if (lane >= o) inc += n;
+        }
+        Wf[warp * 32 + lane] = rf;
+        Wi[warp * 32 + lane] = ri;
+        Wst[warp * 33 + lane] = inc - cnt;
+        if (lane == 31) {
+            Wst[warp * 33 + 32] = inc;
+            wtot[warp] = inc;
+        }
+        __syncthreads();
+        int off[WARPS + 1];   // exclusive prefix of the warps' candidates
+        off[0] = 0;
+#pragma unroll
+        for (int w = 0; w < WARPS; ++w) off[w + 1] = off[w] + wtot[w];
+        const int tot = off[WARPS];
+        const int a = (int)((long long)tot * warp / WARPS), e = (int)((long long)tot * (warp + 1) / WARPS);
+        for (int j0 = a; j0 < e; j0 += 32) {
+            const int c = j0 + lane;
+            if (c < e) {
+                int wb = 0, base = 0;   // the warp whose columns hold candidate c: the last w with off[w] <= c
+#pragma unroll
+                for (int w = 1; w < WARPS; ++w)   // (never an empty block: off[wb + 1] > c)
+                    if (off[w] <= c) {
+                        wb = w;
+                        base = off[w];
+                    }
+                const int j = c - base;
+                const int o = shell_find(Wst + wb * 33, j);
+                shell_candidate(sh, T, Wf[wb * 32 + o], Wi[wb * 32 + o], j - Wst[wb * 33 + o], on_image);
+            }
+            on_batch();
+        }
+        __syncthreads();   // the records are read before the next chunk overwrites them
     }
 }

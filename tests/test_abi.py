@@ -77,11 +77,15 @@ def test_nb_img_and_att2t_match_oracle():
 
 def test_workspace_size_and_validation(lib):
     L, beta = [6.0, 5.0, 3.0], [0.9] * 6
-    # the direct evaluation bins image ids: at least the worst-case id buffer,
-    # 128 RIRs x 895,491 images x 4 B
-    n = ism.ism_workspace_size(L, beta, 4, 32, [73, 87, 141], 0.6, 16000.0, Tw=32 / 16000, prec="fp32_direct")
+    # the direct evaluation of a window other than 32 taps bins image ids: at least
+    # the worst-case id buffer, 128 RIRs x 895,491 images x 4 B
+    n = ism.ism_workspace_size(L, beta, 4, 32, [73, 87, 141], 0.6, 16000.0, Tw=40 / 16000, prec="fp32_direct")
     assert n >= 128 * 73 * 87 * 141 * 4
     assert n % 256 == 0
+    # with a 32-tap window the direct evaluation enumerates its images in the
+    # accumulating CTA: tables and window rows only
+    nd = ism.ism_workspace_size(L, beta, 4, 32, [73, 87, 141], 0.6, 16000.0, Tw=32 / 16000, prec="fp32_direct")
+    assert 128 * 301 * 64 * 4 <= nd < 32 << 20
     # the fused Chebyshev form enumerates its images itself: per-bin counts,
     # tables and window rows only (128 x 301 bins x 64 FP32 rows = 9.9 MB)
     n32 = ism.ism_workspace_size(L, beta, 4, 32, [73, 87, 141], 0.6, 16000.0, Tw=32 / 16000)
@@ -213,27 +217,30 @@ def test_binding_struct_layouts_match_the_header(tmp_path):
             assert got[(name, f[0])] == getattr(cls, f[0]).offset, (name, f[0])
 
 
-def test_plan_takes_the_fused_form_for_dense_rooms_only():
-    """Host-side planning (no GPU needed): a dense 32-tap room takes the fused
-    kernel, which needs no image-id buffer, so its FP32 workspace is a small
-    fraction of the per-tap form's; the sparse 48 kHz array (~36 images per
-    delay bin) takes the direct form in both cases (same workspace); a backward
-    call over a 32-tap window takes the fused adjoint (no ids either), over a
-    6-tap window the per-tap adjoint over binned ids."""
+def test_plan_takes_the_fused_forms_for_32_tap_windows():
+    """Host-side planning (no GPU needed): 32-tap windows take a kernel that
+    enumerates its own images -- the Chebyshev one for a dense room, the fused
+    per-tap one for FP32_DIRECT and for the sparse 48 kHz array (~36 images per
+    delay bin) -- and need no image-id buffer; another window length bins image
+    ids (the per-tap form over a 40-tap window); a backward call over a 32-tap
+    window takes the fused adjoint (no ids either), over a 6-tap window the
+    per-tap adjoint over binned ids."""
     from paper_1810_11359_gb300 import ism
     L = [6.0, 5.0, 3.0]
     beta = ism.ism_beta_sabine(L, 0.6)
     N = ism.ism_nb_img_from_t(0.6, L, 343.0, 32 / 16000)
     fused = ism.ism_workspace_size(L, beta, 4, 32, N, 0.6, 16000.0, Tw=32 / 16000, prec="fp32")
     direct = ism.ism_workspace_size(L, beta, 4, 32, N, 0.6, 16000.0, Tw=32 / 16000, prec="fp32_direct")
+    N40 = ism.ism_nb_img_from_t(0.6, L, 343.0, 40 / 16000)
+    binned = ism.ism_workspace_size(L, beta, 4, 32, N40, 0.6, 16000.0, Tw=40 / 16000, prec="fp32_direct")
     ids = 128 * int(np.prod(N)) * 4
-    assert fused < direct / 10 and direct > ids
+    assert fused == direct and fused < ids / 10 and binned > ids
     L2 = [10.0, 8.0, 3.5]
     b2 = ism.ism_beta_sabine(L2, 1.2)
     N2 = ism.ism_nb_img_from_t(0.3, L2, 343.0, 32 / 48000)
     a = ism.ism_workspace_size(L2, b2, 64, 8, N2, 1.2, 48000.0, Tdiff=0.3, Tw=32 / 48000, prec="fp32")
     b = ism.ism_workspace_size(L2, b2, 64, 8, N2, 1.2, 48000.0, Tdiff=0.3, Tw=32 / 48000, prec="fp32_direct")
-    assert a == b and a > 512 * int(np.prod(N2)) * 4
+    assert a == b and a < 512 * int(np.prod(N2)) * 4
     # backward: host tensors only lend the pointers the host-side checks look at
     import torch
     ps, pr = torch.ones((1, 3)), torch.ones((1, 3))

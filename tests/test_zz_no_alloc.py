@@ -81,18 +81,18 @@ def test_noalloc_matches_workspace_entry_two_calls_in_a_row():
 
 
 def test_noalloc_rejects_simulations_above_its_scratch():
-    # the direct evaluation of the 128-RIR workload bins 0.4 GB of image ids:
-    # more than the 64 MiB scratch
+    # the direct evaluation of the 128-RIR workload with a 40-tap window bins
+    # 0.5 GB of image ids: more than the 64 MiB scratch
     room = workloads.batched_fp32()
     beta = ism.ism_beta_sabine(room.L, room.rt60)
-    N = ism.ism_nb_img_from_t(room.Tmax, room.L, room.c, room.window())
+    N = ism.ism_nb_img_from_t(room.Tmax, room.L, room.c, 40 / 16000)
     out = torch.full((4, 32, 9600), 7.0, device="cuda")
     ps = torch.as_tensor(room.pos_src).cuda()
     pr = torch.as_tensor(room.pos_rcv).cuda()
     r = ism._room(room.L, beta, 343.0)
     lib = ism.load()
     st = lib.ism_simulate_noalloc(ctypes.byref(r), ctypes.c_void_p(ps.data_ptr()), 4, ctypes.c_void_p(pr.data_ptr()),
-                                  32, ism._nb(N), 0.6, 16000.0, 0.0, 32 / 16000, ism.PRECISIONS["fp32_direct"], 0,
+                                  32, ism._nb(N), 0.6, 16000.0, 0.0, 40 / 16000, ism.PRECISIONS["fp32_direct"], 0,
                                   ctypes.c_void_p(out.data_ptr()), None)
     assert st == 8
     assert "scratch" in lib.ism_last_error_message().decode()
