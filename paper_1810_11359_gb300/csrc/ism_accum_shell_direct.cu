@@ -19,14 +19,16 @@
 // P sin phi} (the factorised windowed sinc of ism_accum.cuh: P = A sin(pi f) /
 // (2 pi), phi = 2 pi f / N_w) and the position of its first tap in the
 // shell's window (32 B + 32 samples from 32 q0 - 16, B bins) and stages
-// them in the warp's shared memory.  After every batch of 32 candidates the warp takes the
-// staged images in lane order, and lane t adds tap t of each -- sigma_t
-// (t - 15 - f) by one FFMA, the window by two, one reciprocal and one product --
-// to its warp's window of the shell in shared memory (consecutive lanes,
-// consecutive addresses).  The order in which a warp adds its images is a
-// function of the geometry alone (ism_shell.cuh), so the warp windows are the same in every
-// run; at the end they are summed in warp order.  No atomics: the output is
-// bit-identical from run to run.
+// them in the warp's shared memory.  After every batch of 32 candidates the
+// warp takes the staged images in lane order, two at a time (lanes 2k and
+// 2k + 1), and lane t adds tap t of each -- sigma_t (t - 15 - f) by one FFMA,
+// the window by two, one reciprocal and one product, the FMAs and the product
+// issued as packed f32x2 operations on the pair -- to its warp's window of the
+// shell in shared memory (consecutive lanes, consecutive addresses).  The
+// order in which a warp adds its images is a function of the geometry alone
+// (ism_shell.cuh), so the warp windows are the same in every run; at the end
+// they are summed in warp order.  No atomics: the output is bit-identical from
+// run to run.
 //
 // The shell's window is written as the bins' window rows of the finalize
 // kernel (64 samples from 32 q - 16, summed per sample with the previous
@@ -37,6 +39,31 @@
 #include "ism_shell.cuh"
 
 namespace {
+
+// Two FP32 values in one 64-bit register pair, and the packed FP32 operations of
+// sm_100-class GPUs on them (both lanes rounded as the scalar operations are).
+__device__ __forceinline__ unsigned long long sd_pack(float a, float b)
+{
+    unsigned long long r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(a), "f"(b));
+    return r;
+}
+__device__ __forceinline__ void sd_unpack(unsigned long long r, float& a, float& b)
+{
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(a), "=f"(b) : "l"(r));
+}
+__device__ __forceinline__ unsigned long long sd_fma2(unsigned long long a, unsigned long long b, unsigned long long c)
+{
+    unsigned long long d;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+    return d;
+}
+__device__ __forceinline__ unsigned long long sd_mul2(unsigned long long a, unsigned long long b)
+{
+    unsigned long long d;
+    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
 
 #define SD_B ISM_SD_BINS             // delay bins per CTA, at most
 #define SD_WARPS 8                   // warps per CTA
@@ -71,7 +98,7 @@ __global__ void __launch_bounds__(SD_WARPS * 32, 4) shell_direct_kernel(const __
     int4* reci = reinterpret_cast<int4*>(recf + SD_WARPS * 32);
     int* st = reinterpret_cast<int*>(reci + SD_WARPS * 32);            // [warps][33]
     float* win_all = reinterpret_cast<float*>(st + SD_WARPS * 33);     // [warps][SD_WIN]
-    float4* stage_all = reinterpret_cast<float4*>(win_all + SD_WARPS * SD_WIN);   // [warps][32]
+    float4* stage_all = reinterpret_cast<float4*>(win_all + SD_WARPS * SD_WIN);   // [warps][32] (lane pairs interleaved)
     int* spos_all = reinterpret_cast<int*>(stage_all + SD_WARPS * 32);            // [warps][32]
     int* wtot = spos_all + SD_WARPS * 32;                                          // [warps]
     float* win = win_all + warp * SD_WIN;
@@ -81,7 +108,6 @@ __global__ void __launch_bounds__(SD_WARPS * 32, 4) shell_direct_kernel(const __
     const float4* Tg = tbl + J.tbl_base + (long long)r * n_axis;
     for (int e = threadIdx.x; e < n_axis; e += blockDim.x) T[e] = Tg[e];
     for (int e = threadIdx.x; e < SD_WARPS * SD_WIN; e += blockDim.x) win_all[e] = 0.0f;
-    spos[lane] = -1;
     __syncthreads();
 
     // receiver polar pattern: the unit orientation of this RIR's receiver
@@ -94,18 +120,33 @@ __global__ void __launch_bounds__(SD_WARPS * 32, 4) shell_direct_kernel(const __
         const float inv = 1.0f / sqrtf(__fmaf_rn(ox, ox, __fmaf_rn(oy, oy, oz * oz)));
         orient = make_float3(ox * inv, oy * inv, oz * inv);
     }
-    // lane constants of tap t = lane, j = t - 15 (see ism_accum.cuh)
+    // lane constants of tap t = lane, j = t - 15 (see ism_accum.cuh), twice: two images
+    // go through the packed FP32 pipe together (f32x2 FMA and multiply)
     const int j = lane - 15;
     const float sg = (j & 1) ? 1.0f : -1.0f;   // (-1)^(j+1)
     const float xj = sg * (float)j, nsg = -sg;
     float Sj, Cj;
     sincospif((float)j * (2.0f / 32.0f), &Sj, &Cj);
+    const unsigned long long xj2 = sd_pack(xj, xj), nsg2 = sd_pack(nsg, nsg), Cj2 = sd_pack(Cj, Cj),
+                             Sj2 = sd_pack(Sj, Sj);
     const float twopi_Nw = 6.283185307179586f / 32.0f, inv2Nw = 2.0f / 32.0f;
 
     const int W0 = ISM_SB * q0 - 16;   // first sample of the shell's window
     const Shell sh = shell_setup(J, T, r, ISM_SB * q0 - 1, min(ISM_SB * (q0 + nb) - 1, J.n_ism + J.H - 1));
     const int n_cols = shell_rows(sh, T, rowpre, rowy0);   // (synchronises the CTA)
     const float amp_scale = J.amp_scale;
+    // staged records of lanes 2k and 2k + 1 interleaved: {f_a, f_b, P_a, P_b}, {Pc_a, Pc_b, Ps_a, Ps_b};
+    // a lane without an image leaves the zero-amplitude record {1/2, 0, 0, 0} (it adds 0)
+    float* sl = reinterpret_cast<float*>(stage) + 8 * (lane >> 1) + (lane & 1);
+    auto clear = [&]() {
+        sl[0] = 0.5f;
+        sl[2] = 0.0f;
+        sl[4] = 0.0f;
+        sl[6] = 0.0f;
+        spos[lane] = -1;
+    };
+    clear();
+    __syncwarp();
 
     shell_walk_cta<SD_WARPS>(
         sh, T, rowpre, rowy0, n_cols, make_float2(orient.x, orient.y), recf, reci, st, wtot, warp, lane,
@@ -115,23 +156,36 @@ __global__ void __launch_bounds__(SD_WARPS * 32, 4) shell_direct_kernel(const __
             if (alpha != 1.0f)   // polar pattern: cos(theta) = o . (x_n - x_r) / d
                 amp *= __fmaf_rn(1.0f - alpha, __fmaf_rn(orient.z, tz.w, cf.w) * rs, alpha);
             f = fmaxf(f, 0x1p-60f);   // keeps j - f away from 0 (the reciprocal of the tap j = 0)
-            stage[lane] = ism_sinc_record(f, amp, true, twopi_Nw, inv2Nw);
+            const float4 rc = ism_sinc_record(f, amp, true, twopi_Nw, inv2Nw);
+            sl[0] = rc.x;
+            sl[2] = rc.y;
+            sl[4] = rc.z;
+            sl[6] = rc.w;
             spos[lane] = b - 15 - W0;   // window position of tap 0, in [0, 32 nb - 1)
         },
         [&]() {
             __syncwarp();
-            unsigned m = __ballot_sync(0xffffffffu, spos[lane] >= 0);
-            while (m) {   // the staged images in lane order
-                const int l = __ffs(m) - 1;
+            const unsigned v = __ballot_sync(0xffffffffu, spos[lane] >= 0);
+            unsigned m = (v | (v >> 1)) & 0x55555555u;   // lane pairs holding an image
+            const ulonglong2* st2 = reinterpret_cast<const ulonglong2*>(stage);
+            const int2* sp2 = reinterpret_cast<const int2*>(spos);
+            while (m) {   // pairs in lane order; within a pair lane 2k first
+                const int k = (__ffs(m) - 1) >> 1;
                 m &= m - 1;
-                const float4 rc = stage[l];
-                const int p = spos[l];
-                const float x = __fmaf_rn(nsg, rc.x, xj);
-                const float w = __fmaf_rn(Cj, rc.z, __fmaf_rn(Sj, rc.w, rc.y));
-                win[p + lane] += w * ism_rcp(x);
+                const ulonglong2 fa = st2[2 * k];       // {f_a, f_b}, {P_a, P_b}
+                const ulonglong2 fb = st2[2 * k + 1];   // {Pc_a, Pc_b}, {Ps_a, Ps_b}
+                const int2 pp = sp2[k];
+                const unsigned long long x2 = sd_fma2(nsg2, fa.x, xj2);
+                const unsigned long long w2 = sd_fma2(Cj2, fb.x, sd_fma2(Sj2, fb.y, fa.y));
+                float xa, xb;
+                sd_unpack(x2, xa, xb);
+                float va, vb;
+                sd_unpack(sd_mul2(w2, sd_pack(ism_rcp(xa), ism_rcp(xb))), va, vb);
+                if (pp.x >= 0) win[pp.x + lane] += va;
+                if (pp.y >= 0) win[pp.y + lane] += vb;
             }
             __syncwarp();
-            spos[lane] = -1;
+            clear();
             __syncwarp();
         });
     __syncthreads();
