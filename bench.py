@@ -812,6 +812,8 @@ def main():
                     choices=["batched", "trajectory", "serving", "differentiation", "moving_source"])
     ap.add_argument("--requests", type=int, default=20000, help="serving: requests per arrival pattern")
     ap.add_argument("--prec", default="fp32", choices=list(PREC_ID))
+    ap.add_argument("--envelope", default="sabine", choices=["sabine", "lj"],
+                    help="power envelope of the diffuse tail (workloads with a tail)")
     ap.add_argument("--no-extras", action="store_true",
                     help="default workload: skip the precision forms, the 48 kHz array, serving and single-RIR lines")
     ap.add_argument("--serving-requests", type=int, default=3000,
@@ -874,7 +876,7 @@ def main():
 
     def step():
         ism.ism_simulate(room.L, beta, ps, pr, N, room.Tmax, room.fs, Tdiff=Tdiff, Tw=room.window(), c=room.c,
-                         prec=args.prec, seed=room.seed, out=out, workspace=ws)
+                         prec=args.prec, seed=room.seed, out=out, workspace=ws, envelope=args.envelope)
 
     for _ in range(max(args.warmup, 3)):
         step()

@@ -168,7 +168,7 @@ ism_status plan(const Validated* vs, int n, ism_precision prec, bool backward, J
     for (int i = 0; i < n; ++i)
         set_cols += (long long)vs[i].job.nb_img[0] * vs[i].job.nb_img[1] * vs[i].job.n_src * vs[i].job.n_rcv;
     long long rir = 0, hist = 0, tbl = 0, ecta = 0, acta = 0, adta = 0, tcta = 0, fcta = 0, rows = 0, ids = 0, lut = 0,
-              gpart = 0, srir = 0, scta = 0, env = 0, vcta = 0, sdc = 0;
+              gpart = 0, srir = 0, scta = 0, env = 0, vcta = 0, sdc = 0, vslot = 0;
     for (int i = 0; i < n; ++i) {
         const Validated& v = vs[i];
         const ism_job& in = v.job;
@@ -329,10 +329,12 @@ ism_status plan(const Validated* vs, int n, ism_precision prec, bool backward, J
         J.env_k0 = v.n_ism - J.W_env;
         J.env_base = env;
         J.env_cta_base = vcta;
+        J.env_slot = (int)vslot;
         if (J.has_tail && J.envelope == ISM_ENVELOPE_LJ) {
             const long long n_env = (long long)v.n_S - J.env_k0;
             env += (n_env + 63) / 64 * 64;
             vcta += (n_env + ISM_ENV_CHUNK - 1) / ISM_ENV_CHUNK;
+            ++vslot;
         }
         rows += R * J.Q * 32LL * (J.slots + 1);
         if (prec == ISM_PREC_LUT) lut += (long long)(ism_lut_phases(J.slots) + 1) * 32 * J.slots;
@@ -368,6 +370,7 @@ ism_status plan(const Validated* vs, int n, ism_precision prec, bool backward, J
     p.rgrad_total = backward ? rir * 12 : 0;
     p.env_total = backward ? 0 : env;
     p.env_ctas = backward ? 0 : vcta;
+    p.env_slots = backward ? 0 : vslot;
     p.enum_ctas = ecta;
     p.acc_ctas = acta;
     t.shell_rirs = srir;
@@ -408,6 +411,8 @@ ism_status plan(const Validated* vs, int n, ism_precision prec, bool backward, J
     off = align256(off + (size_t)p.rgrad_total * 4);
     p.env_off = off;
     off = align256(off + (size_t)p.env_total * 4);
+    p.env_nodes_off = off;
+    off = align256(off + (size_t)p.env_slots * ISM_ENV_SLOT * 16);
     p.total = off;
     return ISM_OK;
 }

@@ -124,6 +124,7 @@ struct JobDev {
     // fused direct form (a 32-tap window, every tap evaluated, images enumerated per shell)
     int shell_direct;         // its bins per CTA (0: not this form)
     int sd_cta_base;          // first CTA of the job in its launch (shell_groups CTAs per RIR)
+    int env_slot;             // the job's slot of envelope quadrature nodes (Lehmann-Johansson tails)
 };
 
 struct JobTable {
@@ -155,6 +156,7 @@ struct WsPlan {
     size_t gpart_off;      // float  [gpart_total]: backward, per-(RIR, bin) gradients
     size_t rgrad_off;      // float  [rgrad_total]: backward, per-RIR gradients
     size_t env_off;        // float  [env_total]: per-job envelope tables (Lehmann-Johansson tails)
+    size_t env_nodes_off;  // float4 [env_slots][ISM_ENV_SLOT]: their quadrature nodes and E(t0)
     size_t total;
     long long hist_total;
     long long ids_total;
@@ -166,6 +168,7 @@ struct WsPlan {
     long long rgrad_total;
     long long env_total;
     long long env_ctas;
+    long long env_slots;
     long long n_scan_blocks;
     long long enum_ctas;
     long long acc_ctas;
@@ -177,8 +180,9 @@ struct WsPlan {
 };
 
 #define ISM_TAIL_CHUNK 4096   // tail samples per CTA (256 threads x 16)
-#define ISM_ENV_CHUNK 256     // envelope-table samples per CTA (one per thread)
+#define ISM_ENV_CHUNK 64      // envelope-table samples per CTA (four threads each)
 #define ISM_ENV_MAX_NODES 64  // Gauss-Legendre nodes per angle of the envelope integral
+#define ISM_ENV_SLOT (ISM_ENV_MAX_NODES * ISM_ENV_MAX_NODES + 1)   // float4 per job: nodes, then {n, E(t0)}
 
 // Delay bins (warps) per accumulation CTA: the LUT form copies its ~33 KB
 // table into shared memory once per CTA, so it takes 8 bins per CTA.

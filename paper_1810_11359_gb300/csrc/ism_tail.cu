@@ -97,10 +97,17 @@ __global__ void __launch_bounds__(256) tail_kernel(const __grid_constant__ JobTa
     const int r = (int)(local / per_rir);
     const int c = (int)(local % per_rir);
     const float sqA = sqrtf(amp[J.rir_base + r]);
+    // Sabine envelope of a block of 4 samples from its first one: e_(k+d) = e_k R_d,
+    // R_d = 2^(-hg d) for d = 1 .. 3 (each within 2 ulp, the product rounded once more:
+    // a few 1e-7 of the sample, see ism_exp2_neg)
     __shared__ ff g2_s;
+    __shared__ float R_s[4];
     if (threadIdx.x == 0) g2_s = ism_job_g2(J);
     __syncthreads();
     const ff hg = {0.5f * g2_s.hi, 0.5f * g2_s.lo};   // amplitude: half the power's rate (exact)
+    if (threadIdx.x < 4) R_s[threadIdx.x] = ism_exp2_neg(hg, (int)threadIdx.x);
+    __syncthreads();
+    const float R1 = R_s[1], R2 = R_s[2], R3 = R_s[3];
     const bool lj = J.envelope == ISM_ENVELOPE_LJ;
     const float* envt = env + J.env_base - J.env_k0;   // sqrt(E(t_k) / E(t0)), k >= env_k0
     float* out = J.out + (long long)r * J.n_S;
@@ -115,7 +122,13 @@ __global__ void __launch_bounds__(256) tail_kernel(const __grid_constant__ JobTa
             e1 = sqA * envt[min(max(k + 1, J.n_ism), J.n_S - 1)];
             e2 = sqA * envt[min(max(k + 2, J.n_ism), J.n_S - 1)];
             e3 = sqA * envt[min(max(k + 3, J.n_ism), J.n_S - 1)];
-        } else {
+        } else if (k >= J.n_ism) {
+            const float b0 = ism_exp2_neg(hg, k - J.n_ism);
+            e0 = sqA * b0;
+            e1 = sqA * (b0 * R1);
+            e2 = sqA * (b0 * R2);
+            e3 = sqA * (b0 * R3);
+        } else {   // the block holding sample n_ism (only its samples >= n_ism are written)
             e0 = sqA * ism_exp2_neg(hg, max(k - J.n_ism, 0));
             e1 = sqA * ism_exp2_neg(hg, max(k + 1 - J.n_ism, 0));
             e2 = sqA * ism_exp2_neg(hg, max(k + 2 - J.n_ism, 0));
@@ -139,42 +152,30 @@ __global__ void __launch_bounds__(256) tail_kernel(const __grid_constant__ JobTa
 //   E(t) = (2 / pi) int_0^(pi/2) int_0^(pi/2) 2^(-k g(theta, phi)) sin(theta) dtheta dphi,
 //   g = sum_a |u_a| gamma_a,  gamma_a = -log2 |beta_a0 beta_a1| c / (f_s L_a)
 // (the average over one octant of directions u; log2 of the energy lost per
-// sample along u).  Each CTA builds the Gauss-Legendre product rule itself
-// (nodes by Newton's iteration on the Legendre recurrence, FP64), the node
-// rates g in float-float and the weights in FP32, then each thread sums its
-// sample's n^2 terms 2^(-k g) with Kahan's compensated FP32 summation (all
-// terms positive: relative error ~2 ulp plus exp2f's 2 ulp).  E(t0) is summed
-// the same way by every CTA of the job, so all CTAs agree on it bit for bit.
-// n = clamp(ceil(K / 4) + 12, 16, 64) nodes per angle, K = (n_S / f_s) c
-// |(-ln rho_a / L_a)_a|, the largest exponent (in nepers) over the table.
+// sample along u).  One CTA per job (envelope_nodes_kernel) builds the
+// Gauss-Legendre product rule (nodes by Newton's iteration on the Legendre
+// recurrence, FP64), the node rates g in float-float and the weights in FP32,
+// and E(t0); then four threads of envelope_kernel share each sample: each sums
+// a quarter of its n^2 terms 2^(-k g) with Kahan's compensated FP32 summation
+// (all terms positive: relative error ~2 ulp plus exp2f's 2 ulp), and the four
+// partial sums are added in FP64 in a fixed order (E(t0) likewise).  n =
+// clamp(ceil(K / 4) + 12, 16, 64) nodes per angle, K = (n_S / f_s) c
+// |(-ln rho_a / L_a)_a|, the largest exponent (in nepers) over the table.  A
+// job's node slot holds ISM_ENV_SLOT float4 {g hi, g lo, w, 0}, the last one
+// {n (int bits), 0, E(t0) as the two halves of an FP64}.
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ float env_sum(const float2* g, const float* w, int nn, int k)
+__global__ void __launch_bounds__(256) envelope_nodes_kernel(const __grid_constant__ JobTable t,
+                                                             float4* __restrict__ nodes)
 {
-    float s = 0.0f, comp = 0.0f;
-    for (int i = 0; i < nn; ++i) {
-        const float y = __fsub_rn(__fmul_rn(w[i], ism_exp2_neg(ff{g[i].x, g[i].y}, k)), comp);
-        const float tt = __fadd_rn(s, y);
-        comp = __fsub_rn(__fsub_rn(tt, s), y);
-        s = tt;
-    }
-    return s;
-}
-
-__global__ void __launch_bounds__(ISM_ENV_CHUNK) envelope_kernel(const __grid_constant__ JobTable t,
-                                                                 float* __restrict__ env)
-{
-    extern __shared__ __align__(16) unsigned char smem[];
-    const long long g = blockIdx.x;
-    const int jid = ism_find_job(t, g, [](const JobDev& j) { return j.env_cta_base; });
-    const JobDev& J = t.j[jid];
-    const int chunk = (int)(g - J.env_cta_base);
+    const JobDev& J = t.j[blockIdx.x];
+    if (!J.has_tail || J.envelope != ISM_ENVELOPE_LJ) return;   // CTA-uniform
+    float4* slot = nodes + (long long)J.env_slot * ISM_ENV_SLOT;
     __shared__ double wg[ISM_ENV_MAX_NODES];
     __shared__ double sth[ISM_ENV_MAX_NODES], cth[ISM_ENV_MAX_NODES];
     __shared__ double gam[3];
     __shared__ int n_s;
-    __shared__ float part[ISM_ENV_CHUNK];
-    float2* gn = reinterpret_cast<float2*>(smem);                       // [n * n] node rates
-    float* wn = reinterpret_cast<float*>(gn + ISM_ENV_MAX_NODES * ISM_ENV_MAX_NODES);   // [n * n] weights
+    __shared__ double part[256];
+    __shared__ double inv_m[ISM_ENV_MAX_NODES + 1];   // 1 / m for the Legendre recurrence
     const double PI = 3.141592653589793238462643383279502884;
     if (threadIdx.x == 0) {
         double kn = 0.0;
@@ -188,29 +189,29 @@ __global__ void __launch_bounds__(ISM_ENV_CHUNK) envelope_kernel(const __grid_co
         kn = sqrt(kn);
         n_s = kn < 4.0 * (ISM_ENV_MAX_NODES - 12) ? max(16, (int)ceil(kn / 4.0) + 12) : ISM_ENV_MAX_NODES;
     }
+    if ((int)threadIdx.x <= ISM_ENV_MAX_NODES) inv_m[threadIdx.x] = threadIdx.x ? 1.0 / (double)threadIdx.x : 0.0;
     __syncthreads();
     const int n = n_s;
     // Gauss-Legendre nodes and weights on [-1, 1]: Newton on P_n from the asymptotic guess
     if ((int)threadIdx.x < n) {
         const int i = threadIdx.x;
+        // (from a guess within ~1e-3 of the root, Newton doubles the correct digits: 5 steps)
         double x = cos(PI * (i + 0.75) / (n + 0.5));
         double dp = 1.0;
-        for (int it = 0; it < 100; ++it) {
+        for (int it = 0; it < 5; ++it) {
             double p0 = 1.0, p1 = x;
             for (int m = 2; m <= n; ++m) {
-                const double p2 = ((2.0 * m - 1.0) * x * p1 - (m - 1.0) * p0) / m;
+                const double p2 = ((2.0 * m - 1.0) * x * p1 - (m - 1.0) * p0) * inv_m[m];
                 p0 = p1;
                 p1 = p2;
             }
             dp = n * (x * p1 - p0) / (x * x - 1.0);
-            const double dx = p1 / dp;
-            x -= dx;
-            if (fabs(dx) < 1e-16) break;
+            x -= p1 / dp;
         }
         {   // derivative at the converged root
             double p0 = 1.0, p1 = x;
             for (int m = 2; m <= n; ++m) {
-                const double p2 = ((2.0 * m - 1.0) * x * p1 - (m - 1.0) * p0) / m;
+                const double p2 = ((2.0 * m - 1.0) * x * p1 - (m - 1.0) * p0) * inv_m[m];
                 p0 = p1;
                 p1 = p2;
             }
@@ -222,37 +223,76 @@ __global__ void __launch_bounds__(ISM_ENV_CHUNK) envelope_kernel(const __grid_co
         cth[i] = cos(ang);
     }
     __syncthreads();
-    // nodes (theta_i, phi_j): u = (sin t cos p, sin t sin p, cos t), weight (pi/4)^2 w_i w_j sin t (2 / pi)
+    // nodes (theta_i, phi_j): u = (sin t cos p, sin t sin p, cos t), weight (pi/4)^2 w_i w_j sin t (2 / pi);
+    // E(t0) by the CTA's threads over the nodes, then a fixed-order tree
     const int nn = n * n;
+    float s = 0.0f, comp = 0.0f;
     for (int e = threadIdx.x; e < nn; e += blockDim.x) {
         const int i = e / n, j = e - (e / n) * n;
         const double gr = sth[i] * cth[j] * gam[0] + sth[i] * sth[j] * gam[1] + cth[i] * gam[2];
         const float hi = (float)gr;
-        gn[e] = make_float2(hi, gr < 1.0e29 ? (float)(gr - (double)hi) : 0.0f);
-        wn[e] = (float)(wg[i] * wg[j] * sth[i] * (PI / 8.0));
+        const float lo = gr < 1.0e29 ? (float)(gr - (double)hi) : 0.0f;
+        const float w = (float)(wg[i] * wg[j] * sth[i] * (PI / 8.0));
+        slot[e] = make_float4(hi, lo, w, 0.0f);
+        const float y = __fsub_rn(__fmul_rn(w, ism_exp2_neg(ff{hi, lo}, J.n_ism)), comp);
+        const float tt = __fadd_rn(s, y);
+        comp = __fsub_rn(__fsub_rn(tt, s), y);
+        s = tt;
     }
+    part[threadIdx.x] = (double)s;
     __syncthreads();
-    // E(t0): the CTA's threads split the nodes, then a fixed-order tree
-    {
-        float s = 0.0f, comp = 0.0f;
-        for (int e = threadIdx.x; e < nn; e += blockDim.x) {
-            const float y = __fsub_rn(__fmul_rn(wn[e], ism_exp2_neg(ff{gn[e].x, gn[e].y}, J.n_ism)), comp);
+    for (int w = 128; w > 0; w >>= 1) {   // the partial sums in FP64, a fixed-order tree
+        if ((int)threadIdx.x < w) part[threadIdx.x] += part[threadIdx.x + w];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        const double E0 = part[0];
+        const unsigned long long b = (unsigned long long)__double_as_longlong(E0);
+        slot[ISM_ENV_SLOT - 1] = make_float4(__int_as_float(n), 0.0f, __uint_as_float((unsigned)b),
+                                             __uint_as_float((unsigned)(b >> 32)));
+    }
+}
+
+__global__ void __launch_bounds__(4 * ISM_ENV_CHUNK) envelope_kernel(const __grid_constant__ JobTable t,
+                                                                 const float4* __restrict__ nodes,
+                                                                 float* __restrict__ env)
+{
+    extern __shared__ __align__(16) unsigned char smem[];
+    const long long g = blockIdx.x;
+    const int jid = ism_find_job(t, g, [](const JobDev& j) { return (long long)j.env_cta_base; });
+    const JobDev& J = t.j[jid];
+    const int chunk = (int)(g - J.env_cta_base);
+    const float4* slot = nodes + (long long)J.env_slot * ISM_ENV_SLOT;
+    float4* nd = reinterpret_cast<float4*>(smem);   // [n * n] {g hi, g lo, w, 0}
+    __shared__ float part[4][ISM_ENV_CHUNK];
+    const float4 head = slot[ISM_ENV_SLOT - 1];
+    const int n = __float_as_int(head.x);
+    const double E0 = __longlong_as_double((long long)(((unsigned long long)__float_as_uint(head.w) << 32) |
+                                                       __float_as_uint(head.z)));
+    const int nn = n * n;
+    for (int e = threadIdx.x; e < nn; e += blockDim.x) nd[e] = slot[e];
+    __syncthreads();
+    // sample ks of the chunk, quarter qp of the nodes (i = qp, qp + 4, ...)
+    const int ks = (int)threadIdx.x % ISM_ENV_CHUNK, qp = (int)threadIdx.x / ISM_ENV_CHUNK;
+    const int k = J.env_k0 + chunk * ISM_ENV_CHUNK + ks;
+    float s = 0.0f, comp = 0.0f;
+    if (k < J.n_S && E0 > 0.0) {
+        for (int i = qp; i < nn; i += 4) {
+            const float4 q = nd[i];
+            const float y = __fsub_rn(__fmul_rn(q.z, ism_exp2_neg(ff{q.x, q.y}, k)), comp);
             const float tt = __fadd_rn(s, y);
             comp = __fsub_rn(__fsub_rn(tt, s), y);
             s = tt;
         }
-        part[threadIdx.x] = s;
-        __syncthreads();
-        for (int w = ISM_ENV_CHUNK / 2; w > 0; w >>= 1) {
-            if ((int)threadIdx.x < w) part[threadIdx.x] = __fadd_rn(part[threadIdx.x], part[threadIdx.x + w]);
-            __syncthreads();
-        }
     }
-    const float E0 = part[0];
-    const int k = J.env_k0 + chunk * ISM_ENV_CHUNK + (int)threadIdx.x;
-    if (k >= J.n_S) return;
+    part[qp][ks] = s;
+    __syncthreads();
+    if (qp != 0 || k >= J.n_S) return;
     float v = 0.0f;
-    if (E0 > 0.0f) v = sqrtf(__fdiv_rn(env_sum(gn, wn, nn, k), E0));
+    if (E0 > 0.0) {
+        const double E = (((double)part[0][ks] + part[1][ks]) + part[2][ks]) + part[3][ks];
+        v = (float)sqrt(E / E0);
+    }
     env[J.env_base + (k - J.env_k0)] = v;
 }
 
@@ -288,12 +328,15 @@ int ism_launch_tail(const JobTable& t, const WsPlan& p, char* ws, void* stream)
 int ism_launch_envelope(const JobTable& t, const WsPlan& p, char* ws, void* stream)
 {
     if (p.env_ctas <= 0) return 0;
-    const size_t sm = (size_t)ISM_ENV_MAX_NODES * ISM_ENV_MAX_NODES * (sizeof(float2) + sizeof(float));
-    static std::atomic<unsigned long long> opened{0};
-    int rc = ism_open_smem((const void*)envelope_kernel, &opened);
+    float4* nodes = reinterpret_cast<float4*>(ws + p.env_nodes_off);
+    envelope_nodes_kernel<<<(unsigned)t.n_jobs, 256, 0, (cudaStream_t)stream>>>(t, nodes);
+    int rc = (int)cudaGetLastError();
     if (rc) return rc;
-    envelope_kernel<<<(unsigned)p.env_ctas, ISM_ENV_CHUNK, sm, (cudaStream_t)stream>>>(
-        t, reinterpret_cast<float*>(ws + p.env_off));
+    const size_t sm = (size_t)ISM_ENV_MAX_NODES * ISM_ENV_MAX_NODES * sizeof(float4);
+    static std::atomic<unsigned long long> opened{0};
+    if ((rc = ism_open_smem((const void*)envelope_kernel, &opened))) return rc;
+    envelope_kernel<<<(unsigned)p.env_ctas, 4 * ISM_ENV_CHUNK, sm, (cudaStream_t)stream>>>(
+        t, nodes, reinterpret_cast<float*>(ws + p.env_off));
     return (int)cudaGetLastError();
 }
 
