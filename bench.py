@@ -985,7 +985,9 @@ def main():
         "roofline": {"bound": "alu",
                      "kernel": ("shell_kernel (fused enumeration, exact delays, Chebyshev moments)"
                                 if args.prec == "fp32" and args.workload == "batched"
-                                else f"accum_kernel<1,false,{PREC_ID[args.prec]}>"),
+                                else ("shell_direct_kernel (fused enumeration, every tap evaluated)"
+                                      if args.prec in ("fp32", "fp32_direct")
+                                      else f"accum_kernel<1,false,{PREC_ID[args.prec]}> over binned ids")),
                      "achieved": achieved_tops,
                      "peak": peak_tops, "unit": "Tops/s (FP32 FMA-pipe lane ops)",
                      "frac": achieved_tops / peak_tops,
