@@ -17,8 +17,13 @@ accumulation kernel (the image enumeration and delays are FP32 in all).
 Prints one JSON line (rank 0).  `value` is RIRs/s of the whole job; the line
 also carries image-contributions/s, the live roofline of the accumulation
 kernel, an end-to-end number through the host-buffer C entry point, the
-oracle timed on the host cores (cpu_baseline) and the SM clocks sampled
-during the timed region.
+oracle timed on the host cores and on one core (cpu_baseline) and the SM
+clocks sampled during the timed region and 1.5 s of untimed repeats after it.
+On one GPU the default workload's line adds `extras`, measured in the same
+run: every tap arithmetic against the FP32 path on this workload and on the
+48 kHz array (with the Sabine and the Lehmann-Johansson tail), the serving
+stream's p50/p99 latency at 0.5x and 0.8x load, the single-RIR latency, the
+moving-source filtering (FFT and direct forms) and the training step.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
                     [--workload batched|trajectory] [--prec fp32|fp16x2|bf16x2|lut|lut_tex|fp32_direct]
@@ -570,7 +575,7 @@ def run_serving(args):
     print(json.dumps(line), flush=True)
 
 
-def run_differentiation(args, world, rank, dist):
+def run_differentiation(args, world, rank, dist, quiet=False):
     """One training step per timed step: 256 rooms (sides U(4, 8) m, T60
     U(0.3, 0.8) s, 1 source + 1 receiver, 16 kHz, 0.4 s) forward through the
     autograd front end, L2 loss against fixed targets (the RIRs of the rooms
@@ -689,11 +694,13 @@ def run_differentiation(args, world, rank, dist):
                   "L2 flushed before each (eager_ms_per_step: the same steps launched one by one)",
         "loss": loss_h,
     }
+    if quiet:
+        return line
     if rank == 0:
         print(json.dumps(line), flush=True)
 
 
-def run_moving_source(args, world, rank, dist):
+def run_moving_source(args, world, rank, dist, quiet=False):
     """One step renders a moving source recorded by the 8-microphone array
     (Section 4): the 512 RIRs of the 48 kHz trajectory workload (64 points x 8
     microphones, image sources to 0.3 s, Philox tail to 1.2 s), then a 1.2 s
@@ -797,6 +804,8 @@ def run_moving_source(args, world, rank, dist):
                             "peak": peak_tops, "unit": "T multiply-adds/s (FP32 FMA pipe)",
                             "frac": macs / (direct_ms * 1e-3) / 1e12 / peak_tops, "useful_macs_per_step": macs},
     }
+    if quiet:
+        return line
     if rank == 0:
         print(json.dumps(line), flush=True)
 
@@ -1045,6 +1054,18 @@ def main():
                                         "batches": st["batches"], "inflight_peak": st["inflight_peak"]},
                              "latency": "arrival to RIRs in the caller's page-locked host buffer",
                              "entry": "ism_server_submit_batch / ism_server_wait"}
+        sub = argparse.Namespace(steps=10, warmup=3)
+        ms_line = run_moving_source(sub, 1, 0, None, quiet=True)
+        extras["moving_source_48k_array"] = {
+            k: ms_line[k] for k in ("value", "unit", "ms_per_step", "config", "seconds_of_audio_per_sec",
+                                    "auralize_ms_per_step", "auralize_method", "direct_form_ms",
+                                    "fft_speedup_vs_direct", "fft_vs_direct_max_err_rel_peak", "roofline",
+                                    "direct_roofline")}
+        df_line = run_differentiation(sub, 1, 0, None, quiet=True)
+        extras["differentiation_256rooms"] = {
+            k: df_line[k] for k in ("value", "unit", "ms_per_step", "config", "training_steps_per_sec",
+                                    "eager_ms_per_step", "library_device_ms_per_step", "stage_ms_per_step", "e2e",
+                                    "timing")}
         extras["seconds"] = time.perf_counter() - t_x
         line["extras"] = extras
         line["p50_ms"] = res["poisson_0.8x"]["p50_ms"]
