@@ -35,7 +35,7 @@
 namespace {
 
 #define AF_T 256        // threads of the column passes
-#define AF_T2 128       // threads of the row pass
+#define AF_T2 256       // threads of the row pass
 #define AF_COL_E 8192   // complex values per CTA of the column passes (64 KB)
 #define AF_MAXPG 4      // microphone pairs per row-pass CTA (at most)
 #define AF_ROW_E 2048   // complex values transformed at once by a row-pass CTA (4 radix-4 items per thread)
@@ -272,7 +272,7 @@ __global__ void __launch_bounds__(AF_T) af_cols_kernel(AfPlan pl, int p0, const 
 // row DFTs (over k1 -> n1) and the twiddle W_N^(-n1 k2) -> B[pair][k2][n1]
 // (stored as Y).  Every sum has a fixed order that does not depend on the
 // chunk size.
-__global__ void __launch_bounds__(AF_T2, 4) af_rows_kernel(AfPlan pl, int p0, int n_pts, int first,
+__global__ void __launch_bounds__(AF_T2, 3) af_rows_kernel(AfPlan pl, int p0, int n_pts, int first,
                                                            const float2* __restrict__ A, float2* __restrict__ Yg)
 {
     extern __shared__ __align__(16) unsigned char smem[];
