@@ -69,10 +69,14 @@ __device__ __forceinline__ unsigned long long sd_mul2(unsigned long long a, unsi
 #define SD_WARPS 8                   // warps per CTA
 #define SD_WIN (32 * SD_B + 32)      // samples of the shell's window (taps of b in [32 q0 - 1, 32 (q0 + SD_B) - 1))
 
+template <int PREC>
 __global__ void __launch_bounds__(SD_WARPS * 32, 4) shell_direct_kernel(const __grid_constant__ JobTable t,
                                                                         const float4* __restrict__ tbl,
+                                                                        const float* __restrict__ lut_g,
                                                                         float* __restrict__ rows)
 {
+    constexpr bool HALF = PREC == PREC_FP16 || PREC == PREC_BF16;
+    constexpr int LQ = ism_lut_phases(1);   // table phases per sample (LUT forms)
     constexpr int WIN = 64;   // window row of a bin: 32 (SLOTS + 1), SLOTS = 1
     extern __shared__ __align__(16) unsigned char smem[];
     // CTA -> (job, RIR, shell): job by job, RIR by RIR, outermost (densest) shell first
@@ -130,6 +134,18 @@ __global__ void __launch_bounds__(SD_WARPS * 32, 4) shell_direct_kernel(const __
     const unsigned long long xj2 = sd_pack(xj, xj), nsg2 = sd_pack(nsg, nsg), Cj2 = sd_pack(Cj, Cj),
                              Sj2 = sd_pack(Sj, Sj);
     const float twopi_Nw = 6.283185307179586f / 32.0f, inv2Nw = 2.0f / 32.0f;
+    uint32_t C2 = 0, S2 = 0;
+    if constexpr (HALF) {
+        C2 = pack2<PREC>(Cj, Cj);
+        S2 = pack2<PREC>(Sj, Sj);
+    }
+    // FP16 records are scaled by 2^e (undone, exactly, on each product); f is kept away
+    // from 0 and 1 in the packed forms so that the packed reciprocal stays finite
+    const float rscale = (PREC == PREC_FP16) ? J.half_scale : 1.0f;
+    const float dscale = (PREC == PREC_FP16) ? 1.0f / J.half_scale : 1.0f;
+    const float f_lo = HALF ? 0x1p-13f : 0x1p-60f;
+    const float f_hi = HALF ? 1.0f - 0x1p-13f : 1.0f;
+    const float* lut = PREC == PREC_LUT ? lut_g + J.lut_base + lane : nullptr;
 
     const int W0 = ISM_SB * q0 - 16;   // first sample of the shell's window
     const Shell sh = shell_setup(J, T, r, ISM_SB * q0 - 1, min(ISM_SB * (q0 + nb) - 1, J.n_ism + J.H - 1));
@@ -155,8 +171,22 @@ __global__ void __launch_bounds__(SD_WARPS * 32, 4) shell_direct_kernel(const __
             float amp = cf.z * tz.z * amp_scale * rs;
             if (alpha != 1.0f)   // polar pattern: cos(theta) = o . (x_n - x_r) / d
                 amp *= __fmaf_rn(1.0f - alpha, __fmaf_rn(orient.z, tz.w, cf.w) * rs, alpha);
-            f = fmaxf(f, 0x1p-60f);   // keeps j - f away from 0 (the reciprocal of the tap j = 0)
-            const float4 rc = ism_sinc_record(f, amp, true, twopi_Nw, inv2Nw);
+            f = fminf(fmaxf(f, f_lo), f_hi);   // keeps j - f away from 0 (the reciprocal of the tap j = 0)
+            float4 rc;
+            if constexpr (PREC == PREC_LUT) {
+                // eq. (9): rows floor(f Q) and + 1 of the polyphase table, weights A (1 - phi), A phi
+                const float u = f * (float)LQ;   // exact: LQ is a power of two
+                const float pf = floorf(u);
+                const float ph = u - pf;         // exact
+                rc = make_float4(amp - amp * ph, amp * ph, __int_as_float(ism_int_of_integral(pf) * 32), 0.0f);
+            } else if constexpr (PREC == PREC_TEX) {
+                rc = make_float4(amp, __fmaf_rn(f, (float)LQ, 0.5f), 0.0f, 0.0f);   // texel row f Q, centred
+            } else {
+                rc = ism_sinc_record(f, amp, true, twopi_Nw, inv2Nw);
+                rc.y *= rscale;
+                rc.z *= rscale;
+                rc.w *= rscale;
+            }
             sl[0] = rc.x;
             sl[2] = rc.y;
             sl[4] = rc.z;
@@ -175,12 +205,45 @@ __global__ void __launch_bounds__(SD_WARPS * 32, 4) shell_direct_kernel(const __
                 const ulonglong2 fa = st2[2 * k];       // {f_a, f_b}, {P_a, P_b}
                 const ulonglong2 fb = st2[2 * k + 1];   // {Pc_a, Pc_b}, {Ps_a, Ps_b}
                 const int2 pp = sp2[k];
-                const unsigned long long x2 = sd_fma2(nsg2, fa.x, xj2);
-                const unsigned long long w2 = sd_fma2(Cj2, fb.x, sd_fma2(Sj2, fb.y, fa.y));
-                float xa, xb;
-                sd_unpack(x2, xa, xb);
                 float va, vb;
-                sd_unpack(sd_mul2(w2, sd_pack(ism_rcp(xa), ism_rcp(xb))), va, vb);
+                if constexpr (PREC == PREC_FP32) {
+                    const unsigned long long x2 = sd_fma2(nsg2, fa.x, xj2);
+                    const unsigned long long w2 = sd_fma2(Cj2, fb.x, sd_fma2(Sj2, fb.y, fa.y));
+                    float xa, xb;
+                    sd_unpack(x2, xa, xb);
+                    sd_unpack(sd_mul2(w2, sd_pack(ism_rcp(xa), ism_rcp(xb))), va, vb);
+                } else if constexpr (HALF) {
+                    // x in FP32, then the window and the reciprocal in packed 16-bit arithmetic;
+                    // the products of two 16-bit values are exact in FP32
+                    float xa, xb, Pa, Pb, Pca, Pcb, Psa, Psb;
+                    sd_unpack(sd_fma2(nsg2, fa.x, xj2), xa, xb);
+                    sd_unpack(fa.y, Pa, Pb);
+                    sd_unpack(fb.x, Pca, Pcb);
+                    sd_unpack(fb.y, Psa, Psb);
+                    const uint32_t w = fma2<PREC>(C2, pack2<PREC>(Pca, Pcb), fma2<PREC>(S2, pack2<PREC>(Psa, Psb),
+                                                                                       pack2<PREC>(Pa, Pb)));
+                    va = 0.0f;
+                    vb = 0.0f;
+                    mixed_fma2<PREC>(va, vb, w, rcp2<PREC>(pack2<PREC>(xa, xb)));
+                    va *= dscale;
+                    vb *= dscale;
+                } else if constexpr (PREC == PREC_LUT) {
+                    float w0a, w0b, w1a, w1b, ra, rb;
+                    sd_unpack(fa.x, w0a, w0b);
+                    sd_unpack(fa.y, w1a, w1b);
+                    sd_unpack(fb.x, ra, rb);
+                    const float* pa = lut + __float_as_int(ra);
+                    const float* pb = lut + __float_as_int(rb);
+                    va = __fmaf_rn(w1a, __ldg(pa + 32), w0a * __ldg(pa));
+                    vb = __fmaf_rn(w1b, __ldg(pb + 32), w0b * __ldg(pb));
+                } else {   // PREC_TEX: one filtered fetch per tap
+                    float Aa, Ab, ya, yb;
+                    sd_unpack(fa.x, Aa, Ab);
+                    sd_unpack(fa.y, ya, yb);
+                    const cudaTextureObject_t tex = (cudaTextureObject_t)J.lut_tex;
+                    va = Aa * tex2D<float>(tex, (float)lane + 0.5f, ya);
+                    vb = Ab * tex2D<float>(tex, (float)lane + 0.5f, yb);
+                }
                 if (pp.x >= 0) win[pp.x + lane] += va;
                 if (pp.y >= 0) win[pp.y + lane] += vb;
             }
@@ -224,19 +287,38 @@ size_t shell_direct_smem(const JobTable& t)
 
 }  // namespace
 
-int ism_launch_accum_shell_direct(const JobTable& t, const WsPlan& p, char* ws, void* stream, int* launched)
+template <int PREC>
+static int launch_sd(const JobTable& t, const WsPlan& p, char* ws, cudaStream_t s)
+{
+    const size_t sm = shell_direct_smem(t);
+    static std::atomic<unsigned long long> opened{0};
+    int rc = ism_open_smem((const void*)shell_direct_kernel<PREC>, &opened);
+    if (rc) return rc;
+    cudaError_t e = cudaFuncSetAttribute(shell_direct_kernel<PREC>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                         cudaSharedmemCarveoutMaxShared);
+    if (e != cudaSuccess) return (int)e;
+    shell_direct_kernel<PREC><<<(unsigned)p.sd_ctas, SD_WARPS * 32, sm, s>>>(
+        t, reinterpret_cast<const float4*>(ws + p.tbl_off), reinterpret_cast<const float*>(ws + p.lut_off),
+        reinterpret_cast<float*>(ws + p.rows_off));
+    return (int)cudaGetLastError();
+}
+
+int ism_launch_accum_shell_direct(const JobTable& t, const WsPlan& p, char* ws, ism_precision prec, void* stream,
+                                  int* launched)
 {
     *launched = 0;
     if (p.sd_ctas <= 0) return 0;
-    const size_t sm = shell_direct_smem(t);
-    static std::atomic<unsigned long long> opened{0};
-    int rc = ism_open_smem((const void*)shell_direct_kernel, &opened);
-    if (rc) return rc;
-    cudaError_t e = cudaFuncSetAttribute(shell_direct_kernel, cudaFuncAttributePreferredSharedMemoryCarveout,
-                                         cudaSharedmemCarveoutMaxShared);
-    if (e != cudaSuccess) return (int)e;
-    shell_direct_kernel<<<(unsigned)p.sd_ctas, SD_WARPS * 32, sm, (cudaStream_t)stream>>>(
-        t, reinterpret_cast<const float4*>(ws + p.tbl_off), reinterpret_cast<float*>(ws + p.rows_off));
-    *launched = 1;
-    return (int)cudaGetLastError();
+    cudaStream_t s = (cudaStream_t)stream;
+    int rc;
+    switch (prec) {
+    case ISM_PREC_FP32:
+    case ISM_PREC_FP32_DIRECT: rc = launch_sd<PREC_FP32>(t, p, ws, s); break;
+    case ISM_PREC_FP16X2: rc = launch_sd<PREC_FP16>(t, p, ws, s); break;
+    case ISM_PREC_BF16X2: rc = launch_sd<PREC_BF16>(t, p, ws, s); break;
+    case ISM_PREC_LUT: rc = launch_sd<PREC_LUT>(t, p, ws, s); break;
+    case ISM_PREC_LUT_TEX: rc = launch_sd<PREC_TEX>(t, p, ws, s); break;
+    default: return (int)cudaErrorInvalidValue;
+    }
+    *launched = rc ? 0 : 1;
+    return rc;
 }

@@ -283,11 +283,11 @@ ism_status plan(const Validated* vs, int n, ism_precision prec, bool backward, J
             // backward: a 32-tap window always takes the fused Chebyshev adjoint (an
             // image costs two degree-8 sums there, against 32 tap derivatives)
             J.adj_cheb = (backward && v.Nw == 32.0 && v.H == 16 && v.slots == 1) ? 1 : 0;
-            // the other FP32 forward jobs with a 32-tap window: every tap evaluated, the
-            // images enumerated by the CTA that accumulates them (no ids, no sort)
-            // (the value is the shell's thickness in bins: 32 for sparse bins, 8 for dense ones)
-            J.shell_direct = (!backward && !J.use_cheb && (prec == ISM_PREC_FP32 || prec == ISM_PREC_FP32_DIRECT) &&
-                              v.Nw == 32.0 && v.H == 16 && v.slots == 1) ? (per_bin < 64.0 ? ISM_SD_BINS : 8) : 0;
+            // the other forward jobs with a 32-tap window, in every tap arithmetic: every tap
+            // evaluated, the images enumerated by the CTA that accumulates them (no ids, no
+            // sort); the value is the shell's thickness in bins: 32 for sparse bins, 8 for dense ones
+            J.shell_direct = (!backward && !J.use_cheb && v.Nw == 32.0 && v.H == 16 && v.slots == 1)
+                                 ? (per_bin < 64.0 ? ISM_SD_BINS : 8) : 0;
         }
         const bool cheb = J.use_cheb || J.adj_cheb;
         const bool fused = cheb || J.shell_direct;

@@ -226,7 +226,8 @@ int ism_launch_accum_lut(const JobTable& t, const WsPlan& p, char* ws, void* str
 int ism_launch_accum_tex(const JobTable& t, const WsPlan& p, char* ws, void* stream, int* launched);
 int ism_launch_lut_tables(const JobTable& t, const WsPlan& p, char* ws, void* stream);
 int ism_launch_accum_cheb(const JobTable& t, const WsPlan& p, char* ws, void* stream, int* launched);
-int ism_launch_accum_shell_direct(const JobTable& t, const WsPlan& p, char* ws, void* stream, int* launched);
+int ism_launch_accum_shell_direct(const JobTable& t, const WsPlan& p, char* ws, ism_precision prec, void* stream,
+                                  int* launched);
 int ism_launch_adjoint(const JobTable& t, const WsPlan& p, char* ws, void* stream, int* launched);
 int ism_launch_adjoint_cheb(const JobTable& t, const WsPlan& p, char* ws, void* stream, int* launched);
 int ism_launch_finalize(const JobTable& t, const WsPlan& p, char* ws, void* stream);
