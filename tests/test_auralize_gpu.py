@@ -216,3 +216,32 @@ def test_fft_trajectory_workload_moving_source():
     diff = np.max(np.abs(y.astype(np.float64) - yd)) / scale
     print(f"FFT vs direct form over all outputs: {diff:.3e} of the largest magnitude sum")
     assert diff <= 1e-5
+
+
+@pytest.mark.parametrize("n_x,n_s,n_mics", [(150000, 150001, 8), (400000, 300000, 3)])
+def test_fft_long_signals_sampled_against_the_definition(n_x, n_s, n_mics):
+    """DFT lengths 2^19 (columns of 1024, rows of 512: three microphone pairs per
+    row-pass CTA, so 4 pairs take two groups) and 2^20 (rows of 1024: one pair per
+    CTA), three trajectory points: outputs sampled over the whole length against
+    the definition (scaled by the largest magnitude sum among them), and every
+    output against the direct form."""
+    rng = np.random.default_rng(n_x)
+    x = rng.normal(size=n_x).astype(np.float32)
+    h = (rng.normal(size=(3, n_mics, n_s)) * np.exp(-np.arange(n_s) / (n_s / 4.0))).astype(np.float32)
+    y = run(x, h, method="fft")
+    x64, h64 = x.astype(np.float64), h.astype(np.float64)
+    starts = oracle.segment_starts(n_x, 3)
+    seg = np.searchsorted(starts, np.arange(n_x), side="right") - 1
+    n_out = n_x + n_s - 1
+    errs, mags = [], []
+    for t in rng.integers(0, n_out, 12).tolist() + [0, n_out - 1, n_x - 1]:
+        m = t % n_mics
+        s = np.arange(max(0, t - n_s + 1), min(t, n_x - 1) + 1)
+        terms = x64[s] * h64[seg[s], m, t - s]
+        errs.append(abs(float(y[m, t]) - terms.sum()))
+        mags.append(np.abs(terms).sum())
+    scale = max(mags)
+    print(f"FFT n_out={n_out}: max|err| / max sum|terms| = {max(errs) / scale:.3e}")
+    assert max(errs) <= 1e-5 * scale
+    d = run(x, h, method="direct")
+    assert np.max(np.abs(y.astype(np.float64) - d)) <= 1e-5 * scale

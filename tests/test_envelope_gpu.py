@@ -143,3 +143,24 @@ def test_lj_tail_through_the_server_equals_the_direct_call():
         t, out = srv.submit(L, beta, ps, pr, N, 0.7, 16000.0, Tdiff=0.2, Tw=Tw, seed=9, envelope="lj")
         srv.wait(t)
     assert np.array_equal(out.view(np.uint32), ref.view(np.uint32))
+
+
+def test_lj_tail_with_coefficients_in_device_memory_is_bitwise_the_host_form():
+    """beta read in place from device memory (ism_job.beta_dev): the envelope's
+    quadrature is built on the device from those values, bitwise as from room.beta."""
+    L = np.array([5.3, 4.1, 2.9])
+    beta = np.array([0.9, 0.82, 0.88, 0.75, 0.93, 0.7], np.float32)
+    ps = torch.as_tensor(np.array([[1.2, 1.9, 1.1]], np.float32)).cuda()
+    pr = torch.as_tensor(np.array([[3.7, 2.6, 1.8], [0.9, 3.1, 2.2]], np.float32)).cuda()
+    Tw = 32 / 16000
+    N = oracle.nb_img_from_t(0.08, L, 343.0, Tw)
+    n_S = ism.ism_rir_length(0.5, 16000.0)
+    outs = []
+    for b in (beta, torch.as_tensor(beta).cuda()):
+        out = torch.empty((1, 2, n_S), device="cuda")
+        job = ism.make_job(L, b, ps, pr, N, 0.5, 16000.0, out, Tdiff=0.08, Tw=Tw, seed=5, envelope="lj")
+        ism.ism_simulate_batch([job])
+        torch.cuda.synchronize()
+        outs.append(out.cpu().numpy())
+    assert np.max(np.abs(outs[0])) > 0
+    assert np.array_equal(outs[0].view(np.uint32), outs[1].view(np.uint32))
