@@ -68,6 +68,7 @@ __device__ __forceinline__ unsigned long long sd_mul2(unsigned long long a, unsi
 #define SD_B ISM_SD_BINS             // delay bins per CTA, at most
 #define SD_WARPS 8                   // warps per CTA
 #define SD_WIN (32 * SD_B + 32)      // samples of the shell's window (taps of b in [32 q0 - 1, 32 (q0 + SD_B) - 1))
+#define SD_WINP (SD_WIN + 32)        // per warp: the window, then 32 samples where lanes without an image add 0
 
 template <int PREC>
 __global__ void __launch_bounds__(SD_WARPS * 32, 4) shell_direct_kernel(const __grid_constant__ JobTable t,
@@ -101,17 +102,17 @@ __global__ void __launch_bounds__(SD_WARPS * 32, 4) shell_direct_kernel(const __
     float4* recf = reinterpret_cast<float4*>(rowy0 + ((t.max_axis_sum + 4) & ~3));
     int4* reci = reinterpret_cast<int4*>(recf + SD_WARPS * 32);
     int* st = reinterpret_cast<int*>(reci + SD_WARPS * 32);            // [warps][33]
-    float* win_all = reinterpret_cast<float*>(st + SD_WARPS * 33);     // [warps][SD_WIN]
-    float4* stage_all = reinterpret_cast<float4*>(win_all + SD_WARPS * SD_WIN);   // [warps][32] (lane pairs interleaved)
+    float* win_all = reinterpret_cast<float*>(st + SD_WARPS * 33);     // [warps][SD_WINP]
+    float4* stage_all = reinterpret_cast<float4*>(win_all + SD_WARPS * SD_WINP);  // [warps][32] (lane pairs interleaved)
     int* spos_all = reinterpret_cast<int*>(stage_all + SD_WARPS * 32);            // [warps][32]
     int* wtot = spos_all + SD_WARPS * 32;                                          // [warps]
-    float* win = win_all + warp * SD_WIN;
+    float* winl = win_all + warp * SD_WINP + lane;   // lane's column of the warp's window
     float4* stage = stage_all + warp * 32;
     int* spos = spos_all + warp * 32;
 
     const float4* Tg = tbl + J.tbl_base + (long long)r * n_axis;
     for (int e = threadIdx.x; e < n_axis; e += blockDim.x) T[e] = Tg[e];
-    for (int e = threadIdx.x; e < SD_WARPS * SD_WIN; e += blockDim.x) win_all[e] = 0.0f;
+    for (int e = threadIdx.x; e < SD_WARPS * SD_WINP; e += blockDim.x) win_all[e] = 0.0f;
     __syncthreads();
 
     // receiver polar pattern: the unit orientation of this RIR's receiver
@@ -159,7 +160,7 @@ __global__ void __launch_bounds__(SD_WARPS * 32, 4) shell_direct_kernel(const __
         sl[2] = 0.0f;
         sl[4] = 0.0f;
         sl[6] = 0.0f;
-        spos[lane] = -1;
+        spos[lane] = SD_WIN;   // no image: the record adds 0 beyond the window
     };
     clear();
     __syncwarp();
@@ -195,7 +196,7 @@ __global__ void __launch_bounds__(SD_WARPS * 32, 4) shell_direct_kernel(const __
         },
         [&]() {
             __syncwarp();
-            const unsigned v = __ballot_sync(0xffffffffu, spos[lane] >= 0);
+            const unsigned v = __ballot_sync(0xffffffffu, spos[lane] < SD_WIN);
             unsigned m = (v | (v >> 1)) & 0x55555555u;   // lane pairs holding an image
             const ulonglong2* st2 = reinterpret_cast<const ulonglong2*>(stage);
             const int2* sp2 = reinterpret_cast<const int2*>(spos);
@@ -244,8 +245,8 @@ __global__ void __launch_bounds__(SD_WARPS * 32, 4) shell_direct_kernel(const __
                     va = Aa * tex2D<float>(tex, (float)lane + 0.5f, ya);
                     vb = Ab * tex2D<float>(tex, (float)lane + 0.5f, yb);
                 }
-                if (pp.x >= 0) win[pp.x + lane] += va;
-                if (pp.y >= 0) win[pp.y + lane] += vb;
+                winl[pp.x] += va;
+                winl[pp.y] += vb;
             }
             __syncwarp();
             clear();
@@ -261,7 +262,7 @@ __global__ void __launch_bounds__(SD_WARPS * 32, 4) shell_direct_kernel(const __
             const int p = 32 * ql + lane;   // lower half: samples 32 q - 16 + lane
             float v = win_all[p];
 #pragma unroll
-            for (int w = 1; w < SD_WARPS; ++w) v += win_all[w * SD_WIN + p];
+            for (int w = 1; w < SD_WARPS; ++w) v += win_all[w * SD_WINP + p];
             row[lane] = v;
         }
         {
@@ -270,7 +271,7 @@ __global__ void __launch_bounds__(SD_WARPS * 32, 4) shell_direct_kernel(const __
                 const int p = 32 * nb + lane;
                 v = win_all[p];
 #pragma unroll
-                for (int w = 1; w < SD_WARPS; ++w) v += win_all[w * SD_WIN + p];
+                for (int w = 1; w < SD_WARPS; ++w) v += win_all[w * SD_WINP + p];
             }
             row[32 + lane] = v;
         }
@@ -281,7 +282,7 @@ size_t shell_direct_smem(const JobTable& t)
 {
     return (size_t)((t.max_axis_sum + 1) & ~1) * sizeof(float4) + 2 * (size_t)((t.max_axis_sum + 4) & ~3) * sizeof(int) +
            (size_t)SD_WARPS * 32 * (sizeof(float4) + sizeof(int4)) + (size_t)SD_WARPS * 33 * sizeof(int) +
-           (size_t)SD_WARPS * SD_WIN * sizeof(float) + (size_t)SD_WARPS * 32 * (sizeof(float4) + sizeof(int)) +
+           (size_t)SD_WARPS * SD_WINP * sizeof(float) + (size_t)SD_WARPS * 32 * (sizeof(float4) + sizeof(int)) +
            SD_WARPS * sizeof(int);
 }
 
