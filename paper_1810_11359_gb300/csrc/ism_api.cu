@@ -1109,11 +1109,14 @@ ism_status ism_simulate_host(const ism_room* room, const float* pos_src, int n_s
     vs[0].job.seed = seed;
     // a page-locked `out` is written by the kernels themselves (over the host link, as the
     // RIRs are finished); other host memory receives a copy of the device result
+    // (its address on the current device, where the kernels run: memory pinned in another
+    // device's context without the portable flag has none and takes the copy)
     cudaPointerAttributes attr{};
+    void* dp = nullptr;
     const bool direct = cudaPointerGetAttributes(&attr, out) == cudaSuccess && attr.type == cudaMemoryTypeHost &&
-                        attr.devicePointer != nullptr;
-    cudaGetLastError();   // a pageable pointer may leave an error behind on older drivers
-    if (direct) vs[0].job.out = static_cast<float*>(attr.devicePointer);
+                        cudaHostGetDevicePointer(&dp, static_cast<void*>(out), 0) == cudaSuccess && dp != nullptr;
+    cudaGetLastError();   // a pageable or foreign pointer leaves an error behind
+    if (direct) vs[0].job.out = static_cast<float*>(dp);
     const HostCopy hc{d_out, out};
     if ((s = run_batch(vs, prec, workspace, sim, stream, direct ? nullptr : &hc)) != ISM_OK) return s;
     if ((e = (int)cudaStreamSynchronize(st))) return cuda_fail(e, "stream synchronize");
