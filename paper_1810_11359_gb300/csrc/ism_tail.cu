@@ -195,10 +195,23 @@ __global__ void __launch_bounds__(256) envelope_nodes_kernel(const __grid_consta
     // Gauss-Legendre nodes and weights on [-1, 1]: Newton on P_n from the asymptotic guess
     if ((int)threadIdx.x < n) {
         const int i = threadIdx.x;
-        // (from a guess within ~1e-3 of the root, Newton doubles the correct digits: 5 steps)
-        double x = cos(PI * (i + 0.75) / (n + 0.5));
+        // Newton from a guess within ~1e-3 of the root: three steps in FP32 (to ~1e-7), then
+        // two in FP64 (each doubles the correct digits); the weight takes the derivative of
+        // the last step (its point differs from the root by ~1e-16)
+        float xf = cospif((i + 0.75f) / (n + 0.5f));
+        for (int it = 0; it < 3; ++it) {
+            float p0 = 1.0f, p1 = xf;
+            for (int m = 2; m <= n; ++m) {
+                const float p2 = ((2.0f * m - 1.0f) * xf * p1 - (m - 1.0f) * p0) * (float)inv_m[m];
+                p0 = p1;
+                p1 = p2;
+            }
+            const float dpf = n * (xf * p1 - p0) / (xf * xf - 1.0f);
+            xf -= p1 / dpf;
+        }
+        double x = (double)xf;
         double dp = 1.0;
-        for (int it = 0; it < 5; ++it) {
+        for (int it = 0; it < 2; ++it) {
             double p0 = 1.0, p1 = x;
             for (int m = 2; m <= n; ++m) {
                 const double p2 = ((2.0 * m - 1.0) * x * p1 - (m - 1.0) * p0) * inv_m[m];
@@ -207,15 +220,6 @@ __global__ void __launch_bounds__(256) envelope_nodes_kernel(const __grid_consta
             }
             dp = n * (x * p1 - p0) / (x * x - 1.0);
             x -= p1 / dp;
-        }
-        {   // derivative at the converged root
-            double p0 = 1.0, p1 = x;
-            for (int m = 2; m <= n; ++m) {
-                const double p2 = ((2.0 * m - 1.0) * x * p1 - (m - 1.0) * p0) * inv_m[m];
-                p0 = p1;
-                p1 = p2;
-            }
-            dp = n * (x * p1 - p0) / (x * x - 1.0);
         }
         wg[i] = 2.0 / ((1.0 - x * x) * dp * dp);
         const double ang = (x + 1.0) * (PI / 4.0);   // [-1, 1] -> [0, pi/2]
