@@ -36,9 +36,12 @@
 // integer with 2^e A_max <= min((1 - 2^-10) 2^22, 0.98 2^31 / n - 1), n first
 // four times the expected number of images per integer delay, 4 pi s^2 /
 // (k^3 V) (one image per room volume V), plus 64.  The sums are 32-bit
-// shared-memory atomic adds; integer addition is associative, so the sums --
-// and the FP32 result -- are the same in every run, whatever the order in which
-// lanes and warps add their terms.  The CTA also counts its images per (bin,
+// shared-memory atomic adds of the FFMA's raw bits K + v (K = 0x4B400000, the
+// bits of 1.5 2^23; v the term's integer); with n images at the integer delay
+// the sum of the v is the word minus n K, modulo 2^32, exact while it stays
+// below 2^31 in magnitude.  Integer addition is associative, so the sums --
+// and the FP32 result -- are the same in every run, whatever the order in
+// which lanes and warps add their terms.  The CTA also counts its images per (bin,
 // integer delay); if some count times the largest term could reach 2^31 a sum
 // may have wrapped, and the CTA redoes its shell with scales set from the exact
 // counts (which do not depend on the scales), so the second pass is safe.  The
@@ -47,7 +50,8 @@
 //
 // Finally each warp expands the non-empty offsets of one bin into the taps
 // (lane = tap) and rotates them into the bin's register window, which it
-// stores as the bin's row.
+// stores as the bin's row; the moments of an offset sit together (12 floats),
+// so a warp reads them in three broadcast loads.
 #include "ism_accum.cuh"
 #include "ism_shell.cuh"
 
@@ -58,6 +62,11 @@ namespace {
 #define SH_NO 32            // offsets per bin (rr = -1 .. 30)
 #define SH_RS 33            // row stride of the moment table (conflict-light atomics)
 #define CB_MAGIC 12582912.0f                       // 1.5 * 2^23
+static_assert(ISM_CHEB_N == 9, "the expansion reads the moments as 4 + 4 + 1");
+// the expansion's moment table [bin][offset][12] overlays the sums, the counts, the scales, the
+// row prefix and the column records (all dead by then), which always span more than it needs
+static_assert(SH_B * SH_NO * 12 * 4 <= (SH_B * ISM_CHEB_N * SH_RS + SH_B * SH_RS) * 4 + SH_WARPS * 32 * 32,
+              "moment table larger than the tables it overlays");
 #define CB_MAGIC_BITS 0x4B400000u                  // its bits
 
 // Largest power of two 2^e with 2^e a_max <= min((1 - 2^-10) 2^22, 0.98 2^31 / n - 1):
@@ -90,8 +99,8 @@ __global__ void __launch_bounds__(SH_WARPS * 32, 5) shell_kernel(const __grid_co
     // shared memory: axis tables | moment sums | image counts | per-bin scales | row prefix |
     // per-warp column records
     float4* T = reinterpret_cast<float4*>(smem);
-    int* S = reinterpret_cast<int*>(smem + (size_t)((t.max_axis_sum + 1) & ~1) * sizeof(float4));
-    int* Cn = S + SH_B * ISM_CHEB_N * SH_RS;                                      // [bin][offset] images
+    unsigned* S = reinterpret_cast<unsigned*>(smem + (size_t)((t.max_axis_sum + 1) & ~1) * sizeof(float4));
+    int* Cn = reinterpret_cast<int*>(S + SH_B * ISM_CHEB_N * SH_RS);             // [bin][offset] images
     float* scale_s = reinterpret_cast<float*>(Cn + SH_B * SH_RS);
     float* inv_s = scale_s + SH_B;
     float* amax_s = inv_s + SH_B;                                                 // per-bin amplitude bound
@@ -168,15 +177,15 @@ __global__ void __launch_bounds__(SH_WARPS * 32, 5) shell_kernel(const __grid_co
         const float as = amp * scale_s[ql];
         const float uu = __fmaf_rn(2.0f, f, -1.0f);
         const float u2 = uu + uu;
-        int* Sb = S + ql * (ISM_CHEB_N * SH_RS) + o;
+        unsigned* Sb = S + ql * (ISM_CHEB_N * SH_RS) + o;
         atomicAdd(Cn + ql * SH_RS + o, 1);
-        atomicAdd(Sb, (int)(__float_as_uint(__fadd_rn(as, CB_MAGIC)) - CB_MAGIC_BITS));
-        atomicAdd(Sb + SH_RS, (int)(__float_as_uint(__fmaf_rn(as, uu, CB_MAGIC)) - CB_MAGIC_BITS));
+        atomicAdd(Sb, __float_as_uint(__fadd_rn(as, CB_MAGIC)));   // K + v: the n K go at the expansion
+        atomicAdd(Sb + SH_RS, __float_as_uint(__fmaf_rn(as, uu, CB_MAGIC)));
         float tp = 1.0f, tc = uu;
 #pragma unroll
         for (int k = 2; k < ISM_CHEB_N; ++k) {
             const float tn = __fmaf_rn(u2, tc, -tp);
-            atomicAdd(Sb + k * SH_RS, (int)(__float_as_uint(__fmaf_rn(as, tn, CB_MAGIC)) - CB_MAGIC_BITS));
+            atomicAdd(Sb + k * SH_RS, __float_as_uint(__fmaf_rn(as, tn, CB_MAGIC)));
             tp = tc;
             tc = tn;
         }
@@ -201,17 +210,29 @@ __global__ void __launch_bounds__(SH_WARPS * 32, 5) shell_kernel(const __grid_co
     }
 
     // ---- expansion: warp w owns bin q0 + w; lane o reads the sums of offset o
+    float m[ISM_CHEB_N];
+    bool any = false;
+    if (warp < nb) {
+        const unsigned* Sb = S + warp * (ISM_CHEB_N * SH_RS);
+        const unsigned nk = (unsigned)Cn[warp * SH_RS + lane] * CB_MAGIC_BITS;   // n K (mod 2^32)
+        const float inv = inv_s[warp];
+#pragma unroll
+        for (int k = 0; k < ISM_CHEB_N; ++k) {
+            const int v = (int)(Sb[k * SH_RS + lane] - nk);
+            any |= v != 0;
+            m[k] = __int2float_rn(v) * inv;   // exact scaling by a power of two
+        }
+    }
+    __syncthreads();   // every sum is read before the moment table overwrites the CTA's tables
     if (warp >= nb) return;
     const int q = q0 + warp;
-    int* Sb = S + warp * (ISM_CHEB_N * SH_RS);
-    float* Mb = reinterpret_cast<float*>(Sb);
-    const float inv = inv_s[warp];
-    bool any = false;
-#pragma unroll
-    for (int k = 0; k < ISM_CHEB_N; ++k) {
-        const int v = Sb[k * SH_RS + lane];
-        any |= v != 0;
-        Mb[k * SH_RS + lane] = __int2float_rn(v) * inv;   // exact scaling by a power of two
+    // moments of (bin, offset o) at Mt + 3 (32 bin + o): {M_0..M_3}, {M_4..M_7}, {M_8}
+    float4* Mt = reinterpret_cast<float4*>(S);
+    {
+        float4* mo = Mt + 3 * (32 * warp + lane);
+        mo[0] = make_float4(m[0], m[1], m[2], m[3]);
+        mo[1] = make_float4(m[4], m[5], m[6], m[7]);
+        mo[2] = make_float4(m[8], 0.0f, 0.0f, 0.0f);
     }
     const unsigned nonempty = __ballot_sync(0xffffffffu, any);
     __syncwarp();
@@ -221,10 +242,13 @@ __global__ void __launch_bounds__(SH_WARPS * 32, 5) shell_kernel(const __grid_co
     float acc[2] = {0.0f, 0.0f};
     for (int o = 0; o < SH_NO; ++o) {
         if (!((nonempty >> o) & 1u)) continue;   // warp-uniform
+        const float4* mo = Mt + 3 * (32 * warp + o);
+        const float4 ma = mo[0], mb = mo[1];
+        const float mv[ISM_CHEB_N] = {ma.x, ma.y, ma.z, ma.w, mb.x, mb.y, mb.z, mb.w, mo[2].x};
         float D[1];
-        D[0] = c[0] * Mb[o];
+        D[0] = c[0] * mv[0];
 #pragma unroll
-        for (int k = 1; k < ISM_CHEB_N; ++k) D[0] = __fmaf_rn(c[k], Mb[k * SH_RS + o], D[0]);
+        for (int k = 1; k < ISM_CHEB_N; ++k) D[0] = __fmaf_rn(c[k], mv[k], D[0]);
         flush_run<1, false>(D, acc, o - 1, lane, 1.0f);
     }
     float* row = rows + J.rows_base + ((long long)r * J.Q + q) * WIN;
