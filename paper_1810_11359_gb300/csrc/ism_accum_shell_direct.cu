@@ -80,13 +80,26 @@ __global__ void __launch_bounds__(SD_WARPS * 32, 4) shell_direct_kernel(const __
     constexpr int LQ = ism_lut_phases(1);   // table phases per sample (LUT forms)
     constexpr int WIN = 64;   // window row of a bin: 32 (SLOTS + 1), SLOTS = 1
     extern __shared__ __align__(16) unsigned char smem[];
-    // CTA -> (job, RIR, shell): job by job, RIR by RIR, outermost (densest) shell first
+    // CTA -> (job, RIR, shell): by the shell's rank from the outside over all RIRs of the
+    // launch (every RIR's outermost, densest shell first, the lightest at the end of the
+    // launch) when the jobs' shell counts are alike, else job by job, RIR by RIR, densest
+    // shell first
     const long long g = blockIdx.x;
-    const int jid = ism_find_job(t, g, [](const JobDev& d) { return (long long)d.sd_cta_base; });
+    int jid, r, grp;
+    if (t.sd_rank_rirs) {
+        const int k = (int)(g / t.sd_rank_rirs);
+        const int rr = (int)(g - (long long)k * t.sd_rank_rirs);
+        jid = ism_find_job(t, rr, [](const JobDev& d) { return (long long)d.sd_rir_base; });
+        r = rr - t.j[jid].sd_rir_base;
+        grp = t.j[jid].shell_groups - 1 - k;
+        if (grp < 0) return;   // past the job's shells (CTA-uniform)
+    } else {
+        jid = ism_find_job(t, g, [](const JobDev& d) { return (long long)d.sd_cta_base; });
+        const long long local = g - t.j[jid].sd_cta_base;
+        r = (int)(local / t.j[jid].shell_groups);
+        grp = t.j[jid].shell_groups - 1 - (int)(local % t.j[jid].shell_groups);
+    }
     const JobDev& J = t.j[jid];
-    const long long local = g - J.sd_cta_base;
-    const int r = (int)(local / J.shell_groups);
-    const int grp = J.shell_groups - 1 - (int)(local % J.shell_groups);
     const int B = J.shell_direct;   // bins per shell: 8 (dense rooms) or 32 (sparse ones)
     const int q0 = grp * B;
     const int nb = min(B, J.Q - q0);

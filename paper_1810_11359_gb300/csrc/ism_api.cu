@@ -168,7 +168,8 @@ ism_status plan(const Validated* vs, int n, ism_precision prec, bool backward, J
     for (int i = 0; i < n; ++i)
         set_cols += (long long)vs[i].job.nb_img[0] * vs[i].job.nb_img[1] * vs[i].job.n_src * vs[i].job.n_rcv;
     long long rir = 0, hist = 0, tbl = 0, ecta = 0, acta = 0, adta = 0, tcta = 0, fcta = 0, rows = 0, ids = 0, lut = 0,
-              gpart = 0, srir = 0, scta = 0, env = 0, vcta = 0, sdc = 0, vslot = 0;
+              gpart = 0, srir = 0, scta = 0, env = 0, vcta = 0, sdc = 0, vslot = 0, sdrir = 0;
+    int sd_gmax = 0;   // most shells of a fused direct RIR
     for (int i = 0; i < n; ++i) {
         const Validated& v = vs[i];
         const ism_job& in = v.job;
@@ -299,6 +300,7 @@ ism_status plan(const Validated* vs, int n, ism_precision prec, bool backward, J
         J.shell_rir_base = srir;
         J.shell_cta_base = scta;
         J.sd_cta_base = (int)sdc;
+        J.sd_rir_base = (int)sdrir;
         J.grad_out = v.grad_out;
         J.grad_beta = v.grad_beta;
         J.grad_src = v.grad_src;
@@ -318,7 +320,11 @@ ism_status plan(const Validated* vs, int n, ism_precision prec, bool backward, J
             scta += R * J.shell_groups;
             if (J.shell_groups > t.shell_gmax) t.shell_gmax = J.shell_groups;
         }
-        if (J.shell_direct) sdc += R * J.shell_groups;
+        if (J.shell_direct) {
+            sdc += R * J.shell_groups;
+            sdrir += R;
+            if (J.shell_groups > sd_gmax) sd_gmax = J.shell_groups;
+        }
         fcta += R * J.fin_chunks;
         if (backward && !J.adj_cheb) adta += R * J.n_tiles;
         if (J.has_tail) {
@@ -354,7 +360,7 @@ ism_status plan(const Validated* vs, int n, ism_precision prec, bool backward, J
         return fail(ISM_ERR_UNSUPPORTED, "%lld images in one launch set exceed 2^32; split the batch", ids);
     if (rir > 0x7FFFFFFFll || ecta > 0x7FFFFFFFll || acta > 0x7FFFFFFFll || adta > 0x7FFFFFFFll ||
         tcta > 0x7FFFFFFFll || fcta > 0x7FFFFFFFll || srir * (long long)t.shell_gmax > 0x7FFFFFFFll ||
-        env > 0x7FFFFFFFll || vcta > 0x7FFFFFFFll || sdc > 0x7FFFFFFFll || gpart > 0x7FFFFFFFll ||
+        env > 0x7FFFFFFFll || vcta > 0x7FFFFFFFll || sdrir * (long long)sd_gmax > 0x7FFFFFFFll || gpart > 0x7FFFFFFFll ||
         rir * 12 > 0x7FFFFFFFll || lut > 0x7FFFFFFFll)
         return fail(ISM_ERR_UNSUPPORTED, "launch set too large; split the batch");
     p.hist_total = hist;
@@ -379,7 +385,10 @@ ism_status plan(const Validated* vs, int n, ism_precision prec, bool backward, J
     t.shell_rank_major = (srir * (long long)t.shell_gmax * 7 <= scta * 8) ? 1 : 0;
     p.shell_ctas = t.shell_rank_major ? srir * t.shell_gmax : scta;
     p.adj_ctas = adta;
-    p.sd_ctas = sdc;
+    // the fused direct CTAs the same way (shells of one thickness per job: 8 or 32 bins)
+    const bool sd_rank = sdrir > 0 && sdrir * (long long)sd_gmax * 7 <= sdc * 8;
+    t.sd_rank_rirs = sd_rank ? (int)sdrir : 0;
+    p.sd_ctas = sd_rank ? sdrir * sd_gmax : sdc;
     p.tail_ctas = tcta;
     p.fin_ctas = fcta;
     size_t off = base;

@@ -125,6 +125,7 @@ struct JobDev {
     int shell_direct;         // its bins per CTA (0: not this form)
     int sd_cta_base;          // first CTA of the job in its launch (shell_groups CTAs per RIR)
     int env_slot;             // the job's slot of envelope quadrature nodes (Lehmann-Johansson tails)
+    int sd_rir_base;          // first RIR of the job among the launch set's fused direct RIRs
 };
 
 struct JobTable {
@@ -135,6 +136,7 @@ struct JobTable {
     int any_direct;                    // some job reads delay-binned image ids
     int shell_gmax;                    // most shells of a fused RIR
     int shell_rank_major;              // fused CTAs ordered by shell rank (shell_gmax x shell_rirs) or by job
+    int sd_rank_rirs;                  // fused direct CTAs ordered by shell rank over this many RIRs (0: by job)
     long long shell_rirs;              // RIRs of the fused jobs
     float cheb[32 * ISM_CHEB_N];       // Chebyshev coefficients of the 32 tap functions (32-tap window)
     JobDev j[ISM_MAX_JOBS];
