@@ -12,23 +12,24 @@
 // The shells are 32 bins thick (1024 samples) when the bins hold few images:
 // visiting the grid columns that reach a shell is what thickness amortises;
 // dense rooms take 8 bins, so that their RIRs still split into many CTAs.
-// The candidates of every chunk of columns are split evenly over the CTA's
-// warps (ism_shell.cuh, shell_walk_cta), so no warp waits for another.
+// The candidates of every chunk of columns form batches of 32 dealt to the
+// CTA's warps in turn (ism_shell.cuh, shell_walk_cta), so no warp waits for
+// another by more than one batch.
 //
 // Each lane that finds an image computes its record {f, P, P cos phi,
 // P sin phi} (the factorised windowed sinc of ism_accum.cuh: P = A sin(pi f) /
 // (2 pi), phi = 2 pi f / N_w) and the position of its first tap in the
-// shell's window (32 B + 32 samples from 32 q0 - 16, B bins) and stages
-// them in the warp's shared memory.  After every batch of 32 candidates the
-// warp takes the staged images in lane order, two at a time (lanes 2k and
-// 2k + 1), and lane t adds tap t of each -- sigma_t (t - 15 - f) by one FFMA,
-// the window by two, one reciprocal and one product, the FMAs and the product
-// issued as packed f32x2 operations on the pair -- to its warp's window of the
-// shell in shared memory (consecutive lanes, consecutive addresses).  The
-// order in which a warp adds its images is a function of the geometry alone
-// (ism_shell.cuh), so the warp windows are the same in every run; at the end
-// they are summed in warp order.  No atomics: the output is bit-identical from
-// run to run.
+// shell's window (32 B + 32 samples from 32 q0 - 16, B bins), and puts them
+// in its warp's ring of staged records in shared memory, after the images
+// already waiting, in lane order.  Whenever 32 images wait, the warp takes
+// them two at a time, and lane t adds tap t of each -- sigma_t (t - 15 - f) by
+// one FFMA, the window by two, one reciprocal and one product, the FMAs and
+// the product issued as packed f32x2 operations on the pair -- to its warp's
+// window of the shell in shared memory (consecutive lanes, consecutive
+// addresses).  The order in which a warp meets and adds its images is a
+// function of the geometry alone (ism_shell.cuh), so the warp windows are the
+// same in every run; at the end they are summed in warp order.  No atomics:
+// the output is bit-identical from run to run.
 //
 // The shell's window is written as the bins' window rows of the finalize
 // kernel (64 samples from 32 q - 16, summed per sample with the previous
@@ -67,14 +68,18 @@ __device__ __forceinline__ unsigned long long sd_mul2(unsigned long long a, unsi
 
 #define SD_B ISM_SD_BINS             // delay bins per CTA, at most
 #define SD_WARPS 8                   // warps per CTA
-#define SD_WIN (32 * SD_B + 32)      // samples of the shell's window (taps of b in [32 q0 - 1, 32 (q0 + SD_B) - 1))
-#define SD_WINP (SD_WIN + 32)        // per warp: the window, then 32 samples where lanes without an image add 0
+#define SD_RING 64                   // staged image records per warp (a ring; 32 are added at once)
+
+// Window of a warp: the taps of b in [32 q0 - 1, 32 (q0 + B) - 1) fall in the 32 B + 32
+// samples from 32 q0 - 16, then 32 samples where the padding record of an odd count adds 0.
+__host__ __device__ __forceinline__ int sd_win(int B) { return 32 * B + 32; }
+__host__ __device__ __forceinline__ int sd_winp(int B) { return sd_win(B) + 32; }
 
 template <int PREC>
 __global__ void __launch_bounds__(SD_WARPS * 32, 4) shell_direct_kernel(const __grid_constant__ JobTable t,
                                                                         const float4* __restrict__ tbl,
                                                                         const float* __restrict__ lut_g,
-                                                                        float* __restrict__ rows)
+                                                                        float* __restrict__ rows, int winp)
 {
     constexpr bool HALF = PREC == PREC_FP16 || PREC == PREC_BF16;
     constexpr int LQ = ism_lut_phases(1);   // table phases per sample (LUT forms)
@@ -106,26 +111,28 @@ __global__ void __launch_bounds__(SD_WARPS * 32, 4) shell_direct_kernel(const __
     const int Nx = J.N[0], Ny = J.N[1], Nz = J.N[2];
     const int n_axis = Nx + Ny + Nz;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int win = sd_win(nb);   // this shell's window (the padding row follows it)
 
-    // shared memory: axis tables | row prefix | per-warp column records | per-warp windows |
-    // per-warp staged images
+    // shared memory: axis tables | row prefix | per-warp column records | per-warp staged
+    // images | per-warp windows (winp floats each: the launch's thickest shell)
     float4* T = reinterpret_cast<float4*>(smem);
     int* rowpre = reinterpret_cast<int*>(smem + (size_t)((t.max_axis_sum + 1) & ~1) * sizeof(float4));
     int* rowy0 = rowpre + ((t.max_axis_sum + 4) & ~3);
     float4* recf = reinterpret_cast<float4*>(rowy0 + ((t.max_axis_sum + 4) & ~3));
     int4* reci = reinterpret_cast<int4*>(recf + SD_WARPS * 32);
-    int* st = reinterpret_cast<int*>(reci + SD_WARPS * 32);            // [warps][33]
-    float* win_all = reinterpret_cast<float*>(st + SD_WARPS * 33);     // [warps][SD_WINP]
-    float4* stage_all = reinterpret_cast<float4*>(win_all + SD_WARPS * SD_WINP);  // [warps][32] (lane pairs interleaved)
-    int* spos_all = reinterpret_cast<int*>(stage_all + SD_WARPS * 32);            // [warps][32]
-    int* wtot = spos_all + SD_WARPS * 32;                                          // [warps]
-    float* winl = win_all + warp * SD_WINP + lane;   // lane's column of the warp's window
-    float4* stage = stage_all + warp * 32;
-    int* spos = spos_all + warp * 32;
+    int* st = reinterpret_cast<int*>(reci + SD_WARPS * 32);                          // [warps][33]
+    float4* stage_all = reinterpret_cast<float4*>(st + SD_WARPS * 33 + 8);           // [warps][SD_RING]
+    int* spos_all = reinterpret_cast<int*>(stage_all + SD_WARPS * SD_RING);           // [warps][SD_RING]
+    int* wtot = spos_all + SD_WARPS * SD_RING;                                        // [warps]
+    float* win_all = reinterpret_cast<float*>(wtot + SD_WARPS);                       // [warps][winp]
+    float* winl = win_all + warp * winp + lane;   // lane's column of the warp's window
+    float4* stage = stage_all + warp * SD_RING;
+    int* spos = spos_all + warp * SD_RING;
 
     const float4* Tg = tbl + J.tbl_base + (long long)r * n_axis;
     for (int e = threadIdx.x; e < n_axis; e += blockDim.x) T[e] = Tg[e];
-    for (int e = threadIdx.x; e < SD_WARPS * SD_WINP; e += blockDim.x) win_all[e] = 0.0f;
+    for (int w = 0; w < SD_WARPS; ++w)
+        for (int e = threadIdx.x; e < win + 32; e += blockDim.x) win_all[w * winp + e] = 0.0f;
     __syncthreads();
 
     // receiver polar pattern: the unit orientation of this RIR's receiver
@@ -165,106 +172,116 @@ __global__ void __launch_bounds__(SD_WARPS * 32, 4) shell_direct_kernel(const __
     const Shell sh = shell_setup(J, T, r, ISM_SB * q0 - 1, min(ISM_SB * (q0 + nb) - 1, J.n_ism + J.H - 1));
     const int n_cols = shell_rows(sh, T, rowpre, rowy0);   // (synchronises the CTA)
     const float amp_scale = J.amp_scale;
-    // staged records of lanes 2k and 2k + 1 interleaved: {f_a, f_b, P_a, P_b}, {Pc_a, Pc_b, Ps_a, Ps_b};
-    // a lane without an image leaves the zero-amplitude record {1/2, 0, 0, 0} (it adds 0)
-    float* sl = reinterpret_cast<float*>(stage) + 8 * (lane >> 1) + (lane & 1);
-    auto clear = [&]() {
-        sl[0] = 0.5f;
-        sl[2] = 0.0f;
-        sl[4] = 0.0f;
-        sl[6] = 0.0f;
-        spos[lane] = SD_WIN;   // no image: the record adds 0 beyond the window
+
+    // Staged records: a ring of SD_RING per warp, records 2k and 2k + 1 interleaved as
+    // {f_a, f_b, P_a, P_b}, {Pc_a, Pc_b, Ps_a, Ps_b}; the warp's images enter in the order
+    // it meets them (batch by batch, lane by lane), and whenever 32 wait their taps are
+    // added, two images at a time (lane t adds tap t of each to its column of the window).
+    const ulonglong2* st2 = reinterpret_cast<const ulonglong2*>(stage);
+    const int2* sp2 = reinterpret_cast<const int2*>(spos);
+    int head = 0, n_st = 0;   // (warp-uniform) first pair of the ring not yet added; records waiting
+    auto put = [&](int slot, const float4& rc, int pos) {
+        float* sl = reinterpret_cast<float*>(stage) + 8 * (slot >> 1) + (slot & 1);
+        sl[0] = rc.x;
+        sl[2] = rc.y;
+        sl[4] = rc.z;
+        sl[6] = rc.w;
+        spos[slot] = pos;
     };
-    clear();
-    __syncwarp();
+    auto taps = [&](int n_pairs) {
+        for (int i = 0; i < n_pairs; ++i) {
+            const int k = (head + i) & (SD_RING / 2 - 1);
+            const ulonglong2 fa = st2[2 * k];       // {f_a, f_b}, {P_a, P_b}
+            const ulonglong2 fb = st2[2 * k + 1];   // {Pc_a, Pc_b}, {Ps_a, Ps_b}
+            const int2 pp = sp2[k];
+            float va, vb;
+            if constexpr (PREC == PREC_FP32) {
+                const unsigned long long x2 = sd_fma2(nsg2, fa.x, xj2);
+                const unsigned long long w2 = sd_fma2(Cj2, fb.x, sd_fma2(Sj2, fb.y, fa.y));
+                float xa, xb;
+                sd_unpack(x2, xa, xb);
+                sd_unpack(sd_mul2(w2, sd_pack(ism_rcp(xa), ism_rcp(xb))), va, vb);
+            } else if constexpr (HALF) {
+                // x in FP32, then the window and the reciprocal in packed 16-bit arithmetic;
+                // the products of two 16-bit values are exact in FP32
+                float xa, xb, Pa, Pb, Pca, Pcb, Psa, Psb;
+                sd_unpack(sd_fma2(nsg2, fa.x, xj2), xa, xb);
+                sd_unpack(fa.y, Pa, Pb);
+                sd_unpack(fb.x, Pca, Pcb);
+                sd_unpack(fb.y, Psa, Psb);
+                const uint32_t w = fma2<PREC>(C2, pack2<PREC>(Pca, Pcb), fma2<PREC>(S2, pack2<PREC>(Psa, Psb),
+                                                                                   pack2<PREC>(Pa, Pb)));
+                va = 0.0f;
+                vb = 0.0f;
+                mixed_fma2<PREC>(va, vb, w, rcp2<PREC>(pack2<PREC>(xa, xb)));
+                va *= dscale;
+                vb *= dscale;
+            } else if constexpr (PREC == PREC_LUT) {
+                float w0a, w0b, w1a, w1b, ra, rb;
+                sd_unpack(fa.x, w0a, w0b);
+                sd_unpack(fa.y, w1a, w1b);
+                sd_unpack(fb.x, ra, rb);
+                const float* pa = lut + __float_as_int(ra);
+                const float* pb = lut + __float_as_int(rb);
+                va = __fmaf_rn(w1a, __ldg(pa + 32), w0a * __ldg(pa));
+                vb = __fmaf_rn(w1b, __ldg(pb + 32), w0b * __ldg(pb));
+            } else {   // PREC_TEX: one filtered fetch per tap
+                float Aa, Ab, ya, yb;
+                sd_unpack(fa.x, Aa, Ab);
+                sd_unpack(fa.y, ya, yb);
+                const cudaTextureObject_t tex = (cudaTextureObject_t)J.lut_tex;
+                va = Aa * tex2D<float>(tex, (float)lane + 0.5f, ya);
+                vb = Ab * tex2D<float>(tex, (float)lane + 0.5f, yb);
+            }
+            winl[pp.x] += va;
+            winl[pp.y] += vb;
+        }
+        head = (head + n_pairs) & (SD_RING / 2 - 1);
+    };
 
     shell_walk_cta<SD_WARPS>(
         sh, T, rowpre, rowy0, n_cols, make_float2(orient.x, orient.y), recf, reci, st, wtot, warp, lane,
-        [&](int b, float f, float s, const float4& cf, int, int, const float4& tz) {
-            const float rs = ism_rcp(s);
-            float amp = cf.z * tz.z * amp_scale * rs;
-            if (alpha != 1.0f)   // polar pattern: cos(theta) = o . (x_n - x_r) / d
-                amp *= __fmaf_rn(1.0f - alpha, __fmaf_rn(orient.z, tz.w, cf.w) * rs, alpha);
-            f = fminf(fmaxf(f, f_lo), f_hi);   // keeps j - f away from 0 (the reciprocal of the tap j = 0)
-            float4 rc;
-            if constexpr (PREC == PREC_LUT) {
-                // eq. (9): rows floor(f Q) and + 1 of the polyphase table, weights A (1 - phi), A phi
-                const float u = f * (float)LQ;   // exact: LQ is a power of two
-                const float pf = floorf(u);
-                const float ph = u - pf;         // exact
-                rc = make_float4(amp - amp * ph, amp * ph, __int_as_float(ism_int_of_integral(pf) * 32), 0.0f);
-            } else if constexpr (PREC == PREC_TEX) {
-                rc = make_float4(amp, __fmaf_rn(f, (float)LQ, 0.5f), 0.0f, 0.0f);   // texel row f Q, centred
-            } else {
-                rc = ism_sinc_record(f, amp, true, twopi_Nw, inv2Nw);
-                rc.y *= rscale;
-                rc.z *= rscale;
-                rc.w *= rscale;
-            }
-            sl[0] = rc.x;
-            sl[2] = rc.y;
-            sl[4] = rc.z;
-            sl[6] = rc.w;
-            spos[lane] = b - 15 - W0;   // window position of tap 0, in [0, 32 nb - 1)
-        },
-        [&]() {
-            __syncwarp();
-            const unsigned v = __ballot_sync(0xffffffffu, spos[lane] < SD_WIN);
-            unsigned m = (v | (v >> 1)) & 0x55555555u;   // lane pairs holding an image
-            const ulonglong2* st2 = reinterpret_cast<const ulonglong2*>(stage);
-            const int2* sp2 = reinterpret_cast<const int2*>(spos);
-            while (m) {   // pairs in lane order; within a pair lane 2k first
-                const int k = (__ffs(m) - 1) >> 1;
-                m &= m - 1;
-                const ulonglong2 fa = st2[2 * k];       // {f_a, f_b}, {P_a, P_b}
-                const ulonglong2 fb = st2[2 * k + 1];   // {Pc_a, Pc_b}, {Ps_a, Ps_b}
-                const int2 pp = sp2[k];
-                float va, vb;
-                if constexpr (PREC == PREC_FP32) {
-                    const unsigned long long x2 = sd_fma2(nsg2, fa.x, xj2);
-                    const unsigned long long w2 = sd_fma2(Cj2, fb.x, sd_fma2(Sj2, fb.y, fa.y));
-                    float xa, xb;
-                    sd_unpack(x2, xa, xb);
-                    sd_unpack(sd_mul2(w2, sd_pack(ism_rcp(xa), ism_rcp(xb))), va, vb);
-                } else if constexpr (HALF) {
-                    // x in FP32, then the window and the reciprocal in packed 16-bit arithmetic;
-                    // the products of two 16-bit values are exact in FP32
-                    float xa, xb, Pa, Pb, Pca, Pcb, Psa, Psb;
-                    sd_unpack(sd_fma2(nsg2, fa.x, xj2), xa, xb);
-                    sd_unpack(fa.y, Pa, Pb);
-                    sd_unpack(fb.x, Pca, Pcb);
-                    sd_unpack(fb.y, Psa, Psb);
-                    const uint32_t w = fma2<PREC>(C2, pack2<PREC>(Pca, Pcb), fma2<PREC>(S2, pack2<PREC>(Psa, Psb),
-                                                                                       pack2<PREC>(Pa, Pb)));
-                    va = 0.0f;
-                    vb = 0.0f;
-                    mixed_fma2<PREC>(va, vb, w, rcp2<PREC>(pack2<PREC>(xa, xb)));
-                    va *= dscale;
-                    vb *= dscale;
-                } else if constexpr (PREC == PREC_LUT) {
-                    float w0a, w0b, w1a, w1b, ra, rb;
-                    sd_unpack(fa.x, w0a, w0b);
-                    sd_unpack(fa.y, w1a, w1b);
-                    sd_unpack(fb.x, ra, rb);
-                    const float* pa = lut + __float_as_int(ra);
-                    const float* pb = lut + __float_as_int(rb);
-                    va = __fmaf_rn(w1a, __ldg(pa + 32), w0a * __ldg(pa));
-                    vb = __fmaf_rn(w1b, __ldg(pb + 32), w0b * __ldg(pb));
-                } else {   // PREC_TEX: one filtered fetch per tap
-                    float Aa, Ab, ya, yb;
-                    sd_unpack(fa.x, Aa, Ab);
-                    sd_unpack(fa.y, ya, yb);
-                    const cudaTextureObject_t tex = (cudaTextureObject_t)J.lut_tex;
-                    va = Aa * tex2D<float>(tex, (float)lane + 0.5f, ya);
-                    vb = Ab * tex2D<float>(tex, (float)lane + 0.5f, yb);
+        [&](bool has, int b, float f, float s, const float4& cf, const float4& tz) {
+            float4 rc = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+            if (has) {
+                const float rs = ism_rcp(s);
+                float amp = cf.z * tz.z * amp_scale * rs;
+                if (alpha != 1.0f)   // polar pattern: cos(theta) = o . (x_n - x_r) / d
+                    amp *= __fmaf_rn(1.0f - alpha, __fmaf_rn(orient.z, tz.w, cf.w) * rs, alpha);
+                f = fminf(fmaxf(f, f_lo), f_hi);   // keeps j - f away from 0 (the reciprocal of the tap j = 0)
+                if constexpr (PREC == PREC_LUT) {
+                    // eq. (9): rows floor(f Q) and + 1 of the polyphase table, weights A (1 - phi), A phi
+                    const float u = f * (float)LQ;   // exact: LQ is a power of two
+                    const float pf = floorf(u);
+                    const float ph = u - pf;         // exact
+                    rc = make_float4(amp - amp * ph, amp * ph, __int_as_float(ism_int_of_integral(pf) * 32), 0.0f);
+                } else if constexpr (PREC == PREC_TEX) {
+                    rc = make_float4(amp, __fmaf_rn(f, (float)LQ, 0.5f), 0.0f, 0.0f);   // texel row f Q, centred
+                } else {
+                    rc = ism_sinc_record(f, amp, true, twopi_Nw, inv2Nw);
+                    rc.y *= rscale;
+                    rc.z *= rscale;
+                    rc.w *= rscale;
                 }
-                winl[pp.x] += va;
-                winl[pp.y] += vb;
             }
-            __syncwarp();
-            clear();
-            __syncwarp();
+            const unsigned v = __ballot_sync(0xffffffffu, has);
+            if (has)   // the images of the batch in lane order, after those waiting
+                put((2 * head + n_st + __popc(v & ((1u << lane) - 1u))) & (SD_RING - 1), rc, b - 15 - W0);
+            n_st += __popc(v);
+            if (n_st >= 32) {
+                __syncwarp();
+                taps(16);
+                n_st -= 32;
+                __syncwarp();   // the added records are free before the next batch writes
+            }
         });
+    // the images still waiting (an odd count padded with a record that adds 0 past the window)
+    if (n_st & 1) {
+        if (lane == 0) put((2 * head + n_st) & (SD_RING - 1), make_float4(0.5f, 0.0f, 0.0f, 0.0f), win);
+        ++n_st;
+    }
+    __syncwarp();
+    taps(n_st >> 1);
     __syncthreads();
 
     // the bins' rows: the warps' windows summed in warp order
@@ -275,7 +292,7 @@ __global__ void __launch_bounds__(SD_WARPS * 32, 4) shell_direct_kernel(const __
             const int p = 32 * ql + lane;   // lower half: samples 32 q - 16 + lane
             float v = win_all[p];
 #pragma unroll
-            for (int w = 1; w < SD_WARPS; ++w) v += win_all[w * SD_WINP + p];
+            for (int w = 1; w < SD_WARPS; ++w) v += win_all[w * winp + p];
             row[lane] = v;
         }
         {
@@ -284,19 +301,27 @@ __global__ void __launch_bounds__(SD_WARPS * 32, 4) shell_direct_kernel(const __
                 const int p = 32 * nb + lane;
                 v = win_all[p];
 #pragma unroll
-                for (int w = 1; w < SD_WARPS; ++w) v += win_all[w * SD_WINP + p];
+                for (int w = 1; w < SD_WARPS; ++w) v += win_all[w * winp + p];
             }
             row[32 + lane] = v;
         }
     }
 }
 
+// the launch's thickest shell (bins)
+int sd_bins_max(const JobTable& t)
+{
+    int bmax = 0;
+    for (int i = 0; i < t.n_jobs; ++i) bmax = std::max(bmax, t.j[i].shell_direct);
+    return bmax;
+}
+
 size_t shell_direct_smem(const JobTable& t)
 {
     return (size_t)((t.max_axis_sum + 1) & ~1) * sizeof(float4) + 2 * (size_t)((t.max_axis_sum + 4) & ~3) * sizeof(int) +
-           (size_t)SD_WARPS * 32 * (sizeof(float4) + sizeof(int4)) + (size_t)SD_WARPS * 33 * sizeof(int) +
-           (size_t)SD_WARPS * SD_WINP * sizeof(float) + (size_t)SD_WARPS * 32 * (sizeof(float4) + sizeof(int)) +
-           SD_WARPS * sizeof(int);
+           (size_t)SD_WARPS * 32 * (sizeof(float4) + sizeof(int4)) + ((size_t)SD_WARPS * 33 + 8) * sizeof(int) +
+           (size_t)SD_WARPS * SD_RING * (sizeof(float4) + sizeof(int)) + SD_WARPS * sizeof(int) +
+           (size_t)SD_WARPS * sd_winp(sd_bins_max(t)) * sizeof(float);
 }
 
 }  // namespace
@@ -313,7 +338,7 @@ static int launch_sd(const JobTable& t, const WsPlan& p, char* ws, cudaStream_t 
     if (e != cudaSuccess) return (int)e;
     shell_direct_kernel<PREC><<<(unsigned)p.sd_ctas, SD_WARPS * 32, sm, s>>>(
         t, reinterpret_cast<const float4*>(ws + p.tbl_off), reinterpret_cast<const float*>(ws + p.lut_off),
-        reinterpret_cast<float*>(ws + p.rows_off));
+        reinterpret_cast<float*>(ws + p.rows_off), sd_winp(sd_bins_max(t)));
     return (int)cudaGetLastError();
 }
 

@@ -184,11 +184,12 @@ __device__ __forceinline__ int shell_column(const Shell& sh, const float4* T, co
     return nd + nu;
 }
 
-// Candidate i of a column (record cf, ci): its exact float-float delay; calls
-// on_image(b, f, s, cf, ixy, iz, tz) if its integer delay b lies in [b_lo, b_hi).
-template <class F>
-__device__ __forceinline__ void shell_candidate(const Shell& sh, const float4* T, const float4& cf, const int4& ci,
-                                                int i, F& on_image)
+// Candidate i of a column (record cf, ci): its exact float-float delay; true
+// if its integer delay b lies in [b_lo, b_hi), with b, f = the fractional part
+// in [0, 1), s = the delay in samples (rounded float-float hi part), iz and tz
+// = the z-axis table entry.
+__device__ __forceinline__ bool shell_delay(const Shell& sh, const float4* T, const float4& cf, const int4& ci, int i,
+                                            int* b_out, float* f_out, float* s_out, int* iz_out, float4* tz_out)
 {
     const int iz = i < ci.y ? ci.x + i : ci.z + (i - ci.y);
     const float4 tz = T[sh.Nx + sh.Ny + iz];
@@ -203,7 +204,24 @@ __device__ __forceinline__ void shell_candidate(const Shell& sh, const float4* T
     f = one ? __fsub_rn(f, 1.0f) : f;
     bf = one ? bf + 1.0f : bf;
     const int b = ism_int_of_integral(fminf(bf, 4.0e6f));
-    if (b >= sh.b_lo && b < sh.b_hi) on_image(b, f, sq.hi, cf, ci.w, iz, tz);
+    *b_out = b;
+    *f_out = f;
+    *s_out = sq.hi;
+    *iz_out = iz;
+    *tz_out = tz;
+    return b >= sh.b_lo && b < sh.b_hi;
+}
+
+// Candidate i of a column: calls on_image(b, f, s, cf, ixy, iz, tz) if it is
+// an image of the shell (shell_delay).
+template <class F>
+__device__ __forceinline__ void shell_candidate(const Shell& sh, const float4* T, const float4& cf, const int4& ci,
+                                                int i, F& on_image)
+{
+    int b, iz;
+    float f, s;
+    float4 tz;
+    if (shell_delay(sh, T, cf, ci, i, &b, &f, &s, &iz, &tz)) on_image(b, f, s, cf, ci.w, iz, tz);
 }
 
 // Last index o in [0, 31] with W[o] <= j (W non-decreasing, W[0] = 0 <= j).
@@ -266,19 +284,22 @@ __device__ __forceinline__ void shell_walk(const Shell& sh, const float4* T, con
     }
 }
 
-// The images of the shell for the whole CTA, the candidates of every chunk of
-// WARPS x 32 columns split evenly over the warps: warp w takes the chunk's
-// candidates [w C / WARPS, (w + 1) C / WARPS) in ascending order, 32 at a time
-// (candidate c by lane c mod 32), so every warp has the same work whatever the
-// columns hold, and which warp and lane meet an image is a function of the
-// geometry alone.  on_image as for shell_walk; on_batch() is called by every
-// warp (converged) after each batch of 32 candidates.  Every thread of the
-// CTA calls it.  Wf, Wi: [WARPS x 32] column records; Wst: [WARPS][33] warp
+// The images of the shell for the whole CTA.  The candidates of every chunk of
+// WARPS x 32 columns form batches of 32 (candidate c by lane c mod 32), and
+// warp w takes the chunk's batches w, w + WARPS, ..: the warps differ by at
+// most one batch per chunk, and only the chunk's last batch is partial.  For
+// every batch the warp's 32 lanes call, converged,
+//   on_lane(has, b, f, s, cf, tz)
+// has = the lane's candidate is an image with integer delay b in [b_lo, b_hi)
+// (shell_delay; the other arguments are unspecified when it is not), cf = its
+// column record (as for shell_walk).  Which warp and lane meet an image, and in
+// which order, is a function of the geometry alone.  Every thread of the CTA
+// calls it.  Wf, Wi: [WARPS x 32] column records; Wst: [WARPS][33] warp
 // prefixes; wtot: [WARPS].
-template <int WARPS, class F, class G>
+template <int WARPS, class F>
 __device__ __forceinline__ void shell_walk_cta(const Shell& sh, const float4* T, const int* rowpre, const int* rowy0,
                                                int n_cols, float2 orient_xy, float4* Wf, int4* Wi, int* Wst,
-                                               int* wtot, int warp, int lane, F&& on_image, G&& on_batch)
+                                               int* wtot, int warp, int lane, F&& on_lane)
 {
     for (int c0 = 0; c0 < n_cols; c0 += WARPS * 32) {
         const int cl = c0 + warp * 32 + lane;
@@ -304,11 +325,14 @@ __device__ __forceinline__ void shell_walk_cta(const Shell& sh, const float4* T,
         off[0] = 0;
 #pragma unroll
         for (int w = 0; w < WARPS; ++w) off[w + 1] = off[w] + wtot[w];
-        const int tot = off[WARPS];
-        const int a = (int)((long long)tot * warp / WARPS), e = (int)((long long)tot * (warp + 1) / WARPS);
-        for (int j0 = a; j0 < e; j0 += 32) {
-            const int c = j0 + lane;
-            if (c < e) {
+        const int n_batches = (off[WARPS] + 31) >> 5;
+        for (int bt = warp; bt < n_batches; bt += WARPS) {   // warp-uniform
+            const int c = bt * 32 + lane;
+            bool has = false;
+            int b = 0;
+            float f = 0.0f, s = 1.0f;
+            float4 cf = make_float4(0.0f, 0.0f, 0.0f, 0.0f), tz = cf;
+            if (c < off[WARPS]) {
                 int wb = 0, base = 0;   // the warp whose columns hold candidate c: the last w with off[w] <= c
 #pragma unroll
                 for (int w = 1; w < WARPS; ++w)   // (never an empty block: off[wb + 1] > c)
@@ -318,9 +342,11 @@ __device__ __forceinline__ void shell_walk_cta(const Shell& sh, const float4* T,
                     }
                 const int j = c - base;
                 const int o = shell_find(Wst + wb * 33, j);
-                shell_candidate(sh, T, Wf[wb * 32 + o], Wi[wb * 32 + o], j - Wst[wb * 33 + o], on_image);
+                cf = Wf[wb * 32 + o];
+                int iz;
+                has = shell_delay(sh, T, cf, Wi[wb * 32 + o], j - Wst[wb * 33 + o], &b, &f, &s, &iz, &tz);
             }
-            on_batch();
+            on_lane(has, b, f, s, cf, tz);
         }
         __syncthreads();   // the records are read before the next chunk overwrites them
     }
