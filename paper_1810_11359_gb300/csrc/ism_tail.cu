@@ -37,14 +37,42 @@ __global__ void __launch_bounds__(256) finalize_kernel(const __grid_constant__ J
 
     // eq. (5): sample k is the sum of the window rows of the bins q with
     // 0 <= k - (32 q - H) < WIN, added in ascending q
-    for (int k = k_beg + (int)threadIdx.x; k < k_end; k += blockDim.x) {
-        const int top = k + J.H;                      // k - (32 q - H) = top - 32 q
-        int q_hi = top / ISM_SB;
-        if (q_hi > J.Q - 1) q_hi = J.Q - 1;
-        int q_lo = top - WIN + 1 <= 0 ? 0 : (top - WIN + 1 + ISM_SB - 1) / ISM_SB;
-        float v = 0.0f;
-        for (int q = q_lo; q <= q_hi; ++q) v += R[(long long)q * WIN + (top - ISM_SB * q)];
-        out[k] = v;
+    if ((J.H & 3) == 0) {
+        // four samples from a multiple of 4 share their bins (top = k + H is then a multiple
+        // of 4, and top .. top + 3 lie in one 32-sample block): one 16-byte load per row,
+        // the same sums in the same order
+        for (int k4 = (k_beg & ~3) + 4 * (int)threadIdx.x; k4 < k_end; k4 += 4 * (int)blockDim.x) {
+            const int top = k4 + J.H;
+            int q_hi = top / ISM_SB;
+            if (q_hi > J.Q - 1) q_hi = J.Q - 1;
+            int q_lo = top - WIN + 1 <= 0 ? 0 : (top - WIN + 1 + ISM_SB - 1) / ISM_SB;
+            float4 v = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+            for (int q = q_lo; q <= q_hi; ++q) {
+                const float4 w = *reinterpret_cast<const float4*>(R + (long long)q * WIN + (top - ISM_SB * q));
+                v.x += w.x;
+                v.y += w.y;
+                v.z += w.z;
+                v.w += w.w;
+            }
+            if (J.vec4 && k4 >= k_beg && k4 + 3 < k_end) {
+                *reinterpret_cast<float4*>(out + k4) = v;
+            } else {   // the chunk's ragged ends
+                if (k4 >= k_beg && k4 < k_end) out[k4] = v.x;
+                if (k4 + 1 >= k_beg && k4 + 1 < k_end) out[k4 + 1] = v.y;
+                if (k4 + 2 >= k_beg && k4 + 2 < k_end) out[k4 + 2] = v.z;
+                if (k4 + 3 >= k_beg && k4 + 3 < k_end) out[k4 + 3] = v.w;
+            }
+        }
+    } else {
+        for (int k = k_beg + (int)threadIdx.x; k < k_end; k += blockDim.x) {
+            const int top = k + J.H;                      // k - (32 q - H) = top - 32 q
+            int q_hi = top / ISM_SB;
+            if (q_hi > J.Q - 1) q_hi = J.Q - 1;
+            int q_lo = top - WIN + 1 <= 0 ? 0 : (top - WIN + 1 + ISM_SB - 1) / ISM_SB;
+            float v = 0.0f;
+            for (int q = q_lo; q <= q_hi; ++q) v += R[(long long)q * WIN + (top - ISM_SB * q)];
+            out[k] = v;
+        }
     }
     if (c != 0) return;
     __syncthreads();
