@@ -284,53 +284,6 @@ __device__ __forceinline__ void shell_walk(const Shell& sh, const float4* T, con
     }
 }
 
-// As shell_walk, but for every batch of 32 candidates the warp's 32 lanes call,
-// converged,
-//   on_lane(has, b, f, s, cf, tz)
-// with has = the lane's candidate is an image with integer delay b in
-// [b_lo, b_hi) (the other arguments are unspecified when it is not).
-template <int WARPS, class F>
-__device__ __forceinline__ void shell_walk_lanes(const Shell& sh, const float4* T, const int* rowpre, const int* rowy0,
-                                                 int n_cols, float2 orient_xy, float4* Wf, int4* Wi, int* Wst,
-                                                 int warp, int lane, F&& on_lane)
-{
-    for (int c0 = warp * 32; c0 < n_cols; c0 += WARPS * 32) {
-        const int cl = c0 + lane;
-        int cnt = 0;
-        float4 rf = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
-        int4 ri = make_int4(0, 0, 0, 0);
-        if (cl < n_cols) cnt = shell_column(sh, T, rowpre, rowy0, cl, orient_xy, &rf, &ri);
-        int inc = cnt;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const int n = __shfl_up_sync(0xffffffffu, inc, o);
-            if (lane >= o) inc += n;
-        }
-        const int total = __shfl_sync(0xffffffffu, inc, 31);
-        __syncwarp();
-        Wf[lane] = rf;
-        Wi[lane] = ri;
-        Wst[lane] = inc - cnt;
-        if (lane == 31) Wst[32] = total;
-        __syncwarp();
-        for (int j0 = 0; j0 < total; j0 += 32) {
-            const int j = j0 + lane;
-            bool has = false;
-            int b = 0;
-            float f = 0.0f, s = 1.0f;
-            float4 cf = make_float4(0.0f, 0.0f, 0.0f, 0.0f), tz = cf;
-            if (j < total) {
-                const int o = shell_find(Wst, j);
-                cf = Wf[o];
-                int iz;
-                has = shell_delay(sh, T, cf, Wi[o], j - Wst[o], &b, &f, &s, &iz, &tz);
-            }
-            on_lane(has, b, f, s, cf, tz);
-        }
-        __syncwarp();
-    }
-}
-
 // The images of the shell for the whole CTA.  The candidates of every chunk of
 // WARPS x 32 columns form batches of 32 (candidate c by lane c mod 32), and
 // warp w takes the chunk's batches w, w + WARPS, ..: the warps differ by at
