@@ -336,6 +336,122 @@ __global__ void __launch_bounds__(AF_T2, 3) af_rows_kernel(AfPlan pl, int p0, in
     }
 }
 
+// ---- row pass, one warp per sequence (rows of C = 256 or 512 points, one row per CTA):
+// the same Stockham stages, twiddles and products as af_rows_kernel, so the same
+// results, but each warp transforms its row in its own shared-memory buffer with only
+// warp barriers between the stages.  Warp 0 transforms the segment's row into one of
+// two buffers (alternating per point), warp 1 + qq the row of pair q0 + qq, which
+// then adds the products with the segment's spectrum to its accumulators in
+// registers (element lane + 32 v); one CTA barrier per point.
+template <int RADIX, int LOGL>
+__device__ __forceinline__ void afw_stage(float2* buf, const float2* tw, int lane, int logNs, float sign)
+{
+    constexpr int LR = RADIX == 2 ? 1 : (RADIX == 4 ? 2 : 3);
+    constexpr int L = 1 << LOGL;
+    constexpr int m = L / RADIX;              // items
+    constexpr int IPL = (m + 31) / 32;        // items per lane
+    const int Ns = 1 << logNs;
+    const int tstep = L >> (logNs + LR);
+    auto pad = [](int i) { return i + (i >> 3); };
+    float2 v[IPL][RADIX];
+#pragma unroll
+    for (int it = 0; it < IPL; ++it) {
+        const int j = lane + 32 * it;
+        if (j < m) {
+            const int k = j & (Ns - 1);
+#pragma unroll
+            for (int q = 0; q < RADIX; ++q) {
+                float2 x = buf[pad(j + q * m)];
+                if (q > 0 && k) x = cmul(x, tw[q * k * tstep]);
+                v[it][q] = x;
+            }
+            af_dft<RADIX>(v[it], sign);
+        }
+    }
+    __syncwarp();
+#pragma unroll
+    for (int it = 0; it < IPL; ++it) {
+        const int j = lane + 32 * it;
+        if (j < m) {
+            const int base = ((j >> logNs) << (logNs + LR)) + (j & (Ns - 1));
+#pragma unroll
+            for (int q = 0; q < RADIX; ++q) buf[pad(base + q * Ns)] = v[it][q];
+        }
+    }
+    __syncwarp();
+}
+
+template <int LOGL>
+__device__ __forceinline__ void afw_fft(float2* buf, const float2* tw, int lane, float sign)
+{
+    int logNs = 0;
+#pragma unroll
+    for (int st = 0; st < LOGL / 3; ++st, logNs += 3) afw_stage<8, LOGL>(buf, tw, lane, logNs, sign);
+    if constexpr (LOGL % 3 == 2) afw_stage<4, LOGL>(buf, tw, lane, logNs, sign);
+    else if constexpr (LOGL % 3 == 1) afw_stage<2, LOGL>(buf, tw, lane, logNs, sign);
+}
+
+template <int LOGC>
+__global__ void __launch_bounds__(32 * (1 + AF_MAXPG)) af_rows_warp_kernel(AfPlan pl, int p0, int n_pts, int first,
+                                                                         const float2* __restrict__ A,
+                                                                         float2* __restrict__ Yg)
+{
+    constexpr int C = 1 << LOGC, V = C / 32, CP = C + C / 8;
+    extern __shared__ __align__(16) unsigned char smem[];
+    float2* tw = reinterpret_cast<float2*>(smem);    // [C]
+    float2* bufs = tw + C;                           // [2][CP]: the segment's spectrum, by point parity
+    float2* bufw = bufs + 2 * CP;                    // [npg][CP]: the pairs' rows
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int k2 = blockIdx.x;
+    const int q0 = blockIdx.y * pl.npg;
+    const int nq = min(pl.npg, pl.n_pairs - q0);
+    const int g = blockIdx.z;
+    const int per_point = 1 + pl.n_pairs;
+    auto pad = [](int i) { return i + (i >> 3); };
+    af_table(tw, LOGC, -1.0f);
+    const bool pair = warp >= 1 && warp <= nq;
+    float2* buf = pair ? bufw + (warp - 1) * CP : nullptr;
+    float2 acc[V];
+    const long long yoff = ((long long)g * pl.n_pairs + q0 + (warp - 1)) * pl.N + (long long)k2 * C;
+#pragma unroll
+    for (int v = 0; v < V; ++v)
+        acc[v] = (pair && !first) ? Yg[yoff + lane + 32 * v] : make_float2(0.0f, 0.0f);
+    __syncthreads();   // the twiddle table
+    const int pp0 = ((g - p0) % pl.n_grp + pl.n_grp) % pl.n_grp;
+    int par = 0;
+    for (int pp = pp0; pp < n_pts; pp += pl.n_grp, par ^= 1) {
+        const float2* Ap = A + (long long)pp * per_point * pl.N + (long long)k2 * C;
+        float2* b = warp == 0 ? bufs + par * CP : buf;
+        if (warp == 0 || pair) {
+            const float2* src = Ap + (warp == 0 ? 0 : (long long)(1 + q0 + warp - 1) * pl.N);
+            float2 x[V];
+#pragma unroll
+            for (int v = 0; v < V; ++v) x[v] = src[lane + 32 * v];
+#pragma unroll
+            for (int v = 0; v < V; ++v) b[pad(lane + 32 * v)] = x[v];
+            __syncwarp();
+            afw_fft<LOGC>(b, tw, lane, -1.0f);
+        }
+        __syncthreads();   // the segment's spectrum of this point is complete
+        if (pair) {
+            const float2* xs_b = bufs + par * CP;
+#pragma unroll
+            for (int v = 0; v < V; ++v) {
+                const int i = pad(lane + 32 * v);
+                const float2 xs = xs_b[i], zs = buf[i];
+                float2 a = acc[v];
+                a.x = __fmaf_rn(xs.x, zs.x, __fmaf_rn(-xs.y, zs.y, a.x));
+                a.y = __fmaf_rn(xs.x, zs.y, __fmaf_rn(xs.y, zs.x, a.y));
+                acc[v] = a;
+            }
+        }
+    }
+    if (pair) {
+#pragma unroll
+        for (int v = 0; v < V; ++v) Yg[yoff + lane + 32 * v] = acc[v];
+    }
+}
+
 __global__ void __launch_bounds__(AF_T2) af_combine_kernel(AfPlan pl, const float2* __restrict__ Yg,
                                                            float2* __restrict__ Y)
 {
@@ -471,6 +587,11 @@ static size_t af_rows_smem(const AfPlan& pl)
     return ((size_t)(1 + pl.npg) * pl.rb * (pl.C + (pl.C >> 3)) + (size_t)pl.npg * pl.rb * pl.C + pl.C) *
            sizeof(float2);
 }
+static size_t af_rows_warp_smem(const AfPlan& pl)
+{
+    const size_t cp = (size_t)pl.C + (pl.C >> 3);
+    return ((size_t)pl.C + (2 + (size_t)pl.npg) * cp) * sizeof(float2);
+}
 static size_t af_combine_smem(const AfPlan& pl)
 {
     return ((size_t)pl.npg * pl.rb * (pl.C + (pl.C >> 3)) + pl.C) * sizeof(float2);
@@ -495,8 +616,13 @@ int ism_launch_auralize_fft(const float* x, const float* h, const int* starts, f
         af_cols_kernel<<<dim3((unsigned)(pl.C / pl.cb), (unsigned)(n_pts * per_point)), AF_T, af_cols_smem(pl, pl.cb),
                          s>>>(pl, p0, x, h, starts, A);
         if ((rc = (int)cudaGetLastError())) return rc;
-        af_rows_kernel<<<dim3((unsigned)(pl.R / pl.rb), (unsigned)pl.n_pg, (unsigned)pl.n_grp), AF_T2,
-                         af_rows_smem(pl), s>>>(pl, p0, n_pts, p0 == 0, A, Yg);
+        const dim3 rgrid((unsigned)(pl.R / pl.rb), (unsigned)pl.n_pg, (unsigned)pl.n_grp);
+        if (pl.C == 256 && pl.rb == 1)
+            af_rows_warp_kernel<8><<<rgrid, 32 * (1 + pl.npg), af_rows_warp_smem(pl), s>>>(pl, p0, n_pts, p0 == 0, A, Yg);
+        else if (pl.C == 512 && pl.rb == 1)
+            af_rows_warp_kernel<9><<<rgrid, 32 * (1 + pl.npg), af_rows_warp_smem(pl), s>>>(pl, p0, n_pts, p0 == 0, A, Yg);
+        else
+            af_rows_kernel<<<rgrid, AF_T2, af_rows_smem(pl), s>>>(pl, p0, n_pts, p0 == 0, A, Yg);
         if ((rc = (int)cudaGetLastError())) return rc;
     }
     af_combine_kernel<<<dim3((unsigned)(pl.R / pl.rb), (unsigned)pl.n_pg), AF_T2, af_combine_smem(pl), s>>>(pl, Yg, Y);
