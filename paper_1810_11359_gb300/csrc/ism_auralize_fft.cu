@@ -337,19 +337,26 @@ __global__ void __launch_bounds__(AF_T2, 3) af_rows_kernel(AfPlan pl, int p0, in
 }
 
 // ---- row pass, one warp per sequence (rows of C = 256 or 512 points, one row per CTA):
-// the same Stockham stages, twiddles and products as af_rows_kernel, so the same
-// results, but each warp transforms its row in its own shared-memory buffer with only
-// warp barriers between the stages.  Warp 0 transforms the segment's row into one of
-// two buffers (alternating per point), warp 1 + qq the row of pair q0 + qq, which
-// then adds the products with the segment's spectrum to its accumulators in
-// registers (element lane + 32 v); one CTA barrier per point.
-template <int RADIX, int LOGL>
-__device__ __forceinline__ void afw_stage(float2* buf, const float2* tw, int lane, int logNs, float sign)
+// the Stockham stages of af_fft (same radices, items, twiddles and arithmetic) and the
+// products of af_rows_kernel, so the same results, with each warp transforming its row
+// alone: only warp barriers between the stages.  The row sits in registers at both
+// ends of its transform -- x[v] holds element lane + 32 v on entry and spectrum element
+// lane + 32 v on return: with items j = lane + 32 it and m = L / RADIX >= 32 inputs apart,
+// the first stage reads only the lane's own elements and the last (Ns = m) writes only
+// them, so only the stages in between go through the warp's buffer (element i at
+// i + i / 8).  Warp 0 transforms the segment's row and leaves its spectrum in one of two
+// buffers (alternating per point), warp 1 + qq the row of pair q0 + qq, which then adds
+// the products with the segment's spectrum to its accumulators in registers; one CTA
+// barrier per point.
+template <int RADIX, int LOGL, bool FIRST, bool LAST>
+__device__ __forceinline__ void afw_stage(float2 (&x)[(1 << LOGL) / 32], float2* buf, const float2* tw, int lane,
+                                          int logNs, float sign)
 {
     constexpr int LR = RADIX == 2 ? 1 : (RADIX == 4 ? 2 : 3);
     constexpr int L = 1 << LOGL;
-    constexpr int m = L / RADIX;              // items
-    constexpr int IPL = (m + 31) / 32;        // items per lane
+    constexpr int m = L / RADIX;
+    static_assert(m >= 32, "every stage needs at least one item per lane");
+    constexpr int IPL = m / 32;
     const int Ns = 1 << logNs;
     const int tstep = L >> (logNs + LR);
     auto pad = [](int i) { return i + (i >> 3); };
@@ -357,38 +364,42 @@ __device__ __forceinline__ void afw_stage(float2* buf, const float2* tw, int lan
 #pragma unroll
     for (int it = 0; it < IPL; ++it) {
         const int j = lane + 32 * it;
-        if (j < m) {
-            const int k = j & (Ns - 1);
+        const int k = j & (Ns - 1);
 #pragma unroll
-            for (int q = 0; q < RADIX; ++q) {
-                float2 x = buf[pad(j + q * m)];
-                if (q > 0 && k) x = cmul(x, tw[q * k * tstep]);
-                v[it][q] = x;
-            }
-            af_dft<RADIX>(v[it], sign);
+        for (int q = 0; q < RADIX; ++q) {
+            float2 a = FIRST ? x[it + q * IPL] : buf[pad(j + q * m)];
+            if (q > 0 && k) a = cmul(a, tw[q * k * tstep]);
+            v[it][q] = a;
         }
+        af_dft<RADIX>(v[it], sign);
     }
-    __syncwarp();
+    if constexpr (LAST) {
 #pragma unroll
-    for (int it = 0; it < IPL; ++it) {
-        const int j = lane + 32 * it;
-        if (j < m) {
+        for (int it = 0; it < IPL; ++it)
+#pragma unroll
+            for (int q = 0; q < RADIX; ++q) x[it + q * IPL] = v[it][q];   // base = j when Ns = m
+    } else {
+        __syncwarp();   // every lane has read the buffer (this stage's inputs, or the last row's)
+#pragma unroll
+        for (int it = 0; it < IPL; ++it) {
+            const int j = lane + 32 * it;
             const int base = ((j >> logNs) << (logNs + LR)) + (j & (Ns - 1));
 #pragma unroll
             for (int q = 0; q < RADIX; ++q) buf[pad(base + q * Ns)] = v[it][q];
         }
+        __syncwarp();
     }
-    __syncwarp();
 }
 
 template <int LOGL>
-__device__ __forceinline__ void afw_fft(float2* buf, const float2* tw, int lane, float sign)
+__device__ __forceinline__ void afw_fft(float2 (&x)[(1 << LOGL) / 32], float2* buf, const float2* tw, int lane,
+                                        float sign)
 {
-    int logNs = 0;
-#pragma unroll
-    for (int st = 0; st < LOGL / 3; ++st, logNs += 3) afw_stage<8, LOGL>(buf, tw, lane, logNs, sign);
-    if constexpr (LOGL % 3 == 2) afw_stage<4, LOGL>(buf, tw, lane, logNs, sign);
-    else if constexpr (LOGL % 3 == 1) afw_stage<2, LOGL>(buf, tw, lane, logNs, sign);
+    static_assert(LOGL == 8 || LOGL == 9, "stages of radix 8, 8, 4 or 8, 8, 8 (as af_fft takes them)");
+    afw_stage<8, LOGL, true, false>(x, buf, tw, lane, 0, sign);
+    afw_stage<8, LOGL, false, false>(x, buf, tw, lane, 3, sign);
+    if constexpr (LOGL == 8) afw_stage<4, LOGL, false, true>(x, buf, tw, lane, 6, sign);
+    else afw_stage<8, LOGL, false, true>(x, buf, tw, lane, 6, sign);
 }
 
 template <int LOGC>
@@ -400,7 +411,7 @@ __global__ void __launch_bounds__(32 * (1 + AF_MAXPG)) af_rows_warp_kernel(AfPla
     extern __shared__ __align__(16) unsigned char smem[];
     float2* tw = reinterpret_cast<float2*>(smem);    // [C]
     float2* bufs = tw + C;                           // [2][CP]: the segment's spectrum, by point parity
-    float2* bufw = bufs + 2 * CP;                    // [npg][CP]: the pairs' rows
+    float2* bufw = bufs + 2 * CP;                    // [1 + npg][CP]: each warp's stage buffer
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int k2 = blockIdx.x;
     const int q0 = blockIdx.y * pl.npg;
@@ -410,7 +421,7 @@ __global__ void __launch_bounds__(32 * (1 + AF_MAXPG)) af_rows_warp_kernel(AfPla
     auto pad = [](int i) { return i + (i >> 3); };
     af_table(tw, LOGC, -1.0f);
     const bool pair = warp >= 1 && warp <= nq;
-    float2* buf = pair ? bufw + (warp - 1) * CP : nullptr;
+    float2* buf = bufw + warp * CP;
     float2 acc[V];
     const long long yoff = ((long long)g * pl.n_pairs + q0 + (warp - 1)) * pl.N + (long long)k2 * C;
 #pragma unroll
@@ -421,24 +432,23 @@ __global__ void __launch_bounds__(32 * (1 + AF_MAXPG)) af_rows_warp_kernel(AfPla
     int par = 0;
     for (int pp = pp0; pp < n_pts; pp += pl.n_grp, par ^= 1) {
         const float2* Ap = A + (long long)pp * per_point * pl.N + (long long)k2 * C;
-        float2* b = warp == 0 ? bufs + par * CP : buf;
+        float2 x[V];
         if (warp == 0 || pair) {
             const float2* src = Ap + (warp == 0 ? 0 : (long long)(1 + q0 + warp - 1) * pl.N);
-            float2 x[V];
 #pragma unroll
             for (int v = 0; v < V; ++v) x[v] = src[lane + 32 * v];
+            afw_fft<LOGC>(x, buf, tw, lane, -1.0f);
+            if (warp == 0) {
 #pragma unroll
-            for (int v = 0; v < V; ++v) b[pad(lane + 32 * v)] = x[v];
-            __syncwarp();
-            afw_fft<LOGC>(b, tw, lane, -1.0f);
+                for (int v = 0; v < V; ++v) bufs[par * CP + pad(lane + 32 * v)] = x[v];
+            }
         }
         __syncthreads();   // the segment's spectrum of this point is complete
         if (pair) {
             const float2* xs_b = bufs + par * CP;
 #pragma unroll
             for (int v = 0; v < V; ++v) {
-                const int i = pad(lane + 32 * v);
-                const float2 xs = xs_b[i], zs = buf[i];
+                const float2 xs = xs_b[pad(lane + 32 * v)], zs = x[v];
                 float2 a = acc[v];
                 a.x = __fmaf_rn(xs.x, zs.x, __fmaf_rn(-xs.y, zs.y, a.x));
                 a.y = __fmaf_rn(xs.x, zs.y, __fmaf_rn(xs.y, zs.x, a.y));
@@ -590,7 +600,7 @@ static size_t af_rows_smem(const AfPlan& pl)
 static size_t af_rows_warp_smem(const AfPlan& pl)
 {
     const size_t cp = (size_t)pl.C + (pl.C >> 3);
-    return ((size_t)pl.C + (2 + (size_t)pl.npg) * cp) * sizeof(float2);
+    return ((size_t)pl.C + (3 + (size_t)pl.npg) * cp) * sizeof(float2);
 }
 static size_t af_combine_smem(const AfPlan& pl)
 {
