@@ -793,7 +793,7 @@ def run_moving_source(args, world, rank, dist, quiet=False):
         "direct_form_ms": direct_ms,
         "fft_speedup_vs_direct": direct_ms / au_ms,
         "fft_vs_direct_max_err_rel_peak": fft_vs_direct,
-        "roofline": {"bound": "alu", "kernel": "af_cols_kernel + af_rows_kernel + af_icols_kernel (FFT form)",
+        "roofline": {"bound": "alu", "kernel": "af_cols_kernel + af_rows_warp_kernel + af_combine_kernel + af_icols_kernel (FFT form)",
                      "achieved": fft_flops / (au_ms * 1e-3) / 1e12, "peak": peak_tflops, "unit": "TFLOP/s (FP32)",
                      "frac": fft_flops / (au_ms * 1e-3) / 1e12 / peak_tflops, "flops_per_step": fft_flops,
                      "dft_length": Nf, "dfts_per_step": n_dft,
