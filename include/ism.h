@@ -167,7 +167,17 @@ ism_status ism_simulate(const ism_room* room, const float* pos_src, int n_src, c
  * directly over the host link, any other host memory receives a copy of the
  * device result.  Positions are validated on the host first
  * (ISM_ERR_INVALID_ARG if one lies outside the room).  Synchronous: returns
- * when `out` holds the result.  The workspace is device memory as above. */
+ * when `out` holds the result.  The workspace is device memory as above.
+ * Repeated calls: when `out` is page-locked (and the stage profiler is off), a
+ * call whose arguments other than the positions' values -- room, counts,
+ * nb_img, times, fs, prec, seed, `out`, workspace and its size, the device and
+ * the ism_set_lanes() setting -- equal an earlier call's replays a CUDA graph
+ * of that call's launches, captured once after it ran (the positions are copied
+ * into the workspace first, as always): bit-identical results, without the
+ * planning and the per-launch parameter copies.  The library keeps the 16 most
+ * recently used graphs (each holds its launches' 32 KB job tables); they hold the
+ * workspace and `out` addresses, so freeing either and calling again with the
+ * same addresses is fine, and per-device state ends with cudaDeviceReset. */
 ism_status ism_simulate_host(const ism_room* room, const float* pos_src, int n_src,
                              const float* pos_rcv, int n_rcv, const int nb_img[3], float Tmax,
                              float fs, float Tdiff, float Tw, ism_precision prec, uint64_t seed,

@@ -950,6 +950,79 @@ ism_status ism_fail_message(ism_status s, const char* fmt, ...)
     return s;
 }
 
+// Graphs of the host entry: a call whose arguments -- all but the values of the
+// positions -- match an earlier call's replays the CUDA graph of that call's launches
+// (captured once, after the first such call ran eagerly), so the job tables, the plan
+// and the dozen launches with their 32 KB parameter tables are not built again.  Only
+// calls whose result is written by the kernels themselves (page-locked `out`) are
+// cached, and none while the stage profiler runs.  At most HG_MAX graphs are kept
+// (the least recently used one goes); the lookup and the launch hold one lock, so no
+// thread destroys a graph another is about to launch.
+namespace {
+#define HG_MAX 16
+struct HostGraph {
+    std::string key;
+    cudaGraph_t g = nullptr;
+    cudaGraphExec_t x = nullptr;
+    size_t pos_off = 0;
+    unsigned long long tick = 0;
+};
+std::mutex g_hg_mu;
+std::vector<HostGraph> g_hg;
+unsigned long long g_hg_tick = 0;
+
+template <class T>
+void key_put(std::string& k, const T& v)
+{
+    k.append(reinterpret_cast<const char*>(&v), sizeof v);
+}
+
+std::string host_graph_key(int dev, const ism_room* room, int n_src, int n_rcv, const int nb_img[3], float Tmax,
+                           float fs, float Tdiff, float Tw, ism_precision prec, uint64_t seed, const void* out_dev,
+                           const void* workspace, size_t ws_bytes)
+{
+    std::string k;
+    key_put(k, dev);
+    for (int a = 0; a < 3; ++a) key_put(k, room->L[a]);
+    for (int w = 0; w < 6; ++w) key_put(k, room->beta[w]);
+    key_put(k, room->c);
+    key_put(k, n_src);
+    key_put(k, n_rcv);
+    for (int a = 0; a < 3; ++a) key_put(k, nb_img[a]);
+    key_put(k, Tmax);
+    key_put(k, fs);
+    key_put(k, Tdiff);
+    key_put(k, Tw);
+    key_put(k, (int)prec);
+    key_put(k, seed);
+    key_put(k, out_dev);
+    key_put(k, workspace);
+    key_put(k, ws_bytes);
+    key_put(k, g_lanes.load());
+    return k;
+}
+
+bool profiling_on()
+{
+    Profiler& P = profiler();
+    std::lock_guard<std::mutex> g(P.mu);
+    return P.on;
+}
+
+// capture stream of the calling thread on the current device
+int capture_stream(cudaStream_t* out)
+{
+    thread_local std::vector<cudaStream_t> cs(64, nullptr);
+    int d = 0;
+    int e = (int)cudaGetDevice(&d);
+    if (e) return e;
+    if (d < 0 || d >= 64) return (int)cudaErrorInvalidDevice;
+    if (!cs[d] && (e = (int)cudaStreamCreateWithFlags(&cs[d], cudaStreamNonBlocking))) return e;
+    *out = cs[d];
+    return 0;
+}
+}  // namespace
+
 extern "C" {
 
 const char* ism_status_string(ism_status s)
@@ -1088,6 +1161,39 @@ ism_status ism_simulate_host(const ism_room* room, const float* pos_src, int n_s
         for (int a = 0; a < 3; ++a)
             if (!(pos_rcv[3 * i + a] > 0.0f && (double)pos_rcv[3 * i + a] < room->L[a]))
                 return fail(ISM_ERR_INVALID_ARG, "receiver %d lies outside the room", i);
+    cudaStream_t st = (cudaStream_t)stream;
+    int e;
+    // a page-locked `out` is written by the kernels themselves (over the host link, as the
+    // RIRs are finished); other host memory receives a copy of the device result
+    // (its address on the current device, where the kernels run: memory pinned in another
+    // device's context without the portable flag has none and takes the copy)
+    cudaPointerAttributes attr{};
+    void* dp = nullptr;
+    const bool direct = cudaPointerGetAttributes(&attr, out) == cudaSuccess && attr.type == cudaMemoryTypeHost &&
+                        cudaHostGetDevicePointer(&dp, static_cast<void*>(out), 0) == cudaSuccess && dp != nullptr;
+    cudaGetLastError();   // a pageable or foreign pointer leaves an error behind
+    std::string gkey;
+    if (direct && workspace && !profiling_on()) {
+        int dev = 0;
+        if ((e = (int)cudaGetDevice(&dev))) return cuda_fail(e, "current device");
+        gkey = host_graph_key(dev, room, n_src, n_rcv, nb_img, Tmax, fs, Tdiff, Tw, prec, seed, dp, workspace,
+                              ws_bytes);
+        std::lock_guard<std::mutex> g(g_hg_mu);
+        for (HostGraph& h : g_hg) {
+            if (h.key != gkey) continue;
+            h.tick = ++g_hg_tick;
+            float* d_pos = reinterpret_cast<float*>(static_cast<char*>(workspace) + h.pos_off);
+            if ((e = (int)cudaMemcpyAsync(d_pos, pos_src, (size_t)n_src * 3 * sizeof(float), cudaMemcpyHostToDevice,
+                                          st)))
+                return cuda_fail(e, "copy of source positions");
+            if ((e = (int)cudaMemcpyAsync(d_pos + 3 * n_src, pos_rcv, (size_t)n_rcv * 3 * sizeof(float),
+                                          cudaMemcpyHostToDevice, st)))
+                return cuda_fail(e, "copy of receiver positions");
+            if ((e = (int)cudaGraphLaunch(h.x, st))) return cuda_fail(e, "graph launch");
+            if ((e = (int)cudaStreamSynchronize(st))) return cuda_fail(e, "stream synchronize");
+            return ISM_OK;
+        }
+    }
     ism_job j = make_job(room, nullptr, n_src, nullptr, n_rcv, nb_img, Tmax, fs, Tdiff, Tw, seed, nullptr);
     std::vector<Validated> vs;
     if ((s = validate_all(&j, 1, vs, false)) != ISM_OK) return s;
@@ -1103,10 +1209,8 @@ ism_status ism_simulate_host(const ism_room* room, const float* pos_src, int n_s
         return fail(ISM_ERR_WORKSPACE_TOO_SMALL, "workspace of %zu bytes, need %zu (ism_host_workspace_size)",
                     ws_bytes, need);
     char* ws = static_cast<char*>(workspace);
-    cudaStream_t st = (cudaStream_t)stream;
     float* d_pos = reinterpret_cast<float*>(ws + pos_off);
     float* d_out = reinterpret_cast<float*>(ws + out_off);
-    int e;
     if ((e = (int)cudaMemcpyAsync(d_pos, pos_src, (size_t)n_src * 3 * sizeof(float), cudaMemcpyHostToDevice, st)))
         return cuda_fail(e, "copy of source positions");
     if ((e = (int)cudaMemcpyAsync(d_pos + 3 * n_src, pos_rcv, (size_t)n_rcv * 3 * sizeof(float),
@@ -1116,19 +1220,43 @@ ism_status ism_simulate_host(const ism_room* room, const float* pos_src, int n_s
     vs[0].job.pos_rcv = d_pos + 3 * n_src;
     vs[0].job.out = d_out;
     vs[0].job.seed = seed;
-    // a page-locked `out` is written by the kernels themselves (over the host link, as the
-    // RIRs are finished); other host memory receives a copy of the device result
-    // (its address on the current device, where the kernels run: memory pinned in another
-    // device's context without the portable flag has none and takes the copy)
-    cudaPointerAttributes attr{};
-    void* dp = nullptr;
-    const bool direct = cudaPointerGetAttributes(&attr, out) == cudaSuccess && attr.type == cudaMemoryTypeHost &&
-                        cudaHostGetDevicePointer(&dp, static_cast<void*>(out), 0) == cudaSuccess && dp != nullptr;
-    cudaGetLastError();   // a pageable or foreign pointer leaves an error behind
     if (direct) vs[0].job.out = static_cast<float*>(dp);
     const HostCopy hc{d_out, out};
     if ((s = run_batch(vs, prec, workspace, sim, stream, direct ? nullptr : &hc)) != ISM_OK) return s;
     if ((e = (int)cudaStreamSynchronize(st))) return cuda_fail(e, "stream synchronize");
+    if (!gkey.empty()) {
+        // capture this call's launches for the next identical one (nothing runs while capturing)
+        cudaStream_t cs = nullptr;
+        cudaGraph_t g = nullptr;
+        cudaGraphExec_t x = nullptr;
+        std::lock_guard<std::mutex> lk(g_hg_mu);
+        if (capture_stream(&cs) == 0 &&
+            cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal) == cudaSuccess) {
+            const ism_status sc = run_batch(vs, prec, workspace, sim, cs, nullptr);
+            const cudaError_t ec = cudaStreamEndCapture(cs, &g);
+            if (sc == ISM_OK && ec == cudaSuccess && g && cudaGraphInstantiate(&x, g, 0) == cudaSuccess) {
+                if (g_hg.size() >= HG_MAX) {
+                    size_t old = 0;
+                    for (size_t i = 1; i < g_hg.size(); ++i)
+                        if (g_hg[i].tick < g_hg[old].tick) old = i;
+                    cudaGraphExecDestroy(g_hg[old].x);
+                    cudaGraphDestroy(g_hg[old].g);
+                    g_hg.erase(g_hg.begin() + (long)old);
+                }
+                HostGraph h;
+                h.key = gkey;
+                h.g = g;
+                h.x = x;
+                h.pos_off = pos_off;
+                h.tick = ++g_hg_tick;
+                g_hg.push_back(h);
+            } else if (g) {
+                cudaGraphDestroy(g);
+            }
+        }
+        cudaGetLastError();   // a capture that failed leaves the call's result as it is
+        g_last_error.clear();
+    }
     return ISM_OK;
 }
 
