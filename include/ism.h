@@ -323,7 +323,15 @@ ism_status ism_batch_workspace_size(const ism_job* jobs, int n_jobs, ism_precisi
 
 /* Simulates every job (host array `jobs`, n_jobs >= 1).  Each job's result is
  * the same as a separate ism_simulate call with the same arguments, bit for
- * bit: the jobs share launches, not arithmetic. */
+ * bit: the jobs share launches, not arithmetic.
+ * Repeated calls: a call whose jobs, precision, workspace (address and size),
+ * device and ism_set_lanes() setting equal a recent call's -- the same
+ * pointers, whatever the values behind them -- replays a CUDA graph of that
+ * call's launches, captured (without running) after the second such call: the
+ * same results without the planning and the per-launch parameter copies.  Not
+ * on a stream the caller is capturing (the launches are then captured as
+ * usual), not while the stage profiler runs, not for jobs with beta_dev.  The
+ * graphs share the host entry's store of 16. */
 ism_status ism_simulate_batch(const ism_job* jobs, int n_jobs, ism_precision prec, void* workspace,
                               size_t ws_bytes, void* stream);
 

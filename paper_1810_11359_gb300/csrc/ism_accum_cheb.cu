@@ -23,7 +23,8 @@
 // tap reaches a sample below n_ism: b <= n_ism + 14.
 //
 // One CTA owns B = 8 consecutive bins of one RIR -- a spherical shell of
-// 256 samples around the receiver -- and enumerates the images in it itself
+// 256 samples around the receiver (thinner, down to one bin, when a launch
+// has too few RIRs to fill the GPU) -- and enumerates the images in it itself
 // (ism_shell.cuh): each candidate's exact float-float delay decides its bin,
 // so every image lands in exactly one CTA, the one whose bins hold its b.
 //
@@ -90,8 +91,9 @@ __global__ void __launch_bounds__(SH_WARPS * 32, 5) shell_kernel(const __grid_co
     int jid, r, grp;
     if (!shell_cta(t, blockIdx.x, &jid, &r, &grp)) return;   // CTA-uniform
     const JobDev& J = t.j[jid];
-    const int q0 = grp * SH_B;
-    const int nb = min(SH_B, J.Q - q0);
+    const int B = t.shell_bins;   // bins of this launch's shells: SH_B, fewer for small launch sets
+    const int q0 = grp * B;
+    const int nb = min(B, J.Q - q0);
     const int Nx = J.N[0], Ny = J.N[1], Nz = J.N[2];
     const int n_axis = Nx + Ny + Nz;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;

@@ -379,6 +379,34 @@ ism_status plan(const Validated* vs, int n, ism_precision prec, bool backward, J
     p.env_slots = backward ? 0 : vslot;
     p.enum_ctas = ecta;
     p.acc_ctas = acta;
+    // Small launch sets: thinner Chebyshev shells, so that the fused launch still fills
+    // the GPU (ISM_FILL_CTAS CTAs at least; a single RIR would otherwise run on ~20
+    // SMs): from 8 bins down to 1.  The moment sums are exact integers and each bin's
+    // fixed-point scale depends on that bin alone, so a job's result does not depend on
+    // the thickness, nor on the launch set it shares.  (The direct form keeps each job's
+    // own thickness: there the CTA split sets the order of the floating-point sums.)
+    t.shell_bins = ISM_SHELL_BINS;
+    if (!backward && scta > 0 && scta < ISM_FILL_CTAS) {
+        auto ctas = [&](int bins) {
+            long long c = 0;
+            for (int i = 0; i < n; ++i)
+                if (t.j[i].use_cheb) c += t.j[i].n_rir * (long long)((t.j[i].Q + bins - 1) / bins);
+            return c;
+        };
+        int bc = ISM_SHELL_BINS;
+        while (bc > 1 && ctas(bc) < ISM_FILL_CTAS) bc >>= 1;
+        t.shell_bins = bc;
+        scta = 0;
+        t.shell_gmax = 0;
+        for (int i = 0; i < n; ++i) {
+            JobDev& J = t.j[i];
+            J.shell_cta_base = scta;
+            if (!J.use_cheb) continue;
+            J.shell_groups = (J.Q + bc - 1) / bc;
+            scta += J.n_rir * (long long)J.shell_groups;
+            t.shell_gmax = std::max(t.shell_gmax, J.shell_groups);
+        }
+    }
     t.shell_rirs = srir;
     // shell-rank order when the jobs' shell counts are alike (at most 1/8 of the
     // rank-major grid would be CTAs past their job's shells), else job-major
@@ -950,25 +978,31 @@ ism_status ism_fail_message(ism_status s, const char* fmt, ...)
     return s;
 }
 
-// Graphs of the host entry: a call whose arguments -- all but the values of the
-// positions -- match an earlier call's replays the CUDA graph of that call's launches
-// (captured once, after the first such call ran eagerly), so the job tables, the plan
-// and the dozen launches with their 32 KB parameter tables are not built again.  Only
-// calls whose result is written by the kernels themselves (page-locked `out`) are
-// cached, and none while the stage profiler runs.  At most HG_MAX graphs are kept
-// (the least recently used one goes); the lookup and the launch hold one lock, so no
-// thread destroys a graph another is about to launch.
+// Launch graphs of repeated calls.  A call whose arguments match an earlier call's
+// -- every argument but the values behind the pointers (positions, outputs) --
+// replays the CUDA graph of that call's launches instead of building the job tables
+// and the plan and issuing the dozen launches with their 32 KB parameter tables
+// again.  The graph is captured (nothing runs while capturing) after a call ran
+// eagerly: the host entry captures after its first call, ism_simulate_batch when a
+// key comes back (so that a stream of distinct batches, as the server's, pays
+// nothing but the key).  Calls on a stream being captured by the caller, calls
+// while the stage profiler runs, and jobs with device-resident coefficients run
+// eagerly.  At most HG_MAX graphs are kept (the least recently used one goes); the
+// lookup and the launch hold one lock, so no thread destroys a graph another is
+// about to launch.
 namespace {
 #define HG_MAX 16
+#define HG_SEEN 32
 struct HostGraph {
     std::string key;
     cudaGraph_t g = nullptr;
     cudaGraphExec_t x = nullptr;
-    size_t pos_off = 0;
+    size_t pos_off = 0;   // host entry: where the positions go in the workspace
     unsigned long long tick = 0;
 };
 std::mutex g_hg_mu;
 std::vector<HostGraph> g_hg;
+std::vector<std::string> g_hg_seen;   // keys met once (ism_simulate_batch), most recent last
 unsigned long long g_hg_tick = 0;
 
 template <class T>
@@ -977,15 +1011,20 @@ void key_put(std::string& k, const T& v)
     k.append(reinterpret_cast<const char*>(&v), sizeof v);
 }
 
+void key_room(std::string& k, const ism_room& r)
+{
+    for (int a = 0; a < 3; ++a) key_put(k, r.L[a]);
+    for (int w = 0; w < 6; ++w) key_put(k, r.beta[w]);
+    key_put(k, r.c);
+}
+
 std::string host_graph_key(int dev, const ism_room* room, int n_src, int n_rcv, const int nb_img[3], float Tmax,
                            float fs, float Tdiff, float Tw, ism_precision prec, uint64_t seed, const void* out_dev,
                            const void* workspace, size_t ws_bytes)
 {
-    std::string k;
+    std::string k("H");
     key_put(k, dev);
-    for (int a = 0; a < 3; ++a) key_put(k, room->L[a]);
-    for (int w = 0; w < 6; ++w) key_put(k, room->beta[w]);
-    key_put(k, room->c);
+    key_room(k, *room);
     key_put(k, n_src);
     key_put(k, n_rcv);
     for (int a = 0; a < 3; ++a) key_put(k, nb_img[a]);
@@ -999,6 +1038,38 @@ std::string host_graph_key(int dev, const ism_room* room, int n_src, int n_rcv, 
     key_put(k, workspace);
     key_put(k, ws_bytes);
     key_put(k, g_lanes.load());
+    return k;
+}
+
+std::string batch_graph_key(int dev, const ism_job* jobs, int n, ism_precision prec, const void* workspace,
+                            size_t ws_bytes)
+{
+    std::string k("B");
+    key_put(k, dev);
+    key_put(k, n);
+    key_put(k, (int)prec);
+    key_put(k, workspace);
+    key_put(k, ws_bytes);
+    key_put(k, g_lanes.load());
+    for (int i = 0; i < n; ++i) {
+        const ism_job& j = jobs[i];
+        key_room(k, j.room);
+        key_put(k, j.pos_src);
+        key_put(k, j.n_src);
+        key_put(k, j.pos_rcv);
+        key_put(k, j.n_rcv);
+        for (int a = 0; a < 3; ++a) key_put(k, j.nb_img[a]);
+        key_put(k, j.Tmax);
+        key_put(k, j.fs);
+        key_put(k, j.Tdiff);
+        key_put(k, j.Tw);
+        key_put(k, j.seed);
+        key_put(k, j.out);
+        key_put(k, j.env_amp);
+        key_put(k, j.mic_pattern);
+        key_put(k, j.orient_rcv);
+        key_put(k, j.envelope);
+    }
     return k;
 }
 
@@ -1020,6 +1091,75 @@ int capture_stream(cudaStream_t* out)
     if (!cs[d] && (e = (int)cudaStreamCreateWithFlags(&cs[d], cudaStreamNonBlocking))) return e;
     *out = cs[d];
     return 0;
+}
+
+// The graph of `key`, if one is kept: pre(pos_off) then its launch on `st`, under the
+// lock.  Returns a CUDA error (0 when all went well); *hit tells whether it launched.
+template <class Pre>
+int hg_replay(const std::string& key, cudaStream_t st, Pre pre, bool* hit)
+{
+    *hit = false;
+    std::lock_guard<std::mutex> g(g_hg_mu);
+    for (HostGraph& h : g_hg) {
+        if (h.key != key) continue;
+        h.tick = ++g_hg_tick;
+        int e = pre(h.pos_off);
+        if (!e) e = (int)cudaGraphLaunch(h.x, st);
+        *hit = e == 0;
+        return e;
+    }
+    return 0;
+}
+
+// Whether a batch key came before (and remember it): the batch entry captures on the
+// second sighting.
+bool hg_seen_before(const std::string& key)
+{
+    std::lock_guard<std::mutex> g(g_hg_mu);
+    for (size_t i = 0; i < g_hg_seen.size(); ++i)
+        if (g_hg_seen[i] == key) {
+            g_hg_seen.erase(g_hg_seen.begin() + (long)i);
+            return true;
+        }
+    if (g_hg_seen.size() >= HG_SEEN) g_hg_seen.erase(g_hg_seen.begin());
+    g_hg_seen.push_back(key);
+    return false;
+}
+
+// Captures run(cs) on the thread's capture stream and keeps the graph under `key`.
+// A capture that fails leaves nothing behind (the call's own result is not touched).
+template <class Run>
+void hg_store(const std::string& key, size_t pos_off, Run run)
+{
+    cudaStream_t cs = nullptr;
+    cudaGraph_t g = nullptr;
+    cudaGraphExec_t x = nullptr;
+    std::lock_guard<std::mutex> lk(g_hg_mu);
+    if (capture_stream(&cs) == 0 && cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal) == cudaSuccess) {
+        const ism_status sc = run(cs);
+        const cudaError_t ec = cudaStreamEndCapture(cs, &g);
+        if (sc == ISM_OK && ec == cudaSuccess && g && cudaGraphInstantiate(&x, g, 0) == cudaSuccess) {
+            if (g_hg.size() >= HG_MAX) {
+                size_t old = 0;
+                for (size_t i = 1; i < g_hg.size(); ++i)
+                    if (g_hg[i].tick < g_hg[old].tick) old = i;
+                cudaGraphExecDestroy(g_hg[old].x);
+                cudaGraphDestroy(g_hg[old].g);
+                g_hg.erase(g_hg.begin() + (long)old);
+            }
+            HostGraph h;
+            h.key = key;
+            h.g = g;
+            h.x = x;
+            h.pos_off = pos_off;
+            h.tick = ++g_hg_tick;
+            g_hg.push_back(h);
+        } else if (g) {
+            cudaGraphDestroy(g);
+        }
+    }
+    cudaGetLastError();
+    g_last_error.clear();
 }
 }  // namespace
 
@@ -1085,9 +1225,31 @@ ism_status ism_simulate_batch(const ism_job* jobs, int n_jobs, ism_precision pre
     g_last_error.clear();
     ism_status s = check_prec(prec);
     if (s != ISM_OK) return s;
+    // a call like an earlier one replays its launch graph (see hg_replay)
+    cudaStream_t st = (cudaStream_t)stream;
+    std::string gkey;
+    bool cacheable = jobs && n_jobs >= 1 && workspace && !profiling_on();
+    for (int i = 0; cacheable && i < n_jobs; ++i) cacheable = jobs[i].beta_dev == nullptr;
+    cudaStreamCaptureStatus cst = cudaStreamCaptureStatusNone;
+    if (cacheable && (cudaStreamIsCapturing(st, &cst) != cudaSuccess || cst != cudaStreamCaptureStatusNone)) {
+        cudaGetLastError();
+        cacheable = false;
+    }
+    if (cacheable) {
+        int dev = 0;
+        int e = (int)cudaGetDevice(&dev);
+        if (e) return cuda_fail(e, "current device");
+        gkey = batch_graph_key(dev, jobs, n_jobs, prec, workspace, ws_bytes);
+        bool hit = false;
+        if ((e = hg_replay(gkey, st, [](size_t) { return 0; }, &hit))) return cuda_fail(e, "graph launch");
+        if (hit) return ISM_OK;
+    }
     std::vector<Validated> vs;
     if ((s = validate_all(jobs, n_jobs, vs, true)) != ISM_OK) return s;
-    return run_batch(vs, prec, workspace, ws_bytes, stream);
+    if ((s = run_batch(vs, prec, workspace, ws_bytes, stream)) != ISM_OK) return s;
+    if (!gkey.empty() && hg_seen_before(gkey))
+        hg_store(gkey, 0, [&](cudaStream_t cs) { return run_batch(vs, prec, workspace, ws_bytes, cs); });
+    return ISM_OK;
 }
 
 ism_status ism_simulate(const ism_room* room, const float* pos_src, int n_src, const float* pos_rcv, int n_rcv,
@@ -1178,18 +1340,17 @@ ism_status ism_simulate_host(const ism_room* room, const float* pos_src, int n_s
         if ((e = (int)cudaGetDevice(&dev))) return cuda_fail(e, "current device");
         gkey = host_graph_key(dev, room, n_src, n_rcv, nb_img, Tmax, fs, Tdiff, Tw, prec, seed, dp, workspace,
                               ws_bytes);
-        std::lock_guard<std::mutex> g(g_hg_mu);
-        for (HostGraph& h : g_hg) {
-            if (h.key != gkey) continue;
-            h.tick = ++g_hg_tick;
-            float* d_pos = reinterpret_cast<float*>(static_cast<char*>(workspace) + h.pos_off);
-            if ((e = (int)cudaMemcpyAsync(d_pos, pos_src, (size_t)n_src * 3 * sizeof(float), cudaMemcpyHostToDevice,
-                                          st)))
-                return cuda_fail(e, "copy of source positions");
-            if ((e = (int)cudaMemcpyAsync(d_pos + 3 * n_src, pos_rcv, (size_t)n_rcv * 3 * sizeof(float),
-                                          cudaMemcpyHostToDevice, st)))
-                return cuda_fail(e, "copy of receiver positions");
-            if ((e = (int)cudaGraphLaunch(h.x, st))) return cuda_fail(e, "graph launch");
+        bool hit = false;
+        e = hg_replay(gkey, st, [&](size_t pos_off) {
+            float* d_pos = reinterpret_cast<float*>(static_cast<char*>(workspace) + pos_off);
+            int r = (int)cudaMemcpyAsync(d_pos, pos_src, (size_t)n_src * 3 * sizeof(float), cudaMemcpyHostToDevice, st);
+            if (!r)
+                r = (int)cudaMemcpyAsync(d_pos + 3 * n_src, pos_rcv, (size_t)n_rcv * 3 * sizeof(float),
+                                         cudaMemcpyHostToDevice, st);
+            return r;
+        }, &hit);
+        if (e) return cuda_fail(e, "copy of the positions or graph launch");
+        if (hit) {
             if ((e = (int)cudaStreamSynchronize(st))) return cuda_fail(e, "stream synchronize");
             return ISM_OK;
         }
@@ -1224,39 +1385,8 @@ ism_status ism_simulate_host(const ism_room* room, const float* pos_src, int n_s
     const HostCopy hc{d_out, out};
     if ((s = run_batch(vs, prec, workspace, sim, stream, direct ? nullptr : &hc)) != ISM_OK) return s;
     if ((e = (int)cudaStreamSynchronize(st))) return cuda_fail(e, "stream synchronize");
-    if (!gkey.empty()) {
-        // capture this call's launches for the next identical one (nothing runs while capturing)
-        cudaStream_t cs = nullptr;
-        cudaGraph_t g = nullptr;
-        cudaGraphExec_t x = nullptr;
-        std::lock_guard<std::mutex> lk(g_hg_mu);
-        if (capture_stream(&cs) == 0 &&
-            cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal) == cudaSuccess) {
-            const ism_status sc = run_batch(vs, prec, workspace, sim, cs, nullptr);
-            const cudaError_t ec = cudaStreamEndCapture(cs, &g);
-            if (sc == ISM_OK && ec == cudaSuccess && g && cudaGraphInstantiate(&x, g, 0) == cudaSuccess) {
-                if (g_hg.size() >= HG_MAX) {
-                    size_t old = 0;
-                    for (size_t i = 1; i < g_hg.size(); ++i)
-                        if (g_hg[i].tick < g_hg[old].tick) old = i;
-                    cudaGraphExecDestroy(g_hg[old].x);
-                    cudaGraphDestroy(g_hg[old].g);
-                    g_hg.erase(g_hg.begin() + (long)old);
-                }
-                HostGraph h;
-                h.key = gkey;
-                h.g = g;
-                h.x = x;
-                h.pos_off = pos_off;
-                h.tick = ++g_hg_tick;
-                g_hg.push_back(h);
-            } else if (g) {
-                cudaGraphDestroy(g);
-            }
-        }
-        cudaGetLastError();   // a capture that failed leaves the call's result as it is
-        g_last_error.clear();
-    }
+    // capture this call's launches for the next identical one
+    if (!gkey.empty()) hg_store(gkey, pos_off, [&](cudaStream_t cs) { return run_batch(vs, prec, workspace, sim, cs, nullptr); });
     return ISM_OK;
 }
 

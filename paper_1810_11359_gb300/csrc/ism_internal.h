@@ -47,6 +47,7 @@
 #define ISM_CHEB_N 9              // Chebyshev terms of a tap function (degree 8)
 #define ISM_SHELL_BINS 8          // delay bins per CTA of the fused Chebyshev accumulation
 #define ISM_SD_BINS 32            // delay bins per CTA of the fused direct accumulation
+#define ISM_FILL_CTAS 304         // fused CTAs a launch set should have at least (two per SM of a GB300)
 
 // Device-side description of one job.  Everything the kernels need is here
 // so that a whole launch set takes its jobs as one kernel parameter.
@@ -140,6 +141,7 @@ struct JobTable {
     long long shell_rirs;              // RIRs of the fused jobs
     float cheb[32 * ISM_CHEB_N];       // Chebyshev coefficients of the 32 tap functions (32-tap window)
     JobDev j[ISM_MAX_JOBS];
+    int shell_bins;                    // delay bins per CTA of the fused Chebyshev forward (<= ISM_SHELL_BINS)
 };
 
 static_assert(sizeof(JobTable) <= 32000, "the job table is passed as one kernel parameter");

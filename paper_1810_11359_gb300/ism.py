@@ -315,7 +315,19 @@ def ism_simulate(L, beta, pos_src, pos_rcv, nb_img, Tmax, fs, Tdiff=0.0, Tw=0.0,
     dev = torch.device("cuda", torch.cuda.current_device())
     ps = torch.as_tensor(pos_src, dtype=torch.float32).to(dev).reshape(-1, 3).contiguous()
     pr = torch.as_tensor(pos_rcv, dtype=torch.float32).to(dev).reshape(-1, 3).contiguous()
-    n_S = ism_rir_length(Tmax, fs)
+    # the room struct, images per axis, workspace bytes and RIR length of these arguments
+    key = (np.asarray(L, np.float64).tobytes(), np.asarray(beta, np.float64).tobytes(),
+           np.asarray(nb_img, np.int64).tobytes(), ps.shape[0], pr.shape[0], float(Tmax), float(fs),
+           float(Tdiff or 0.0), float(Tw or 0.0), float(c), prec, _lanes_setting[0])
+    hit = _dev_sizes.get(key)
+    if hit is None:
+        if len(_dev_sizes) > 256:
+            _dev_sizes.clear()
+        hit = _dev_sizes[key] = (_room(L, beta, c), _nb(nb_img),
+                                 ism_workspace_size(L, beta, ps.shape[0], pr.shape[0], nb_img, Tmax, fs, Tdiff, Tw,
+                                                    c, prec),
+                                 ism_rir_length(Tmax, fs))
+    r, nb, nbytes, n_S = hit
     if out is None:
         out = torch.empty((ps.shape[0], pr.shape[0], n_S), dtype=torch.float32, device=dev)
     if mic_pattern != "omni" or envelope != "sabine":   # these travel in the job struct: the batch entry point
@@ -328,11 +340,9 @@ def ism_simulate(L, beta, pos_src, pos_rcv, nb_img, Tmax, fs, Tdiff=0.0, Tw=0.0,
                        mic_pattern=mic_pattern, orient_rcv=orient, envelope=envelope)
         ism_simulate_batch([job], prec=prec, workspace=workspace, stream=stream)
         return out
-    nbytes = ism_workspace_size(L, beta, ps.shape[0], pr.shape[0], nb_img, Tmax, fs, Tdiff, Tw, c, prec)
     buf = _workspace(workspace, nbytes)
-    r = _room(L, beta, c)
     _check(load().ism_simulate(ctypes.byref(r), ctypes.c_void_p(ps.data_ptr()), int(ps.shape[0]),
-                               ctypes.c_void_p(pr.data_ptr()), int(pr.shape[0]), _nb(nb_img), float(Tmax), float(fs),
+                               ctypes.c_void_p(pr.data_ptr()), int(pr.shape[0]), nb, float(Tmax), float(fs),
                                float(Tdiff or 0.0), float(Tw or 0.0), PRECISIONS[prec], int(seed) & (2 ** 64 - 1),
                                ctypes.c_void_p(out.data_ptr()), ctypes.c_void_p(buf.data_ptr()),
                                int(buf.numel()), _stream_ptr(stream)))
@@ -340,6 +350,7 @@ def ism_simulate(L, beta, pos_src, pos_rcv, nb_img, Tmax, fs, Tdiff=0.0, Tw=0.0,
 
 
 _host_sizes = {}     # (arguments) -> (room struct, nb, host-entry workspace bytes, RIR length)
+_dev_sizes = {}      # the same for the device entry point
 _lanes_setting = [2]
 
 

@@ -336,6 +336,83 @@ def test_host_entry_repeated_calls_equal_fresh_calls():
             assert np.array_equal(dev.cpu().numpy().view(np.uint32), host.view(np.uint32))
 
 
+def test_repeated_device_calls_replay_graphs_bitwise():
+    """From the second identical call on, ism_simulate_batch (and ism_simulate)
+    replays a CUDA graph of the launches; the position buffers keep their
+    addresses and get new values between calls.  Every result must equal, bit
+    for bit, an eager call (the stage profiler on: no graphs) on the same
+    positions; and the call captured in the caller's own CUDA graph after the
+    library has cached it must replay the same RIRs."""
+    rng = np.random.default_rng(33)
+    room = workloads.batched_fp32()
+    beta = ism.ism_beta_sabine(room.L, room.rt60)
+    N = ism.ism_nb_img_from_t(0.3, room.L, room.c, room.window())
+    n_S = ism.ism_rir_length(0.3, room.fs)
+    ps = torch.empty((2, 3), device="cuda")
+    pr = torch.empty((5, 3), device="cuda")
+    out = torch.empty((2, 5, n_S), device="cuda")
+    ws = ism.Workspace()
+    pos = [(workloads._uniform_inside(rng, room.L, 2), workloads._uniform_inside(rng, room.L, 5)) for _ in range(5)]
+    got = []
+    for a, b in pos:
+        ps.copy_(torch.as_tensor(a))
+        pr.copy_(torch.as_tensor(b))
+        ism.ism_simulate(room.L, beta, ps, pr, N, 0.3, room.fs, Tw=room.window(), out=out, workspace=ws)
+        got.append(out.cpu().numpy().copy())
+    ref_out = torch.empty_like(out)
+    ws_ref = ism.Workspace()
+    ism.ism_profile_enable(True)
+    try:
+        for (a, b), g in zip(pos, got):
+            ism.ism_simulate(room.L, beta, torch.as_tensor(a).cuda(), torch.as_tensor(b).cuda(), N, 0.3, room.fs,
+                             Tw=room.window(), out=ref_out, workspace=ws_ref)
+            assert np.array_equal(ref_out.cpu().numpy().view(np.uint32), g.view(np.uint32))
+    finally:
+        ism.ism_profile_enable(False)
+    # the caller's own capture of the (cached) call
+    s = torch.cuda.Stream()
+    s.wait_stream(torch.cuda.current_stream())
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.stream(s):
+        with torch.cuda.graph(graph, stream=s):
+            ism.ism_simulate(room.L, beta, ps, pr, N, 0.3, room.fs, Tw=room.window(), out=out, workspace=ws)
+    for (a, b), g in zip(pos[:2], got[:2]):
+        ps.copy_(torch.as_tensor(a))
+        pr.copy_(torch.as_tensor(b))
+        out.fill_(float("nan"))
+        graph.replay()
+        torch.cuda.synchronize()
+        assert np.array_equal(out.cpu().numpy().view(np.uint32), g.view(np.uint32))
+
+
+def test_thin_shells_of_a_small_call_equal_the_batched_result():
+    """A launch set with few fused CTAs (the single-RIR workload: 19 shells of
+    8 bins) takes thinner Chebyshev shells, down to one bin per CTA, so that it
+    fills the GPU; the moment sums are exact integers with per-bin scales, so
+    the RIR must equal, bit for bit, the same job run beside a large one (8-bin
+    shells), and stay within the FP32 tolerance of the oracle."""
+    room = workloads.single_rir()
+    big = workloads.batched_fp32()
+    beta_b = ism.ism_beta_sabine(big.L, big.rt60)
+    N_b = ism.ism_nb_img_from_t(big.Tmax, big.L, big.c, big.window())
+    ps = torch.as_tensor(room.pos_src).cuda()
+    pr = torch.as_tensor(room.pos_rcv).cuda()
+    alone = torch.empty((1, 1, 4800), device="cuda")
+    ism.ism_simulate(room.L, room.beta, ps, pr, room.nb_img, room.Tmax, room.fs, Tw=room.window(), out=alone)
+    ps_b = torch.as_tensor(big.pos_src).cuda()
+    pr_b = torch.as_tensor(big.pos_rcv).cuda()
+    out_b = torch.empty((4, 32, ism.ism_rir_length(big.Tmax, big.fs)), device="cuda")
+    mixed = torch.empty((1, 1, 4800), device="cuda")
+    jobs = [ism.make_job(big.L, beta_b, ps_b, pr_b, N_b, big.Tmax, big.fs, out_b, Tw=big.window()),
+            ism.make_job(room.L, room.beta, ps, pr, room.nb_img, room.Tmax, room.fs, mixed, Tw=room.window())]
+    ism.ism_simulate_batch(jobs)
+    torch.cuda.synchronize()
+    a, m = alone.cpu().numpy(), mixed.cpu().numpy()
+    assert np.array_equal(a.view(np.uint32), m.view(np.uint32))
+    ref = oracle_ism(room.L, room.beta, room.pos_src, room.pos_rcv, room.nb_img, 4800, room.fs, room.window())
+    assert np.max(np.abs(a.reshape(-1) - ref.reshape(-1))) <= TOL_FP32 * np.max(np.abs(ref))
+
+
 def test_sabine_on_device_fp64():
     rooms = workloads.serving_requests(64, seed=9)
     L = torch.tensor(np.stack([r.room.L for r in rooms]), dtype=torch.float64, device="cuda")
