@@ -661,6 +661,40 @@ Profiler& profiler()
     return *p;
 }
 
+bool profiling_on()
+{
+    Profiler& P = profiler();
+    std::lock_guard<std::mutex> g(P.mu);
+    return P.on;
+}
+
+// Side stream of the calling thread on the current device, with the events that fork
+// it from and join it back into a launch stream (the envelope kernels run there,
+// beside the enumeration and the accumulation they do not depend on).
+struct Side {
+    int dev = -1;
+    cudaStream_t s = nullptr;
+    cudaEvent_t fork = nullptr, join = nullptr;
+};
+
+int side_of_device(Side** out)
+{
+    thread_local std::vector<Side> all(64);
+    int d = 0;
+    int e = (int)cudaGetDevice(&d);
+    if (e) return e;
+    if (d < 0 || d >= 64) return (int)cudaErrorInvalidDevice;
+    Side& S = all[d];
+    if (S.dev != d) {
+        if ((e = (int)cudaStreamCreateWithFlags(&S.s, cudaStreamNonBlocking))) return e;
+        if ((e = (int)cudaEventCreateWithFlags(&S.fork, cudaEventDisableTiming))) return e;
+        if ((e = (int)cudaEventCreateWithFlags(&S.join, cudaEventDisableTiming))) return e;
+        S.dev = d;
+    }
+    *out = &S;
+    return 0;
+}
+
 // Brackets one stage; a no-op unless profiling is on.
 struct StageTimer {
     int stage;
@@ -752,10 +786,22 @@ ism_status run_set(const std::vector<Validated>& set, ism_precision prec, size_t
         if ((e = ism_launch_geometry(t, p, ws, stream))) return cuda_fail(e, "geometry kernel");
         tm.done(p.rir_total > 0);
     }
-    if (p.env_ctas > 0) {   // envelope tables of Lehmann-Johansson tails (read by finalize and tail)
-        StageTimer tm(ISM_STAGE_TAIL, st);
-        if ((e = ism_launch_envelope(t, p, ws, stream))) return cuda_fail(e, "envelope kernel");
-        tm.done(1);
+    // envelope tables of Lehmann-Johansson tails (read by finalize and tail): on the side
+    // stream, joined back before finalize (on the launch stream while profiling, so that
+    // the stage times stay those of one stream)
+    Side* side = nullptr;
+    if (p.env_ctas > 0) {
+        if (!profiling_on()) {
+            if ((e = side_of_device(&side))) return cuda_fail(e, "internal stream");
+            if ((e = (int)cudaEventRecord(side->fork, st))) return cuda_fail(e, "event record");
+            if ((e = (int)cudaStreamWaitEvent(side->s, side->fork, 0))) return cuda_fail(e, "stream wait");
+            if ((e = ism_launch_envelope(t, p, ws, (void*)side->s))) return cuda_fail(e, "envelope kernel");
+            if ((e = (int)cudaEventRecord(side->join, side->s))) return cuda_fail(e, "event record");
+        } else {
+            StageTimer tm(ISM_STAGE_TAIL, st);
+            if ((e = ism_launch_envelope(t, p, ws, stream))) return cuda_fail(e, "envelope kernel");
+            tm.done(1);
+        }
     }
     {
         StageTimer tm(ISM_STAGE_ENUM_COUNT, st);
@@ -783,6 +829,7 @@ ism_status run_set(const std::vector<Validated>& set, ism_precision prec, size_t
         if ((e = ism_launch_accum(t, p, ws, prec, stream, &acc_launched))) return cuda_fail(e, "accumulation kernel");
         tm.done(launched + acc_launched);
     }
+    if (side && (e = (int)cudaStreamWaitEvent(st, side->join, 0))) return cuda_fail(e, "stream wait");
     {
         StageTimer tm(ISM_STAGE_FINALIZE, st);
         if ((e = ism_launch_finalize(t, p, ws, stream))) return cuda_fail(e, "finalize kernel");
@@ -1071,13 +1118,6 @@ std::string batch_graph_key(int dev, const ism_job* jobs, int n, ism_precision p
         key_put(k, j.envelope);
     }
     return k;
-}
-
-bool profiling_on()
-{
-    Profiler& P = profiler();
-    std::lock_guard<std::mutex> g(P.mu);
-    return P.on;
 }
 
 // capture stream of the calling thread on the current device
