@@ -218,10 +218,13 @@ def test_fft_trajectory_workload_moving_source():
     assert diff <= 1e-5
 
 
-@pytest.mark.parametrize("n_x,n_s,n_mics", [(150000, 150001, 8), (400000, 300000, 3)])
+@pytest.mark.parametrize("n_x,n_s,n_mics", [(30000, 20000, 8), (100000, 90000, 5), (150000, 150001, 8),
+                                             (400000, 300000, 3)])
 def test_fft_long_signals_sampled_against_the_definition(n_x, n_s, n_mics):
-    """DFT lengths 2^19 (columns of 1024, rows of 512: three microphone pairs per
-    row-pass CTA, so 4 pairs take two groups) and 2^20 (rows of 1024: one pair per
+    """DFT lengths 2^16 (rows of 256, one warp per row sequence), 2^18 (rows of
+    512, three pairs in one group), 2^19 (columns of 1024, rows of 512: three
+    microphone pairs per row-pass CTA, so 4 pairs take two groups, the second
+    with idle warps) and 2^20 (rows of 1024, the CTA-wide row pass: one pair per
     CTA), three trajectory points: outputs sampled over the whole length against
     the definition (scaled by the largest magnitude sum among them), and every
     output against the direct form."""
