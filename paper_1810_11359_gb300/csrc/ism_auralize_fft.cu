@@ -187,6 +187,61 @@ __device__ void af_fft(float2* buf, const float2* tw, int logL, int ncol, int lo
     else if (logL - logNs == 1) af_stage<COLS, 2, NV>(buf, tw, logL, ncol, logc, logNs, sign);
 }
 
+// The column stages with every size known at compile time (2^LOGC columns of 2^LOGL,
+// AF_T threads): the same items, twiddles and arithmetic as af_stage<true, ...>, so the
+// same results, with the index arithmetic folded.
+template <int RADIX, int LOGL, int LOGC, int LOGNS>
+__device__ __forceinline__ void af_stage_c(float2* buf, const float2* tw, float sign)
+{
+    constexpr int LR = RADIX == 2 ? 1 : (RADIX == 4 ? 2 : 3);
+    constexpr int m = 1 << (LOGL - LR);
+    constexpr int Ns = 1 << LOGNS;
+    constexpr int tstep = (1 << LOGL) >> (LOGNS + LR);
+    constexpr int nitems = m << LOGC;
+    constexpr int IPT = (nitems + AF_T - 1) / AF_T;
+    float2 v[IPT][RADIX];
+#pragma unroll
+    for (int it = 0; it < IPT; ++it) {
+        const int w = (int)threadIdx.x + it * AF_T;
+        if (w < nitems) {
+            const int c = w & ((1 << LOGC) - 1), j = w >> LOGC;
+            const int k = j & (Ns - 1);
+#pragma unroll
+            for (int q = 0; q < RADIX; ++q) {
+                float2 x = buf[((j + q * m) << LOGC) + c];
+                if (q > 0 && k) x = cmul(x, tw[q * k * tstep]);
+                v[it][q] = x;
+            }
+            af_dft<RADIX>(v[it], sign);
+        }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int it = 0; it < IPT; ++it) {
+        const int w = (int)threadIdx.x + it * AF_T;
+        if (w < nitems) {
+            const int c = w & ((1 << LOGC) - 1), j = w >> LOGC;
+            const int base = ((j >> LOGNS) << (LOGNS + LR)) + (j & (Ns - 1));
+#pragma unroll
+            for (int q = 0; q < RADIX; ++q) buf[((base + q * Ns) << LOGC) + c] = v[it][q];
+        }
+    }
+    __syncthreads();
+}
+
+template <int LOGL, int LOGC, int LOGNS = 0>
+__device__ __forceinline__ void af_fft_c(float2* buf, const float2* tw, float sign)
+{
+    if constexpr (LOGL - LOGNS >= 3) {
+        af_stage_c<8, LOGL, LOGC, LOGNS>(buf, tw, sign);
+        af_fft_c<LOGL, LOGC, LOGNS + 3>(buf, tw, sign);
+    } else if constexpr (LOGL - LOGNS == 2) {
+        af_stage_c<4, LOGL, LOGC, LOGNS>(buf, tw, sign);
+    } else if constexpr (LOGL - LOGNS == 1) {
+        af_stage_c<2, LOGL, LOGC, LOGNS>(buf, tw, sign);
+    }
+}
+
 // ---- column pass: segments' signals and microphone-pair RIRs -> A[seq][k2][n1]
 // seq = p_local (1 + n_pairs) + 0 for the segment of point p, + 1 + q for pair q.
 __global__ void __launch_bounds__(AF_T) af_cols_kernel(AfPlan pl, int p0, const float* __restrict__ x,
@@ -251,7 +306,9 @@ __global__ void __launch_bounds__(AF_T) af_cols_kernel(AfPlan pl, int p0, const 
         }
     }
     __syncthreads();
-    af_fft<true, AF_COL_E / AF_T>(buf, tw, pl.logR, pl.cb, 31 - __clz(pl.cb), -1.0f);
+    if (pl.logR == 9 && pl.cb == 16) af_fft_c<9, 4>(buf, tw, -1.0f);        // the common shapes, folded
+    else if (pl.logR == 8 && pl.cb == 32) af_fft_c<8, 5>(buf, tw, -1.0f);
+    else af_fft<true, AF_COL_E / AF_T>(buf, tw, pl.logR, pl.cb, 31 - __clz(pl.cb), -1.0f);
     float2* out = A + (long long)seq * pl.N;
     for (int e = threadIdx.x; e < pl.R * pl.cb; e += blockDim.x) {
         const int k2 = e >> lcb, c = e & (pl.cb - 1);
@@ -522,7 +579,9 @@ __global__ void __launch_bounds__(AF_T) af_icols_kernel(AfPlan pl, const float2*
         }
     }
     __syncthreads();
-    af_fft<true, AF_COL_E / AF_T>(buf, tw, pl.logR, pl.cb3, 31 - __clz(pl.cb3), 1.0f);
+    if (pl.logR == 9 && pl.cb3 == 4) af_fft_c<9, 2>(buf, tw, 1.0f);
+    else if (pl.logR == 8 && pl.cb3 == 8) af_fft_c<8, 3>(buf, tw, 1.0f);
+    else af_fft<true, AF_COL_E / AF_T>(buf, tw, pl.logR, pl.cb3, 31 - __clz(pl.cb3), 1.0f);
     const float inv_n = __int_as_float((127 - pl.logN) << 23);   // 1 / N, exact
     const int m = 2 * q;
     float* y0 = y + (long long)m * pl.n_out;
