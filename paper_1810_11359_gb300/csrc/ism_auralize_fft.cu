@@ -244,30 +244,34 @@ __device__ __forceinline__ void af_fft_c(float2* buf, const float2* tw, float si
 
 // ---- column pass: segments' signals and microphone-pair RIRs -> A[seq][k2][n1]
 // seq = p_local (1 + n_pairs) + 0 for the segment of point p, + 1 + q for pair q.
+// LOGR_T, LCB_T: log2 of the column length and of the columns per CTA when known at
+// compile time (0: from the plan).
+template <int LOGR_T, int LCB_T>
 __global__ void __launch_bounds__(AF_T) af_cols_kernel(AfPlan pl, int p0, const float* __restrict__ x,
                                                        const float* __restrict__ h, const int* __restrict__ starts,
                                                        float2* __restrict__ A)
 {
     extern __shared__ __align__(16) unsigned char smem[];
+    const int logR = LOGR_T ? LOGR_T : pl.logR, R = 1 << logR;
+    const int lcb = LCB_T ? LCB_T : 31 - __clz(pl.cb), cb = 1 << lcb;
     float2* buf = reinterpret_cast<float2*>(smem);   // [R][cb]
-    float2* tw = buf + pl.R * pl.cb;                 // [R]
+    float2* tw = buf + R * cb;                       // [R]
     // W_N^t = W_N^(t_hi 2^s) W_N^(t_lo), t = t_hi 2^s + t_lo: two short tables instead of
     // one sincospif per element (the product of two correctly rounded roots: ~2 ulp)
     const int s_lo = (pl.logN + 1) >> 1;
-    float2* thi = tw + pl.R;                         // [2^(logN - s_lo)]: W_N^(j 2^s_lo)
+    float2* thi = tw + R;                         // [2^(logN - s_lo)]: W_N^(j 2^s_lo)
     float2* tlo = thi + (1 << (pl.logN - s_lo));     // [2^s_lo]: W_N^j
     const int per_point = 1 + pl.n_pairs;
     const int seq = blockIdx.y;
     const int p = p0 + seq / per_point;
     const int kind = seq % per_point;   // 0: segment, 1 + q: pair q
-    const int n1_0 = blockIdx.x * pl.cb;
-    af_table(tw, pl.logR, -1.0f);
+    const int n1_0 = blockIdx.x * cb;
+    af_table(tw, logR, -1.0f);
     af_table(thi, pl.logN - s_lo, -1.0f);
     af_table(tlo, pl.logN, -1.0f, 1 << s_lo);
     // the inputs, 8 loads in flight per thread: a segment of the signal (real) or
     // the RIRs of a microphone pair (real and imaginary parts)
-    const int total = pl.R * pl.cb;
-    const int lcb = 31 - __clz(pl.cb);
+    const int total = R * cb;
     if (kind == 0) {
         const int a = af_start(p, pl.n_x, pl.P, starts), b = max(a, af_start(p + 1, pl.n_x, pl.P, starts));
         for (int e0 = 0; e0 < total; e0 += 8 * AF_T) {
@@ -275,7 +279,7 @@ __global__ void __launch_bounds__(AF_T) af_cols_kernel(AfPlan pl, int p0, const 
 #pragma unroll
             for (int u = 0; u < 8; ++u) {
                 const int e = e0 + u * AF_T + (int)threadIdx.x;
-                const int n = n1_0 + (e & (pl.cb - 1)) + pl.C * (e >> lcb);
+                const int n = n1_0 + (e & (cb - 1)) + pl.C * (e >> lcb);
                 v[u] = (e < total && n >= a && n < b) ? x[n] : 0.0f;
             }
 #pragma unroll
@@ -294,7 +298,7 @@ __global__ void __launch_bounds__(AF_T) af_cols_kernel(AfPlan pl, int p0, const 
 #pragma unroll
             for (int u = 0; u < 8; ++u) {
                 const int e = e0 + u * AF_T + (int)threadIdx.x;
-                const int n = n1_0 + (e & (pl.cb - 1)) + pl.C * (e >> lcb);
+                const int n = n1_0 + (e & (cb - 1)) + pl.C * (e >> lcb);
                 const bool in = e < total && n < pl.n_S;
                 v[u] = make_float2(in ? h0[n] : 0.0f, in ? h1[n] * im : 0.0f);
             }
@@ -306,12 +310,11 @@ __global__ void __launch_bounds__(AF_T) af_cols_kernel(AfPlan pl, int p0, const 
         }
     }
     __syncthreads();
-    if (pl.logR == 9 && pl.cb == 16) af_fft_c<9, 4>(buf, tw, -1.0f);        // the common shapes, folded
-    else if (pl.logR == 8 && pl.cb == 32) af_fft_c<8, 5>(buf, tw, -1.0f);
-    else af_fft<true, AF_COL_E / AF_T>(buf, tw, pl.logR, pl.cb, 31 - __clz(pl.cb), -1.0f);
+    if constexpr (LOGR_T != 0 && LCB_T != 0) af_fft_c<LOGR_T, LCB_T>(buf, tw, -1.0f);   // sizes folded
+    else af_fft<true, AF_COL_E / AF_T>(buf, tw, logR, cb, lcb, -1.0f);
     float2* out = A + (long long)seq * pl.N;
-    for (int e = threadIdx.x; e < pl.R * pl.cb; e += blockDim.x) {
-        const int k2 = e >> lcb, c = e & (pl.cb - 1);
+    for (int e = threadIdx.x; e < total; e += blockDim.x) {
+        const int k2 = e >> lcb, c = e & (cb - 1);
         const int n1 = n1_0 + c;
         const int t = (n1 * k2) & (pl.N - 1);
         const float2 w = cmul(thi[t >> s_lo], tlo[t & ((1 << s_lo) - 1)]);
@@ -675,15 +678,24 @@ int ism_launch_auralize_fft(const float* x, const float* h, const int* starts, f
     float2* A = Yg + (size_t)pl.n_grp * pl.n_pairs * pl.N;
     static std::atomic<unsigned long long> o1{0}, o2{0}, o3{0}, o4{0};
     int rc;
-    if ((rc = ism_open_smem((const void*)af_cols_kernel, &o1))) return rc;
+    static std::atomic<unsigned long long> o1b{0}, o1c{0};
+    if ((rc = ism_open_smem((const void*)af_cols_kernel<0, 0>, &o1))) return rc;
+    if ((rc = ism_open_smem((const void*)af_cols_kernel<9, 4>, &o1b))) return rc;
+    if ((rc = ism_open_smem((const void*)af_cols_kernel<8, 5>, &o1c))) return rc;
     if ((rc = ism_open_smem((const void*)af_rows_kernel, &o2))) return rc;
     if ((rc = ism_open_smem((const void*)af_icols_kernel, &o3))) return rc;
     if ((rc = ism_open_smem((const void*)af_combine_kernel, &o4))) return rc;
     const int per_point = 1 + pl.n_pairs;
     for (int p0 = 0; p0 < pl.P; p0 += pl.pc) {
         const int n_pts = std::min(pl.pc, pl.P - p0);
-        af_cols_kernel<<<dim3((unsigned)(pl.C / pl.cb), (unsigned)(n_pts * per_point)), AF_T, af_cols_smem(pl, pl.cb),
-                         s>>>(pl, p0, x, h, starts, A);
+        const dim3 cgrid((unsigned)(pl.C / pl.cb), (unsigned)(n_pts * per_point));
+        const size_t csm = af_cols_smem(pl, pl.cb);
+        if (pl.logR == 9 && pl.cb == 16)
+            af_cols_kernel<9, 4><<<cgrid, AF_T, csm, s>>>(pl, p0, x, h, starts, A);
+        else if (pl.logR == 8 && pl.cb == 32)
+            af_cols_kernel<8, 5><<<cgrid, AF_T, csm, s>>>(pl, p0, x, h, starts, A);
+        else
+            af_cols_kernel<0, 0><<<cgrid, AF_T, csm, s>>>(pl, p0, x, h, starts, A);
         if ((rc = (int)cudaGetLastError())) return rc;
         const dim3 rgrid((unsigned)(pl.R / pl.rb), (unsigned)pl.n_pg, (unsigned)pl.n_grp);
         if (pl.C == 256 && pl.rb == 1)
