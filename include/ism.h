@@ -18,7 +18,10 @@
  * Conventions shared by every call:
  *   - No call allocates device memory on the simulation path: the caller
  *     passes a device workspace whose size the matching *_workspace_size call
- *     returns.  Pointers are borrowed for the duration of the work.
+ *     returns.  Pointers are borrowed for the duration of the work.  (The
+ *     launch graphs kept for repeated calls -- see ism_simulate_batch and
+ *     ism_simulate_host -- hold the driver's own memory for their executable
+ *     form; the allocation-free entry point keeps none.)
  *   - "device" pointers are CUDA device (or managed) memory of the current
  *     device; "host" pointers are ordinary host memory.
  *   - Work is enqueued on `stream` (a cudaStream_t passed as void*; NULL is
