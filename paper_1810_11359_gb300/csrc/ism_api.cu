@@ -1030,9 +1030,10 @@ ism_status ism_fail_message(ism_status s, const char* fmt, ...)
 // replays the CUDA graph of that call's launches instead of building the job tables
 // and the plan and issuing the dozen launches with their 32 KB parameter tables
 // again.  The graph is captured (nothing runs while capturing) after a call ran
-// eagerly: the host entry captures after its first call, ism_simulate_batch when a
-// key comes back (so that a stream of distinct batches, as the server's, pays
-// nothing but the key).  Calls on a stream being captured by the caller, calls
+// eagerly: the host entry captures after its first call (when the kernels write its
+// page-locked result themselves), ism_simulate_batch when a key comes back (so that
+// a stream of distinct batches, as the server's, pays nothing but the key).  Calls
+// on a stream being captured by the caller, calls
 // while the stage profiler runs, and jobs with device-resident coefficients run
 // eagerly.  At most HG_MAX graphs are kept (the least recently used one goes); the
 // lookup and the launch hold one lock, so no thread destroys a graph another is
@@ -1426,7 +1427,8 @@ ism_status ism_simulate_host(const ism_room* room, const float* pos_src, int n_s
     if ((s = run_batch(vs, prec, workspace, sim, stream, direct ? nullptr : &hc)) != ISM_OK) return s;
     if ((e = (int)cudaStreamSynchronize(st))) return cuda_fail(e, "stream synchronize");
     // capture this call's launches for the next identical one
-    if (!gkey.empty()) hg_store(gkey, pos_off, [&](cudaStream_t cs) { return run_batch(vs, prec, workspace, sim, cs, nullptr); });
+    if (!gkey.empty())
+        hg_store(gkey, pos_off, [&](cudaStream_t cs) { return run_batch(vs, prec, workspace, sim, cs, nullptr); });
     return ISM_OK;
 }
 
