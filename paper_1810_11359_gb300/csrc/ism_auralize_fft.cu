@@ -522,6 +522,39 @@ __global__ void __launch_bounds__(32 * (1 + AF_MAXPG)) af_rows_warp_kernel(AfPla
     }
 }
 
+// af_combine_kernel with one warp per pair (rows of 256 or 512 points, one row per CTA):
+// the same group sums, inverse Stockham stages and twiddles, so the same results.
+template <int LOGC>
+__global__ void __launch_bounds__(32 * AF_MAXPG) af_combine_warp_kernel(AfPlan pl, const float2* __restrict__ Yg,
+                                                                      float2* __restrict__ Y)
+{
+    constexpr int C = 1 << LOGC, V = C / 32, CP = C + C / 8;
+    extern __shared__ __align__(16) unsigned char smem[];
+    float2* tw = reinterpret_cast<float2*>(smem);    // [C]
+    float2* bufw = tw + C;                           // [npg][CP]: each warp's stage buffer
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int k2 = blockIdx.x;
+    const int q0 = blockIdx.y * pl.npg;
+    const int nq = min(pl.npg, pl.n_pairs - q0);
+    af_table(tw, LOGC, 1.0f);
+    __syncthreads();
+    if (warp >= nq) return;   // (no barrier follows)
+    const long long off = (long long)(q0 + warp) * pl.N + (long long)k2 * C;
+    float2 x[V];
+#pragma unroll
+    for (int v = 0; v < V; ++v) {
+        float2 a = Yg[off + lane + 32 * v];
+        for (int gg = 1; gg < pl.n_grp; ++gg) a = cadd(a, Yg[(long long)gg * pl.n_pairs * pl.N + off + lane + 32 * v]);
+        x[v] = a;
+    }
+    afw_fft<LOGC>(x, bufw + warp * CP, tw, lane, 1.0f);
+#pragma unroll
+    for (int v = 0; v < V; ++v) {
+        const int n1 = lane + 32 * v;
+        Y[off + n1] = cmul(x[v], af_root((n1 * k2) & (pl.N - 1), pl.logN, 1.0f));
+    }
+}
+
 __global__ void __launch_bounds__(AF_T2) af_combine_kernel(AfPlan pl, const float2* __restrict__ Yg,
                                                            float2* __restrict__ Y)
 {
@@ -706,7 +739,14 @@ int ism_launch_auralize_fft(const float* x, const float* h, const int* starts, f
             af_rows_kernel<<<rgrid, AF_T2, af_rows_smem(pl), s>>>(pl, p0, n_pts, p0 == 0, A, Yg);
         if ((rc = (int)cudaGetLastError())) return rc;
     }
-    af_combine_kernel<<<dim3((unsigned)(pl.R / pl.rb), (unsigned)pl.n_pg), AF_T2, af_combine_smem(pl), s>>>(pl, Yg, Y);
+    const dim3 cgrid2((unsigned)(pl.R / pl.rb), (unsigned)pl.n_pg);
+    const size_t wsm = ((size_t)pl.C + (size_t)pl.npg * (pl.C + (pl.C >> 3))) * sizeof(float2);
+    if (pl.C == 256 && pl.rb == 1)
+        af_combine_warp_kernel<8><<<cgrid2, 32 * pl.npg, wsm, s>>>(pl, Yg, Y);
+    else if (pl.C == 512 && pl.rb == 1)
+        af_combine_warp_kernel<9><<<cgrid2, 32 * pl.npg, wsm, s>>>(pl, Yg, Y);
+    else
+        af_combine_kernel<<<cgrid2, AF_T2, af_combine_smem(pl), s>>>(pl, Yg, Y);
     if ((rc = (int)cudaGetLastError())) return rc;
     af_icols_kernel<<<dim3((unsigned)(pl.C / pl.cb3), (unsigned)pl.n_pairs), AF_T, af_cols_smem(pl, pl.cb3), s>>>(
         pl, Y, y);
