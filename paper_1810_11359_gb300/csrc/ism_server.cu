@@ -339,17 +339,22 @@ struct ism_server {
                 cv_complete.wait_for(lk, std::chrono::milliseconds(50));
                 continue;
             }
+            // poll the batches in flight without the lock (only this thread removes them),
+            // yielding between polls rather than sleeping: a sleep of a few microseconds
+            // lasts tens with the kernel's timer slack, and every batch's latency would pay it
+            std::vector<Batch*> snap(inflight.begin(), inflight.end());
+            lk.unlock();
             std::vector<Batch*> ready;
-            for (Batch* b : inflight) {
+            for (Batch* b : snap) {
                 cudaError_t e = cudaEventQuery(b->ev);
                 if (e != cudaErrorNotReady) ready.push_back(b);
             }
             if (ready.empty()) {
-                lk.unlock();
-                std::this_thread::sleep_for(std::chrono::microseconds(20));
+                std::this_thread::yield();
                 lk.lock();
                 continue;
             }
+            lk.lock();
             for (Batch* b : ready) inflight.erase(std::find(inflight.begin(), inflight.end(), b));
             lk.unlock();
             std::vector<std::pair<ism_status, std::string>> res;
