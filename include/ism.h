@@ -505,8 +505,9 @@ ism_status ism_auralize(const float* signal, int n_x, const float* rirs, int n_p
  * that of an FP32 FFT: a few 1e-7 of the largest sum |x| * |h|, spread over
  * all outputs.  ISM_AURALIZE_DIRECT is ism_auralize (no workspace).
  * ISM_AURALIZE_AUTO takes the FFT form when its operation count is less than
- * half the direct form's (n_mics n_x n_S multiply-adds) and the workspace
- * holds at least one chunk, else the direct form.
+ * 1 / 2.55 of the direct form's (n_mics n_x n_S multiply-adds; the ratio of the
+ * two forms' measured rates on GB300) and the workspace holds at least one
+ * chunk, else the direct form.
  *   workspace  device, 256-byte aligned, >= ism_auralize_workspace_size()
  *              bytes for the FFT form (scratch; may be NULL for DIRECT);
  *              a larger workspace processes more points per chunk.
