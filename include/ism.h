@@ -78,9 +78,9 @@ typedef enum {
  * accumulation is always FP32.
  *   ISM_PREC_FP32: for a window of exactly 32 taps, the windowed sinc of tap
  *   j as a function of the fractional delay f, delta'(j - f), is expanded in
- *   Chebyshev polynomials of 2f - 1 (degree 8, error < 6.5e-8 of the image's
+ *   Chebyshev polynomials of 2f - 1 (degree 7, error < 4.3e-7 of the image's
  *   amplitude); the images of a delay bin that share their integer offset
- *   are summed as 9 moments sum A T_i(2f - 1), each term rounded to a
+ *   are summed as 8 moments sum A T_i(2f - 1), each term rounded to a
  *   fixed-point integer with a step of 2^-23 of the bin's largest possible
  *   amplitude and summed exactly (so the result does not depend on the
  *   order of the images), and each offset's moments are expanded once into

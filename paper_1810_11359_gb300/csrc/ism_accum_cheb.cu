@@ -7,14 +7,17 @@
 // N_w = 32 taps every tap function g_j(f) = delta'(j - f), j = -15 .. 16, is
 // an entire function of f on [0, 1] (the window's zeros fall at the ends of
 // the interval, so no mask cuts it), and its Chebyshev series in u = 2f - 1
-// converges fast: degree 8 reproduces each g_j to 6.4e-8 of the image's
-// amplitude (degree 9: 2.1e-9; degree 7: 4.2e-7), below the fixed-point step
-// of the moment terms (see below).  The coefficients c_{j,i}, interpolated at
-// the 9 Chebyshev-Gauss nodes in FP64 on the host, travel in the kernel's
-// parameter table.  Hence for the images that share the integer delay b,
+// converges fast: degree 7 reproduces each g_j to 4.2e-7 of the image's
+// amplitude (degree 8: 6.4e-8; degree 9: 2.1e-9), about twice the fixed-point
+// step of the moment terms (see below); together they keep an RIR within a few
+// 1e-7 of its peak, far inside FP32's 1e-5, and degree 7 spares one shared-
+// memory atomic per image against degree 8.  The coefficients c_{j,i},
+// interpolated at the 8 Chebyshev-Gauss nodes in FP64 on the host, travel in
+// the kernel's parameter table.  Hence for the images that share the integer
+// delay b,
 //   sum_n A_n g_j(f_n) = sum_i c_{j,i} M_i,   M_i = sum_n A_n T_i(2 f_n - 1),
-// so each image costs 9 moment terms instead of 32 tap evaluations, and each
-// integer delay costs 9 FMAs per tap once.
+// so each image costs 8 moment terms instead of 32 tap evaluations, and each
+// integer delay costs 8 FMAs per tap once.
 //
 // Delay bins.  Bin q holds the images with b in [32 q - 1, 32 q + 31), i.e.
 // offsets rr = b - 32 q in [-1, 30] (32 offsets, one per lane); its taps fall
@@ -63,10 +66,10 @@ namespace {
 #define SH_NO 32            // offsets per bin (rr = -1 .. 30)
 #define SH_RS 33            // row stride of the moment table (conflict-light atomics)
 #define CB_MAGIC 12582912.0f                       // 1.5 * 2^23
-static_assert(ISM_CHEB_N == 9, "the expansion reads the moments as 4 + 4 + 1");
+static_assert(ISM_CHEB_NF == 8, "the expansion reads the moments as 4 + 4");
 // the expansion's moment table [bin][offset][12] overlays the sums, the counts, the scales, the
 // row prefix and the column records (all dead by then), which always span more than it needs
-static_assert(SH_B * SH_NO * 12 * 4 <= (SH_B * ISM_CHEB_N * SH_RS + SH_B * SH_RS) * 4 + SH_WARPS * 32 * 32,
+static_assert(SH_B * SH_NO * 8 * 4 <= (SH_B * ISM_CHEB_NF * SH_RS + SH_B * SH_RS) * 4 + SH_WARPS * 32 * 32,
               "moment table larger than the tables it overlays");
 #define CB_MAGIC_BITS 0x4B400000u                  // its bits
 
@@ -102,7 +105,7 @@ __global__ void __launch_bounds__(SH_WARPS * 32, 5) shell_kernel(const __grid_co
     // per-warp column records
     float4* T = reinterpret_cast<float4*>(smem);
     unsigned* S = reinterpret_cast<unsigned*>(smem + (size_t)((t.max_axis_sum + 1) & ~1) * sizeof(float4));
-    int* Cn = reinterpret_cast<int*>(S + SH_B * ISM_CHEB_N * SH_RS);             // [bin][offset] images
+    int* Cn = reinterpret_cast<int*>(S + SH_B * ISM_CHEB_NF * SH_RS);             // [bin][offset] images
     float* scale_s = reinterpret_cast<float*>(Cn + SH_B * SH_RS);
     float* inv_s = scale_s + SH_B;
     float* amax_s = inv_s + SH_B;                                                 // per-bin amplitude bound
@@ -164,7 +167,7 @@ __global__ void __launch_bounds__(SH_WARPS * 32, 5) shell_kernel(const __grid_co
 
     const float amp_scale = J.amp_scale;
     for (int pass = 0; pass < 2; ++pass) {
-    for (int e = threadIdx.x; e < SH_B * ISM_CHEB_N * SH_RS; e += blockDim.x) S[e] = 0;
+    for (int e = threadIdx.x; e < SH_B * ISM_CHEB_NF * SH_RS; e += blockDim.x) S[e] = 0;
     for (int e = threadIdx.x; e < SH_B * SH_RS; e += blockDim.x) Cn[e] = 0;
     __syncthreads();
     shell_walk<SH_WARPS>(sh, T, rowpre, rowy0, n_cols, make_float2(orient.x, orient.y), Wf, Wi, Wst, warp, lane,
@@ -179,13 +182,13 @@ __global__ void __launch_bounds__(SH_WARPS * 32, 5) shell_kernel(const __grid_co
         const float as = amp * scale_s[ql];
         const float uu = __fmaf_rn(2.0f, f, -1.0f);
         const float u2 = uu + uu;
-        unsigned* Sb = S + ql * (ISM_CHEB_N * SH_RS) + o;
+        unsigned* Sb = S + ql * (ISM_CHEB_NF * SH_RS) + o;
         atomicAdd(Cn + ql * SH_RS + o, 1);
         atomicAdd(Sb, __float_as_uint(__fadd_rn(as, CB_MAGIC)));   // K + v: the n K go at the expansion
         atomicAdd(Sb + SH_RS, __float_as_uint(__fmaf_rn(as, uu, CB_MAGIC)));
         float tp = 1.0f, tc = uu;
 #pragma unroll
-        for (int k = 2; k < ISM_CHEB_N; ++k) {
+        for (int k = 2; k < ISM_CHEB_NF; ++k) {
             const float tn = __fmaf_rn(u2, tc, -tp);
             atomicAdd(Sb + k * SH_RS, __float_as_uint(__fmaf_rn(as, tn, CB_MAGIC)));
             tp = tc;
@@ -212,14 +215,14 @@ __global__ void __launch_bounds__(SH_WARPS * 32, 5) shell_kernel(const __grid_co
     }
 
     // ---- expansion: warp w owns bin q0 + w; lane o reads the sums of offset o
-    float m[ISM_CHEB_N];
+    float m[ISM_CHEB_NF];
     bool any = false;
     if (warp < nb) {
-        const unsigned* Sb = S + warp * (ISM_CHEB_N * SH_RS);
+        const unsigned* Sb = S + warp * (ISM_CHEB_NF * SH_RS);
         const unsigned nk = (unsigned)Cn[warp * SH_RS + lane] * CB_MAGIC_BITS;   // n K (mod 2^32)
         const float inv = inv_s[warp];
 #pragma unroll
-        for (int k = 0; k < ISM_CHEB_N; ++k) {
+        for (int k = 0; k < ISM_CHEB_NF; ++k) {
             const int v = (int)(Sb[k * SH_RS + lane] - nk);
             any |= v != 0;
             m[k] = __int2float_rn(v) * inv;   // exact scaling by a power of two
@@ -228,29 +231,28 @@ __global__ void __launch_bounds__(SH_WARPS * 32, 5) shell_kernel(const __grid_co
     __syncthreads();   // every sum is read before the moment table overwrites the CTA's tables
     if (warp >= nb) return;
     const int q = q0 + warp;
-    // moments of (bin, offset o) at Mt + 3 (32 bin + o): {M_0..M_3}, {M_4..M_7}, {M_8}
+    // moments of (bin, offset o) at Mt + 2 (32 bin + o): {M_0..M_3}, {M_4..M_7}
     float4* Mt = reinterpret_cast<float4*>(S);
     {
-        float4* mo = Mt + 3 * (32 * warp + lane);
+        float4* mo = Mt + 2 * (32 * warp + lane);
         mo[0] = make_float4(m[0], m[1], m[2], m[3]);
         mo[1] = make_float4(m[4], m[5], m[6], m[7]);
-        mo[2] = make_float4(m[8], 0.0f, 0.0f, 0.0f);
     }
     const unsigned nonempty = __ballot_sync(0xffffffffu, any);
     __syncwarp();
-    float c[ISM_CHEB_N];   // lane = tap t: Chebyshev coefficients of g_(t - 15)
+    float c[ISM_CHEB_NF];   // lane = tap t: Chebyshev coefficients of g_(t - 15)
 #pragma unroll
-    for (int i = 0; i < ISM_CHEB_N; ++i) c[i] = t.cheb[lane * ISM_CHEB_N + i];
+    for (int i = 0; i < ISM_CHEB_NF; ++i) c[i] = t.cheb[lane * ISM_CHEB_N + i];
     float acc[2] = {0.0f, 0.0f};
     for (int o = 0; o < SH_NO; ++o) {
         if (!((nonempty >> o) & 1u)) continue;   // warp-uniform
-        const float4* mo = Mt + 3 * (32 * warp + o);
+        const float4* mo = Mt + 2 * (32 * warp + o);
         const float4 ma = mo[0], mb = mo[1];
-        const float mv[ISM_CHEB_N] = {ma.x, ma.y, ma.z, ma.w, mb.x, mb.y, mb.z, mb.w, mo[2].x};
+        const float mv[ISM_CHEB_NF] = {ma.x, ma.y, ma.z, ma.w, mb.x, mb.y, mb.z, mb.w};
         float D[1];
         D[0] = c[0] * mv[0];
 #pragma unroll
-        for (int k = 1; k < ISM_CHEB_N; ++k) D[0] = __fmaf_rn(c[k], mv[k], D[0]);
+        for (int k = 1; k < ISM_CHEB_NF; ++k) D[0] = __fmaf_rn(c[k], mv[k], D[0]);
         flush_run<1, false>(D, acc, o - 1, lane, 1.0f);
     }
     float* row = rows + J.rows_base + ((long long)r * J.Q + q) * WIN;
@@ -260,7 +262,7 @@ __global__ void __launch_bounds__(SH_WARPS * 32, 5) shell_kernel(const __grid_co
 
 size_t shell_smem(const JobTable& t)
 {
-    return (size_t)((t.max_axis_sum + 1) & ~1) * sizeof(float4) + (size_t)SH_B * ISM_CHEB_N * SH_RS * sizeof(int) +
+    return (size_t)((t.max_axis_sum + 1) & ~1) * sizeof(float4) + (size_t)SH_B * ISM_CHEB_NF * SH_RS * sizeof(int) +
            (size_t)SH_B * SH_RS * sizeof(int) + 3 * SH_B * sizeof(float) + 4 * sizeof(int) +
            2 * (size_t)((t.max_axis_sum + 4) & ~3) * sizeof(int) +
            (size_t)SH_WARPS * 32 * (sizeof(float4) + sizeof(int4)) + (size_t)SH_WARPS * 33 * sizeof(int);

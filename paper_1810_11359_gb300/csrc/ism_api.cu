@@ -127,12 +127,11 @@ ism_status validate_job(const ism_job& in, Validated& v, bool need_ptrs)
 // g_t(f) = delta'(t - 15 - f) (eq. (6)), f = (u + 1) / 2, interpolated at the
 // Chebyshev-Gauss nodes u_k = cos(pi (k + 1/2) / N): c_i = (2 / N) sum_k
 // g_t(u_k) T_i(u_k), c_0 halved.  FP64 on the host, once per process.
-const float* cheb_coefficients()
+// Chebyshev interpolation coefficients of the 32 tap functions at N nodes (degree
+// N - 1): N = ISM_CHEB_NF for the forward's moments, ISM_CHEB_N for the adjoint's
+// tables; stride ISM_CHEB_N per tap either way (unused terms zero).
+static void cheb_fill(float* c, int N)
 {
-    static float c[32 * ISM_CHEB_N];
-    static std::once_flag once;
-    std::call_once(once, [] {
-        const int N = ISM_CHEB_N;
         for (int tap = 0; tap < 32; ++tap) {
             const int j = tap - 15;
             for (int i = 0; i < N; ++i) {
@@ -149,11 +148,20 @@ const float* cheb_coefficients()
                 }
                 s *= 2.0 / N;
                 if (i == 0) s *= 0.5;
-                c[tap * N + i] = (float)s;
+                c[tap * ISM_CHEB_N + i] = (float)s;
             }
         }
+}
+
+const float* cheb_coefficients(bool forward)
+{
+    static float cf[32 * ISM_CHEB_N], ca[32 * ISM_CHEB_N];
+    static std::once_flag once;
+    std::call_once(once, [] {
+        cheb_fill(cf, ISM_CHEB_NF);
+        cheb_fill(ca, ISM_CHEB_N);
     });
-    return c;
+    return forward ? cf : ca;
 }
 
 // Lays the launch set out in the workspace from byte offset `base` on (the
@@ -369,7 +377,7 @@ ism_status plan(const Validated* vs, int n, ism_precision prec, bool backward, J
     if (p.n_scan_blocks < 1) p.n_scan_blocks = 1;
     p.tbl_total = tbl;
     p.rows_total = rows;
-    if (t.any_cheb) std::memcpy(t.cheb, cheb_coefficients(), sizeof t.cheb);
+    if (t.any_cheb) std::memcpy(t.cheb, cheb_coefficients(!backward), sizeof t.cheb);
     p.rir_total = rir;
     p.lut_total = lut;
     p.gpart_total = gpart;

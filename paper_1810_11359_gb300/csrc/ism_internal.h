@@ -44,7 +44,8 @@
 #define ISM_SCAN_BLOCK 4096       // elements per scan block
 #define ISM_SCAN_TOP 16384        // max scan blocks (one top-level block)
 #define ISM_FIT_WINDOW_S 0.02     // envelope fit: last 20 ms of the ISM part
-#define ISM_CHEB_N 9              // Chebyshev terms of a tap function (degree 8)
+#define ISM_CHEB_N 9              // Chebyshev terms of a tap function in the adjoint (degree 8); table stride
+#define ISM_CHEB_NF 8             // Chebyshev terms of the forward's moments (degree 7)
 #define ISM_SHELL_BINS 8          // delay bins per CTA of the fused Chebyshev accumulation
 #define ISM_SD_BINS 32            // delay bins per CTA of the fused direct accumulation
 #define ISM_FILL_CTAS 304         // fused CTAs a launch set should have at least (two per SM of a GB300)
