@@ -274,9 +274,10 @@ ism_status plan(const Validated* vs, int n, ism_precision prec, bool backward, J
         // Chebyshev moments pay off when a delay bin holds enough images to
         // amortise the expansion of its 33 offsets and the shell's enumeration
         // set-up: estimate the images in reach per bin from the sphere of radius
-        // n_ism + H samples.  Measured crossover: 64 (the 16 kHz serving mix and
-        // training rooms gain down to ~16 per bin, the 48 kHz array with ~36 per
-        // bin is 1.5x faster in the direct form)
+        // n_ism + H samples.  Measured against the fused direct form (64 RIRs a
+        // call): 84 per bin, the same time; 181, 6 % faster; 338, 31 %; 1352, 2.7x;
+        // the 48 kHz array with ~36 per bin is 2.9x faster in the direct form.  The
+        // crossover lies near 64-100; 64 is kept.
         {
             const double reach = ((double)v.n_ism + v.H) / k;                     // metres
             const double vol = in.room.L[0] * in.room.L[1] * in.room.L[2];
