@@ -54,8 +54,8 @@
 //
 // Finally each warp expands the non-empty offsets of one bin into the taps
 // (lane = tap) and rotates them into the bin's register window, which it
-// stores as the bin's row; the moments of an offset sit together (12 floats),
-// so a warp reads them in three broadcast loads.
+// stores as the bin's row; the moments of an offset sit together (8 floats),
+// so a warp reads them in two broadcast loads.
 #include "ism_accum.cuh"
 #include "ism_shell.cuh"
 
@@ -67,7 +67,7 @@ namespace {
 #define SH_RS 33            // row stride of the moment table (conflict-light atomics)
 #define CB_MAGIC 12582912.0f                       // 1.5 * 2^23
 static_assert(ISM_CHEB_NF == 8, "the expansion reads the moments as 4 + 4");
-// the expansion's moment table [bin][offset][12] overlays the sums, the counts, the scales, the
+// the expansion's moment table [bin][offset][8] overlays the sums, the counts, the scales, the
 // row prefix and the column records (all dead by then), which always span more than it needs
 static_assert(SH_B * SH_NO * 8 * 4 <= (SH_B * ISM_CHEB_NF * SH_RS + SH_B * SH_RS) * 4 + SH_WARPS * 32 * 32,
               "moment table larger than the tables it overlays");
