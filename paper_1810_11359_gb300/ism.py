@@ -202,6 +202,16 @@ def _stream_ptr(stream=None):
 # --------------------------------------------------------------------------- #
 # Helpers of Section 4 (host FP64)
 # --------------------------------------------------------------------------- #
+def _rir_len(T, fs) -> int:
+    key = (float(T), float(fs))
+    n = _rir_lens.get(key)
+    if n is None:
+        if len(_rir_lens) > 256:
+            _rir_lens.clear()
+        n = _rir_lens[key] = ism_rir_length(T, fs)
+    return n
+
+
 def ism_rir_length(T: float, fs: float) -> int:
     n = ctypes.c_int()
     _check(load().ism_rir_length(float(T), float(fs), ctypes.byref(n)))
@@ -315,6 +325,18 @@ def ism_simulate(L, beta, pos_src, pos_rcv, nb_img, Tmax, fs, Tdiff=0.0, Tw=0.0,
     dev = torch.device("cuda", torch.cuda.current_device())
     ps = torch.as_tensor(pos_src, dtype=torch.float32).to(dev).reshape(-1, 3).contiguous()
     pr = torch.as_tensor(pos_rcv, dtype=torch.float32).to(dev).reshape(-1, 3).contiguous()
+    if out is None:
+        out = torch.empty((ps.shape[0], pr.shape[0], _rir_len(Tmax, fs)), dtype=torch.float32, device=dev)
+    if mic_pattern != "omni" or envelope != "sabine":   # these travel in the job struct: the batch entry point
+        orient = None
+        if mic_pattern != "omni":
+            orient = torch.as_tensor(orient_rcv, dtype=torch.float32).to(dev).reshape(-1, 3).contiguous()
+            if orient.shape[0] != pr.shape[0]:
+                raise ValueError("orient_rcv needs one vector per receiver")
+        job = make_job(L, beta, ps, pr, nb_img, Tmax, fs, out, Tdiff=Tdiff, Tw=Tw, c=c, seed=seed,
+                       mic_pattern=mic_pattern, orient_rcv=orient, envelope=envelope)
+        ism_simulate_batch([job], prec=prec, workspace=workspace, stream=stream)
+        return out
     # the room struct, images per axis, workspace bytes and RIR length of these arguments
     key = (np.asarray(L, np.float64).tobytes(), np.asarray(beta, np.float64).tobytes(),
            np.asarray(nb_img, np.int64).tobytes(), ps.shape[0], pr.shape[0], float(Tmax), float(fs),
@@ -326,20 +348,8 @@ def ism_simulate(L, beta, pos_src, pos_rcv, nb_img, Tmax, fs, Tdiff=0.0, Tw=0.0,
         hit = _dev_sizes[key] = (_room(L, beta, c), _nb(nb_img),
                                  ism_workspace_size(L, beta, ps.shape[0], pr.shape[0], nb_img, Tmax, fs, Tdiff, Tw,
                                                     c, prec),
-                                 ism_rir_length(Tmax, fs))
+                                 _rir_len(Tmax, fs))
     r, nb, nbytes, n_S = hit
-    if out is None:
-        out = torch.empty((ps.shape[0], pr.shape[0], n_S), dtype=torch.float32, device=dev)
-    if mic_pattern != "omni" or envelope != "sabine":   # these travel in the job struct: the batch entry point
-        orient = None
-        if mic_pattern != "omni":
-            orient = torch.as_tensor(orient_rcv, dtype=torch.float32).to(dev).reshape(-1, 3).contiguous()
-            if orient.shape[0] != pr.shape[0]:
-                raise ValueError("orient_rcv needs one vector per receiver")
-        job = make_job(L, beta, ps, pr, nb_img, Tmax, fs, out, Tdiff=Tdiff, Tw=Tw, c=c, seed=seed,
-                       mic_pattern=mic_pattern, orient_rcv=orient, envelope=envelope)
-        ism_simulate_batch([job], prec=prec, workspace=workspace, stream=stream)
-        return out
     buf = _workspace(workspace, nbytes)
     _check(load().ism_simulate(ctypes.byref(r), ctypes.c_void_p(ps.data_ptr()), int(ps.shape[0]),
                                ctypes.c_void_p(pr.data_ptr()), int(pr.shape[0]), nb, float(Tmax), float(fs),
@@ -350,6 +360,7 @@ def ism_simulate(L, beta, pos_src, pos_rcv, nb_img, Tmax, fs, Tdiff=0.0, Tw=0.0,
 
 
 _host_sizes = {}     # (arguments) -> (room struct, nb, host-entry workspace bytes, RIR length)
+_rir_lens = {}
 _dev_sizes = {}      # the same for the device entry point
 _lanes_setting = [2]
 
