@@ -158,3 +158,23 @@ def test_training_step_captured_in_a_cuda_graph_matches_eager():
     torch.cuda.synchronize()
     for a, b in zip(eager, [g_loss, beta.grad, ps.grad, pr.grad]):
         assert torch.equal(a, b)
+
+
+def test_simulate_with_device_beta_pattern_and_envelope_is_bitwise_the_host_beta():
+    """ism.ism_simulate with the coefficients as a CUDA tensor, a cardioid
+    receiver pattern and the Lehmann-Johansson tail (the batch entry point of
+    the binding): bitwise the same call with host coefficients, and the same
+    again on a repeated call."""
+    rng = np.random.default_rng(8)
+    L = np.array([5.0, 4.0, 3.0])
+    beta_h = np.array([0.9, 0.8, 0.85, 0.7, 0.6, 0.75], np.float32)
+    ps = workloads._uniform_inside(rng, L, 2)
+    pr = workloads._uniform_inside(rng, L, 3)
+    orient = rng.normal(size=(3, 3)).astype(np.float32)
+    N = ism.ism_nb_img_from_t(0.2, L, 343.0, 32 / 16000)
+    kw = dict(Tdiff=0.1, Tw=32 / 16000, mic_pattern="cardioid", orient_rcv=orient, envelope="lj", seed=3)
+    host = ism.ism_simulate(L, beta_h, ps, pr, N, 0.4, 16000.0, **kw).cpu().numpy()
+    beta_d = torch.as_tensor(beta_h).cuda()
+    for _ in range(2):
+        dev = ism.ism_simulate(L, beta_d, ps, pr, N, 0.4, 16000.0, **kw).cpu().numpy()
+        assert np.array_equal(dev.view(np.uint32), host.view(np.uint32))
